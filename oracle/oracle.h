@@ -1,0 +1,79 @@
+/*
+ * CPU FP64 oracle of the parallel iterated extended / cubature Kalman smoothers.
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the CPU
+ * baseline of the benchmark, never by the product library. See oracle.c.
+ */
+#ifndef PES_ORACLE_H
+#define PES_ORACLE_H
+
+#include <stdint.h>
+
+#define ORC_OK 0
+#define ORC_NOT_PD 2
+#define ORC_NOT_CONVERGED 4
+
+#define ORC_IEKS 0
+#define ORC_CUBATURE 1
+
+#define ORC_MODEL_CT_BEARINGS 0
+#define ORC_MODEL_LINEAR 1
+
+/* |omega dt| below which the coordinated-turn coefficients use their series
+ * (kept through a^4: truncation below 2e-16 relative up to here, whereas the
+ * closed forms lose up to ~1e-8 relative to cancellation near 1e-4) */
+#define ORC_CT_SERIES 1e-2
+
+typedef struct {
+    int kind;       /* ORC_MODEL_CT_BEARINGS or ORC_MODEL_LINEAR */
+    int q_form;     /* CT: 0 = diag(0,0,q_c dt,q_c dt,q_w dt); 1 = continuous white acceleration */
+    double dt, q_c, q_w, r_std;
+    const double* sensors; /* [1 or B][4] = s1x, s1y, s2x, s2y */
+    int sensors_per_traj;
+    /* linear model x' = F x + c + q, y = H x + d + r (full matrices, row-major) */
+    double F[25], c[5], Q[25], H[10], d[2], R[4];
+} orc_model;
+
+typedef struct { double A[25], b[5], C[25], eta[5], J[25]; } orc_felem;
+typedef struct { double E[25], g[5], L[25]; } orc_selem;
+
+double orc_wrap(double a);
+void orc_ct_f(const double x[5], double dt, double out[5]);
+void orc_ct_jacobian(const double x[5], double dt, double F[25]);
+void orc_bearings_h(const double x[5], const double s[4], double out[2]);
+void orc_bearings_jacobian(const double x[5], const double s[4], double H[10]);
+void orc_process_noise(const orc_model* m, double Q[25]);
+void orc_measurement_noise(const orc_model* m, double R[4]);
+
+int orc_slr(const orc_model* m, int which, int64_t b, const double xbar[5], const double Pbar[25],
+            double* G, double* offset, double* Lam);
+int orc_linearize(const orc_model* m, int method, int64_t N, const int64_t* offsets, int64_t B,
+                  const double* xbar, const double* Pbar, const double* y,
+                  double* F, double* c, double* Qp, double* H, double* d, double* Rp, double* y_used);
+int orc_kf_rts(int64_t N, const int64_t* offsets, int64_t B,
+               const double* F, const double* c, const double* Qp,
+               const double* H, const double* d, const double* Rp, const double* y,
+               const double* m0, const double* P0,
+               double* xf, double* Pf, double* xs, double* Ps);
+int orc_iterated_smoother(const orc_model* m, int method, int64_t N, const int64_t* offsets, int64_t B,
+                          const double* y, const double* m0, const double* P0,
+                          const double* x_init, const double* P_init, int max_iters, double tol,
+                          double* x_out, double* P_out, int* iters_used, double* rel_history);
+
+int orc_filter_element(const double F[25], const double c[5], const double Qp[25],
+                       const double H[10], const double d[2], const double Rp[4], const double y[2],
+                       orc_felem* e);
+void orc_filter_prior_element(const double m0[5], const double P0[25], orc_felem* e);
+int orc_filter_combine(const orc_felem* ei, const orc_felem* ej, orc_felem* out);
+int orc_smoother_element(const double xf[5], const double Pf[25], const double F[25], const double c[5],
+                         const double Qp[25], orc_selem* e);
+void orc_smoother_last_element(const double xf[5], const double Pf[25], orc_selem* e);
+void orc_smoother_combine(const orc_selem* ei, const orc_selem* ej, orc_selem* out);
+int orc_filter_by_elements(int64_t N, const int64_t* offsets, int64_t B,
+                           const double* F, const double* c, const double* Qp,
+                           const double* H, const double* d, const double* Rp, const double* y,
+                           const double* m0, const double* P0, double* xf, double* Pf);
+int orc_smoother_by_elements(int64_t N, const int64_t* offsets, int64_t B,
+                             const double* F, const double* c, const double* Qp,
+                             const double* xf, const double* Pf, double* xs, double* Ps);
+
+#endif

@@ -1,0 +1,165 @@
+"""Pins for the oracle's linearisation and iteration on the coordinated-turn /
+bearings model (Secs. 3 and 5).
+
+* Cubature SLR (Eqs. 7-9) is exact for affine functions, recovers the
+  Jacobian of the coordinates in which f is affine, and tends to the Taylor
+  linearisation (Eq. 10) as the covariance shrinks.
+* Every IEKS iteration is one Gauss-Newton step of the MAP problem (checked
+  against a dense Gauss-Newton solve, positive-definite Q), and at
+  convergence the MAP gradient vanishes.
+* Every iteration of either method equals dense Gaussian conditioning of the
+  stacked affine model built from the oracle's own linearisation.
+* Covariances are symmetric positive semi-definite; the last filtered and
+  smoothed moments coincide.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2102_00514_gb300 import synth
+from tests.dense_reference import dense_smoother, gauss_newton_step
+
+
+def ct_model(q_form=0, sensors=None):
+    s = np.array(synth.SENSORS if sensors is None else sensors)
+    return oracle.Model.ct_bearings(synth.DT, synth.Q_C, synth.Q_W, synth.R_STD, s, q_form=q_form)
+
+
+def test_slr_exact_for_linear_model():
+    rng = np.random.default_rng(3)
+    F = rng.standard_normal((5, 5)); c = rng.standard_normal(5)
+    H = rng.standard_normal((2, 5)); d = rng.standard_normal(2)
+    m = oracle.Model.linear(F, c, np.eye(5), H, d, np.eye(2))
+    xbar = rng.standard_normal(5)
+    A = rng.standard_normal((5, 5)); P = A @ A.T + np.eye(5)
+    G, off, Lam = oracle.slr(m, 0, 0, xbar, P)
+    np.testing.assert_allclose(G, F, atol=1e-12)
+    np.testing.assert_allclose(off, c, atol=1e-12)
+    np.testing.assert_allclose(Lam, 0, atol=1e-12)
+    G, off, Om = oracle.slr(m, 1, 0, xbar, P)
+    np.testing.assert_allclose(G, H, atol=1e-12)
+    np.testing.assert_allclose(off, d, atol=1e-12)
+    np.testing.assert_allclose(Om, 0, atol=1e-12)
+
+
+def test_slr_exact_in_coordinates_where_ct_is_affine():
+    """With (almost) no turn-rate uncertainty f is affine in (p, v): the SLR
+    recovers the Jacobian there and Lambda vanishes."""
+    m = ct_model()
+    xbar = np.array([0.4, -0.2, 1.1, 0.3, 0.8])
+    P = np.diag([0.5, 0.3, 0.2, 0.4, 1e-24])
+    P[0, 2] = P[2, 0] = 0.1
+    G, off, Lam = oracle.slr(m, 0, 0, xbar, P)
+    J = oracle.ct_jacobian(xbar, synth.DT)
+    np.testing.assert_allclose(G[:, :4], J[:, :4], atol=1e-12)
+    np.testing.assert_allclose(off + G @ xbar, oracle.ct_f(xbar, synth.DT), atol=1e-12)
+    np.testing.assert_allclose(Lam, 0, atol=1e-12)
+
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_slr_small_covariance_tends_to_taylor(which):
+    m = ct_model()
+    xbar = np.array([0.4, -0.2, 1.1, 0.3, 0.8])
+    J = oracle.ct_jacobian(xbar, synth.DT) if which == 0 else oracle.bearings_jacobian(xbar, synth.SENSORS)
+    errs = []
+    for eps in (1e-2, 1e-3, 1e-4):
+        G, off, Lam = oracle.slr(m, which, 0, xbar, eps * eps * np.eye(5))
+        errs.append(np.abs(G - J).max())
+        assert np.all(np.linalg.eigvalsh(Lam) > -1e-15)
+    # second-order convergence in the sigma-point spread
+    assert errs[1] < 0.02 * errs[0] + 1e-12 and errs[2] < 0.02 * errs[1] + 1e-12
+
+
+def test_slr_unwraps_bearings_across_branch_cut():
+    """A target just across the -pi/pi cut from a sensor: without unwrapping the
+    sigma-point spread of atan2 would be ~2 pi."""
+    s = np.array([0.0, 0.0, 5.0, 5.0])
+    m = ct_model(sensors=s)
+    xbar = np.array([-3.0, 1e-4, 1.0, 0.0, 0.0])
+    G, off, Om = oracle.slr(m, 1, 0, xbar, 1e-4 * np.eye(5))
+    J = oracle.bearings_jacobian(xbar, s)
+    np.testing.assert_allclose(G, J, atol=1e-4)
+    assert np.abs(Om).max() < 1e-6
+
+
+def _ct_gn(wl, model, x):
+    Q = model.Q(); R = model.R()
+    s = wl["sensors"][0]
+    return gauss_newton_step(
+        x, lambda v: oracle.ct_f(v, wl["dt"]), lambda v: oracle.ct_jacobian(v, wl["dt"]),
+        lambda v: oracle.bearings_h(v, s), lambda v: oracle.bearings_jacobian(v, s),
+        Q, R, wl["y"].T, wl["m0"][0], oracle.sym_full(wl["P0"][0], 5))
+
+
+def test_ieks_iterations_are_gauss_newton_steps():
+    wl = synth.ct_bearings([15], seed=11, q_form=1)
+    model = oracle.Model.from_workload(wl)
+    off = wl["offsets"]
+    x = np.tile(wl["m0"][0], (16, 1))
+    for it in range(1, 5):
+        out = oracle.iterated_smoother(model, oracle.IEKS, off, wl["y"], wl["m0"], wl["P0"], iters=it)
+        x, _ = _ct_gn(wl, model, x)
+        np.testing.assert_allclose(out["x"].T, x, rtol=1e-8, atol=1e-9)
+
+
+def test_ieks_fixed_point_zeroes_map_gradient():
+    wl = synth.ct_bearings([20], seed=12, q_form=1)
+    model = oracle.Model.from_workload(wl)
+    out = oracle.iterated_smoother(model, oracle.IEKS, wl["offsets"], wl["y"], wl["m0"], wl["P0"], iters=50, tol=1e-12)
+    assert out["status"] == oracle.OK
+    x = out["x"].T
+    x_next, grad = _ct_gn(wl, model, x)
+    # the Gauss-Newton step from the fixed point vanishes (Newton decrement), and
+    # the gradient is at rounding level for weights of order |Q^-1| ~ 1e8
+    assert np.abs(x_next - x).max() < 1e-10
+    assert np.abs(grad).max() < 1e-5
+
+
+@pytest.mark.parametrize("method", [oracle.IEKS, oracle.CUBATURE])
+def test_each_iteration_is_dense_conditioning(method):
+    wl = synth.ct_bearings([18], seed=13)
+    model = oracle.Model.from_workload(wl)
+    off = wl["offsets"]
+    N = 19
+    xbar = np.tile(wl["m0"][0][:, None], (1, N))
+    Pbar = np.tile(wl["P0"][0][:, None], (1, N))
+    for it in range(3):
+        lin = oracle.linearize(model, method, off, xbar, Pbar, wl["y"])
+        F = oracle._aos(lin["F"]).reshape(N, 5, 5)[:N - 1]
+        c = lin["c"].T[:N - 1]
+        Q = oracle.sym_full(lin["Qp"].T, 5)[:N - 1]
+        H = oracle._aos(lin["H"]).reshape(N, 2, 5)
+        R = oracle.sym_full(lin["Rp"].T, 2)
+        xs, Ps = dense_smoother(F, c, Q, H, lin["d"].T, R, lin["y_used"].T, wl["m0"][0],
+                                oracle.sym_full(wl["P0"][0], 5))
+        out = oracle.iterated_smoother(model, method, off, wl["y"], wl["m0"], wl["P0"],
+                                       x_init=xbar, P_init=Pbar, iters=1)
+        np.testing.assert_allclose(out["x"].T, xs, rtol=1e-8, atol=1e-9)
+        np.testing.assert_allclose(oracle.sym_full(out["P"].T, 5), Ps, rtol=1e-8, atol=1e-9)
+        xbar, Pbar = out["x"], out["P"]
+
+
+@pytest.mark.parametrize("method", [oracle.IEKS, oracle.CUBATURE])
+def test_covariance_invariants(method):
+    wl = synth.workload("ieks_T500")
+    model = oracle.Model.from_workload(wl)
+    out = oracle.iterated_smoother(model, method, wl["offsets"], wl["y"], wl["m0"], wl["P0"], iters=5)
+    P = oracle.sym_full(out["P"].T, 5)
+    ev = np.linalg.eigvalsh(P)
+    assert ev.min() > -1e-12 * ev.max()
+    # the smoother's last state is the filter's last state
+    N = wl["y"].shape[1]
+    lin = oracle.linearize(model, method, wl["offsets"], out["x"], out["P"], wl["y"])
+    kr = oracle.kf_rts(wl["offsets"], lin, lin["y_used"], wl["m0"], wl["P0"])
+    np.testing.assert_array_equal(kr["xs"][:, N - 1], kr["xf"][:, N - 1])
+    np.testing.assert_array_equal(kr["Ps"][:, N - 1], kr["Pf"][:, N - 1])
+
+
+def test_tolerance_mode_reports_not_converged():
+    wl = synth.workload("ieks_T500")
+    model = oracle.Model.from_workload(wl)
+    out = oracle.iterated_smoother(model, oracle.IEKS, wl["offsets"], wl["y"], wl["m0"], wl["P0"], iters=3, tol=1e-6)
+    assert out["status"] == oracle.NOT_CONVERGED and out["iters_used"] == 3
+    out = oracle.iterated_smoother(model, oracle.IEKS, wl["offsets"], wl["y"], wl["m0"], wl["P0"], iters=50, tol=1e-6)
+    assert out["status"] == oracle.OK and out["iters_used"] < 50
+    assert out["rel_history"][-1] <= 1e-6 < out["rel_history"][-2]
