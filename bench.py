@@ -1,0 +1,423 @@
+#!/usr/bin/env python
+"""Benchmark of the parallel iterated smoothers on GB300.
+
+Metric: smoothed steps per second per iteration, i.e. (states smoothed) x
+(iterations) / time, for the fused IEKS and cubature IPLS runs (pes_ieks_run).
+
+One *step* = one full pass of the hot path over one batch of synthetic input:
+an IEKS run and a cubature IPLS run of 10 iterations each (linearise, filter
+scan, smoother scan, re-linearise) on a single coordinated-turn / bearings
+trajectory of T = 2^20 measurements, FP32, inputs resident in HBM.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pes|reference]
+Under torchrun (N > 1) every rank smooths its own replica of the workload
+(weak scaling; no data-path collective exists in this method).
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import csv
+import hashlib
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "smoothed steps/sec per iteration (FP32 vs FP64, same GPU) at oracle tol; iters saved"
+UNIT = "smoothed steps/s per iteration"
+# Algorithmic work per state and iteration (FLOP), from the per-step operation
+# count of the method (linearise + element build + one combine per scan):
+# IEKS ~2,710 FMA, cubature IPLS ~4,260 FMA.
+ALG_FLOP = {"ieks": 2 * 2710, "cubature": 2 * 4260}
+# CUDA-core FP32 peak from unit counts and clock: SMs x 128 FMA lanes x 2 flops x f_SM.
+FP32_LANES_PER_SM = 128
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["pes", "reference"], default="pes")
+    ap.add_argument("--T", type=int, default=1 << 20)
+    ap.add_argument("--iters", type=int, default=10)
+    ap.add_argument("--no-parity", action="store_true", help="skip the full-size oracle parity check")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=1 << 17, help="states in the oracle's timed sample")
+    return ap.parse_args()
+
+
+def peaks_file():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2102_00514_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(method: str, T: int, iters: int):
+    """DRAM bytes per launch from the committed ncu capture, if it was taken on
+    the current kernel sources (scaled by states x iterations)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except OSError:
+        return None
+    if rec.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    per = rec.get("bytes_per_state_iteration", {}).get(method)
+    return None if per is None else per * T * iters
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (clocks and throttle reasons)."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self, index: int):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=10)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r for r in csv.reader(io.StringIO(out)) if len(r) >= 9]
+        rows = [[c.strip() for c in r] for r in rows if r[0].strip() == str(index)] or \
+               [[c.strip() for c in r] for r in rows]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def rel_err(a, b, offsets):
+    import numpy as np
+    worst = 0.0
+    for i in range(len(offsets) - 1):
+        sl = slice(int(offsets[i]), int(offsets[i + 1]))
+        den = np.linalg.norm(b[:, sl])
+        worst = max(worst, np.linalg.norm(a[:, sl] - b[:, sl]) / (den if den > 0 else 1.0))
+    return float(worst)
+
+
+def oracle_timed(wl_sample, iters):
+    """The oracle as it stands on one host core: both methods on the sample."""
+    import oracle
+    model = oracle.Model.from_workload(wl_sample)
+    out = {}
+    for name, m in (("ieks", oracle.IEKS), ("cubature", oracle.CUBATURE)):
+        t0 = time.perf_counter()
+        oracle.iterated_smoother(model, m, wl_sample["offsets"], wl_sample["y"], wl_sample["m0"], wl_sample["P0"],
+                                 iters=iters)
+        out[name] = time.perf_counter() - t0
+    return out
+
+
+def sample_workload(wl, S):
+    """The first S states of a single-trajectory workload."""
+    import numpy as np
+    return dict(wl, offsets=np.array([0, S], dtype=np.int64), y=np.ascontiguousarray(wl["y"][:, :S]),
+                x_true=np.ascontiguousarray(wl["x_true"][:, :S]))
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle, as it stands, on the host cores."""
+    if rank != 0:
+        return
+    from paper_2102_00514_gb300 import build, synth
+    build.build_synth()
+    import oracle
+    oracle.build()
+    wl = synth.workload(f"sweep_T{args.T}")
+    S = min(args.cpu_sample, wl["y"].shape[1])
+    sample = sample_workload(wl, S)
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle_timed(sample_workload(wl, min(S, 4096)), 1)
+    times = []
+    for _ in range(args.steps):
+        t = oracle_timed(sample, args.iters)
+        times.append(t["ieks"] + t["cubature"])
+    total = sum(times)
+    value = 2 * S * args.iters * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": f"synthetic coordinated-turn / bearings, seed {wl['seed']}",
+            "config": {"workload": f"first {S} states of the T={args.T} trajectory, IEKS + cubature IPLS, "
+                                   f"{args.iters} iterations each (sequential FP64 oracle)",
+                       "T_sample": S, "iterations": args.iters},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"first {S} of {args.T} states, both methods, {args.iters} iterations"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2102_00514_gb300 import build, pes, synth
+    build.build_all()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = dist_mod
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    T, iters = args.T, args.iters
+    wl = synth.workload(f"sweep_T{T}")
+    N = wl["y"].shape[1]
+    dev = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    sm = pes.Smoother(N, 1)
+    methods = (("ieks", pes.IEKS), ("cubature", pes.CUBATURE))
+
+    def device_inputs(prec):
+        dt = torch.float32 if prec == pes.FP32 else torch.float64
+        return dict(y=dev(wl["y"], dt), offsets=dev(wl["offsets"], torch.int64), m0=dev(wl["m0"], dt),
+                    P0=dev(wl["P0"], dt), model=pes.Model.from_workload(wl),
+                    x=torch.empty((5, N), dtype=dt, device="cuda"), P=torch.empty((15, N), dtype=dt, device="cuda"))
+
+    def run_step(d, prec, ev=None):
+        outs = {}
+        for i, (name, m) in enumerate(methods):
+            if ev is not None:
+                ev[i][0].record()
+            sm.ieks_run(d["model"], m, prec, d["y"], d["offsets"], d["m0"], d["P0"], iters=iters,
+                        x_out=d["x"], P_out=d["P"])
+            if ev is not None:
+                ev[i][1].record()
+        return outs
+
+    # L2 is flushed before every timed step by writing a buffer larger than L2.
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    d32 = device_inputs(pes.FP32)
+    for _ in range(args.warmup):
+        run_step(d32, pes.FP32)
+    sm.sync()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler()
+    clocks.start()
+    step_ms, meth_ms = [], {name: [] for name, _ in methods}
+    for _ in range(args.steps):
+        flush.zero_()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in methods]
+        run_step(d32, pes.FP32, ev)
+        torch.cuda.synchronize()
+        per = [ev[i][0].elapsed_time(ev[i][1]) for i in range(len(methods))]
+        for (name, _), ms in zip(methods, per):
+            meth_ms[name].append(ms)
+        step_ms.append(sum(per))
+    sm.sync()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    clk = clocks.stop(int(vis.split(",")[local]) if vis and vis.split(",")[local].isdigit() else local)
+
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    work_per_step = len(methods) * (N - 1) * iters
+    value = world * work_per_step * args.steps / (total_ms * 1e-3)
+    ms_per_step = total_ms / args.steps
+    launches_per_run = 3   # offsets validation, nominal initialisation, persistent smoother
+
+    nb, nt, L = sm.launch_shape(pes.IEKS, pes.FP32, N)
+    nbc, ntc, Lc = sm.launch_shape(pes.CUBATURE, pes.FP32, N)
+
+    result = None
+    if rank == 0:
+        peaks = peaks_file()
+        props = torch.cuda.get_device_properties(local)
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
+        per_method = {}
+        for name, _ in methods:
+            ms = statistics.mean(meth_ms[name])
+            flop = ALG_FLOP[name] * (N - 1) * iters
+            per_method[name] = {"ms_per_run": ms, "value": (N - 1) * iters / (ms * 1e-3),
+                                "achieved_tflops": flop / (ms * 1e-3) / 1e12}
+        dom = max(per_method, key=lambda k: per_method[k]["ms_per_run"])
+        achieved = per_method[dom]["achieved_tflops"]
+        try:
+            probe32, probe64 = pes.measure_fma_peak()
+        except Exception:
+            probe32, probe64 = None, None
+        roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": achieved / fp32_peak, "traffic": traffic_for(dom, N - 1, iters),
+                    "kernel": f"pes_persistent_kernel<float, {dom}>",
+                    "peak_source": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
+                                   f"{sm_max:.0f} MHz (max SM clock)",
+                    "fma_probe_tflops": {"fp32": probe32 / 1e3 if probe32 else None,
+                                         "fp64": probe64 / 1e3 if probe64 else None},
+                    "alg_flop_per_state_iteration": ALG_FLOP[dom]}
+        result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                  "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                  "vs_baseline": None, "dtype": "f32",
+                  "data": f"synthetic coordinated-turn / bearings (seeded, seed {wl['seed']}), inputs resident in HBM",
+                  "config": {"workload": f"single trajectory T={T}, IEKS + cubature IPLS, {iters} iterations each, "
+                                         "FP32, prior initialisation",
+                             "T": T, "B": 1, "iterations": iters, "methods": ["ieks", "cubature"],
+                             "precision": "fp32", "l2": "flushed before every step (512 MB write)",
+                             "launch": {"ieks": {"blocks": nb, "threads": nt, "steps_per_thread": L},
+                                        "cubature": {"blocks": nbc, "threads": ntc, "steps_per_thread": Lc}}},
+                  "roofline": roofline, "per_method": per_method,
+                  "gpu_launches": launches_per_run * len(methods) * args.steps, "clocks": clk}
+
+    # FP64 on the same GPU (the metric compares FP32 with FP64)
+    if not args.no_fp64:
+        d64 = device_inputs(pes.FP64)
+        run_step(d64, pes.FP64)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in methods]
+        flush.zero_()
+        run_step(d64, pes.FP64, ev)
+        torch.cuda.synchronize()
+        per = [ev[i][0].elapsed_time(ev[i][1]) for i in range(len(methods))]
+        if rank == 0:
+            result["fp64"] = {"value": work_per_step / (sum(per) * 1e-3), "ms_per_step": sum(per),
+                              "per_method_ms": dict(zip([m for m, _ in methods], per))}
+        x64 = {}
+        for name, m in methods:
+            x, P, _, _ = sm.ieks_run(d64["model"], m, pes.FP64, d64["y"], d64["offsets"], d64["m0"], d64["P0"],
+                                     iters=iters)
+            x64[name] = (x.cpu().numpy(), P.cpu().numpy())
+        del d64
+
+    # FP32 results for the parity check
+    x32 = {}
+    for name, m in methods:
+        x, P, _, _ = sm.ieks_run(d32["model"], m, pes.FP32, d32["y"], d32["offsets"], d32["m0"], d32["P0"],
+                                 iters=iters)
+        x32[name] = (x.double().cpu().numpy(), P.double().cpu().numpy())
+    sm.sync()
+
+    # end-to-end through the host-buffer entry point (copies inside the timed region)
+    if not args.no_e2e:
+        pin = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).pin_memory()
+        hy, hoff = pin(wl["y"], torch.float32), pin(wl["offsets"], torch.int64)
+        hm0, hP0 = pin(wl["m0"], torch.float32), pin(wl["P0"], torch.float32)
+        hs = pin(wl["sensors"], torch.float64)
+        hx = torch.empty((5, N), dtype=torch.float32).pin_memory()
+        hP = torch.empty((15, N), dtype=torch.float32).pin_memory()
+
+        def e2e_step():
+            for _, m in methods:
+                sm.ieks_run_host(d32["model"], m, pes.FP32, hy, hoff, hm0, hP0, iters=iters, x_out=hx, P_out=hP,
+                                 sensors_host=hs)
+
+        for _ in range(args.warmup):
+            e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        e2e_s = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        if rank == 0:
+            h2d = len(methods) * (hy.numel() * 4 + hoff.numel() * 8 + hm0.numel() * 4 + hP0.numel() * 4 +
+                                  hs.numel() * 8)
+            d2h = len(methods) * (hx.numel() * 4 + hP.numel() * 4)
+            result["e2e"] = {"value": world * work_per_step * args.steps / e2e_s, "unit": UNIT,
+                             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                             "ms_per_step": 1e3 * e2e_s / args.steps}
+
+    if rank == 0:
+        import oracle
+        oracle.build()
+        # CPU baseline: the oracle as it stands on one host core, bounded sample
+        if not args.no_cpu_baseline:
+            S = min(args.cpu_sample, N)
+            t = oracle_timed(sample_workload(wl, S), iters)
+            result["cpu_baseline"] = {"value": 2 * S * iters / (t["ieks"] + t["cubature"]), "unit": UNIT,
+                                      "cores": 1, "kind": "oracle",
+                                      "sample": f"first {S} of {N} states, IEKS + cubature, {iters} iterations, "
+                                                "sequential FP64 oracle"}
+        # parity of this very run against the oracle on the full workload
+        if not args.no_parity:
+            model = oracle.Model.from_workload(wl)
+
+            def orc(m):
+                return oracle.iterated_smoother(model, m, wl["offsets"], wl["y"], wl["m0"], wl["P0"], iters=iters)
+
+            with cf.ThreadPoolExecutor(2) as ex:
+                refs = dict(zip(("ieks", "cubature"), ex.map(orc, (oracle.IEKS, oracle.CUBATURE))))
+            par = {}
+            for name, _ in methods:
+                r = refs[name]
+                par[name] = {"fp32_means": rel_err(x32[name][0], r["x"], wl["offsets"]),
+                             "fp32_covs": rel_err(x32[name][1], r["P"], wl["offsets"])}
+                if not args.no_fp64:
+                    par[name]["fp64_means"] = rel_err(x64[name][0], r["x"], wl["offsets"])
+                    par[name]["fp64_covs"] = rel_err(x64[name][1], r["P"], wl["offsets"])
+            tol_ok = all(v["fp32_means"] <= 1e-4 and v["fp32_covs"] <= 1e-4 for v in par.values())
+            result["parity"] = {"vs": "CPU FP64 oracle, full workload", "rel_frobenius": par,
+                                "fp32_tol": 1e-4, "fp64_tol": 1e-9, "fp32_within_tol": tol_ok}
+        print(json.dumps(result), flush=True)
+    sm.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,227 @@
+/*
+ * pes.h — C ABI of the GB300 (sm_103a) parallel iterated extended (IEKS) and
+ * cubature sigma-point (IPLS) Kalman smoother.
+ *
+ * Method: Yaghoobi, Corenflos, Hassan, Sarkka, "Parallel Iterated Extended and
+ * Sigma-Point Kalman Smoothers" (ICASSP 2021). One iteration linearises every
+ * step about the previous smoothed trajectory (Eq. 10 for IEKS, Eqs. 7-9 for
+ * the cubature IPLS), runs the associative filtering scan over the elements
+ * of Eqs. 13-14 with the operator of Eq. 15, then the associative smoothing
+ * scan over the elements of Eqs. 17-18 with the operator of Eq. 19 (Sec. 4);
+ * the iteration of Sec. 3 repeats this about the new smoothed means.
+ *
+ * Conventions shared by every entry point
+ * -----------------------------------------
+ * State dimension n_x = 5 (x = [px, py, vx, vy, omega] for the coordinated-turn
+ * model), measurement dimension n_y = 2.
+ *
+ * Trajectories. B trajectories are concatenated. offsets[B+1] (int64, DEVICE
+ * memory) gives the state ranges: trajectory b owns states
+ * offsets[b] .. offsets[b+1]-1, offsets[0] = 0, offsets[B] = N, strictly
+ * increasing. State offsets[b] is that trajectory's x_0 (prior N(m0_b, P0_b),
+ * no measurement); states offsets[b]+1 .. offsets[b+1]-1 are x_1 .. x_{T_b},
+ * each with a measurement y_k (Eq. 4). A trajectory may have T_b = 0.
+ *
+ * Layout. Per-state arrays are structure-of-arrays, component-major:
+ * comp c of state k is at ptr[c * N + k]. Symmetric matrices are packed
+ * upper-triangular row-major: 5x5 -> 15 components (00,01,02,03,04,11,12,13,
+ * 14,22,23,24,33,34,44), 2x2 -> 3 components (00,01,11). General matrices
+ * are row-major: F (5x5) -> 25 components, H (2x5) -> 10 components.
+ * y is [2][N]; the entries at the x_0 slots are ignored.
+ * Per-trajectory priors: m0 [B][5], P0 [B][15] (packed), row-major.
+ * Transitions are indexed by their source state: F[:, k], c[:, k], Qp[:, k]
+ * describe x_{k+1} = F_k x_k + c_k + q, q ~ N(0, Qp_k) (Eq. 11; entries at the
+ * last state of a trajectory are ignored). Observations by their own state:
+ * y_k = H_k x_k + d_k + r, r ~ N(0, Rp_k).
+ *
+ * Precision. PES_FP64: every floating-point array is double. PES_FP32: every
+ * floating-point array (except the model's sensors) is float.
+ * PES_MIXED: not supported yet (returns PES_ERR_UNSUPPORTED).
+ *
+ * Memory and ownership. Unless stated otherwise every pointer is DEVICE memory
+ * owned by the caller and must stay valid until the work on `stream` has
+ * completed. The handle owns only its workspace. `stream` is a cudaStream_t
+ * passed as void* (NULL = the legacy default stream).
+ *
+ * Execution and errors. Arguments are validated on the host before anything
+ * is launched (PES_ERR_INVALID_ARG, nothing launched). Entry points enqueue
+ * their kernels on `stream` and return; faults found on the device (a
+ * covariance that is not positive definite, a non-finite result, malformed
+ * offsets, an internal wait that ran out of time) are recorded in the
+ * handle's device status word and returned by the next pes_sync(), or by an
+ * entry point that synchronises (documented per call). pes_last_error()
+ * describes the most recent failure. No exception crosses this interface.
+ * Calls on one handle must not overlap in time (they share the workspace).
+ */
+#ifndef PES_H
+#define PES_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PES_OK = 0,
+    PES_ERR_INVALID_ARG = 1,
+    PES_ERR_NOT_PD = 2,        /* a covariance / innovation matrix was not positive definite */
+    PES_ERR_NONFINITE = 3,     /* a non-finite smoothed mean was produced */
+    PES_ERR_NOT_CONVERGED = 4, /* tolerance mode: max_iters reached first */
+    PES_ERR_CUDA = 5,          /* a CUDA runtime call failed */
+    PES_ERR_UNSUPPORTED = 6,
+    PES_ERR_TIMEOUT = 7        /* an internal grid-wide wait exceeded its time limit */
+} pes_status;
+
+typedef enum { PES_IEKS = 0, PES_CUBATURE = 1 } pes_method;
+typedef enum { PES_FP64 = 0, PES_FP32 = 1, PES_MIXED = 2 } pes_precision;
+typedef enum { PES_MODEL_CT_BEARINGS = 0, PES_MODEL_LINEAR = 1 } pes_model_kind;
+
+/*
+ * The state-space model of Eq. 4 with additive Gaussian noise.
+ *
+ * PES_MODEL_CT_BEARINGS (the simulated experiment of Sec. 5): coordinated
+ * turn with sampling period dt,
+ *   px' = px + sin(w dt)/w vx - (1-cos(w dt))/w vy,  py' = py + (1-cos(w dt))/w vx + sin(w dt)/w vy,
+ *   vx' = cos(w dt) vx - sin(w dt) vy,  vy' = sin(w dt) vx + cos(w dt) vy,  w' = w,
+ * process noise q_form 0: Q = diag(0, 0, q_c dt, q_c dt, q_w dt); q_form 1:
+ * q_c [[dt^3/3, dt^2/2], [dt^2/2, dt]] on each (position, velocity) axis pair
+ * and q_w dt on w. Measurements: the bearings atan2(py - s_y, px - s_x) from two
+ * sensors, R = r_std^2 I. Bearings are unwrapped to the branch nearest the
+ * nominal's predicted bearing. `sensors` is a DEVICE array of doubles
+ * [n][4] = (s1x, s1y, s2x, s2y), n = 1 (sensors_per_traj = 0) or B (1).
+ *
+ * PES_MODEL_LINEAR: x' = F x + c + q, y = H x + d + r with q ~ N(0, Q),
+ * r ~ N(0, R); F, c, Q (packed), H, d, R (packed) are given here by value.
+ */
+typedef struct {
+    int32_t kind;
+    int32_t q_form;
+    double dt;
+    double q_c;
+    double q_w;
+    double r_std;
+    const double* sensors;
+    int32_t sensors_per_traj;
+    double F[25];
+    double c[5];
+    double Q[15];
+    double H[10];
+    double d[2];
+    double R[3];
+} pes_model;
+
+typedef struct pes_handle pes_handle;
+
+/* Create a handle on the current CUDA device with workspace for up to
+ * max_states concatenated states and max_batch trajectories. Allocates device
+ * memory once; later calls with N <= max_states and B <= max_batch allocate
+ * nothing on the device (except pes_ieks_run_host, see there). */
+pes_status pes_create(pes_handle** out, int64_t max_states, int32_t max_batch);
+
+/* Free the handle and its workspace (synchronises the device first). */
+pes_status pes_destroy(pes_handle* h);
+
+/* Human-readable description of the handle's most recent failure ("" if none).
+ * The string is owned by the handle. */
+const char* pes_last_error(const pes_handle* h);
+
+/* Wait for `stream` and report (then clear) the device status of prior calls. */
+pes_status pes_sync(pes_handle* h, void* stream);
+
+/*
+ * Linearisation of every step about a nominal trajectory (Sec. 3):
+ *   PES_IEKS: Taylor expansion, Eq. 10 (Lambda = Omega = 0): F_k = grad f(xbar_k),
+ *             c_k = f(xbar_k) - F_k xbar_k, H_k = grad h(xbar_k), d_k = h(xbar_k) - H_k xbar_k;
+ *   PES_CUBATURE: statistical linear regression with the 3rd-degree cubature
+ *             rule (2 n_x points xbar +- sqrt(n_x) chol(Pbar) e_i), Eqs. 7-9.
+ * Outputs Qp = Q + Lambda, Rp = R + Omega (Eq. 11) and y_used, the measurement
+ * unwrapped to the branch nearest h(xbar_k) (copied unchanged for the linear
+ * model). Inputs: x_nom [5][N], P_nom [15][N] (cubature only; may be NULL for
+ * IEKS), y [2][N]. Outputs: F [25][N], c [5][N], Qp [15][N], H [10][N],
+ * d [2][N], Rp [3][N], y_used [2][N] (y_used may be NULL). Entries that do not
+ * exist (transition of a last state, observation of an x_0) are set to 0.
+ */
+pes_status pes_linearize(pes_handle* h, const pes_model* model, pes_method method, pes_precision prec,
+                         const void* x_nom, const void* P_nom, const void* y,
+                         const int64_t* offsets, int32_t B, int64_t N,
+                         void* F, void* c, void* Qp, void* H, void* d, void* Rp, void* y_used,
+                         void* stream);
+
+/*
+ * Filtering by the associative scan of Sec. 4 (elements Eqs. 13-14, operator
+ * Eq. 15, prefix products as in Sec. 2) for given linearisation parameters:
+ * the filtered means xf [5][N] and covariances Pf [15][N] of every state,
+ * x_0 included (its prior).
+ */
+pes_status pes_filter_scan(pes_handle* h, pes_precision prec,
+                           const void* F, const void* c, const void* Qp,
+                           const void* H, const void* d, const void* Rp, const void* y,
+                           const void* m0, const void* P0, const int64_t* offsets, int32_t B, int64_t N,
+                           void* xf, void* Pf, void* stream);
+
+/*
+ * Smoothing by the reverse associative scan of Sec. 4 (elements Eqs. 17-18,
+ * operator Eq. 19, suffix products as in Sec. 2) from filtered moments
+ * xf [5][N], Pf [15][N] and the transitions F, c, Qp: smoothed means
+ * xs [5][N] and covariances Ps [15][N].
+ */
+pes_status pes_smooth_scan(pes_handle* h, pes_precision prec,
+                           const void* F, const void* c, const void* Qp,
+                           const void* xf, const void* Pf, const int64_t* offsets, int32_t B, int64_t N,
+                           void* xs, void* Ps, void* stream);
+
+/*
+ * The iterated smoother (Sec. 3 with the parallel filter and smoother of
+ * Sec. 4), all iterations in one persistent launch:
+ *   nominal^(0): x_init [5][N] (NULL: every state of trajectory b at m0_b),
+ *                P_init [15][N] (cubature only; NULL: P0_b);
+ *   iteration i: linearise about nominal^(i-1), filter, smooth; nominal^(i) =
+ *                the smoothed moments.
+ * max_iters >= 1. tol <= 0: exactly max_iters iterations. tol > 0: stop after
+ * the first iteration whose relative update norm
+ * ||X^(i) - X^(i-1)||_F / ||X^(i)||_F (per trajectory, worst trajectory) is
+ * <= tol; PES_ERR_NOT_CONVERGED if max_iters iterations did not reach it
+ * (outputs still hold the last iterate).
+ * Outputs: x_out [5][N] smoothed means, P_out [15][N] smoothed covariances of
+ * the last iteration. x_out / P_out may equal x_init / P_init.
+ * iters_used: HOST int* (may be NULL) receiving the number of iterations run.
+ * Synchronises `stream` (and returns device status) when tol > 0 or
+ * iters_used != NULL; otherwise it is asynchronous (status via pes_sync).
+ */
+pes_status pes_ieks_run(pes_handle* h, const pes_model* model, pes_method method, pes_precision prec,
+                        const void* y, const int64_t* offsets, int32_t B, int64_t N,
+                        const void* m0, const void* P0, const void* x_init, const void* P_init,
+                        int32_t max_iters, double tol, void* x_out, void* P_out, int32_t* iters_used,
+                        void* stream);
+
+/*
+ * pes_ieks_run with HOST buffers: y, offsets, m0, P0, x_init, P_init, the
+ * model's sensors, x_out and P_out are HOST memory (pinned memory gives the
+ * fastest copies). Copies the inputs to the device, runs, copies the outputs
+ * back and synchronises `stream`. Device buffers for these copies are
+ * allocated by the first call on the handle (sized for max_states / max_batch)
+ * and reused afterwards.
+ */
+pes_status pes_ieks_run_host(pes_handle* h, const pes_model* model, pes_method method, pes_precision prec,
+                             const void* y, const int64_t* offsets, int32_t B, int64_t N,
+                             const void* m0, const void* P0, const void* x_init, const void* P_init,
+                             int32_t max_iters, double tol, void* x_out, void* P_out, int32_t* iters_used,
+                             void* stream);
+
+/* Launch shape the next call of the given kind would use (for tests and the
+ * benchmark): blocks, threads per block, steps per thread. */
+pes_status pes_launch_shape(pes_handle* h, pes_method method, pes_precision prec, int64_t N,
+                            int32_t* blocks, int32_t* threads, int32_t* steps_per_thread);
+
+/* Measured arithmetic throughput of this device's CUDA cores (a diagnostic for
+ * roofline accounting, not part of the method): a dependent-chain-free FMA
+ * loop over all SMs, timed with CUDA events. Outputs in GFLOP/s (2 flops per
+ * FMA) for fp32 and fp64; either pointer may be NULL. Synchronises the device. */
+pes_status pes_measure_fma_peak(double* fp32_gflops, double* fp64_gflops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PES_H */

@@ -1,0 +1,483 @@
+// Host side of the C ABI declared in include/pes.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "pes.h"
+#include "pes_internal.h"
+
+using namespace pes;
+
+struct pes_handle {
+    int device = 0;
+    int num_sms = 0;
+    int64_t max_states = 0;
+    int32_t max_batch = 0;
+    int nl_max = 0;      // lanes the workspace is sized for
+    int nb_max = 0;      // blocks the workspace is sized for
+    void* hand = nullptr;
+    void* aggF = nullptr;
+    void* aggS = nullptr;
+    unsigned* bar = nullptr;
+    int* status = nullptr;
+    double* conv = nullptr;
+    int* iters_done = nullptr;
+    // device copies for pes_ieks_run_host (allocated by its first call)
+    void* hy = nullptr;
+    int64_t* hoff = nullptr;
+    void* hm0 = nullptr;
+    void* hP0 = nullptr;
+    void* hx = nullptr;
+    void* hP = nullptr;
+    void* hxi = nullptr;
+    void* hPi = nullptr;
+    double* hsens = nullptr;
+    long long timeout_ns = 2000000000LL;
+    char err[512] = {0};
+};
+
+namespace {
+
+constexpr int kMaxBlocksPerSM = 2;   // largest occupancy of any compiled configuration
+constexpr int kMaxThreads = 256;
+constexpr int kMinStepsPerThread = 8;
+
+pes_status fail(pes_handle* h, pes_status st, const char* fmt, ...)
+{
+    if (h) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(h->err, sizeof(h->err), fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+pes_status cuda_fail(pes_handle* h, cudaError_t e, const char* what)
+{
+    return fail(h, PES_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define PES_CUDA(h, call)                                 \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+size_t scalar_size(pes_precision p) { return p == PES_FP64 ? sizeof(double) : sizeof(float); }
+
+pes_status check_common(pes_handle* h, pes_precision prec, const int64_t* offsets, int32_t B, int64_t N)
+{
+    if (!h) return PES_ERR_INVALID_ARG;
+    if (prec == PES_MIXED) return fail(h, PES_ERR_UNSUPPORTED, "PES_MIXED is not supported yet");
+    if (prec != PES_FP32 && prec != PES_FP64) return fail(h, PES_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    if (!offsets) return fail(h, PES_ERR_INVALID_ARG, "offsets is NULL");
+    if (B < 1) return fail(h, PES_ERR_INVALID_ARG, "B must be >= 1 (got %d)", (int)B);
+    if (N < B) return fail(h, PES_ERR_INVALID_ARG, "N (%lld) must be >= B (%d)", (long long)N, (int)B);
+    if (N > h->max_states) return fail(h, PES_ERR_INVALID_ARG, "N (%lld) exceeds max_states (%lld)", (long long)N, (long long)h->max_states);
+    if (B > h->max_batch) return fail(h, PES_ERR_INVALID_ARG, "B (%d) exceeds max_batch (%d)", (int)B, (int)h->max_batch);
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != h->device)
+        return fail(h, PES_ERR_INVALID_ARG, "the current device (%d) is not the handle's device (%d)", dev, h->device);
+    return PES_OK;
+}
+
+DevModel to_dev_model(const pes_model& m)
+{
+    DevModel d;
+    memset(&d, 0, sizeof(d));
+    d.kind = m.kind;
+    d.sensors_per_traj = m.sensors_per_traj;
+    d.dt = m.dt;
+    d.sensors = m.sensors;
+    if (m.kind == PES_MODEL_LINEAR) {
+        memcpy(d.Q, m.Q, sizeof(d.Q));
+        memcpy(d.R, m.R, sizeof(d.R));
+        memcpy(d.F, m.F, sizeof(d.F));
+        memcpy(d.c, m.c, sizeof(d.c));
+        memcpy(d.H, m.H, sizeof(d.H));
+        memcpy(d.d, m.d, sizeof(d.d));
+    } else {
+        const double dt = m.dt;
+        if (m.q_form == 1) {
+            for (int ax = 0; ax < 2; ++ax) {
+                const int pp = ax, v = ax + 2;
+                d.Q[si(pp, pp)] = m.q_c * dt * dt * dt / 3.0;
+                d.Q[si(pp, v)] = m.q_c * dt * dt / 2.0;
+                d.Q[si(v, v)] = m.q_c * dt;
+            }
+        } else {
+            d.Q[si(2, 2)] = m.q_c * dt;
+            d.Q[si(3, 3)] = m.q_c * dt;
+        }
+        d.Q[si(4, 4)] = m.q_w * dt;
+        d.R[0] = m.r_std * m.r_std;
+        d.R[1] = 0.0;
+        d.R[2] = m.r_std * m.r_std;
+    }
+    return d;
+}
+
+pes_status check_model(pes_handle* h, const pes_model* m)
+{
+    if (!m) return fail(h, PES_ERR_INVALID_ARG, "model is NULL");
+    if (m->kind == PES_MODEL_CT_BEARINGS) {
+        if (!m->sensors) return fail(h, PES_ERR_INVALID_ARG, "model.sensors is NULL");
+        if (!(m->dt > 0.0) || !(m->r_std > 0.0) || m->q_c < 0.0 || m->q_w < 0.0)
+            return fail(h, PES_ERR_INVALID_ARG, "model needs dt > 0, r_std > 0, q_c >= 0, q_w >= 0");
+        if (m->q_form != 0 && m->q_form != 1) return fail(h, PES_ERR_INVALID_ARG, "model.q_form must be 0 or 1");
+        return PES_OK;
+    }
+    if (m->kind == PES_MODEL_LINEAR) return PES_OK;
+    return fail(h, PES_ERR_INVALID_ARG, "unknown model kind %d", (int)m->kind);
+}
+
+// Block size per precision (the autotuned choice lives here).
+int choose_nt(pes_precision prec) { return prec == PES_FP64 ? 128 : 256; }
+
+struct Shape {
+    int nb, nt, L;
+};
+
+template <typename T>
+pes_status make_shape(pes_handle* h, int lin, pes_precision prec, int64_t N, Shape& s)
+{
+    s.nt = choose_nt(prec);
+    const int cap = coop_capacity(T(0), lin, s.nt, h->device);
+    if (cap <= 0) return fail(h, PES_ERR_CUDA, "the smoother kernel cannot be made co-resident on this device");
+    const int64_t want = (N + (int64_t)s.nt * kMinStepsPerThread - 1) / ((int64_t)s.nt * kMinStepsPerThread);
+    s.nb = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)cap, want, (int64_t)h->nb_max}));
+    const int64_t lanes = (int64_t)s.nb * s.nt;
+    s.L = (int)((N + lanes - 1) / lanes);
+    return PES_OK;
+}
+
+template <typename T>
+void fill_workspace(pes_handle* h, KParams<T>& p, const Shape& s)
+{
+    p.hand = static_cast<T*>(h->hand);
+    p.aggF = static_cast<T*>(h->aggF);
+    p.aggS = static_cast<T*>(h->aggS);
+    p.bar = h->bar;
+    p.status = h->status;
+    p.conv = h->conv;
+    p.iters_done = h->iters_done;
+    p.L = s.L;
+    p.NL = s.nb * s.nt;
+    p.timeout_ns = h->timeout_ns;
+}
+
+pes_status read_status(pes_handle* h, cudaStream_t st, int* iters = nullptr)
+{
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    int status = 0;
+    PES_CUDA(h, cudaMemcpy(&status, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+    PES_CUDA(h, cudaMemset(h->status, 0, sizeof(int)));
+    if (iters) PES_CUDA(h, cudaMemcpy(iters, h->iters_done, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status & ST_BADARG) return fail(h, PES_ERR_INVALID_ARG, "offsets are malformed (need 0 = o[0] < o[1] < ... < o[B] = N)");
+    if (status & ST_TIMEOUT) return fail(h, PES_ERR_TIMEOUT, "a grid-wide wait exceeded its time limit");
+    if (status & ST_NOT_PD) return fail(h, PES_ERR_NOT_PD, "a covariance or innovation matrix was not positive definite");
+    if (status & ST_NONFINITE) return fail(h, PES_ERR_NONFINITE, "a non-finite smoothed mean was produced");
+    if (status & ST_NOT_CONVERGED) return fail(h, PES_ERR_NOT_CONVERGED, "the tolerance was not reached within max_iters");
+    return PES_OK;
+}
+
+template <typename T>
+pes_status run_persistent(pes_handle* h, KParams<T>& p, int lin, pes_precision prec, cudaStream_t st)
+{
+    Shape s;
+    pes_status r = make_shape<T>(h, lin, prec, p.N, s);
+    if (r != PES_OK) return r;
+    fill_workspace(h, p, s);
+    PES_CUDA(h, cudaMemsetAsync(h->bar, 0, sizeof(unsigned), st));
+    if (p.mode == MODE_RUN && p.tol > 0.0) PES_CUDA(h, cudaMemsetAsync(h->conv, 0, sizeof(double) * 4 * p.B, st));
+    cudaError_t e = launch_persistent(p, lin, s.nt, s.nb, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cooperative launch of the smoother kernel");
+    return PES_OK;
+}
+
+}  // namespace
+
+template <typename T>
+static pes_status filter_scan_t(pes_handle* h, const void* F, const void* c, const void* Qp, const void* H,
+                                const void* d, const void* Rp, const void* y, const void* m0, const void* P0,
+                                const int64_t* offsets, int32_t B, int64_t N, void* xf, void* Pf, pes_precision prec,
+                                cudaStream_t st)
+{
+    KParams<T> p{};
+    p.N = N; p.offsets = offsets; p.B = B; p.mode = MODE_FILTER; p.iters = 1;
+    p.F = (const T*)F; p.c = (const T*)c; p.Qp = (const T*)Qp; p.H = (const T*)H; p.d = (const T*)d;
+    p.Rp = (const T*)Rp; p.y = (const T*)y; p.m0 = (const T*)m0; p.P0 = (const T*)P0;
+    p.xf = (T*)xf; p.Pf = (T*)Pf;
+    return run_persistent<T>(h, p, LIN_ARRAYS, prec, st);
+}
+
+template <typename T>
+static pes_status smooth_scan_t(pes_handle* h, const void* F, const void* c, const void* Qp, const void* xf,
+                                const void* Pf, const int64_t* offsets, int32_t B, int64_t N, void* xs, void* Ps,
+                                pes_precision prec, cudaStream_t st)
+{
+    KParams<T> p{};
+    p.N = N; p.offsets = offsets; p.B = B; p.mode = MODE_SMOOTH; p.iters = 1;
+    p.F = (const T*)F; p.c = (const T*)c; p.Qp = (const T*)Qp;
+    p.xf = (T*)xf; p.Pf = (T*)Pf; p.x = (T*)xs; p.P = (T*)Ps;
+    return run_persistent<T>(h, p, LIN_ARRAYS, prec, st);
+}
+
+template <typename T>
+static pes_status ieks_run_t(pes_handle* h, const pes_model* model, pes_method method, pes_precision prec,
+                             const void* y, const int64_t* offsets, int32_t B, int64_t N, const void* m0,
+                             const void* P0, const void* x_init, const void* P_init, int32_t max_iters, double tol,
+                             void* x_out, void* P_out, int32_t* iters_used, cudaStream_t st)
+{
+    const size_t ts = sizeof(T);
+    // nominal^(0) in the output buffers
+    if (x_init) {
+        if (x_init != x_out) PES_CUDA(h, cudaMemcpyAsync(x_out, x_init, ts * 5 * N, cudaMemcpyDeviceToDevice, st));
+    }
+    const bool need_P0_fill = (method == PES_CUBATURE) && !P_init;
+    if (method == PES_CUBATURE && P_init && P_init != P_out)
+        PES_CUDA(h, cudaMemcpyAsync(P_out, P_init, ts * 15 * N, cudaMemcpyDeviceToDevice, st));
+    if (!x_init || need_P0_fill)
+        PES_CUDA(h, launch_init_nominal<T>(offsets, B, N, (const T*)m0, (const T*)P0, x_init ? nullptr : (T*)x_out,
+                                           need_P0_fill ? (T*)P_out : nullptr, st));
+    KParams<T> p{};
+    p.N = N; p.offsets = offsets; p.B = B; p.mode = MODE_RUN; p.iters = max_iters; p.tol = tol;
+    p.write_P_every_iter = tol > 0.0 ? 1 : 0;
+    p.model = to_dev_model(*model);
+    p.y = (const T*)y; p.m0 = (const T*)m0; p.P0 = (const T*)P0;
+    p.x = (T*)x_out; p.P = (T*)P_out;
+    const int lin = method == PES_CUBATURE ? LIN_CUBATURE : LIN_IEKS;
+    pes_status r = run_persistent<T>(h, p, lin, prec, st);
+    if (r != PES_OK) return r;
+    if (tol > 0.0 || iters_used) {
+        int it = 0;
+        r = read_status(h, st, &it);
+        if (iters_used) *iters_used = it;
+        return r;
+    }
+    return PES_OK;
+}
+
+extern "C" {
+
+pes_status pes_create(pes_handle** out, int64_t max_states, int32_t max_batch)
+{
+    if (!out || max_states < 1 || max_batch < 1) return PES_ERR_INVALID_ARG;
+    *out = nullptr;
+    pes_handle* h = new (std::nothrow) pes_handle();
+    if (!h) return PES_ERR_CUDA;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return PES_ERR_CUDA;
+    }
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
+    if (!coop) {
+        delete h;
+        return PES_ERR_UNSUPPORTED;
+    }
+    if (const char* env = getenv("PES_BARRIER_TIMEOUT_MS")) {
+        const long long ms = atoll(env);
+        if (ms > 0) h->timeout_ns = ms * 1000000LL;
+    }
+    h->max_states = max_states;
+    h->max_batch = max_batch;
+    h->nb_max = h->num_sms * kMaxBlocksPerSM;
+    h->nl_max = h->nb_max * kMaxThreads;
+    const size_t hand_elems = (size_t)HAND * ((size_t)max_states + (size_t)h->nl_max);
+    e = cudaMalloc(&h->hand, hand_elems * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->aggF, (size_t)h->nb_max * FE * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->aggS, (size_t)h->nb_max * SE * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->bar, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->conv, sizeof(double) * 4 * (size_t)max_batch);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->iters_done, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        pes_destroy(h);
+        return PES_ERR_CUDA;
+    }
+    *out = h;
+    return PES_OK;
+}
+
+pes_status pes_destroy(pes_handle* h)
+{
+    if (!h) return PES_ERR_INVALID_ARG;
+    cudaDeviceSynchronize();
+    void* ptrs[] = {h->hand, h->aggF, h->aggS, h->bar, h->status, h->conv, h->iters_done,
+                    h->hy, h->hoff, h->hm0, h->hP0, h->hx, h->hP, h->hxi, h->hPi, h->hsens};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete h;
+    return PES_OK;
+}
+
+const char* pes_last_error(const pes_handle* h) { return h ? h->err : "null handle"; }
+
+pes_status pes_sync(pes_handle* h, void* stream)
+{
+    if (!h) return PES_ERR_INVALID_ARG;
+    return read_status(h, (cudaStream_t)stream);
+}
+
+pes_status pes_launch_shape(pes_handle* h, pes_method method, pes_precision prec, int64_t N, int32_t* blocks,
+                            int32_t* threads, int32_t* steps_per_thread)
+{
+    if (!h || N < 1) return PES_ERR_INVALID_ARG;
+    if (prec == PES_MIXED) return PES_ERR_UNSUPPORTED;
+    const int lin = method == PES_CUBATURE ? LIN_CUBATURE : LIN_IEKS;
+    Shape s;
+    pes_status r = (prec == PES_FP64) ? make_shape<double>(h, lin, prec, N, s) : make_shape<float>(h, lin, prec, N, s);
+    if (r != PES_OK) return r;
+    if (blocks) *blocks = s.nb;
+    if (threads) *threads = s.nt;
+    if (steps_per_thread) *steps_per_thread = s.L;
+    return PES_OK;
+}
+
+pes_status pes_linearize(pes_handle* h, const pes_model* model, pes_method method, pes_precision prec,
+                         const void* x_nom, const void* P_nom, const void* y, const int64_t* offsets, int32_t B,
+                         int64_t N, void* F, void* c, void* Qp, void* H, void* d, void* Rp, void* y_used,
+                         void* stream)
+{
+    pes_status r = check_common(h, prec, offsets, B, N);
+    if (r != PES_OK) return r;
+    if ((r = check_model(h, model)) != PES_OK) return r;
+    if (method != PES_IEKS && method != PES_CUBATURE) return fail(h, PES_ERR_INVALID_ARG, "unknown method");
+    if (!x_nom || !y || !F || !c || !Qp || !H || !d || !Rp) return fail(h, PES_ERR_INVALID_ARG, "NULL array");
+    if (method == PES_CUBATURE && !P_nom) return fail(h, PES_ERR_INVALID_ARG, "cubature needs P_nom");
+    cudaStream_t st = (cudaStream_t)stream;
+    PES_CUDA(h, launch_validate_offsets(offsets, B, N, h->status, st));
+    const int lin = method == PES_CUBATURE ? LIN_CUBATURE : LIN_IEKS;
+    if (prec == PES_FP64) {
+        KParams<double> p{};
+        p.N = N; p.offsets = offsets; p.B = B; p.model = to_dev_model(*model);
+        p.x = (double*)x_nom; p.P = (double*)P_nom; p.y = (const double*)y; p.status = h->status;
+        PES_CUDA(h, launch_linearize<double>(p, lin, (double*)F, (double*)c, (double*)Qp, (double*)H, (double*)d,
+                                             (double*)Rp, (double*)y_used, st));
+    } else {
+        KParams<float> p{};
+        p.N = N; p.offsets = offsets; p.B = B; p.model = to_dev_model(*model);
+        p.x = (float*)x_nom; p.P = (float*)P_nom; p.y = (const float*)y; p.status = h->status;
+        PES_CUDA(h, launch_linearize<float>(p, lin, (float*)F, (float*)c, (float*)Qp, (float*)H, (float*)d,
+                                            (float*)Rp, (float*)y_used, st));
+    }
+    return PES_OK;
+}
+
+
+pes_status pes_filter_scan(pes_handle* h, pes_precision prec, const void* F, const void* c, const void* Qp,
+                           const void* H, const void* d, const void* Rp, const void* y, const void* m0,
+                           const void* P0, const int64_t* offsets, int32_t B, int64_t N, void* xf, void* Pf,
+                           void* stream)
+{
+    pes_status r = check_common(h, prec, offsets, B, N);
+    if (r != PES_OK) return r;
+    if (!F || !c || !Qp || !H || !d || !Rp || !y || !m0 || !P0 || !xf || !Pf)
+        return fail(h, PES_ERR_INVALID_ARG, "NULL array");
+    cudaStream_t st = (cudaStream_t)stream;
+    PES_CUDA(h, launch_validate_offsets(offsets, B, N, h->status, st));
+    if (prec == PES_FP64) return filter_scan_t<double>(h, F, c, Qp, H, d, Rp, y, m0, P0, offsets, B, N, xf, Pf, prec, st);
+    return filter_scan_t<float>(h, F, c, Qp, H, d, Rp, y, m0, P0, offsets, B, N, xf, Pf, prec, st);
+}
+
+
+pes_status pes_smooth_scan(pes_handle* h, pes_precision prec, const void* F, const void* c, const void* Qp,
+                           const void* xf, const void* Pf, const int64_t* offsets, int32_t B, int64_t N, void* xs,
+                           void* Ps, void* stream)
+{
+    pes_status r = check_common(h, prec, offsets, B, N);
+    if (r != PES_OK) return r;
+    if (!F || !c || !Qp || !xf || !Pf || !xs || !Ps) return fail(h, PES_ERR_INVALID_ARG, "NULL array");
+    cudaStream_t st = (cudaStream_t)stream;
+    PES_CUDA(h, launch_validate_offsets(offsets, B, N, h->status, st));
+    if (prec == PES_FP64) return smooth_scan_t<double>(h, F, c, Qp, xf, Pf, offsets, B, N, xs, Ps, prec, st);
+    return smooth_scan_t<float>(h, F, c, Qp, xf, Pf, offsets, B, N, xs, Ps, prec, st);
+}
+
+
+pes_status pes_ieks_run(pes_handle* h, const pes_model* model, pes_method method, pes_precision prec, const void* y,
+                        const int64_t* offsets, int32_t B, int64_t N, const void* m0, const void* P0,
+                        const void* x_init, const void* P_init, int32_t max_iters, double tol, void* x_out,
+                        void* P_out, int32_t* iters_used, void* stream)
+{
+    pes_status r = check_common(h, prec, offsets, B, N);
+    if (r != PES_OK) return r;
+    if ((r = check_model(h, model)) != PES_OK) return r;
+    if (method != PES_IEKS && method != PES_CUBATURE) return fail(h, PES_ERR_INVALID_ARG, "unknown method");
+    if (!y || !m0 || !P0 || !x_out || !P_out) return fail(h, PES_ERR_INVALID_ARG, "NULL array");
+    if (max_iters < 1) return fail(h, PES_ERR_INVALID_ARG, "max_iters must be >= 1");
+    if (!(tol == tol)) return fail(h, PES_ERR_INVALID_ARG, "tol is NaN");
+    cudaStream_t st = (cudaStream_t)stream;
+    PES_CUDA(h, launch_validate_offsets(offsets, B, N, h->status, st));
+    if (prec == PES_FP64)
+        return ieks_run_t<double>(h, model, method, prec, y, offsets, B, N, m0, P0, x_init, P_init, max_iters, tol,
+                                  x_out, P_out, iters_used, st);
+    return ieks_run_t<float>(h, model, method, prec, y, offsets, B, N, m0, P0, x_init, P_init, max_iters, tol, x_out,
+                             P_out, iters_used, st);
+}
+
+pes_status pes_ieks_run_host(pes_handle* h, const pes_model* model, pes_method method, pes_precision prec,
+                             const void* y, const int64_t* offsets, int32_t B, int64_t N, const void* m0,
+                             const void* P0, const void* x_init, const void* P_init, int32_t max_iters, double tol,
+                             void* x_out, void* P_out, int32_t* iters_used, void* stream)
+{
+    if (!h) return PES_ERR_INVALID_ARG;
+    if (prec == PES_MIXED) return fail(h, PES_ERR_UNSUPPORTED, "PES_MIXED is not supported yet");
+    if (prec != PES_FP32 && prec != PES_FP64) return fail(h, PES_ERR_INVALID_ARG, "unknown precision");
+    if (!model || !y || !offsets || !m0 || !P0 || !x_out || !P_out) return fail(h, PES_ERR_INVALID_ARG, "NULL array");
+    if (B < 1 || N < B || N > h->max_states || B > h->max_batch)
+        return fail(h, PES_ERR_INVALID_ARG, "sizes out of range (N %lld, B %d)", (long long)N, (int)B);
+    // host-side offsets check (they are host memory here)
+    if (offsets[0] != 0 || offsets[B] != N) return fail(h, PES_ERR_INVALID_ARG, "offsets must start at 0 and end at N");
+    for (int32_t b = 0; b < B; ++b)
+        if (offsets[b + 1] <= offsets[b]) return fail(h, PES_ERR_INVALID_ARG, "offsets must increase strictly");
+    const size_t ts = scalar_size(prec);
+    const size_t Nmax = (size_t)h->max_states, Bmax = (size_t)h->max_batch;
+    if (!h->hy) {
+        cudaError_t e = cudaMalloc(&h->hy, sizeof(double) * 2 * Nmax);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&h->hoff, sizeof(int64_t) * (Bmax + 1));
+        if (e == cudaSuccess) e = cudaMalloc(&h->hm0, sizeof(double) * 5 * Bmax);
+        if (e == cudaSuccess) e = cudaMalloc(&h->hP0, sizeof(double) * 15 * Bmax);
+        if (e == cudaSuccess) e = cudaMalloc(&h->hx, sizeof(double) * 5 * Nmax);
+        if (e == cudaSuccess) e = cudaMalloc(&h->hP, sizeof(double) * 15 * Nmax);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&h->hsens, sizeof(double) * 4 * Bmax);
+        if (e != cudaSuccess) return cuda_fail(h, e, "allocating the host-path buffers");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    pes_model dm = *model;
+    if (model->kind == PES_MODEL_CT_BEARINGS) {
+        if (!model->sensors) return fail(h, PES_ERR_INVALID_ARG, "model.sensors is NULL");
+        const size_t ns = model->sensors_per_traj ? (size_t)B : 1;
+        PES_CUDA(h, cudaMemcpyAsync(h->hsens, model->sensors, sizeof(double) * 4 * ns, cudaMemcpyHostToDevice, st));
+        dm.sensors = h->hsens;
+    }
+    PES_CUDA(h, cudaMemcpyAsync(h->hy, y, ts * 2 * N, cudaMemcpyHostToDevice, st));
+    PES_CUDA(h, cudaMemcpyAsync(h->hoff, offsets, sizeof(int64_t) * (B + 1), cudaMemcpyHostToDevice, st));
+    PES_CUDA(h, cudaMemcpyAsync(h->hm0, m0, ts * 5 * B, cudaMemcpyHostToDevice, st));
+    PES_CUDA(h, cudaMemcpyAsync(h->hP0, P0, ts * 15 * B, cudaMemcpyHostToDevice, st));
+    if (x_init) PES_CUDA(h, cudaMemcpyAsync(h->hx, x_init, ts * 5 * N, cudaMemcpyHostToDevice, st));
+    if (P_init && method == PES_CUBATURE)
+        PES_CUDA(h, cudaMemcpyAsync(h->hP, P_init, ts * 15 * N, cudaMemcpyHostToDevice, st));
+    int32_t it = 0;
+    pes_status r = pes_ieks_run(h, &dm, method, prec, h->hy, h->hoff, B, N, h->hm0, h->hP0, x_init ? h->hx : nullptr,
+                                (P_init && method == PES_CUBATURE) ? h->hP : nullptr, max_iters, tol, h->hx, h->hP,
+                                &it, stream);
+    if (iters_used) *iters_used = it;
+    if (r != PES_OK && r != PES_ERR_NOT_CONVERGED) return r;
+    PES_CUDA(h, cudaMemcpyAsync(x_out, h->hx, ts * 5 * N, cudaMemcpyDeviceToHost, st));
+    PES_CUDA(h, cudaMemcpyAsync(P_out, h->hP, ts * 15 * N, cudaMemcpyDeviceToHost, st));
+    PES_CUDA(h, cudaStreamSynchronize(st));
+    return r;
+}
+
+}  // extern "C"

@@ -1,0 +1,37 @@
+// Host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "pes_kernel.cuh"
+
+namespace pes {
+
+// One configuration of the persistent kernel (defined in pes_launch_impl.cuh,
+// instantiated by the pes_k_*.cu translation units).
+template <typename T, int LIN, int NT>
+cudaError_t launch_cfg(const KParams<T>& p, int nb, cudaStream_t st);
+template <typename T, int LIN, int NT>
+int capacity_cfg(int device);
+
+// Dispatch over the compiled configurations (pes_dispatch.cu). `lin` is one of
+// LIN_ARRAYS / LIN_IEKS / LIN_CUBATURE; `nt` a compiled block size.
+cudaError_t launch_persistent(const KParams<float>& p, int lin, int nt, int nb, cudaStream_t st);
+cudaError_t launch_persistent(const KParams<double>& p, int lin, int nt, int nb, cudaStream_t st);
+// Largest cooperative grid (co-resident blocks on the whole device), 0 if unsupported.
+int coop_capacity(float, int lin, int nt, int device);
+int coop_capacity(double, int lin, int nt, int device);
+// Block sizes compiled per precision.
+bool nt_supported(float, int nt);
+bool nt_supported(double, int nt);
+
+// Element-wise helpers (pes_aux.cu).
+template <typename T>
+cudaError_t launch_linearize(const KParams<T>& p, int lin, T* F, T* c, T* Qp, T* H, T* d, T* Rp, T* y_used,
+                             cudaStream_t st);
+template <typename T>
+cudaError_t launch_init_nominal(const int64_t* offsets, int B, int64_t N, const T* m0, const T* P0, T* x, T* P,
+                                cudaStream_t st);
+cudaError_t launch_validate_offsets(const int64_t* offsets, int B, int64_t N, int* status, cudaStream_t st);
+
+}  // namespace pes

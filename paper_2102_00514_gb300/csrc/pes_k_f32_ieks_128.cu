@@ -1,0 +1,3 @@
+// Persistent smoother kernel: float, LIN_IEKS, 128 threads per block.
+#include "pes_launch_impl.cuh"
+PES_INSTANTIATE(float, pes::LIN_IEKS, 128)

@@ -1,0 +1,448 @@
+// State-space model (Eq. 4) and its linearisation (Eqs. 7-10) on the device.
+//
+// Model: coordinated turn, x = [px, py, vx, vy, omega], with bearings from two
+// sensors (the experiment of Sec. 5), or a linear-Gaussian model.
+//
+// Linearisations are kept *about the nominal*: the affine approximation
+// f(x) ~ F x + c of Eq. 5 is stored as f(x) ~ fx + F (x - xn) with xn the
+// nominal state, fx = F xn + c; likewise h(x) ~ hx + H (x - xn) with the
+// measurement residual r = y - hx. This is the same affine map; it keeps
+// single precision accurate when states are large (positions of thousands
+// of units) because c = f(xn) - F xn cancels there.
+#pragma once
+
+#include "pes_math.cuh"
+
+namespace pes {
+
+enum { MODEL_CT_BEARINGS = 0, MODEL_LINEAR = 1 };
+enum { LIN_ARRAYS = 0, LIN_IEKS = 1, LIN_CUBATURE = 2 };
+enum { ST_NOT_PD = 1, ST_NONFINITE = 2, ST_TIMEOUT = 4, ST_NOT_CONVERGED = 8, ST_BADARG = 16 };
+
+// Model parameters as passed to the kernels. Q and R are packed (upper).
+struct DevModel {
+    int kind;
+    int sensors_per_traj;
+    double dt;
+    const double* sensors;   // device, [1 or B][4]
+    double Q[15];
+    double R[3];
+    double F[25], c[5], H[10], d[2];   // linear model
+};
+
+// Transition k -> k+1 linearised about xn = xbar_k: x_{k+1} ~ fx + F (x_k - xn) + N(0, Q')
+template <typename T>
+struct Trans {
+    T F[25];
+    T fx[5];
+    T xn[5];
+    T Q[15];
+};
+
+// Observation at k linearised about xn = xbar_k: y_k - hx ~ r-form, i.e. the
+// innovation of a state x is  r - H (x - xn),  noise N(0, R')
+template <typename T>
+struct Obs {
+    T H[10];
+    T xn[5];
+    T r[2];
+    T R[3];
+};
+
+template <typename T> PES_DEV void tsincos(T a, T* s, T* c);
+template <> PES_DEV void tsincos<float>(float a, float* s, float* c) { sincosf(a, s, c); }
+template <> PES_DEV void tsincos<double>(double a, double* s, double* c) { sincos(a, s, c); }
+template <typename T> PES_DEV T tatan2(T y, T x);
+template <> PES_DEV float tatan2<float>(float y, float x) { return atan2f(y, x); }
+template <> PES_DEV double tatan2<double>(double y, double x) { return atan2(y, x); }
+template <typename T> PES_DEV T tfloor(T x);
+template <> PES_DEV float tfloor<float>(float x) { return floorf(x); }
+template <> PES_DEV double tfloor<double>(double x) { return floor(x); }
+
+template <typename T>
+PES_DEV T wrap_angle(T a)
+{
+    const T pi = T(3.14159265358979323846);
+    const T two_pi = T(6.28318530717958647692);
+    return a - two_pi * tfloor((a + pi) / two_pi);
+}
+
+// ---- coordinated turn --------------------------------------------------------
+// With a = omega dt:  A1 = sin(a)/omega,  A2 = (1 - cos a)/omega  and their
+// omega-derivatives. Below |a| < thr their Taylor series in a are used.
+template <typename T>
+struct CTCoef {
+    T s, c, A1, A2, dA1, dA2;
+};
+
+template <typename T>
+PES_DEV CTCoef<T> ct_coef(T w, T dt)
+{
+    CTCoef<T> k;
+    const T a = w * dt;
+    tsincos(a, &k.s, &k.c);
+    const T thr = sizeof(T) == 4 ? T(0.05) : T(0.01);
+    if (fabs(a) < thr) {
+        const T a2 = a * a;
+        k.A1 = dt * (T(1) - a2 * (T(1) / T(6)) + a2 * a2 * (T(1) / T(120)));
+        k.A2 = dt * a * (T(0.5) - a2 * (T(1) / T(24)) + a2 * a2 * (T(1) / T(720)));
+        k.dA1 = dt * dt * a * (-T(1) / T(3) + a2 * (T(1) / T(30)) - a2 * a2 * (T(1) / T(840)));
+        k.dA2 = dt * dt * (T(0.5) - a2 * T(0.125) + a2 * a2 * (T(1) / T(144)));
+    } else {
+        // 1 - cos a without cancellation for cos a > 0
+        const T omc = (k.c > T(0)) ? k.s * k.s / (T(1) + k.c) : T(1) - k.c;
+        const T iw = T(1) / w;
+        k.A1 = k.s * iw;
+        k.A2 = omc * iw;
+        k.dA1 = (a * k.c - k.s) * iw * iw;
+        k.dA2 = (a * k.s - omc) * iw * iw;
+    }
+    return k;
+}
+
+// f(x) split as position increment and the rest:
+//   out = [A1 vx - A2 vy, A2 vx + A1 vy, c vx - s vy, s vx + c vy, omega]
+// so that f(x) = out + [px, py, 0, 0, 0].
+template <typename T>
+PES_DEV void ct_increment(const T* x, const CTCoef<T>& k, T* out)
+{
+    out[0] = k.A1 * x[2] - k.A2 * x[3];
+    out[1] = k.A2 * x[2] + k.A1 * x[3];
+    out[2] = k.c * x[2] - k.s * x[3];
+    out[3] = k.s * x[2] + k.c * x[3];
+    out[4] = x[4];
+}
+
+template <typename T>
+PES_DEV void ct_jacobian(const T* x, const CTCoef<T>& k, T dt, T* F)
+{
+#pragma unroll
+    for (int i = 0; i < 25; ++i) F[i] = T(0);
+    F[0] = T(1);
+    F[2] = k.A1;
+    F[3] = -k.A2;
+    F[4] = k.dA1 * x[2] - k.dA2 * x[3];
+    F[6] = T(1);
+    F[7] = k.A2;
+    F[8] = k.A1;
+    F[9] = k.dA2 * x[2] + k.dA1 * x[3];
+    F[12] = k.c;
+    F[13] = -k.s;
+    F[14] = -dt * (k.s * x[2] + k.c * x[3]);
+    F[17] = k.s;
+    F[18] = k.c;
+    F[19] = dt * (k.c * x[2] - k.s * x[3]);
+    F[24] = T(1);
+}
+
+template <typename T>
+PES_DEV void load_sensors(const DevModel& m, int b, T* s)
+{
+    const double* p = m.sensors + (m.sensors_per_traj ? 4 * b : 0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) s[i] = T(__ldg(p + i));
+}
+
+template <typename T>
+PES_DEV void bearings(const T* x, const T* s, T* out)
+{
+    out[0] = tatan2(x[1] - s[1], x[0] - s[0]);
+    out[1] = tatan2(x[1] - s[3], x[0] - s[2]);
+}
+
+template <typename T>
+PES_DEV void bearings_jacobian(const T* x, const T* s, T* H)
+{
+#pragma unroll
+    for (int i = 0; i < 10; ++i) H[i] = T(0);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const T dx = x[0] - s[2 * r], dy = x[1] - s[2 * r + 1];
+        const T ir2 = T(1) / (dx * dx + dy * dy);
+        H[r * 5 + 0] = -dy * ir2;
+        H[r * 5 + 1] = dx * ir2;
+    }
+}
+
+// ---- Taylor linearisation (IEKS, Eq. 10) ---------------------------------------
+
+template <typename T>
+PES_DEV void lin_trans_taylor(const DevModel& m, const T* xn, Trans<T>& tr)
+{
+#pragma unroll
+    for (int i = 0; i < 5; ++i) tr.xn[i] = xn[i];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) tr.Q[i] = T(m.Q[i]);
+    if (m.kind == MODEL_LINEAR) {
+#pragma unroll
+        for (int i = 0; i < 25; ++i) tr.F[i] = T(m.F[i]);
+        T Fx[5];
+        mv(tr.F, xn, Fx);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) tr.fx[i] = Fx[i] + T(m.c[i]);
+    } else {
+        const T dt = T(m.dt);
+        const CTCoef<T> k = ct_coef(xn[4], dt);
+        ct_jacobian(xn, k, dt, tr.F);
+        T inc[5];
+        ct_increment(xn, k, inc);
+        tr.fx[0] = xn[0] + inc[0];
+        tr.fx[1] = xn[1] + inc[1];
+        tr.fx[2] = inc[2];
+        tr.fx[3] = inc[3];
+        tr.fx[4] = inc[4];
+    }
+}
+
+template <typename T>
+PES_DEV void lin_obs_taylor(const DevModel& m, int b, const T* xn, const T* y, Obs<T>& ob)
+{
+#pragma unroll
+    for (int i = 0; i < 5; ++i) ob.xn[i] = xn[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ob.R[i] = T(m.R[i]);
+    if (m.kind == MODEL_LINEAR) {
+#pragma unroll
+        for (int i = 0; i < 10; ++i) ob.H[i] = T(m.H[i]);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            T hx = T(m.d[r]);
+#pragma unroll
+            for (int l = 0; l < 5; ++l) hx = fma(ob.H[r * 5 + l], xn[l], hx);
+            ob.r[r] = y[r] - hx;
+        }
+    } else {
+        T s[4];
+        load_sensors(m, b, s);
+        bearings_jacobian(xn, s, ob.H);
+        T hx[2];
+        bearings(xn, s, hx);
+        ob.r[0] = wrap_angle(y[0] - hx[0]);
+        ob.r[1] = wrap_angle(y[1] - hx[1]);
+    }
+}
+
+// ---- cubature statistical linear regression (IPLS, Eqs. 7-9) -------------------
+//
+// Sigma points X_{i+-} = xbar +- sqrt(n) L e_i (P = L L^T, weights 1/(2n)).
+// With D_i = Z_{i+} - Z_{i-} and u_i = (Z_{i+} + Z_{i-})/2 - zbar, the moments of
+// Eq. 8 give, exactly for this symmetric point set,
+//     F = Psi^T P^{-1} = D L^{-1} / (2 sqrt(n)),     Lambda = Phi - F P F^T = (1/n) sum_i u_i u_i^T,
+// the second being positive semi-definite by construction. Deviations
+// Z - f(xbar) are formed directly (position increments, wrapped bearings).
+
+// Deviation of the transition: f(xbar + sg) - f(xbar).
+template <typename T>
+PES_DEV void dev_f(const DevModel& m, const T* xbar, const T* inc_ref, const T* sg, T* out)
+{
+    if (m.kind == MODEL_LINEAR) {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            T s = T(0);
+#pragma unroll
+            for (int l = 0; l < 5; ++l) s = fma(T(m.F[i * 5 + l]), sg[l], s);
+            out[i] = s;
+        }
+    } else {
+        T x[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) x[i] = xbar[i] + sg[i];
+        const CTCoef<T> k = ct_coef(x[4], T(m.dt));
+        T inc[5];
+        ct_increment(x, k, inc);
+        out[0] = sg[0] + (inc[0] - inc_ref[0]);
+        out[1] = sg[1] + (inc[1] - inc_ref[1]);
+        out[2] = inc[2] - inc_ref[2];
+        out[3] = inc[3] - inc_ref[3];
+        out[4] = sg[4];
+    }
+}
+
+// Deviation of the observation: h(xbar + sg) - h(xbar), bearings wrapped.
+template <typename T>
+PES_DEV void dev_h(const DevModel& m, const T* xbar, const T* s, const T* h_ref, const T* sg, T* out)
+{
+    if (m.kind == MODEL_LINEAR) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            T v = T(0);
+#pragma unroll
+            for (int l = 0; l < 5; ++l) v = fma(T(m.H[r * 5 + l]), sg[l], v);
+            out[r] = v;
+        }
+    } else {
+        T x[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) x[i] = xbar[i] + sg[i];
+        T hz[2];
+        bearings(x, s, hz);
+        out[0] = wrap_angle(hz[0] - h_ref[0]);
+        out[1] = wrap_angle(hz[1] - h_ref[1]);
+    }
+}
+
+// Solve G L = Dsc (row vectors) for G: each row g satisfies sum_{l>=c} g_l L_{lc} = Dsc_c.
+template <typename T, int NZ>
+PES_DEV void solve_rows_lower_t(const T* L, const T* rdiag, const T* Dsc, T* G)
+{
+#pragma unroll
+    for (int r = 0; r < NZ; ++r)
+#pragma unroll
+        for (int c = NX - 1; c >= 0; --c) {
+            T s = Dsc[r * NX + c];
+#pragma unroll
+            for (int l = c + 1; l < NX; ++l) s = fma(-G[r * NX + l], L[l * NX + c], s);
+            G[r * NX + c] = s * rdiag[c];
+        }
+}
+
+// Cubature factor of Pbar; false if Pbar is not positive definite.
+template <typename T>
+PES_DEV bool cub_factor(const T* Pbar, T* L, T* rdiag)
+{
+    return chol_pd(Pbar, L, rdiag);
+}
+
+template <typename T>
+PES_DEV void lin_trans_cubature(const DevModel& m, const T* xbar, const T* L, const T* rdiag, Trans<T>& tr)
+{
+    const T sq = tsqrt(T(NX));
+    T inc_ref[5];
+    if (m.kind == MODEL_LINEAR) {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) inc_ref[i] = T(0);
+    } else {
+        const CTCoef<T> k = ct_coef(xbar[4], T(m.dt));
+        ct_increment(xbar, k, inc_ref);
+    }
+    T Dm[25];       // columns D_i (row-major: Dm[r*5 + i])
+    T U[25];        // columns u_i + zdev (before centring)
+    T zdev[5] = {T(0), T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+        T sg[5], zp[5], zm[5];
+#pragma unroll
+        for (int r = 0; r < 5; ++r) sg[r] = sq * L[r * NX + i];
+        dev_f(m, xbar, inc_ref, sg, zp);
+#pragma unroll
+        for (int r = 0; r < 5; ++r) sg[r] = -sg[r];
+        dev_f(m, xbar, inc_ref, sg, zm);
+#pragma unroll
+        for (int r = 0; r < 5; ++r) {
+            Dm[r * NX + i] = zp[r] - zm[r];
+            const T h = T(0.5) * (zp[r] + zm[r]);
+            U[r * NX + i] = h;
+            zdev[r] += h;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 5; ++r) zdev[r] *= T(1) / T(NX);
+    // F = D L^{-1} / (2 sqrt(n))
+    const T sc = T(0.5) / sq;
+#pragma unroll
+    for (int i = 0; i < 25; ++i) Dm[i] *= sc;
+    solve_rows_lower_t<T, 5>(L, rdiag, Dm, tr.F);
+    // Lambda = (1/n) sum_i u_i u_i^T with u_i = U_i - zdev
+#pragma unroll
+    for (int r = 0; r < 5; ++r)
+#pragma unroll
+        for (int i = 0; i < NX; ++i) U[r * NX + i] -= zdev[r];
+#pragma unroll
+    for (int r = 0; r < 5; ++r)
+#pragma unroll
+        for (int q = r; q < 5; ++q) {
+            T s = T(0);
+#pragma unroll
+            for (int i = 0; i < NX; ++i) s = fma(U[r * NX + i], U[q * NX + i], s);
+            tr.Q[si(r, q)] = T(m.Q[si(r, q)]) + s * (T(1) / T(NX));
+        }
+    // fx = zbar = f(xbar) + zdev
+    if (m.kind == MODEL_LINEAR) {
+        T Fx[5];
+        T Fm[25];
+#pragma unroll
+        for (int i = 0; i < 25; ++i) Fm[i] = T(m.F[i]);
+        mv(Fm, xbar, Fx);
+#pragma unroll
+        for (int r = 0; r < 5; ++r) tr.fx[r] = Fx[r] + T(m.c[r]) + zdev[r];
+    } else {
+        tr.fx[0] = xbar[0] + inc_ref[0] + zdev[0];
+        tr.fx[1] = xbar[1] + inc_ref[1] + zdev[1];
+        tr.fx[2] = inc_ref[2] + zdev[2];
+        tr.fx[3] = inc_ref[3] + zdev[3];
+        tr.fx[4] = inc_ref[4] + zdev[4];
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) tr.xn[i] = xbar[i];
+}
+
+template <typename T>
+PES_DEV void lin_obs_cubature(const DevModel& m, int b, const T* xbar, const T* L, const T* rdiag, const T* y,
+                              Obs<T>& ob)
+{
+    const T sq = tsqrt(T(NX));
+    T s[4] = {T(0), T(0), T(0), T(0)};
+    T h_ref[2];
+    if (m.kind == MODEL_LINEAR) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            T v = T(m.d[r]);
+#pragma unroll
+            for (int l = 0; l < 5; ++l) v = fma(T(m.H[r * 5 + l]), xbar[l], v);
+            h_ref[r] = v;
+        }
+    } else {
+        load_sensors(m, b, s);
+        bearings(xbar, s, h_ref);
+    }
+    T Dm[10], U[10];
+    T zdev[2] = {T(0), T(0)};
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+        T sg[5], zp[2], zm[2];
+#pragma unroll
+        for (int r = 0; r < 5; ++r) sg[r] = sq * L[r * NX + i];
+        dev_h(m, xbar, s, h_ref, sg, zp);
+#pragma unroll
+        for (int r = 0; r < 5; ++r) sg[r] = -sg[r];
+        dev_h(m, xbar, s, h_ref, sg, zm);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            Dm[r * NX + i] = zp[r] - zm[r];
+            const T h = T(0.5) * (zp[r] + zm[r]);
+            U[r * NX + i] = h;
+            zdev[r] += h;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) zdev[r] *= T(1) / T(NX);
+    const T sc = T(0.5) / sq;
+#pragma unroll
+    for (int i = 0; i < 10; ++i) Dm[i] *= sc;
+    solve_rows_lower_t<T, 2>(L, rdiag, Dm, ob.H);
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int i = 0; i < NX; ++i) U[r * NX + i] -= zdev[r];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int q = r; q < 2; ++q) {
+            T v = T(0);
+#pragma unroll
+            for (int i = 0; i < NX; ++i) v = fma(U[r * NX + i], U[q * NX + i], v);
+            ob.R[si2(r, q)] = T(m.R[si2(r, q)]) + v * (T(1) / T(NX));
+        }
+    // residual about zbar = h(xbar) + zdev, measurement unwrapped nearest h(xbar)
+    if (m.kind == MODEL_LINEAR) {
+        ob.r[0] = y[0] - h_ref[0] - zdev[0];
+        ob.r[1] = y[1] - h_ref[1] - zdev[1];
+    } else {
+        ob.r[0] = wrap_angle(y[0] - h_ref[0]) - zdev[0];
+        ob.r[1] = wrap_angle(y[1] - h_ref[1]) - zdev[1];
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) ob.xn[i] = xbar[i];
+}
+
+}  // namespace pes

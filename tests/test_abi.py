@@ -1,0 +1,39 @@
+"""The C-ABI library loads and exports every entry point include/pes.h declares
+(no compute calls: this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2102_00514_gb300 import build, pes
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "pes.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pes_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ("pes_linearize", "pes_filter_scan", "pes_smooth_scan", "pes_ieks_run"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    build.build_cuda()
+    lib = ctypes.CDLL(pes.LIB_PATH)
+    missing = [n for n in declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert sorted(pes.EXPORTED) == declared_symbols()
+
+
+def test_binding_refuses_without_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(RuntimeError):
+        pes.Smoother(16)

@@ -1,0 +1,152 @@
+"""GPU parity of the fused iterated smoother (pes_ieks_run) and of the
+linearisation (pes_linearize) against the oracle, element by element."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2102_00514_gb300 import pes, synth
+from tests.gpu_common import (TOL_FP32, TOL_FP64, gpu_run, oracle_run, rel_err, to_dev, workload_to_dev)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sm():
+    s = pes.Smoother(1 << 21, 4096)
+    yield s
+    s.close()
+
+
+@pytest.mark.parametrize("method", [pes.IEKS, pes.CUBATURE])
+@pytest.mark.parametrize("prec", [pes.FP64, pes.FP32])
+def test_linearize_matches_oracle(sm, method, prec):
+    wl = synth.ct_bearings([40, 1, 300], seed=21, sensor_jitter=0.2, omega0_halfwidth=1.0)
+    # a non-trivial nominal: one oracle iteration from the prior
+    out = oracle_run(wl, method, iters=1)
+    om = oracle.Model.from_workload(wl)
+    ref = oracle.linearize(om, oracle.IEKS if method == pes.IEKS else oracle.CUBATURE, wl["offsets"],
+                           out["x"], out["P"], wl["y"])
+    dt = torch.float64 if prec == pes.FP64 else torch.float32
+    d = workload_to_dev(wl, prec)
+    got = sm.linearize(d["model"], method, prec, to_dev(out["x"], dt), to_dev(out["P"], dt), d["y"], d["offsets"])
+    sm.sync()
+    tol = 1e-10 if prec == pes.FP64 else 2e-4
+    for k in ("F", "c", "Qp", "H", "d", "Rp", "y_used"):
+        g = got[k].double().cpu().numpy()
+        scale = max(np.abs(ref[k]).max(), 1e-30)
+        assert np.abs(g - ref[k]).max() / scale < tol, k
+
+
+@pytest.mark.parametrize("name,method", [("ieks_T500", pes.IEKS), ("ipls_T10000", pes.CUBATURE),
+                                         ("ipls_T10000", pes.IEKS), ("ieks_T500", pes.CUBATURE)])
+def test_ieks_run_fp64_matches_oracle(sm, name, method):
+    wl = synth.workload(name)
+    ref = oracle_run(wl, method, iters=10)
+    x, P, used, _ = gpu_run(sm, wl, method, pes.FP64, iters=10)
+    assert used == 10
+    assert rel_err(x, ref["x"], wl["offsets"]) < TOL_FP64
+    assert rel_err(P, ref["P"], wl["offsets"]) < TOL_FP64
+
+
+@pytest.mark.parametrize("name,method", [("ieks_T500", pes.IEKS), ("ipls_T10000", pes.CUBATURE),
+                                         ("ipls_T10000", pes.IEKS)])
+def test_ieks_run_fp32_matches_oracle(sm, name, method):
+    wl = synth.workload(name)
+    ref = oracle_run(wl, method, iters=10)
+    x, P, used, _ = gpu_run(sm, wl, method, pes.FP32, iters=10)
+    ex = rel_err(x, ref["x"], wl["offsets"])
+    eP = rel_err(P, ref["P"], wl["offsets"])
+    print(f"{name} method {method} FP32: means {ex:.3e} covariances {eP:.3e}")
+    assert ex < TOL_FP32 and eP < TOL_FP32
+
+
+@pytest.mark.parametrize("method", [pes.IEKS, pes.CUBATURE])
+def test_batched_segmented_fp64(sm, method):
+    wl = synth.workload("batch64_T1_400")
+    ref = oracle_run(wl, method, iters=5)
+    x, P, used, _ = gpu_run(sm, wl, method, pes.FP64, iters=5)
+    assert rel_err(x, ref["x"], wl["offsets"]) < TOL_FP64
+    assert rel_err(P, ref["P"], wl["offsets"]) < TOL_FP64
+
+
+def test_batched_equals_separate_runs(sm):
+    wl = synth.workload("batch8_T1_3000")
+    xb, Pb, _, _ = gpu_run(sm, wl, pes.CUBATURE, pes.FP64, iters=3)
+    off = wl["offsets"]
+    for b in range(len(off) - 1):
+        sl = slice(int(off[b]), int(off[b + 1]))
+        one = dict(wl, offsets=np.array([0, off[b + 1] - off[b]]), y=wl["y"][:, sl], m0=wl["m0"][b:b + 1],
+                   P0=wl["P0"][b:b + 1], sensors=wl["sensors"][b:b + 1])
+        x1, P1, _, _ = gpu_run(sm, one, pes.CUBATURE, pes.FP64, iters=3)
+        assert rel_err(x1, xb[:, sl], one["offsets"]) < 1e-11
+        assert rel_err(P1, Pb[:, sl], one["offsets"]) < 1e-11
+
+
+def test_tolerance_mode_matches_oracle_iterations(sm):
+    wl = synth.workload("ieks_T500")
+    ref = oracle_run(wl, pes.IEKS, iters=50, tol=1e-6)
+    x, P, used, st = gpu_run(sm, wl, pes.IEKS, pes.FP64, iters=50, tol=1e-6)
+    assert st == pes.OK and used == ref["iters_used"]
+    assert rel_err(x, ref["x"], wl["offsets"]) < TOL_FP64
+    x, P, used, st = gpu_run(sm, wl, pes.IEKS, pes.FP64, iters=3, tol=1e-6, allow_not_converged=True)
+    assert st == pes.NOT_CONVERGED and used == 3
+
+
+def test_prior_init_equals_explicit_init(sm):
+    wl = synth.workload("ieks_T500")
+    d = workload_to_dev(wl, pes.FP64)
+    N = wl["y"].shape[1]
+    x0 = torch.tensor(np.tile(wl["m0"][0][:, None], (1, N)), dtype=torch.float64, device="cuda")
+    P0 = torch.tensor(np.tile(wl["P0"][0][:, None], (1, N)), dtype=torch.float64, device="cuda")
+    xa, Pa, _, _ = sm.ieks_run(d["model"], pes.CUBATURE, pes.FP64, d["y"], d["offsets"], d["m0"], d["P0"], iters=2)
+    xb, Pb, _, _ = sm.ieks_run(d["model"], pes.CUBATURE, pes.FP64, d["y"], d["offsets"], d["m0"], d["P0"],
+                               x_init=x0, P_init=P0, iters=2)
+    sm.sync()
+    assert torch.equal(xa, xb) and torch.equal(Pa, Pb)
+
+
+def test_host_entry_point_equals_device_entry_point(sm):
+    wl = synth.workload("ieks_T500")
+    d = workload_to_dev(wl, pes.FP32)
+    xd, Pd, _, _ = sm.ieks_run(d["model"], pes.IEKS, pes.FP32, d["y"], d["offsets"], d["m0"], d["P0"], iters=4)
+    sm.sync()
+    h = lambda a, dt=torch.float32: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).pin_memory()
+    xh, Ph, used, _ = sm.ieks_run_host(d["model"], pes.IEKS, pes.FP32, h(wl["y"]), h(wl["offsets"], torch.int64),
+                                       h(wl["m0"]), h(wl["P0"]), iters=4,
+                                       sensors_host=h(wl["sensors"], torch.float64))
+    assert used == 4
+    assert torch.equal(xh, xd.cpu()) and torch.equal(Ph, Pd.cpu())
+
+
+def test_invalid_arguments_rejected_before_launch(sm):
+    wl = synth.workload("ieks_T500")
+    d = workload_to_dev(wl, pes.FP64)
+    with pytest.raises(pes.PesError) as ei:
+        sm.ieks_run(d["model"], pes.IEKS, pes.FP64, d["y"], d["offsets"], d["m0"], d["P0"], iters=0)
+    assert ei.value.status == pes.INVALID_ARG
+    with pytest.raises(pes.PesError) as ei:
+        sm.ieks_run(d["model"], pes.IEKS, pes.MIXED, d["y"].float(), d["offsets"], d["m0"].float(),
+                    d["P0"].float(), iters=1)
+    assert ei.value.status == pes.UNSUPPORTED
+
+
+def test_nonfinite_measurement_reported(sm):
+    wl = synth.workload("ieks_T500")
+    wl = dict(wl, y=wl["y"].copy())
+    wl["y"][0, 250] = np.nan
+    with pytest.raises(pes.PesError) as ei:
+        gpu_run(sm, wl, pes.IEKS, pes.FP64, iters=2)
+    assert ei.value.status in (pes.NONFINITE, pes.NOT_PD)
+    # the handle is usable afterwards
+    x, P, used, st = gpu_run(sm, synth.workload("ieks_T500"), pes.IEKS, pes.FP64, iters=1)
+    assert st == pes.OK
+
+
+def test_not_positive_definite_prior_reported(sm):
+    wl = synth.workload("ieks_T500")
+    wl = dict(wl, P0=wl["P0"].copy())
+    wl["P0"][0, 0] = -1.0   # P0[0,0] < 0
+    with pytest.raises(pes.PesError) as ei:
+        gpu_run(sm, wl, pes.CUBATURE, pes.FP64, iters=2)
+    assert ei.value.status in (pes.NOT_PD, pes.NONFINITE)
