@@ -53,7 +53,35 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 17, help="states in the oracle's timed sample")
+    ap.add_argument("--profile", choices=["ieks", "cubature"], default=None,
+                    help="profiling case: only `warmup` + 1 FP32 runs of one method, no JSON line")
+    ap.add_argument("--prec", choices=["fp32", "fp64"], default="fp32", help="precision of --profile")
     return ap.parse_args()
+
+
+def run_profile_case(args):
+    """A short, single-method case for ncu captures: `warmup` launches, then one."""
+    import numpy as np
+    import torch
+
+    from paper_2102_00514_gb300 import build, pes, synth
+    build.build_all()
+    wl = synth.workload(f"sweep_T{args.T}")
+    N = wl["y"].shape[1]
+    prec = pes.FP32 if args.prec == "fp32" else pes.FP64
+    dt = torch.float32 if prec == pes.FP32 else torch.float64
+    dev = lambda a, d=dt: torch.as_tensor(np.ascontiguousarray(a), dtype=d, device="cuda")
+    sm = pes.Smoother(N, 1)
+    m = pes.IEKS if args.profile == "ieks" else pes.CUBATURE
+    y, off, m0, P0 = dev(wl["y"]), dev(wl["offsets"], torch.int64), dev(wl["m0"]), dev(wl["P0"])
+    model = pes.Model.from_workload(wl)
+    for i in range(args.warmup + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sm.ieks_run(model, m, prec, y, off, m0, P0, iters=args.iters)
+        sm.sync()
+        print(f"run {i}: {1e3 * (time.perf_counter() - t0):.3f} ms", flush=True)
+    sm.close()
 
 
 def peaks_file():
@@ -196,6 +224,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.profile:
+        run_profile_case(args)
         return
 
     import numpy as np
