@@ -214,6 +214,17 @@ pes_status pes_ieks_run_host(pes_handle* h, const pes_model* model, pes_method m
 pes_status pes_launch_shape(pes_handle* h, pes_method method, pes_precision prec, int64_t N,
                             int32_t* blocks, int32_t* threads, int32_t* steps_per_thread);
 
+/* Diagnostic: per-phase durations of the first iteration of the last
+ * persistent launch, when the handle was created with the environment variable
+ * PES_PHASE_TIMES=1 (else PES_ERR_UNSUPPORTED). mean_ns[i] / max_ns[i] (max_ns
+ * may be NULL) receive the mean / maximum over blocks of the time between
+ * phase boundaries i and i+1: 0 fold, 1 filter up-sweep, 2 barrier, 3 filter
+ * top level, 4 filter down-sweep, 5 filter re-run, 6 smoother up-sweep,
+ * 7 barrier, 8 smoother top level, 9 smoother down-sweep, 10 RTS re-run,
+ * 11 (unused), 12 end-of-iteration barrier; -1 where not recorded.
+ * Synchronises the device. */
+pes_status pes_debug_phase_times(pes_handle* h, double* mean_ns, double* max_ns, int32_t n);
+
 /* Measured arithmetic throughput of this device's CUDA cores (a diagnostic for
  * roofline accounting, not part of the method): a dependent-chain-free FMA
  * loop over all SMs, timed with CUDA events. Outputs in GFLOP/s (2 flops per

@@ -36,6 +36,10 @@ struct pes_handle {
     void* hxi = nullptr;
     void* hPi = nullptr;
     double* hsens = nullptr;
+    void* sensT = nullptr;   // sensors converted to the kernel precision
+    void* lanes = nullptr;   // x, P, y in the kernel's lane-major layout
+    long long* ptime = nullptr;   // phase timestamps (PES_PHASE_TIMES=1)
+    int ptime_blocks = 0;
     long long timeout_ns = 2000000000LL;
     char err[512] = {0};
 };
@@ -86,41 +90,48 @@ pes_status check_common(pes_handle* h, pes_precision prec, const int64_t* offset
     return PES_OK;
 }
 
-DevModel to_dev_model(const pes_model& m)
+template <typename T>
+DevModel<T> to_dev_model(const pes_model& m, const T* sensors_T)
 {
-    DevModel d;
+    DevModel<T> d;
     memset(&d, 0, sizeof(d));
     d.kind = m.kind;
     d.sensors_per_traj = m.sensors_per_traj;
-    d.dt = m.dt;
-    d.sensors = m.sensors;
+    d.dt = T(m.dt);
+    d.sensors = sensors_T;
+    double Q[15] = {0}, R[3] = {0};
     if (m.kind == PES_MODEL_LINEAR) {
-        memcpy(d.Q, m.Q, sizeof(d.Q));
-        memcpy(d.R, m.R, sizeof(d.R));
-        memcpy(d.F, m.F, sizeof(d.F));
-        memcpy(d.c, m.c, sizeof(d.c));
-        memcpy(d.H, m.H, sizeof(d.H));
-        memcpy(d.d, m.d, sizeof(d.d));
+        memcpy(Q, m.Q, sizeof(Q));
+        memcpy(R, m.R, sizeof(R));
+        for (int i = 0; i < 25; ++i) d.F[i] = T(m.F[i]);
+        for (int i = 0; i < 5; ++i) d.c[i] = T(m.c[i]);
+        for (int i = 0; i < 10; ++i) d.H[i] = T(m.H[i]);
+        for (int i = 0; i < 2; ++i) d.d[i] = T(m.d[i]);
     } else {
         const double dt = m.dt;
         if (m.q_form == 1) {
             for (int ax = 0; ax < 2; ++ax) {
                 const int pp = ax, v = ax + 2;
-                d.Q[si(pp, pp)] = m.q_c * dt * dt * dt / 3.0;
-                d.Q[si(pp, v)] = m.q_c * dt * dt / 2.0;
-                d.Q[si(v, v)] = m.q_c * dt;
+                Q[si(pp, pp)] = m.q_c * dt * dt * dt / 3.0;
+                Q[si(pp, v)] = m.q_c * dt * dt / 2.0;
+                Q[si(v, v)] = m.q_c * dt;
             }
         } else {
-            d.Q[si(2, 2)] = m.q_c * dt;
-            d.Q[si(3, 3)] = m.q_c * dt;
+            Q[si(2, 2)] = m.q_c * dt;
+            Q[si(3, 3)] = m.q_c * dt;
         }
-        d.Q[si(4, 4)] = m.q_w * dt;
-        d.R[0] = m.r_std * m.r_std;
-        d.R[1] = 0.0;
-        d.R[2] = m.r_std * m.r_std;
+        Q[si(4, 4)] = m.q_w * dt;
+        R[0] = m.r_std * m.r_std;
+        R[2] = m.r_std * m.r_std;
     }
+    for (int i = 0; i < 15; ++i) d.Q[i] = T(Q[i]);
+    for (int i = 0; i < 3; ++i) d.R[i] = T(R[i]);
     return d;
 }
+
+// The model's sensors in the kernel precision, in the handle's workspace.
+template <typename T>
+pes_status device_model(pes_handle* h, const pes_model& m, int32_t B, cudaStream_t st, DevModel<T>& out);
 
 pes_status check_model(pes_handle* h, const pes_model* m)
 {
@@ -136,8 +147,17 @@ pes_status check_model(pes_handle* h, const pes_model* m)
     return fail(h, PES_ERR_INVALID_ARG, "unknown model kind %d", (int)m->kind);
 }
 
-// Block size per precision (the autotuned choice lives here).
-int choose_nt(pes_precision prec) { return prec == PES_FP64 ? 128 : 256; }
+// Block size per precision. PES_FP32_THREADS (128 or 256) overrides the FP32
+// choice, for tuning.
+int choose_nt(pes_precision prec)
+{
+    if (prec == PES_FP64) return 128;
+    if (const char* env = getenv("PES_FP32_THREADS")) {
+        const int v = atoi(env);
+        if (v == 128 || v == 256) return v;
+    }
+    return 256;
+}
 
 struct Shape {
     int nb, nt, L;
@@ -168,7 +188,10 @@ void fill_workspace(pes_handle* h, KParams<T>& p, const Shape& s)
     p.iters_done = h->iters_done;
     p.L = s.L;
     p.NL = s.nb * s.nt;
+    p.cs = p.lanes_layout ? (int64_t)s.L * p.NL : p.N;
     p.timeout_ns = h->timeout_ns;
+    p.ptime = h->ptime;
+    h->ptime_blocks = s.nb;
 }
 
 pes_status read_status(pes_handle* h, cudaStream_t st, int* iters = nullptr)
@@ -188,17 +211,35 @@ pes_status read_status(pes_handle* h, cudaStream_t st, int* iters = nullptr)
 }
 
 template <typename T>
-pes_status run_persistent(pes_handle* h, KParams<T>& p, int lin, pes_precision prec, cudaStream_t st)
+pes_status device_model(pes_handle* h, const pes_model& m, int32_t B, cudaStream_t st, DevModel<T>& out)
 {
-    Shape s;
-    pes_status r = make_shape<T>(h, lin, prec, p.N, s);
-    if (r != PES_OK) return r;
+    T* sensT = static_cast<T*>(h->sensT);
+    out = to_dev_model<T>(m, sensT);
+    if (m.kind == PES_MODEL_CT_BEARINGS) {
+        const int n = 4 * (m.sensors_per_traj ? (int)B : 1);
+        PES_CUDA(h, launch_convert<T>(m.sensors, sensT, n, st));
+    }
+    return PES_OK;
+}
+
+template <typename T>
+pes_status run_persistent_shaped(pes_handle* h, KParams<T>& p, int lin, const Shape& s, cudaStream_t st)
+{
     fill_workspace(h, p, s);
     PES_CUDA(h, cudaMemsetAsync(h->bar, 0, sizeof(unsigned), st));
     if (p.mode == MODE_RUN && p.tol > 0.0) PES_CUDA(h, cudaMemsetAsync(h->conv, 0, sizeof(double) * 4 * p.B, st));
     cudaError_t e = launch_persistent(p, lin, s.nt, s.nb, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "cooperative launch of the smoother kernel");
     return PES_OK;
+}
+
+template <typename T>
+pes_status run_persistent(pes_handle* h, KParams<T>& p, int lin, pes_precision prec, cudaStream_t st)
+{
+    Shape s;
+    pes_status r = make_shape<T>(h, lin, prec, p.N, s);
+    if (r != PES_OK) return r;
+    return run_persistent_shaped(h, p, lin, s, st);
 }
 
 }  // namespace
@@ -235,26 +276,35 @@ static pes_status ieks_run_t(pes_handle* h, const pes_model* model, pes_method m
                              const void* P0, const void* x_init, const void* P_init, int32_t max_iters, double tol,
                              void* x_out, void* P_out, int32_t* iters_used, cudaStream_t st)
 {
-    const size_t ts = sizeof(T);
-    // nominal^(0) in the output buffers
-    if (x_init) {
-        if (x_init != x_out) PES_CUDA(h, cudaMemcpyAsync(x_out, x_init, ts * 5 * N, cudaMemcpyDeviceToDevice, st));
-    }
-    const bool need_P0_fill = (method == PES_CUBATURE) && !P_init;
-    if (method == PES_CUBATURE && P_init && P_init != P_out)
-        PES_CUDA(h, cudaMemcpyAsync(P_out, P_init, ts * 15 * N, cudaMemcpyDeviceToDevice, st));
-    if (!x_init || need_P0_fill)
-        PES_CUDA(h, launch_init_nominal<T>(offsets, B, N, (const T*)m0, (const T*)P0, x_init ? nullptr : (T*)x_out,
-                                           need_P0_fill ? (T*)P_out : nullptr, st));
+    const int lin = method == PES_CUBATURE ? LIN_CUBATURE : LIN_IEKS;
+    Shape s;
+    pes_status r = make_shape<T>(h, lin, prec, N, s);
+    if (r != PES_OK) return r;
+    // the kernel's lane-major copies of x, P and y (state k = lane * L + s)
+    const int NL = s.nb * s.nt;
+    const int64_t cs = (int64_t)s.L * NL;
+    T* lx = static_cast<T*>(h->lanes);
+    T* lP = lx + 5 * cs;
+    T* ly = lP + 15 * cs;
+    PES_CUDA(h, launch_lanes_transpose<T>((const T*)y, ly, 2, N, s.L, NL, true, st));
+    const bool cub = (method == PES_CUBATURE);
+    if (x_init) PES_CUDA(h, launch_lanes_transpose<T>((const T*)x_init, lx, 5, N, s.L, NL, true, st));
+    if (cub && P_init) PES_CUDA(h, launch_lanes_transpose<T>((const T*)P_init, lP, 15, N, s.L, NL, true, st));
+    if (!x_init || (cub && !P_init))
+        PES_CUDA(h, launch_init_nominal_lanes<T>(offsets, B, N, s.L, NL, (const T*)m0, (const T*)P0,
+                                                 x_init ? nullptr : lx, (cub && !P_init) ? lP : nullptr, st));
     KParams<T> p{};
     p.N = N; p.offsets = offsets; p.B = B; p.mode = MODE_RUN; p.iters = max_iters; p.tol = tol;
     p.write_P_every_iter = tol > 0.0 ? 1 : 0;
-    p.model = to_dev_model(*model);
-    p.y = (const T*)y; p.m0 = (const T*)m0; p.P0 = (const T*)P0;
-    p.x = (T*)x_out; p.P = (T*)P_out;
-    const int lin = method == PES_CUBATURE ? LIN_CUBATURE : LIN_IEKS;
-    pes_status r = run_persistent<T>(h, p, lin, prec, st);
+    pes_status rm = device_model<T>(h, *model, B, st, p.model);
+    if (rm != PES_OK) return rm;
+    p.y = ly; p.m0 = (const T*)m0; p.P0 = (const T*)P0;
+    p.x = lx; p.P = lP;
+    p.lanes_layout = 1;
+    r = run_persistent_shaped<T>(h, p, lin, s, st);
     if (r != PES_OK) return r;
+    PES_CUDA(h, launch_lanes_transpose<T>(lx, (T*)x_out, 5, N, s.L, NL, false, st));
+    PES_CUDA(h, launch_lanes_transpose<T>(lP, (T*)P_out, 15, N, s.L, NL, false, st));
     if (tol > 0.0 || iters_used) {
         int it = 0;
         r = read_status(h, st, &it);
@@ -294,12 +344,18 @@ pes_status pes_create(pes_handle** out, int64_t max_states, int32_t max_batch)
     h->nl_max = h->nb_max * kMaxThreads;
     const size_t hand_elems = (size_t)HAND * ((size_t)max_states + (size_t)h->nl_max);
     e = cudaMalloc(&h->hand, hand_elems * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->lanes, (size_t)22 * ((size_t)max_states + (size_t)h->nl_max) * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&h->aggF, (size_t)h->nb_max * FE * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&h->aggS, (size_t)h->nb_max * SE * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->bar, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->status, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->conv, sizeof(double) * 4 * (size_t)max_batch);
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->iters_done, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->sensT, sizeof(double) * 4 * (size_t)max_batch);
+    if (e == cudaSuccess && getenv("PES_PHASE_TIMES") && atoi(getenv("PES_PHASE_TIMES")) > 0) {
+        e = cudaMalloc((void**)&h->ptime, sizeof(long long) * NPHASE * (size_t)h->nb_max);
+        if (e == cudaSuccess) e = cudaMemset(h->ptime, 0, sizeof(long long) * NPHASE * (size_t)h->nb_max);
+    }
     if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(int));
     if (e != cudaSuccess) {
         pes_destroy(h);
@@ -313,7 +369,7 @@ pes_status pes_destroy(pes_handle* h)
 {
     if (!h) return PES_ERR_INVALID_ARG;
     cudaDeviceSynchronize();
-    void* ptrs[] = {h->hand, h->aggF, h->aggS, h->bar, h->status, h->conv, h->iters_done,
+    void* ptrs[] = {h->hand, h->lanes, h->aggF, h->aggS, h->bar, h->status, h->conv, h->iters_done, h->sensT, h->ptime,
                     h->hy, h->hoff, h->hm0, h->hP0, h->hx, h->hP, h->hxi, h->hPi, h->hsens};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -327,6 +383,37 @@ pes_status pes_sync(pes_handle* h, void* stream)
 {
     if (!h) return PES_ERR_INVALID_ARG;
     return read_status(h, (cudaStream_t)stream);
+}
+
+pes_status pes_debug_phase_times(pes_handle* h, double* mean_ns, double* max_ns, int32_t n)
+{
+    if (!h || !mean_ns || n < 1) return PES_ERR_INVALID_ARG;
+    if (!h->ptime || h->ptime_blocks < 1) return fail(h, PES_ERR_UNSUPPORTED, "phase timing is off (set PES_PHASE_TIMES=1 before pes_create)");
+    const int nb = h->ptime_blocks;
+    long long* buf = (long long*)malloc(sizeof(long long) * NPHASE * nb);
+    if (!buf) return PES_ERR_CUDA;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(buf, h->ptime, sizeof(long long) * NPHASE * nb, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        free(buf);
+        return cuda_fail(h, e, "reading phase timestamps");
+    }
+    for (int i = 0; i < n && i < NPHASE - 1; ++i) {
+        double sum = 0.0, mx = 0.0;
+        int cnt = 0;
+        for (int b = 0; b < nb; ++b) {
+            const long long t0 = buf[b * NPHASE + i], t1 = buf[b * NPHASE + i + 1];
+            if (t0 > 0 && t1 >= t0) {
+                sum += double(t1 - t0);
+                mx = std::max(mx, double(t1 - t0));
+                ++cnt;
+            }
+        }
+        mean_ns[i] = cnt ? sum / cnt : -1.0;
+        if (max_ns) max_ns[i] = cnt ? mx : -1.0;
+    }
+    free(buf);
+    return PES_OK;
 }
 
 pes_status pes_launch_shape(pes_handle* h, pes_method method, pes_precision prec, int64_t N, int32_t* blocks,
@@ -360,14 +447,16 @@ pes_status pes_linearize(pes_handle* h, const pes_model* model, pes_method metho
     const int lin = method == PES_CUBATURE ? LIN_CUBATURE : LIN_IEKS;
     if (prec == PES_FP64) {
         KParams<double> p{};
-        p.N = N; p.offsets = offsets; p.B = B; p.model = to_dev_model(*model);
-        p.x = (double*)x_nom; p.P = (double*)P_nom; p.y = (const double*)y; p.status = h->status;
+        p.N = N; p.offsets = offsets; p.B = B;
+        if ((r = device_model<double>(h, *model, B, st, p.model)) != PES_OK) return r;
+        p.x = (double*)x_nom; p.P = (double*)P_nom; p.y = (const double*)y; p.status = h->status; p.cs = N;
         PES_CUDA(h, launch_linearize<double>(p, lin, (double*)F, (double*)c, (double*)Qp, (double*)H, (double*)d,
                                              (double*)Rp, (double*)y_used, st));
     } else {
         KParams<float> p{};
-        p.N = N; p.offsets = offsets; p.B = B; p.model = to_dev_model(*model);
-        p.x = (float*)x_nom; p.P = (float*)P_nom; p.y = (const float*)y; p.status = h->status;
+        p.N = N; p.offsets = offsets; p.B = B;
+        if ((r = device_model<float>(h, *model, B, st, p.model)) != PES_OK) return r;
+        p.x = (float*)x_nom; p.P = (float*)P_nom; p.y = (const float*)y; p.status = h->status; p.cs = N;
         PES_CUDA(h, launch_linearize<float>(p, lin, (float*)F, (float*)c, (float*)Qp, (float*)H, (float*)d,
                                             (float*)Rp, (float*)y_used, st));
     }

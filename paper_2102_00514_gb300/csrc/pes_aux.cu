@@ -40,6 +40,111 @@ PES_DEV int traj_of(const int64_t* offsets, int B, int64_t k)
 }
 
 template <typename T>
+__global__ void convert_kernel(const double* in, T* out, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = T(in[i]);
+}
+
+template <typename T>
+cudaError_t launch_convert(const double* in, T* out, int n, cudaStream_t st)
+{
+    const int threads = 256;
+    const int blocks = std::max(1, std::min((n + threads - 1) / threads, 1024));
+    convert_kernel<T><<<blocks, threads, 0, st>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_convert<float>(const double*, float*, int, cudaStream_t);
+template cudaError_t launch_convert<double>(const double*, double*, int, cudaStream_t);
+
+// Caller layout [nc][N] <-> the kernel's lane-major layout [nc][L][NL], where
+// state k = lane * L + s sits at s * NL + lane. 32 x 32 tiles through shared
+// memory keep both sides coalesced.
+template <typename T, bool TO_LANES>
+__global__ void lanes_transpose_kernel(const T* src, T* dst, int64_t N, int L, int NL, int64_t cs)
+{
+    __shared__ T tile[32][33];
+    const int c = blockIdx.z;
+    const int l0 = blockIdx.x * 32, s0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    for (int r = ty; r < 32; r += 8) {
+        if (TO_LANES) {
+            // read: for lane l0 + r, steps s0 + tx (contiguous in the caller layout)
+            const int l = l0 + r, s = s0 + tx;
+            const int64_t k = (int64_t)l * L + s;
+            if (l < NL && s < L && k < N) tile[r][tx] = src[(int64_t)c * N + k];
+        } else {
+            // read: for step s0 + r, lanes l0 + tx (contiguous in the lane layout)
+            const int l = l0 + tx, s = s0 + r;
+            const int64_t k = (int64_t)l * L + s;
+            if (l < NL && s < L && k < N) tile[tx][r] = src[(int64_t)c * cs + (int64_t)s * NL + l];
+        }
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        if (TO_LANES) {
+            const int l = l0 + tx, s = s0 + r;
+            const int64_t k = (int64_t)l * L + s;
+            if (l < NL && s < L && k < N) dst[(int64_t)c * cs + (int64_t)s * NL + l] = tile[tx][r];
+        } else {
+            const int l = l0 + r, s = s0 + tx;
+            const int64_t k = (int64_t)l * L + s;
+            if (l < NL && s < L && k < N) dst[(int64_t)c * N + k] = tile[r][tx];
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_lanes_transpose(const T* src, T* dst, int nc, int64_t N, int L, int NL, bool to_lanes,
+                                   cudaStream_t st)
+{
+    const dim3 grid((NL + 31) / 32, (L + 31) / 32, nc), block(32, 8);
+    if (to_lanes) lanes_transpose_kernel<T, true><<<grid, block, 0, st>>>(src, dst, N, L, NL, (int64_t)L * NL);
+    else lanes_transpose_kernel<T, false><<<grid, block, 0, st>>>(src, dst, N, L, NL, (int64_t)L * NL);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_lanes_transpose<float>(const float*, float*, int, int64_t, int, int, bool, cudaStream_t);
+template cudaError_t launch_lanes_transpose<double>(const double*, double*, int, int64_t, int, int, bool, cudaStream_t);
+
+// Prior nominal in the lane-major layout: state k of trajectory b gets (m0_b, P0_b).
+template <typename T>
+__global__ void init_nominal_lanes_kernel(const int64_t* offsets, int B, int64_t N, int L, int NL, const T* m0,
+                                          const T* P0, T* x, T* P)
+{
+    const int64_t cs = (int64_t)L * NL;
+    const int64_t total = cs;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int s = (int)(i / NL), l = (int)(i - (int64_t)s * NL);
+        const int64_t k = (int64_t)l * L + s;
+        if (k >= N) continue;
+        const int b = traj_of(offsets, B, k);
+        if (x)
+#pragma unroll
+            for (int c = 0; c < 5; ++c) x[c * cs + i] = m0[5 * b + c];
+        if (P)
+#pragma unroll
+            for (int c = 0; c < 15; ++c) P[c * cs + i] = P0[15 * b + c];
+    }
+}
+
+template <typename T>
+cudaError_t launch_init_nominal_lanes(const int64_t* offsets, int B, int64_t N, int L, int NL, const T* m0,
+                                      const T* P0, T* x, T* P, cudaStream_t st)
+{
+    const int threads = 256;
+    const int64_t total = (int64_t)L * NL;
+    const int blocks = (int)std::min<int64_t>((total + threads - 1) / threads, 152 * 32);
+    init_nominal_lanes_kernel<T><<<blocks, threads, 0, st>>>(offsets, B, N, L, NL, m0, P0, x, P);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_init_nominal_lanes<float>(const int64_t*, int, int64_t, int, int, const float*,
+                                                      const float*, float*, float*, cudaStream_t);
+template cudaError_t launch_init_nominal_lanes<double>(const int64_t*, int, int64_t, int, int, const double*,
+                                                       const double*, double*, double*, cudaStream_t);
+
+template <typename T>
 __global__ void init_nominal_kernel(const int64_t* offsets, int B, int64_t N, const T* m0, const T* P0, T* x, T* P)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -78,7 +183,7 @@ __global__ void linearize_kernel(const KParams<T> p, T* F, T* c, T* Qp, T* H, T*
         const bool has_obs = k > __ldg(p.offsets + b);
         if (has_next) {
             Trans<T> tr;
-            ok &= get_trans<T, LIN>(p, k, tr);
+            ok &= get_trans<T, LIN>(p, k, k, tr);
             T Fx[5];
             mv(tr.F, tr.xn, Fx);
 #pragma unroll
@@ -97,8 +202,7 @@ __global__ void linearize_kernel(const KParams<T> p, T* F, T* c, T* Qp, T* H, T*
         }
         if (has_obs) {
             Obs<T> ob;
-            Trans<T> unused;
-            ok &= get_obs<T, LIN>(p, k, b, ob, false, unused);
+            ok &= get_obs<T, LIN>(p, k, k, b, ob);
             T y[2];
             load_y(p, k, y);
             // h(xn), the measurement y_used and d = zbar - H xn with zbar = y_used - r_offset
@@ -106,9 +210,9 @@ __global__ void linearize_kernel(const KParams<T> p, T* F, T* c, T* Qp, T* H, T*
             if (p.model.kind == MODEL_LINEAR) {
 #pragma unroll
                 for (int r = 0; r < 2; ++r) {
-                    T v = T(p.model.d[r]);
+                    T v = p.model.d[r];
 #pragma unroll
-                    for (int l = 0; l < 5; ++l) v = fma(T(p.model.H[r * 5 + l]), ob.xn[l], v);
+                    for (int l = 0; l < 5; ++l) v = fma(p.model.H[r * 5 + l], ob.xn[l], v);
                     hx[r] = v;
                 }
             } else {

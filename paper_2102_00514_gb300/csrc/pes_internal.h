@@ -32,6 +32,16 @@ cudaError_t launch_linearize(const KParams<T>& p, int lin, T* F, T* c, T* Qp, T*
 template <typename T>
 cudaError_t launch_init_nominal(const int64_t* offsets, int B, int64_t N, const T* m0, const T* P0, T* x, T* P,
                                 cudaStream_t st);
+// Element-wise double -> T copy (model sensors into the kernel precision).
+template <typename T>
+cudaError_t launch_convert(const double* in, T* out, int n, cudaStream_t st);
+// Caller layout [nc][N] <-> lane-major [nc][L][NL] (state k = lane * L + s).
+template <typename T>
+cudaError_t launch_lanes_transpose(const T* src, T* dst, int nc, int64_t N, int L, int NL, bool to_lanes,
+                                   cudaStream_t st);
+template <typename T>
+cudaError_t launch_init_nominal_lanes(const int64_t* offsets, int B, int64_t N, int L, int NL, const T* m0,
+                                      const T* P0, T* x, T* P, cudaStream_t st);
 cudaError_t launch_validate_offsets(const int64_t* offsets, int B, int64_t N, int* status, cudaStream_t st);
 
 }  // namespace pes

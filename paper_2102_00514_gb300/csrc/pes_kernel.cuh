@@ -34,7 +34,7 @@ enum { MODE_FILTER = 0, MODE_SMOOTH = 1, MODE_RUN = 2 };
 constexpr int FE = sizeof(FElem<double>) / sizeof(double);   // 70
 constexpr int SE = sizeof(SElem<double>) / sizeof(double);   // 50
 constexpr int GE = sizeof(Gauss<double>) / sizeof(double);   // 20
-constexpr int HAND = 20;                                      // handoff scalars per state
+constexpr int HAND = 50;                                      // handoff scalars per state: one SElem
 
 template <typename T>
 struct KParams {
@@ -45,7 +45,7 @@ struct KParams {
     int iters;                // RUN: maximum iterations; otherwise 1
     double tol;               // RUN: relative update-norm tolerance (<= 0: fixed iterations)
     int write_P_every_iter;   // RUN: write smoothed covariances in every iteration
-    DevModel model;
+    DevModel<T> model;
     const T* y;               // [2][N] (slot of each x_0 ignored)
     const T* m0;              // [B][5]
     const T* P0;              // [B][15]
@@ -63,7 +63,7 @@ struct KParams {
     T* x;
     T* P;
     // workspace
-    T* hand;           // MODE_RUN handoff: [(s * HAND + c) * NL + lane]
+    T* hand;           // MODE_RUN handoff of smoothing elements: [warp][s][c][32 lanes]
     T* aggF;           // [NB][FE]
     T* aggS;           // [NB][SE]
     unsigned* bar;     // grid barrier counter, zero at launch
@@ -72,8 +72,20 @@ struct KParams {
     int* iters_done;
     int L;             // steps per lane
     int NL;            // lanes = NB * NT
+    int lanes_layout;  // x, P, y use the kernel's lane-major layout (MODE_RUN)
+    int64_t cs;        // component stride of x, P, y
     long long timeout_ns;
+    long long* ptime;  // optional per-block phase timestamps of the first iteration (NULL: off)
 };
+
+constexpr int NPHASE = 16;
+// Phase timestamps: thread 0 of every block records %globaltimer at the phase
+// boundaries of the first iteration when p.ptime is set.
+#define PES_PHASE(p, it, i)                                                        \
+    do {                                                                           \
+        if ((p).ptime && (it) == 0 && threadIdx.x == 0)                            \
+            (p).ptime[(size_t)blockIdx.x * NPHASE + (i)] = globaltimer_ns();      \
+    } while (0)
 
 // ---- small device utilities ------------------------------------------------
 
@@ -163,32 +175,87 @@ PES_DEV void load_prior(const KParams<T>& p, int b, T* m0, T* P0)
     for (int i = 0; i < 15; ++i) P0[i] = __ldg(p.P0 + 15 * b + i);
 }
 
+// The nominal trajectory is rewritten by every iteration. Reads of it (and of
+// other data written earlier in the same launch) are plain L1-cached loads:
+// every such read follows a grid barrier, whose gpu-scope acquire and fence
+// make the other blocks' writes visible, and consecutive steps of a lane share
+// cache sectors.
 template <typename T>
-PES_DEV void load_nominal(const KParams<T>& p, int64_t k, T* x)
+PES_DEV void load_nominal(const KParams<T>& p, int64_t ix, T* x)
 {
 #pragma unroll
-    for (int i = 0; i < 5; ++i) x[i] = __ldcg(p.x + i * p.N + k);
+    for (int i = 0; i < 5; ++i) x[i] = p.x[i * p.cs + ix];
 }
 
 template <typename T>
-PES_DEV void load_nominal_cov(const KParams<T>& p, int64_t k, T* P)
+PES_DEV void load_nominal_cov(const KParams<T>& p, int64_t ix, T* P)
 {
 #pragma unroll
-    for (int i = 0; i < 15; ++i) P[i] = __ldcg(p.P + i * p.N + k);
+    for (int i = 0; i < 15; ++i) P[i] = p.P[i * p.cs + ix];
 }
 
 template <typename T>
-PES_DEV void load_y(const KParams<T>& p, int64_t k, T* y)
+PES_DEV void load_y(const KParams<T>& p, int64_t ix, T* y)
 {
-    y[0] = __ldg(p.y + k);
-    y[1] = __ldg(p.y + p.N + k);
+    y[0] = __ldg(p.y + ix);
+    y[1] = __ldg(p.y + p.cs + ix);
+}
+
+// Index of state k of the chunk [a, e) of `lane` in the per-state arrays the
+// kernel reads and writes (x, P, y): in MODE_RUN the kernel's lane-major
+// layout [component][step][lane], in which a warp's accesses at one step are
+// contiguous; otherwise the caller's [component][N] layout.
+template <typename T>
+PES_DEV int64_t state_ix(const KParams<T>& p, int64_t k, int64_t a, int lane)
+{
+    return p.lanes_layout ? (k - a) * p.NL + lane : k;
+}
+
+// Index of the state just before the chunk (k = a - 1): the last state of the
+// previous lane's chunk, which is full.
+template <typename T>
+PES_DEV int64_t prev_ix(const KParams<T>& p, int64_t a, int lane)
+{
+    return p.lanes_layout ? (int64_t)(p.L - 1) * p.NL + (lane - 1) : a - 1;
 }
 
 // ---- linearisation of one step ------------------------------------------------
 
-// Transition k -> k+1.
+// Per-state inputs of the linearisation, loaded one step ahead of their use
+// so that the loads overlap the previous step's arithmetic.
 template <typename T, int LIN>
-PES_DEV bool get_trans(const KParams<T>& p, int64_t k, Trans<T>& tr)
+struct StateIn {
+    T x[5];    // nominal mean (IEKS, cubature)
+    T P[15];   // nominal covariance (cubature)
+    T y[2];    // measurement
+};
+
+template <typename T, int LIN>
+PES_DEV void load_state(const KParams<T>& p, int64_t ix, StateIn<T, LIN>& s)
+{
+    if (LIN != LIN_ARRAYS) load_nominal(p, ix, s.x);
+    if (LIN == LIN_CUBATURE) load_nominal_cov(p, ix, s.P);
+    load_y(p, ix, s.y);
+}
+
+// Sigma-point factor of the state's nominal covariance (cubature only).
+template <typename T, int LIN>
+struct Factor {
+    T L[LIN == LIN_CUBATURE ? 25 : 1];
+    T rd[LIN == LIN_CUBATURE ? 5 : 1];
+};
+
+template <typename T, int LIN>
+PES_DEV bool factor_state(const StateIn<T, LIN>& s, Factor<T, LIN>& f)
+{
+    if (LIN == LIN_CUBATURE) return cub_factor(s.P, f.L, f.rd);
+    return true;
+}
+
+// Transition k -> k+1 (Eq. 10 or Eq. 7).
+template <typename T, int LIN>
+PES_DEV void lin_trans(const KParams<T>& p, int64_t k, const StateIn<T, LIN>& s, const Factor<T, LIN>& f,
+                       Trans<T>& tr)
 {
     if (LIN == LIN_ARRAYS) {
 #pragma unroll
@@ -200,62 +267,62 @@ PES_DEV bool get_trans(const KParams<T>& p, int64_t k, Trans<T>& tr)
         }
 #pragma unroll
         for (int i = 0; i < 15; ++i) tr.Q[i] = __ldg(p.Qp + i * p.N + k);
-        return true;
     } else if (LIN == LIN_IEKS) {
-        T xn[5];
-        load_nominal(p, k, xn);
-        lin_trans_taylor(p.model, xn, tr);
-        return true;
+        lin_trans_taylor(p.model, s.x, tr);
     } else {
-        T xn[5], Pn[15], L[25], rd[5];
-        load_nominal(p, k, xn);
-        load_nominal_cov(p, k, Pn);
-        const bool ok = cub_factor(Pn, L, rd);
-        lin_trans_cubature(p.model, xn, L, rd, tr);
-        return ok;
+        lin_trans_cubature(p.model, s.x, f.L, f.rd, tr);
     }
 }
 
-// Observation at k (optionally also the transition k -> k+1, which shares
-// the nominal and, for cubature, the sigma points' factor).
+// Observation at k (Eq. 10 or Eq. 9).
 template <typename T, int LIN>
-PES_DEV bool get_obs(const KParams<T>& p, int64_t k, int b, Obs<T>& ob, bool want_trans, Trans<T>& tr)
+PES_DEV void lin_obs(const KParams<T>& p, int64_t k, int b, const StateIn<T, LIN>& s, const Factor<T, LIN>& f,
+                     Obs<T>& ob)
 {
-    T y[2];
-    load_y(p, k, y);
     if (LIN == LIN_ARRAYS) {
 #pragma unroll
         for (int i = 0; i < 10; ++i) ob.H[i] = __ldg(p.H + i * p.N + k);
-        ob.r[0] = y[0] - __ldg(p.d + k);
-        ob.r[1] = y[1] - __ldg(p.d + p.N + k);
+        ob.r[0] = s.y[0] - __ldg(p.d + k);
+        ob.r[1] = s.y[1] - __ldg(p.d + p.N + k);
 #pragma unroll
         for (int i = 0; i < 5; ++i) ob.xn[i] = T(0);
 #pragma unroll
         for (int i = 0; i < 3; ++i) ob.R[i] = __ldg(p.Rp + i * p.N + k);
-        if (want_trans) get_trans<T, LIN>(p, k, tr);
-        return true;
     } else if (LIN == LIN_IEKS) {
-        T xn[5];
-        load_nominal(p, k, xn);
-        lin_obs_taylor(p.model, b, xn, y, ob);
-        if (want_trans) lin_trans_taylor(p.model, xn, tr);
-        return true;
+        lin_obs_taylor(p.model, b, s.x, s.y, ob);
     } else {
-        T xn[5], Pn[15], L[25], rd[5];
-        load_nominal(p, k, xn);
-        load_nominal_cov(p, k, Pn);
-        const bool ok = cub_factor(Pn, L, rd);
-        lin_obs_cubature(p.model, b, xn, L, rd, y, ob);
-        if (want_trans) lin_trans_cubature(p.model, xn, L, rd, tr);
-        return ok;
+        lin_obs_cubature(p.model, b, s.x, f.L, f.rd, s.y, ob);
     }
+}
+
+// One-shot forms used by the stand-alone linearisation kernel.
+template <typename T, int LIN>
+PES_DEV bool get_trans(const KParams<T>& p, int64_t k, int64_t ix, Trans<T>& tr)
+{
+    StateIn<T, LIN> s;
+    load_state(p, ix, s);
+    Factor<T, LIN> f;
+    const bool ok = factor_state(s, f);
+    lin_trans(p, k, s, f, tr);
+    return ok;
+}
+
+template <typename T, int LIN>
+PES_DEV bool get_obs(const KParams<T>& p, int64_t k, int64_t ix, int b, Obs<T>& ob)
+{
+    StateIn<T, LIN> s;
+    load_state(p, ix, s);
+    Factor<T, LIN> f;
+    const bool ok = factor_state(s, f);
+    lin_obs(p, k, b, s, f, ob);
+    return ok;
 }
 
 // ---- lane-level passes -------------------------------------------------------------
 
 // Filtering, level 1: fold the lane's chunk [a, e) into one element.
 template <typename T, int LIN>
-PES_DEV bool fold_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, FElem<T>& acc)
+PES_DEV bool fold_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int lane, FElem<T>& acc)
 {
     bool ok = true;
     T zero[5] = {T(0), T(0), T(0), T(0), T(0)};
@@ -267,63 +334,111 @@ PES_DEV bool fold_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, FElem<
     cur.init(p.offsets, p.B, a);
     Trans<T> tr;
     if (!cur.is_head(a)) {
-        ok &= get_trans<T, LIN>(p, a - 1, tr);
+        ok &= get_trans<T, LIN>(p, a - 1, prev_ix(p, a, lane), tr);
         felem_identity(acc, tr.xn);
     } else {
         felem_identity(acc, zero);
     }
-    for (int64_t k = a; k < e; ++k) {
+    const int64_t dix = p.lanes_layout ? p.NL : 1;
+    int64_t ix = state_ix(p, a, a, lane);
+    StateIn<T, LIN> sc, sn;
+    load_state(p, ix, sc);
+#pragma unroll 1
+    for (int64_t k = a; k < e; ++k, ix += dix) {
         cur.forward(k);
-        const bool want_trans = (k + 1 < e) && !cur.is_tail(k);
+        if (k + 1 < e) load_state(p, ix + dix, sn);
+        Factor<T, LIN> f;
+        ok &= factor_state(sc, f);
         if (cur.is_head(k)) {
             T m0[5], P0[15];
             load_prior(p, cur.b, m0, P0);
             felem_apply_prior(acc, m0, P0);
-            if (want_trans) ok &= get_trans<T, LIN>(p, k, tr);
         } else {
             Obs<T> ob;
-            Trans<T> trn;
-            ok &= get_obs<T, LIN>(p, k, cur.b, ob, want_trans, trn);
+            lin_obs(p, k, cur.b, sc, f, ob);
             ok &= fold_filter_step(acc, tr, ob);
-            if (want_trans) tr = trn;
         }
+        if (k + 1 < e && !cur.is_tail(k)) lin_trans(p, k, sc, f, tr);
+        sc = sn;
     }
     return ok;
 }
 
+// Filtered moments in the caller's arrays (MODE_FILTER output, MODE_SMOOTH input).
 template <typename T>
-PES_DEV void store_filtered(const KParams<T>& p, int64_t k, int s, int lane, const T* m, const T* P)
+PES_DEV void store_filtered(const KParams<T>& p, int64_t k, const T* m, const T* P)
 {
-    if (p.mode == MODE_RUN) {
-        T* h = p.hand + (size_t)s * HAND * p.NL + lane;
 #pragma unroll
-        for (int i = 0; i < 5; ++i) h[(size_t)i * p.NL] = m[i];
+    for (int i = 0; i < 5; ++i) p.xf[i * p.N + k] = m[i];
 #pragma unroll
-        for (int i = 0; i < 15; ++i) h[(size_t)(5 + i) * p.NL] = P[i];
-    } else {
-#pragma unroll
-        for (int i = 0; i < 5; ++i) p.xf[i * p.N + k] = m[i];
-#pragma unroll
-        for (int i = 0; i < 15; ++i) p.Pf[i * p.N + k] = P[i];
-    }
+    for (int i = 0; i < 15; ++i) p.Pf[i * p.N + k] = P[i];
 }
 
 template <typename T>
-PES_DEV void load_filtered(const KParams<T>& p, int64_t k, int s, int lane, T* m, T* P)
+PES_DEV void load_filtered(const KParams<T>& p, int64_t k, T* m, T* P)
 {
-    if (p.mode == MODE_RUN) {
-        const T* h = p.hand + (size_t)s * HAND * p.NL + lane;
 #pragma unroll
-        for (int i = 0; i < 5; ++i) m[i] = h[(size_t)i * p.NL];
+    for (int i = 0; i < 5; ++i) m[i] = __ldg(p.xf + i * p.N + k);
 #pragma unroll
-        for (int i = 0; i < 15; ++i) P[i] = h[(size_t)(5 + i) * p.NL];
-    } else {
-#pragma unroll
-        for (int i = 0; i < 5; ++i) m[i] = __ldg(p.xf + i * p.N + k);
-#pragma unroll
-        for (int i = 0; i < 15; ++i) P[i] = __ldg(p.Pf + i * p.N + k);
-    }
+    for (int i = 0; i < 15; ++i) P[i] = __ldg(p.Pf + i * p.N + k);
 }
+
+// MODE_RUN: the smoothing element of state a + s of a lane, kept between the
+// filtering re-run that builds it and the RTS pass that applies it. Layout
+// [warp][s][component][32 lanes]: a warp's accesses for one step are one
+// contiguous, coalesced run, and its consecutive steps are adjacent.
+template <typename T>
+PES_DEV T* selem_slot(const KParams<T>& p, int s, int lane)
+{
+    return p.hand + ((size_t)(lane >> 5) * p.L + s) * (HAND * 32) + (lane & 31);
+}
+
+template <typename T>
+PES_DEV void store_selem(const KParams<T>& p, int s, int lane, const SElem<T>& el)
+{
+    T* h = selem_slot(p, s, lane);
+    const T* src = reinterpret_cast<const T*>(&el);
+#pragma unroll
+    for (int i = 0; i < HAND; ++i) h[i * 32] = src[i];
+}
+
+template <typename T>
+PES_DEV void load_selem(const KParams<T>& p, int s, int lane, SElem<T>& el)
+{
+    const T* h = selem_slot(p, s, lane);
+    T* dst = reinterpret_cast<T*>(&el);
+#pragma unroll
+    for (int i = 0; i < HAND; ++i) dst[i] = h[i * 32];
+}
+
+// MODE_RUN handoff alternative: the filtered moments (x*, P*) of state a + s,
+// from which the RTS pass rebuilds the smoothing element (same slot layout).
+template <typename T>
+PES_DEV void store_xP(const KParams<T>& p, int s, int lane, const T* m, const T* P)
+{
+    T* h = selem_slot(p, s, lane);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) h[i * 32] = m[i];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) h[(5 + i) * 32] = P[i];
+}
+
+template <typename T>
+PES_DEV void load_xP(const KParams<T>& p, int s, int lane, T* m, T* P)
+{
+    const T* h = selem_slot(p, s, lane);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) m[i] = h[i * 32];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) P[i] = h[(5 + i) * 32];
+}
+
+// Whether the filtering re-run hands the RTS pass finished smoothing elements
+// (50 scalars per state) or the filtered moments (20 scalars per state) from
+// which the RTS pass rebuilds them. Rebuilding costs a transition
+// linearisation, which is cheap for Taylor (IEKS) and dear for cubature.
+template <int LIN>
+constexpr bool kStoreElements = (LIN == LIN_CUBATURE);
 
 // Filtering, level 5: re-run the chunk from the Gaussian of the state before it,
 // storing filtered moments; in MODE_RUN also build and fold the chunk's
@@ -344,33 +459,45 @@ PES_DEV bool rerun_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int l
 #pragma unroll
     for (int i = 0; i < 15; ++i) P[i] = G.P[i];
     Trans<T> tr;
-    if (!cur.is_head(a)) ok &= get_trans<T, LIN>(p, a - 1, tr);
-    for (int64_t k = a; k < e; ++k) {
+    if (!cur.is_head(a)) ok &= get_trans<T, LIN>(p, a - 1, prev_ix(p, a, lane), tr);
+    const int64_t dix = p.lanes_layout ? p.NL : 1;
+    int64_t ix = state_ix(p, a, a, lane);
+    StateIn<T, LIN> sc, sn;
+    load_state(p, ix, sc);
+#pragma unroll 1
+    for (int64_t k = a; k < e; ++k, ix += dix) {
         cur.forward(k);
-        const bool want_trans = !cur.is_tail(k) && (k + 1 < p.N);
+        if (k + 1 < e) load_state(p, ix + dix, sn);
+        Factor<T, LIN> f;
+        ok &= factor_state(sc, f);
         if (cur.is_head(k)) {
             if (smooth && k > a) {
                 SElem<T> el;
                 selem_last(el, m, P);
                 combine_smoother(accS, el, accS);
+                if (kStoreElements<LIN>) store_selem(p, (int)(k - 1 - a), lane, el);
             }
             load_prior(p, cur.b, m, P);
-            if (want_trans) ok &= get_trans<T, LIN>(p, k, tr);
         } else {
-            T mp[5], FP[25], Pp[15];
-            predict(tr, m, P, mp, FP, Pp);
-            if (smooth && k > a) {
-                SElem<T> el;
-                ok &= selem_from_prediction(m, P, FP, Pp, mp, el);
-                combine_smoother(accS, el, accS);
+            T mp[5], Pp[15];
+            {
+                T FP[25];
+                predict(tr, m, P, mp, FP, Pp);
+                if (smooth && k > a) {
+                    SElem<T> el;
+                    ok &= selem_from_prediction(m, P, FP, Pp, mp, el);
+                    combine_smoother(accS, el, accS);
+                    if (kStoreElements<LIN>) store_selem(p, (int)(k - 1 - a), lane, el);
+                }
             }
             Obs<T> ob;
-            Trans<T> trn;
-            ok &= get_obs<T, LIN>(p, k, cur.b, ob, want_trans, trn);
+            lin_obs(p, k, cur.b, sc, f, ob);
             ok &= kf_update(ob, mp, Pp, m, P);
-            if (want_trans) tr = trn;
         }
-        store_filtered(p, k, (int)(k - a), lane, m, P);
+        if (!smooth) store_filtered(p, k, m, P);
+        else if (!kStoreElements<LIN>) store_xP(p, (int)(k - a), lane, m, P);
+        if (!cur.is_tail(k) && (k + 1 < e || smooth)) lin_trans(p, k, sc, f, tr);
+        sc = sn;
     }
     if (smooth) {
         // smoothing element of the chunk's last state
@@ -383,6 +510,7 @@ PES_DEV bool rerun_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int l
             ok &= selem_from_prediction(m, P, FP, Pp, mp, el);
         }
         combine_smoother(accS, el, accS);
+        if (kStoreElements<LIN>) store_selem(p, (int)(e - 1 - a), lane, el);
     }
     return ok;
 }
@@ -397,16 +525,17 @@ PES_DEV bool fold_smoother_chunk(const KParams<T>& p, int64_t a, int64_t e, int 
     if (a >= e) return ok;
     SegCursor cur;
     cur.init(p.offsets, p.B, a);
+#pragma unroll 1
     for (int64_t k = a; k < e; ++k) {
         cur.forward(k);
         T m[5], P[15];
-        load_filtered(p, k, (int)(k - a), lane, m, P);
+        load_filtered(p, k, m, P);
         SElem<T> el;
         if (cur.is_tail(k)) {
             selem_last(el, m, P);
         } else {
             Trans<T> tr;
-            ok &= get_trans<T, LIN>(p, k, tr);
+            ok &= get_trans<T, LIN>(p, k, k, tr);
             T mp[5], FP[25], Pp[15];
             predict(tr, m, P, mp, FP, Pp);
             ok &= selem_from_prediction(m, P, FP, Pp, mp, el);
@@ -418,8 +547,9 @@ PES_DEV bool fold_smoother_chunk(const KParams<T>& p, int64_t a, int64_t e, int 
 
 // Smoothing, level 5: Rauch-Tung-Striebel re-run backwards from the Gaussian of
 // the state after the chunk: x_k ~ E_k (x_{k+1} - xr_k) + g_k with covariance
-// E P E^T + L. Writes the smoothed moments; in MODE_RUN they replace the
-// nominal in place (each state's nominal is read before it is overwritten).
+// E P E^T + L (a last state has E = 0). In MODE_RUN the elements were stored by
+// the filtering re-run and the smoothed moments replace the nominal in place;
+// in MODE_SMOOTH the elements are rebuilt from the given filtered moments.
 template <typename T, int LIN>
 PES_DEV bool rts_chunk(const KParams<T>& p, int64_t a, int64_t e, int lane, const Gauss<T>& G, bool write_P,
                        bool want_norm, double* conv, int& nb, double& num, double& den)
@@ -429,40 +559,42 @@ PES_DEV bool rts_chunk(const KParams<T>& p, int64_t a, int64_t e, int lane, cons
     SegCursor cur;
     cur.init(p.offsets, p.B, e - 1);
     Gauss<T> s = G;
+    const bool stored = (p.mode == MODE_RUN) && kStoreElements<LIN>;
+    SElem<T> ec, en;
+    if (stored) load_selem(p, (int)(e - 1 - a), lane, ec);
+#pragma unroll 1
     for (int64_t k = e - 1; k >= a; --k) {
         cur.backward(k);
-        T m[5], P[15];
-        load_filtered(p, k, (int)(k - a), lane, m, P);
-        T xold[5];
-        if (cur.is_tail(k)) {
-#pragma unroll
-            for (int i = 0; i < 5; ++i) s.m[i] = m[i];
-#pragma unroll
-            for (int i = 0; i < 15; ++i) s.P[i] = P[i];
-            if (want_norm) load_nominal(p, k, xold);
+        if (stored) {
+            if (k > a) load_selem(p, (int)(k - 1 - a), lane, en);
         } else {
-            Trans<T> tr;
-            ok &= get_trans<T, LIN>(p, k, tr);
-            if (want_norm) {
-#pragma unroll
-                for (int i = 0; i < 5; ++i) xold[i] = tr.xn[i];
+            T m[5], P[15];
+            if (p.mode == MODE_RUN) load_xP(p, (int)(k - a), lane, m, P);
+            else load_filtered(p, k, m, P);
+            if (cur.is_tail(k)) {
+                selem_last(ec, m, P);
+            } else {
+                Trans<T> tr;
+                ok &= get_trans<T, LIN>(p, k, state_ix(p, k, a, lane), tr);
+                T mp[5], FP[25], Pp[15];
+                predict(tr, m, P, mp, FP, Pp);
+                ok &= selem_from_prediction(m, P, FP, Pp, mp, ec);
             }
-            T mp[5], FP[25], Pp[15];
-            predict(tr, m, P, mp, FP, Pp);
-            SElem<T> el;
-            ok &= selem_from_prediction(m, P, FP, Pp, mp, el);
-            apply_smoother(el, s, s);
         }
+        apply_smoother(ec, s, s);
+        const int64_t ix = state_ix(p, k, a, lane);
+        T xold[5];
+        if (want_norm) load_nominal(p, ix, xold);
         bool finite = true;
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
             finite = finite && isfinite(s.m[i]);
-            p.x[i * p.N + k] = s.m[i];
+            p.x[i * p.cs + ix] = s.m[i];
         }
         if (!finite) atomicOr(p.status, ST_NONFINITE);
         if (write_P) {
 #pragma unroll
-            for (int i = 0; i < 15; ++i) p.P[i * p.N + k] = s.P[i];
+            for (int i = 0; i < 15; ++i) p.P[i * p.cs + ix] = s.P[i];
         }
         if (want_norm) {
             if (cur.b != nb) {
@@ -481,6 +613,7 @@ PES_DEV bool rts_chunk(const KParams<T>& p, int64_t a, int64_t e, int lane, cons
                 den += double(s.m[i]) * double(s.m[i]);
             }
         }
+        if (stored) ec = en;
     }
     return ok;
 }
@@ -497,17 +630,20 @@ PES_DEV void copy_elem_to_global(const T* src, T* dst)
 // the Gaussian of the state before lane t's chunk.
 template <typename T, int NT>
 PES_DEV void filter_block_scan(const KParams<T>& p, FElem<T>* elem, FElem<T>* top, Gauss<T>* gs,
-                               Gauss<T>* gblock, unsigned& gen, Gauss<T>& out)
+                               Gauss<T>* gblock, unsigned& gen, Gauss<T>& out, int it)
 {
     const int t = threadIdx.x;
     __syncthreads();
+    PES_PHASE(p, it, 1);
 #pragma unroll 1
     for (int s = 1; s < NT; s <<= 1) {
         if (((t + 1) & (2 * s - 1)) == 0) combine_filter(elem[t - s], elem[t], elem[t]);
         __syncthreads();
     }
     copy_elem_to_global<T, FE>(reinterpret_cast<const T*>(&elem[NT - 1]), p.aggF + (size_t)blockIdx.x * FE);
+    PES_PHASE(p, it, 2);
     grid_barrier(p, gen);
+    PES_PHASE(p, it, 3);
     // level 3: Gaussian of the state before this block = product of blocks [0, blockIdx)
     if (t == 0) {
 #pragma unroll
@@ -521,7 +657,7 @@ PES_DEV void filter_block_scan(const KParams<T>& p, FElem<T>* elem, FElem<T>* to
         const int n = min(NT, j - c0);
         __syncthreads();
         for (int i = t; i < n * FE; i += NT)
-            reinterpret_cast<T*>(top)[i] = __ldcg(p.aggF + (size_t)c0 * FE + i);
+            reinterpret_cast<T*>(top)[i] = p.aggF[(size_t)c0 * FE + i];
         __syncthreads();
 #pragma unroll 1
         for (int s = 1; s < n; s <<= 1) {
@@ -531,6 +667,7 @@ PES_DEV void filter_block_scan(const KParams<T>& p, FElem<T>* elem, FElem<T>* to
         if (t == 0) apply_filter(*gblock, top[0], *gblock);
     }
     __syncthreads();
+    PES_PHASE(p, it, 4);
     // level 4: down-sweep
     if (t == NT - 1) gs[NT - 1] = *gblock;
     __syncthreads();
@@ -547,23 +684,27 @@ PES_DEV void filter_block_scan(const KParams<T>& p, FElem<T>* elem, FElem<T>* to
     }
     out = gs[t];
     __syncthreads();
+    PES_PHASE(p, it, 5);
 }
 
 // Smoothing levels 2-4 (mirrored: subtrees accumulate at their left end).
 // Returns the Gaussian of the state after lane t's chunk.
 template <typename T, int NT>
 PES_DEV void smoother_block_scan(const KParams<T>& p, SElem<T>* elem, SElem<T>* top, Gauss<T>* gs,
-                                 Gauss<T>* gblock, unsigned& gen, Gauss<T>& out)
+                                 Gauss<T>* gblock, unsigned& gen, Gauss<T>& out, int it)
 {
     const int t = threadIdx.x;
     __syncthreads();
+    PES_PHASE(p, it, 7);
 #pragma unroll 1
     for (int s = 1; s < NT; s <<= 1) {
         if ((t & (2 * s - 1)) == 0) combine_smoother(elem[t], elem[t + s], elem[t]);
         __syncthreads();
     }
     copy_elem_to_global<T, SE>(reinterpret_cast<const T*>(&elem[0]), p.aggS + (size_t)blockIdx.x * SE);
+    PES_PHASE(p, it, 8);
     grid_barrier(p, gen);
+    PES_PHASE(p, it, 9);
     if (t == 0) {
 #pragma unroll
         for (int i = 0; i < 5; ++i) gblock->m[i] = T(0);
@@ -578,7 +719,7 @@ PES_DEV void smoother_block_scan(const KParams<T>& p, SElem<T>* elem, SElem<T>* 
         const int c0 = c1 - n;
         __syncthreads();
         for (int i = t; i < n * SE; i += NT)
-            reinterpret_cast<T*>(top)[i] = __ldcg(p.aggS + (size_t)c0 * SE + i);
+            reinterpret_cast<T*>(top)[i] = p.aggS[(size_t)c0 * SE + i];
         __syncthreads();
 #pragma unroll 1
         for (int s = 1; s < n; s <<= 1) {
@@ -589,6 +730,7 @@ PES_DEV void smoother_block_scan(const KParams<T>& p, SElem<T>* elem, SElem<T>* 
         c1 = c0;
     }
     __syncthreads();
+    PES_PHASE(p, it, 10);
     if (t == 0) gs[0] = *gblock;
     __syncthreads();
 #pragma unroll 1
@@ -604,6 +746,7 @@ PES_DEV void smoother_block_scan(const KParams<T>& p, SElem<T>* elem, SElem<T>* 
     }
     out = gs[t];
     __syncthreads();
+    PES_PHASE(p, it, 11);
 }
 
 template <int NT>
@@ -645,13 +788,15 @@ __global__ void __launch_bounds__(NT, 1) pes_persistent_kernel(const KParams<T> 
         if (*(volatile int*)p.status & (ST_TIMEOUT | ST_BADARG)) break;
         const bool last = (it == p.iters - 1);
         SElem<T> accS;
+        PES_PHASE(p, it, 0);
         if (do_filter) {
             FElem<T> acc;
-            ok &= fold_filter_chunk<T, LIN>(p, a, e, acc);
+            ok &= fold_filter_chunk<T, LIN>(p, a, e, lane, acc);
             elemF[t] = acc;
             Gauss<T> G;
-            filter_block_scan<T, NT>(p, elemF, topF, gs, gblock, gen, G);
+            filter_block_scan<T, NT>(p, elemF, topF, gs, gblock, gen, G, it);
             ok &= rerun_filter_chunk<T, LIN>(p, a, e, lane, G, accS);
+            PES_PHASE(p, it, 6);
             if (track && blockIdx.x == 0) {
                 // the accumulators of the next iteration were last read before
                 // this iteration's first barrier; clear them for reuse
@@ -664,12 +809,14 @@ __global__ void __launch_bounds__(NT, 1) pes_persistent_kernel(const KParams<T> 
         if (do_smooth) {
             elemS[t] = accS;
             Gauss<T> Gs;
-            smoother_block_scan<T, NT>(p, elemS, topS, gs, gblock, gen, Gs);
+            smoother_block_scan<T, NT>(p, elemS, topS, gs, gblock, gen, Gs, it);
             const bool write_P = (p.mode != MODE_RUN) || (LIN == LIN_CUBATURE) || last || p.write_P_every_iter;
             int nb = -1;
             double num = 0.0, den = 0.0;
             double* conv = p.conv + (size_t)(it & 1) * 2 * p.B;
             ok &= rts_chunk<T, LIN>(p, a, e, lane, Gs, write_P, track, conv, nb, num, den);
+            __syncthreads();
+            PES_PHASE(p, it, 12);
             if (track && nb >= 0) {
                 atomicAdd(conv + 2 * nb, num);
                 atomicAdd(conv + 2 * nb + 1, den);
@@ -677,6 +824,7 @@ __global__ void __launch_bounds__(NT, 1) pes_persistent_kernel(const KParams<T> 
         }
         if (p.mode == MODE_RUN && (!last || track)) {
             grid_barrier(p, gen);
+            PES_PHASE(p, it, 13);
             if (track) {
                 // worst relative update norm over trajectories, identical in every block
                 const double* conv = p.conv + (size_t)(it & 1) * 2 * p.B;

@@ -19,15 +19,17 @@ enum { MODEL_CT_BEARINGS = 0, MODEL_LINEAR = 1 };
 enum { LIN_ARRAYS = 0, LIN_IEKS = 1, LIN_CUBATURE = 2 };
 enum { ST_NOT_PD = 1, ST_NONFINITE = 2, ST_TIMEOUT = 4, ST_NOT_CONVERGED = 8, ST_BADARG = 16 };
 
-// Model parameters as passed to the kernels. Q and R are packed (upper).
+// Model parameters as passed to the kernels, already in the kernel's
+// precision (no conversions on the device). Q and R are packed (upper).
+template <typename T>
 struct DevModel {
     int kind;
     int sensors_per_traj;
-    double dt;
-    const double* sensors;   // device, [1 or B][4]
-    double Q[15];
-    double R[3];
-    double F[25], c[5], H[10], d[2];   // linear model
+    T dt;
+    const T* sensors;   // device, [1 or B][4]
+    T Q[15];
+    T R[3];
+    T F[25], c[5], H[10], d[2];   // linear model
 };
 
 // Transition k -> k+1 linearised about xn = xbar_k: x_{k+1} ~ fx + F (x_k - xn) + N(0, Q')
@@ -136,11 +138,11 @@ PES_DEV void ct_jacobian(const T* x, const CTCoef<T>& k, T dt, T* F)
 }
 
 template <typename T>
-PES_DEV void load_sensors(const DevModel& m, int b, T* s)
+PES_DEV void load_sensors(const DevModel<T>& m, int b, T* s)
 {
-    const double* p = m.sensors + (m.sensors_per_traj ? 4 * b : 0);
+    const T* p = m.sensors + (m.sensors_per_traj ? 4 * b : 0);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) s[i] = T(__ldg(p + i));
+    for (int i = 0; i < 4; ++i) s[i] = __ldg(p + i);
 }
 
 template <typename T>
@@ -167,21 +169,21 @@ PES_DEV void bearings_jacobian(const T* x, const T* s, T* H)
 // ---- Taylor linearisation (IEKS, Eq. 10) ---------------------------------------
 
 template <typename T>
-PES_DEV void lin_trans_taylor(const DevModel& m, const T* xn, Trans<T>& tr)
+PES_DEV void lin_trans_taylor(const DevModel<T>& m, const T* xn, Trans<T>& tr)
 {
 #pragma unroll
     for (int i = 0; i < 5; ++i) tr.xn[i] = xn[i];
 #pragma unroll
-    for (int i = 0; i < 15; ++i) tr.Q[i] = T(m.Q[i]);
+    for (int i = 0; i < 15; ++i) tr.Q[i] = m.Q[i];
     if (m.kind == MODEL_LINEAR) {
 #pragma unroll
-        for (int i = 0; i < 25; ++i) tr.F[i] = T(m.F[i]);
+        for (int i = 0; i < 25; ++i) tr.F[i] = m.F[i];
         T Fx[5];
         mv(tr.F, xn, Fx);
 #pragma unroll
-        for (int i = 0; i < 5; ++i) tr.fx[i] = Fx[i] + T(m.c[i]);
+        for (int i = 0; i < 5; ++i) tr.fx[i] = Fx[i] + m.c[i];
     } else {
-        const T dt = T(m.dt);
+        const T dt = m.dt;
         const CTCoef<T> k = ct_coef(xn[4], dt);
         ct_jacobian(xn, k, dt, tr.F);
         T inc[5];
@@ -195,18 +197,18 @@ PES_DEV void lin_trans_taylor(const DevModel& m, const T* xn, Trans<T>& tr)
 }
 
 template <typename T>
-PES_DEV void lin_obs_taylor(const DevModel& m, int b, const T* xn, const T* y, Obs<T>& ob)
+PES_DEV void lin_obs_taylor(const DevModel<T>& m, int b, const T* xn, const T* y, Obs<T>& ob)
 {
 #pragma unroll
     for (int i = 0; i < 5; ++i) ob.xn[i] = xn[i];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) ob.R[i] = T(m.R[i]);
+    for (int i = 0; i < 3; ++i) ob.R[i] = m.R[i];
     if (m.kind == MODEL_LINEAR) {
 #pragma unroll
-        for (int i = 0; i < 10; ++i) ob.H[i] = T(m.H[i]);
+        for (int i = 0; i < 10; ++i) ob.H[i] = m.H[i];
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
-            T hx = T(m.d[r]);
+            T hx = m.d[r];
 #pragma unroll
             for (int l = 0; l < 5; ++l) hx = fma(ob.H[r * 5 + l], xn[l], hx);
             ob.r[r] = y[r] - hx;
@@ -233,21 +235,21 @@ PES_DEV void lin_obs_taylor(const DevModel& m, int b, const T* xn, const T* y, O
 
 // Deviation of the transition: f(xbar + sg) - f(xbar).
 template <typename T>
-PES_DEV void dev_f(const DevModel& m, const T* xbar, const T* inc_ref, const T* sg, T* out)
+PES_DEV void dev_f(const DevModel<T>& m, const T* xbar, const T* inc_ref, const T* sg, T* out)
 {
     if (m.kind == MODEL_LINEAR) {
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
             T s = T(0);
 #pragma unroll
-            for (int l = 0; l < 5; ++l) s = fma(T(m.F[i * 5 + l]), sg[l], s);
+            for (int l = 0; l < 5; ++l) s = fma(m.F[i * 5 + l], sg[l], s);
             out[i] = s;
         }
     } else {
         T x[5];
 #pragma unroll
         for (int i = 0; i < 5; ++i) x[i] = xbar[i] + sg[i];
-        const CTCoef<T> k = ct_coef(x[4], T(m.dt));
+        const CTCoef<T> k = ct_coef(x[4], m.dt);
         T inc[5];
         ct_increment(x, k, inc);
         out[0] = sg[0] + (inc[0] - inc_ref[0]);
@@ -260,14 +262,14 @@ PES_DEV void dev_f(const DevModel& m, const T* xbar, const T* inc_ref, const T* 
 
 // Deviation of the observation: h(xbar + sg) - h(xbar), bearings wrapped.
 template <typename T>
-PES_DEV void dev_h(const DevModel& m, const T* xbar, const T* s, const T* h_ref, const T* sg, T* out)
+PES_DEV void dev_h(const DevModel<T>& m, const T* xbar, const T* s, const T* h_ref, const T* sg, T* out)
 {
     if (m.kind == MODEL_LINEAR) {
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             T v = T(0);
 #pragma unroll
-            for (int l = 0; l < 5; ++l) v = fma(T(m.H[r * 5 + l]), sg[l], v);
+            for (int l = 0; l < 5; ++l) v = fma(m.H[r * 5 + l], sg[l], v);
             out[r] = v;
         }
     } else {
@@ -304,7 +306,7 @@ PES_DEV bool cub_factor(const T* Pbar, T* L, T* rdiag)
 }
 
 template <typename T>
-PES_DEV void lin_trans_cubature(const DevModel& m, const T* xbar, const T* L, const T* rdiag, Trans<T>& tr)
+PES_DEV void lin_trans_cubature(const DevModel<T>& m, const T* xbar, const T* L, const T* rdiag, Trans<T>& tr)
 {
     const T sq = tsqrt(T(NX));
     T inc_ref[5];
@@ -312,7 +314,7 @@ PES_DEV void lin_trans_cubature(const DevModel& m, const T* xbar, const T* L, co
 #pragma unroll
         for (int i = 0; i < 5; ++i) inc_ref[i] = T(0);
     } else {
-        const CTCoef<T> k = ct_coef(xbar[4], T(m.dt));
+        const CTCoef<T> k = ct_coef(xbar[4], m.dt);
         ct_increment(xbar, k, inc_ref);
     }
     T Dm[25];       // columns D_i (row-major: Dm[r*5 + i])
@@ -354,17 +356,17 @@ PES_DEV void lin_trans_cubature(const DevModel& m, const T* xbar, const T* L, co
             T s = T(0);
 #pragma unroll
             for (int i = 0; i < NX; ++i) s = fma(U[r * NX + i], U[q * NX + i], s);
-            tr.Q[si(r, q)] = T(m.Q[si(r, q)]) + s * (T(1) / T(NX));
+            tr.Q[si(r, q)] = m.Q[si(r, q)] + s * (T(1) / T(NX));
         }
     // fx = zbar = f(xbar) + zdev
     if (m.kind == MODEL_LINEAR) {
         T Fx[5];
         T Fm[25];
 #pragma unroll
-        for (int i = 0; i < 25; ++i) Fm[i] = T(m.F[i]);
+        for (int i = 0; i < 25; ++i) Fm[i] = m.F[i];
         mv(Fm, xbar, Fx);
 #pragma unroll
-        for (int r = 0; r < 5; ++r) tr.fx[r] = Fx[r] + T(m.c[r]) + zdev[r];
+        for (int r = 0; r < 5; ++r) tr.fx[r] = Fx[r] + m.c[r] + zdev[r];
     } else {
         tr.fx[0] = xbar[0] + inc_ref[0] + zdev[0];
         tr.fx[1] = xbar[1] + inc_ref[1] + zdev[1];
@@ -377,7 +379,7 @@ PES_DEV void lin_trans_cubature(const DevModel& m, const T* xbar, const T* L, co
 }
 
 template <typename T>
-PES_DEV void lin_obs_cubature(const DevModel& m, int b, const T* xbar, const T* L, const T* rdiag, const T* y,
+PES_DEV void lin_obs_cubature(const DevModel<T>& m, int b, const T* xbar, const T* L, const T* rdiag, const T* y,
                               Obs<T>& ob)
 {
     const T sq = tsqrt(T(NX));
@@ -386,9 +388,9 @@ PES_DEV void lin_obs_cubature(const DevModel& m, int b, const T* xbar, const T* 
     if (m.kind == MODEL_LINEAR) {
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
-            T v = T(m.d[r]);
+            T v = m.d[r];
 #pragma unroll
-            for (int l = 0; l < 5; ++l) v = fma(T(m.H[r * 5 + l]), xbar[l], v);
+            for (int l = 0; l < 5; ++l) v = fma(m.H[r * 5 + l], xbar[l], v);
             h_ref[r] = v;
         }
     } else {
@@ -431,7 +433,7 @@ PES_DEV void lin_obs_cubature(const DevModel& m, int b, const T* xbar, const T* 
             T v = T(0);
 #pragma unroll
             for (int i = 0; i < NX; ++i) v = fma(U[r * NX + i], U[q * NX + i], v);
-            ob.R[si2(r, q)] = T(m.R[si2(r, q)]) + v * (T(1) / T(NX));
+            ob.R[si2(r, q)] = m.R[si2(r, q)] + v * (T(1) / T(NX));
         }
     // residual about zbar = h(xbar) + zdev, measurement unwrapped nearest h(xbar)
     if (m.kind == MODEL_LINEAR) {

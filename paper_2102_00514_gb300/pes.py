@@ -28,7 +28,8 @@ FP64, FP32, MIXED = 0, 1, 2
 MODEL_CT_BEARINGS, MODEL_LINEAR = 0, 1
 
 EXPORTED = ["pes_create", "pes_destroy", "pes_last_error", "pes_sync", "pes_linearize", "pes_filter_scan",
-            "pes_smooth_scan", "pes_ieks_run", "pes_ieks_run_host", "pes_launch_shape", "pes_measure_fma_peak"]
+            "pes_smooth_scan", "pes_ieks_run", "pes_ieks_run_host", "pes_launch_shape", "pes_measure_fma_peak",
+            "pes_debug_phase_times"]
 
 
 class PesError(RuntimeError):
@@ -74,6 +75,7 @@ def load_library():
     lib.pes_launch_shape.argtypes = [p, i32, i32, i64, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                      ctypes.POINTER(i32)]
     lib.pes_measure_fma_peak.argtypes = [ctypes.POINTER(d), ctypes.POINTER(d)]
+    lib.pes_debug_phase_times.argtypes = [p, ctypes.POINTER(d), ctypes.POINTER(d), i32]
     for name in EXPORTED:
         if name != "pes_last_error":
             getattr(lib, name).restype = ctypes.c_int
@@ -199,6 +201,18 @@ class Smoother:
 
     def sync(self, stream=None):
         return self._check(self.lib.pes_sync(self.h, _stream(stream)))
+
+    PHASES = ["fold", "filter up-sweep", "barrier", "filter top level", "filter down-sweep", "filter re-run",
+              "smoother up-sweep", "barrier", "smoother top level", "smoother down-sweep", "RTS re-run", "-",
+              "end barrier"]
+
+    def phase_times(self):
+        """Per-phase (mean, max) ns of the first iteration of the last launch
+        (needs PES_PHASE_TIMES=1 in the environment before the handle is made)."""
+        n = len(self.PHASES)
+        mean, mx = (ctypes.c_double * n)(), (ctypes.c_double * n)()
+        self._check(self.lib.pes_debug_phase_times(self.h, mean, mx, n))
+        return {name: (mean[i], mx[i]) for i, name in enumerate(self.PHASES) if name != "-"}
 
     def launch_shape(self, method: int, prec: int, N: int):
         nb, nt, L = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
