@@ -38,6 +38,7 @@ struct pes_handle {
     double* hsens = nullptr;
     void* sensT = nullptr;   // sensors converted to the kernel precision
     void* lanes = nullptr;   // x, P, y in the kernel's lane-major layout
+    void* lin = nullptr;     // cubature linearisation handed from the fold to the re-run
     long long* ptime = nullptr;   // phase timestamps (PES_PHASE_TIMES=1)
     int ptime_blocks = 0;
     long long timeout_ns = 2000000000LL;
@@ -180,6 +181,7 @@ template <typename T>
 void fill_workspace(pes_handle* h, KParams<T>& p, const Shape& s)
 {
     p.hand = static_cast<T*>(h->hand);
+    p.lin = static_cast<T*>(h->lin);
     p.aggF = static_cast<T*>(h->aggF);
     p.aggS = static_cast<T*>(h->aggS);
     p.bar = h->bar;
@@ -345,6 +347,7 @@ pes_status pes_create(pes_handle** out, int64_t max_states, int32_t max_batch)
     const size_t hand_elems = (size_t)HAND * ((size_t)max_states + (size_t)h->nl_max);
     e = cudaMalloc(&h->hand, hand_elems * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&h->lanes, (size_t)22 * ((size_t)max_states + (size_t)h->nl_max) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->lin, (size_t)LINS * ((size_t)max_states + (size_t)h->nl_max) * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&h->aggF, (size_t)h->nb_max * FE * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&h->aggS, (size_t)h->nb_max * SE * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->bar, sizeof(unsigned));
@@ -369,7 +372,7 @@ pes_status pes_destroy(pes_handle* h)
 {
     if (!h) return PES_ERR_INVALID_ARG;
     cudaDeviceSynchronize();
-    void* ptrs[] = {h->hand, h->lanes, h->aggF, h->aggS, h->bar, h->status, h->conv, h->iters_done, h->sensT, h->ptime,
+    void* ptrs[] = {h->hand, h->lanes, h->lin, h->aggF, h->aggS, h->bar, h->status, h->conv, h->iters_done, h->sensT, h->ptime,
                     h->hy, h->hoff, h->hm0, h->hP0, h->hx, h->hP, h->hxi, h->hPi, h->hsens};
     for (void* p : ptrs)
         if (p) cudaFree(p);

@@ -25,7 +25,7 @@
 // they set ST_TIMEOUT and return, so the kernel always terminates.
 #pragma once
 
-#include "pes_ops.cuh"
+#include "pes_team.cuh"
 
 namespace pes {
 
@@ -35,6 +35,7 @@ constexpr int FE = sizeof(FElem<double>) / sizeof(double);   // 70
 constexpr int SE = sizeof(SElem<double>) / sizeof(double);   // 50
 constexpr int GE = sizeof(Gauss<double>) / sizeof(double);   // 20
 constexpr int HAND = 50;                                      // handoff scalars per state: one SElem
+constexpr int LINS = 65;                                      // stored linearisation scalars per state
 
 template <typename T>
 struct KParams {
@@ -64,6 +65,7 @@ struct KParams {
     T* P;
     // workspace
     T* hand;           // MODE_RUN handoff of smoothing elements: [warp][s][c][32 lanes]
+    T* lin;            // MODE_RUN cubature linearisation handed from the fold to the re-run: [warp][s][LINS][32]
     T* aggF;           // [NB][FE]
     T* aggS;           // [NB][SE]
     unsigned* bar;     // grid barrier counter, zero at launch
@@ -320,6 +322,77 @@ PES_DEV bool get_obs(const KParams<T>& p, int64_t k, int64_t ix, int b, Obs<T>& 
 
 // ---- lane-level passes -------------------------------------------------------------
 
+// Whether the fold hands its linearisation of every state to the filtering
+// re-run (65 scalars per state) instead of the re-run linearising again. The
+// cubature linearisation (2 n_x sigma points through f and h) costs far more
+// than the traffic; the Taylor one does not.
+template <int LIN>
+constexpr bool kStoreLin = (LIN == LIN_CUBATURE);
+
+// Layout [warp][s][LINS][32 lanes]; per state: H (10), r (2), R' (3), xn (5),
+// F (25), fx (5), Q' (15).
+template <typename T>
+PES_DEV T* lin_slot(const KParams<T>& p, int s, int lane)
+{
+    return p.lin + ((size_t)(lane >> 5) * p.L + s) * (LINS * 32) + (lane & 31);
+}
+
+template <typename T>
+PES_DEV void store_lin_obs(const KParams<T>& p, int s, int lane, const Obs<T>& ob)
+{
+    T* h = lin_slot(p, s, lane);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) h[(15 + i) * 32] = ob.xn[i];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) h[i * 32] = ob.H[i];
+    h[10 * 32] = ob.r[0];
+    h[11 * 32] = ob.r[1];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) h[(12 + i) * 32] = ob.R[i];
+}
+
+template <typename T>
+PES_DEV void store_lin_trans(const KParams<T>& p, int s, int lane, const Trans<T>& tr)
+{
+    T* h = lin_slot(p, s, lane);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) h[(15 + i) * 32] = tr.xn[i];
+#pragma unroll
+    for (int i = 0; i < 25; ++i) h[(20 + i) * 32] = tr.F[i];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) h[(45 + i) * 32] = tr.fx[i];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) h[(50 + i) * 32] = tr.Q[i];
+}
+
+template <typename T>
+PES_DEV void load_lin_obs(const KParams<T>& p, int s, int lane, Obs<T>& ob)
+{
+    const T* h = lin_slot(p, s, lane);
+#pragma unroll
+    for (int i = 0; i < 10; ++i) ob.H[i] = h[i * 32];
+    ob.r[0] = h[10 * 32];
+    ob.r[1] = h[11 * 32];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ob.R[i] = h[(12 + i) * 32];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) ob.xn[i] = h[(15 + i) * 32];
+}
+
+template <typename T>
+PES_DEV void load_lin_trans(const KParams<T>& p, int s, int lane, Trans<T>& tr)
+{
+    const T* h = lin_slot(p, s, lane);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) tr.xn[i] = h[(15 + i) * 32];
+#pragma unroll
+    for (int i = 0; i < 25; ++i) tr.F[i] = h[(20 + i) * 32];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) tr.fx[i] = h[(45 + i) * 32];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) tr.Q[i] = h[(50 + i) * 32];
+}
+
 // Filtering, level 1: fold the lane's chunk [a, e) into one element.
 template <typename T, int LIN>
 PES_DEV bool fold_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int lane, FElem<T>& acc)
@@ -357,8 +430,12 @@ PES_DEV bool fold_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int la
             Obs<T> ob;
             lin_obs(p, k, cur.b, sc, f, ob);
             ok &= fold_filter_step(acc, tr, ob);
+            if (kStoreLin<LIN> && p.mode == MODE_RUN) store_lin_obs(p, (int)(k - a), lane, ob);
         }
-        if (k + 1 < e && !cur.is_tail(k)) lin_trans(p, k, sc, f, tr);
+        if (!cur.is_tail(k) && (k + 1 < e || (kStoreLin<LIN> && p.mode == MODE_RUN))) {
+            lin_trans(p, k, sc, f, tr);
+            if (kStoreLin<LIN> && p.mode == MODE_RUN) store_lin_trans(p, (int)(k - a), lane, tr);
+        }
         sc = sn;
     }
     return ok;
@@ -458,18 +535,24 @@ PES_DEV bool rerun_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int l
     for (int i = 0; i < 5; ++i) m[i] = G.m[i];
 #pragma unroll
     for (int i = 0; i < 15; ++i) P[i] = G.P[i];
+    // with a stored linearisation the re-run reads it instead of linearising
+    constexpr bool stored_lin = kStoreLin<LIN>;
+    const bool use_lin = stored_lin && smooth;
     Trans<T> tr;
-    if (!cur.is_head(a)) ok &= get_trans<T, LIN>(p, a - 1, prev_ix(p, a, lane), tr);
+    if (!cur.is_head(a)) {
+        if (use_lin) load_lin_trans(p, p.L - 1, lane - 1, tr);
+        else ok &= get_trans<T, LIN>(p, a - 1, prev_ix(p, a, lane), tr);
+    }
     const int64_t dix = p.lanes_layout ? p.NL : 1;
     int64_t ix = state_ix(p, a, a, lane);
     StateIn<T, LIN> sc, sn;
-    load_state(p, ix, sc);
+    if (!use_lin) load_state(p, ix, sc);
 #pragma unroll 1
     for (int64_t k = a; k < e; ++k, ix += dix) {
         cur.forward(k);
-        if (k + 1 < e) load_state(p, ix + dix, sn);
+        if (!use_lin && k + 1 < e) load_state(p, ix + dix, sn);
         Factor<T, LIN> f;
-        ok &= factor_state(sc, f);
+        if (!use_lin) ok &= factor_state(sc, f);
         if (cur.is_head(k)) {
             if (smooth && k > a) {
                 SElem<T> el;
@@ -491,13 +574,17 @@ PES_DEV bool rerun_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int l
                 }
             }
             Obs<T> ob;
-            lin_obs(p, k, cur.b, sc, f, ob);
+            if (use_lin) load_lin_obs(p, (int)(k - a), lane, ob);
+            else lin_obs(p, k, cur.b, sc, f, ob);
             ok &= kf_update(ob, mp, Pp, m, P);
         }
         if (!smooth) store_filtered(p, k, m, P);
         else if (!kStoreElements<LIN>) store_xP(p, (int)(k - a), lane, m, P);
-        if (!cur.is_tail(k) && (k + 1 < e || smooth)) lin_trans(p, k, sc, f, tr);
-        sc = sn;
+        if (!cur.is_tail(k) && (k + 1 < e || smooth)) {
+            if (use_lin) load_lin_trans(p, (int)(k - a), lane, tr);
+            else lin_trans(p, k, sc, f, tr);
+        }
+        if (!use_lin) sc = sn;
     }
     if (smooth) {
         // smoothing element of the chunk's last state
@@ -628,16 +715,40 @@ PES_DEV void copy_elem_to_global(const T* src, T* dst)
 
 // Filtering levels 2-4. elem[t] holds lane t's folded element on entry; returns
 // the Gaussian of the state before lane t's chunk.
+// Team size for a tree level with n operator applications on NT threads:
+// teams of 8..32 lanes when at most NT/8 applications remain, otherwise one
+// thread per application.
+template <int NT>
+PES_DEV int team_tau(int n)
+{
+    int tau = 32;
+    while (tau > 1 && tau * n > NT) tau >>= 1;
+    return tau >= 8 ? tau : 1;
+}
+
+// Filtering levels 2-4. elem[t] holds lane t's folded element on entry; returns
+// the Gaussian of the state before lane t's chunk.
 template <typename T, int NT>
 PES_DEV void filter_block_scan(const KParams<T>& p, FElem<T>* elem, FElem<T>* top, Gauss<T>* gs,
-                               Gauss<T>* gblock, unsigned& gen, Gauss<T>& out, int it)
+                               Gauss<T>* gblock, TeamScratch<T>* scratch, unsigned& gen, Gauss<T>& out, int it)
 {
     const int t = threadIdx.x;
     __syncthreads();
     PES_PHASE(p, it, 1);
+    // level 2: up-sweep; node (q+1) 2s - 1 combines its left child (q+1) 2s - 1 - s
 #pragma unroll 1
     for (int s = 1; s < NT; s <<= 1) {
-        if (((t + 1) & (2 * s - 1)) == 0) combine_filter(elem[t - s], elem[t], elem[t]);
+        const int n = NT / (2 * s);
+        const int tau = team_tau<NT>(n);
+        if (tau == 1) {
+            if (((t + 1) & (2 * s - 1)) == 0) combine_filter(elem[t - s], elem[t], elem[t]);
+        } else {
+            const int q = t / tau;
+            if (q < n) {
+                const int node = (q + 1) * 2 * s - 1;
+                team_combine_filter(elem[node - s], elem[node], elem[node], scratch[q], make_team(tau));
+            }
+        }
         __syncthreads();
     }
     copy_elem_to_global<T, FE>(reinterpret_cast<const T*>(&elem[NT - 1]), p.aggF + (size_t)blockIdx.x * FE);
@@ -656,15 +767,24 @@ PES_DEV void filter_block_scan(const KParams<T>& p, FElem<T>* elem, FElem<T>* to
     for (int c0 = 0; c0 < j; c0 += NT) {
         const int n = min(NT, j - c0);
         __syncthreads();
-        for (int i = t; i < n * FE; i += NT)
-            reinterpret_cast<T*>(top)[i] = p.aggF[(size_t)c0 * FE + i];
+        for (int i = t; i < n * FE; i += NT) reinterpret_cast<T*>(top)[i] = p.aggF[(size_t)c0 * FE + i];
         __syncthreads();
 #pragma unroll 1
         for (int s = 1; s < n; s <<= 1) {
-            if ((t & (2 * s - 1)) == 0 && t + s < n) combine_filter(top[t], top[t + s], top[t]);
+            const int pairs = (n - 1 - s) / (2 * s) + 1;
+            const int tau = team_tau<NT>(pairs);
+            if (tau == 1) {
+                if ((t & (2 * s - 1)) == 0 && t + s < n) combine_filter(top[t], top[t + s], top[t]);
+            } else {
+                const int q = t / tau;
+                if (q < pairs) {
+                    const int node = q * 2 * s;
+                    team_combine_filter(top[node], top[node + s], top[node], scratch[q], make_team(tau));
+                }
+            }
             __syncthreads();
         }
-        if (t == 0) apply_filter(*gblock, top[0], *gblock);
+        if (t < 32) team_apply_filter(*gblock, top[0], *gblock, scratch[0], make_team(32));
     }
     __syncthreads();
     PES_PHASE(p, it, 4);
@@ -673,12 +793,26 @@ PES_DEV void filter_block_scan(const KParams<T>& p, FElem<T>* elem, FElem<T>* to
     __syncthreads();
 #pragma unroll 1
     for (int s = NT / 2; s >= 1; s >>= 1) {
-        if (((t + 1) & (2 * s - 1)) == 0) {
-            const Gauss<T> gin = gs[t];
-            Gauss<T> gr;
-            apply_filter(gin, elem[t - s], gr);
-            gs[t - s] = gin;
-            gs[t] = gr;
+        const int n = NT / (2 * s);
+        const int tau = team_tau<NT>(n);
+        if (tau == 1) {
+            if (((t + 1) & (2 * s - 1)) == 0) {
+                const Gauss<T> gin = gs[t];
+                Gauss<T> gr;
+                apply_filter(gin, elem[t - s], gr);
+                gs[t - s] = gin;
+                gs[t] = gr;
+            }
+        } else {
+            const int q = t / tau;
+            if (q < n) {
+                const int node = (q + 1) * 2 * s - 1;
+                const Team tm = make_team(tau);
+                for (int i = tm.r; i < GE; i += tau)
+                    reinterpret_cast<T*>(&gs[node - s])[i] = reinterpret_cast<const T*>(&gs[node])[i];
+                tm.sync();
+                team_apply_filter(gs[node - s], elem[node - s], gs[node], scratch[q], tm);
+            }
         }
         __syncthreads();
     }
@@ -691,14 +825,24 @@ PES_DEV void filter_block_scan(const KParams<T>& p, FElem<T>* elem, FElem<T>* to
 // Returns the Gaussian of the state after lane t's chunk.
 template <typename T, int NT>
 PES_DEV void smoother_block_scan(const KParams<T>& p, SElem<T>* elem, SElem<T>* top, Gauss<T>* gs,
-                                 Gauss<T>* gblock, unsigned& gen, Gauss<T>& out, int it)
+                                 Gauss<T>* gblock, TeamScratch<T>* scratch, unsigned& gen, Gauss<T>& out, int it)
 {
     const int t = threadIdx.x;
     __syncthreads();
     PES_PHASE(p, it, 7);
 #pragma unroll 1
     for (int s = 1; s < NT; s <<= 1) {
-        if ((t & (2 * s - 1)) == 0) combine_smoother(elem[t], elem[t + s], elem[t]);
+        const int n = NT / (2 * s);
+        const int tau = team_tau<NT>(n);
+        if (tau == 1) {
+            if ((t & (2 * s - 1)) == 0) combine_smoother(elem[t], elem[t + s], elem[t]);
+        } else {
+            const int q = t / tau;
+            if (q < n) {
+                const int node = q * 2 * s;
+                team_combine_smoother(elem[node], elem[node + s], elem[node], scratch[q], make_team(tau));
+            }
+        }
         __syncthreads();
     }
     copy_elem_to_global<T, SE>(reinterpret_cast<const T*>(&elem[0]), p.aggS + (size_t)blockIdx.x * SE);
@@ -718,15 +862,24 @@ PES_DEV void smoother_block_scan(const KParams<T>& p, SElem<T>* elem, SElem<T>* 
         const int n = min(NT, c1 - (j + 1));
         const int c0 = c1 - n;
         __syncthreads();
-        for (int i = t; i < n * SE; i += NT)
-            reinterpret_cast<T*>(top)[i] = p.aggS[(size_t)c0 * SE + i];
+        for (int i = t; i < n * SE; i += NT) reinterpret_cast<T*>(top)[i] = p.aggS[(size_t)c0 * SE + i];
         __syncthreads();
 #pragma unroll 1
         for (int s = 1; s < n; s <<= 1) {
-            if ((t & (2 * s - 1)) == 0 && t + s < n) combine_smoother(top[t], top[t + s], top[t]);
+            const int pairs = (n - 1 - s) / (2 * s) + 1;
+            const int tau = team_tau<NT>(pairs);
+            if (tau == 1) {
+                if ((t & (2 * s - 1)) == 0 && t + s < n) combine_smoother(top[t], top[t + s], top[t]);
+            } else {
+                const int q = t / tau;
+                if (q < pairs) {
+                    const int node = q * 2 * s;
+                    team_combine_smoother(top[node], top[node + s], top[node], scratch[q], make_team(tau));
+                }
+            }
             __syncthreads();
         }
-        if (t == 0) apply_smoother(top[0], *gblock, *gblock);
+        if (t < 32) team_apply_smoother(top[0], *gblock, *gblock, scratch[0], make_team(32));
         c1 = c0;
     }
     __syncthreads();
@@ -735,12 +888,26 @@ PES_DEV void smoother_block_scan(const KParams<T>& p, SElem<T>* elem, SElem<T>* 
     __syncthreads();
 #pragma unroll 1
     for (int s = NT / 2; s >= 1; s >>= 1) {
-        if ((t & (2 * s - 1)) == 0) {
-            const Gauss<T> gin = gs[t];
-            Gauss<T> gl;
-            apply_smoother(elem[t + s], gin, gl);
-            gs[t + s] = gin;
-            gs[t] = gl;
+        const int n = NT / (2 * s);
+        const int tau = team_tau<NT>(n);
+        if (tau == 1) {
+            if ((t & (2 * s - 1)) == 0) {
+                const Gauss<T> gin = gs[t];
+                Gauss<T> gl;
+                apply_smoother(elem[t + s], gin, gl);
+                gs[t + s] = gin;
+                gs[t] = gl;
+            }
+        } else {
+            const int q = t / tau;
+            if (q < n) {
+                const int node = q * 2 * s;
+                const Team tm = make_team(tau);
+                for (int i = tm.r; i < GE; i += tau)
+                    reinterpret_cast<T*>(&gs[node + s])[i] = reinterpret_cast<const T*>(&gs[node])[i];
+                tm.sync();
+                team_apply_smoother(elem[node + s], gs[node + s], gs[node], scratch[q], tm);
+            }
         }
         __syncthreads();
     }
@@ -749,12 +916,14 @@ PES_DEV void smoother_block_scan(const KParams<T>& p, SElem<T>* elem, SElem<T>* 
     PES_PHASE(p, it, 11);
 }
 
+constexpr int TS = sizeof(TeamScratch<double>) / sizeof(double);   // scalars of one team's scratch
+
 template <int NT>
 constexpr size_t smem_bytes_for(size_t scalar)
 {
     // lane tree (filtering elements; smoothing elements alias it), top-level
-    // buffer, down-sweep Gaussians, one block Gaussian
-    return scalar * (size_t(NT) * FE * 2 + size_t(NT) * GE + GE);
+    // buffer, down-sweep Gaussians, one block Gaussian, NT/8 team scratches
+    return scalar * (size_t(NT) * FE * 2 + size_t(NT) * GE + GE + size_t(NT / 8) * TS);
 }
 
 template <typename T, int LIN, int NT>
@@ -767,6 +936,7 @@ __global__ void __launch_bounds__(NT, 1) pes_persistent_kernel(const KParams<T> 
     SElem<T>* topS = reinterpret_cast<SElem<T>*>(topF);
     Gauss<T>* gs = reinterpret_cast<Gauss<T>*>(topF + NT);
     Gauss<T>* gblock = gs + NT;
+    TeamScratch<T>* scratch = reinterpret_cast<TeamScratch<T>*>(gblock + 1);
     __shared__ int s_flag;
     __shared__ double s_red[NT];
 
@@ -794,7 +964,7 @@ __global__ void __launch_bounds__(NT, 1) pes_persistent_kernel(const KParams<T> 
             ok &= fold_filter_chunk<T, LIN>(p, a, e, lane, acc);
             elemF[t] = acc;
             Gauss<T> G;
-            filter_block_scan<T, NT>(p, elemF, topF, gs, gblock, gen, G, it);
+            filter_block_scan<T, NT>(p, elemF, topF, gs, gblock, scratch, gen, G, it);
             ok &= rerun_filter_chunk<T, LIN>(p, a, e, lane, G, accS);
             PES_PHASE(p, it, 6);
             if (track && blockIdx.x == 0) {
@@ -809,7 +979,7 @@ __global__ void __launch_bounds__(NT, 1) pes_persistent_kernel(const KParams<T> 
         if (do_smooth) {
             elemS[t] = accS;
             Gauss<T> Gs;
-            smoother_block_scan<T, NT>(p, elemS, topS, gs, gblock, gen, Gs, it);
+            smoother_block_scan<T, NT>(p, elemS, topS, gs, gblock, scratch, gen, Gs, it);
             const bool write_P = (p.mode != MODE_RUN) || (LIN == LIN_CUBATURE) || last || p.write_P_every_iter;
             int nb = -1;
             double num = 0.0, den = 0.0;
