@@ -25,7 +25,7 @@
 // they set ST_TIMEOUT and return, so the kernel always terminates.
 #pragma once
 
-#include "pes_team.cuh"
+#include "pes_ops.cuh"
 
 namespace pes {
 
@@ -715,40 +715,18 @@ PES_DEV void copy_elem_to_global(const T* src, T* dst)
 
 // Filtering levels 2-4. elem[t] holds lane t's folded element on entry; returns
 // the Gaussian of the state before lane t's chunk.
-// Team size for a tree level with n operator applications on NT threads:
-// teams of 8..32 lanes when at most NT/8 applications remain, otherwise one
-// thread per application.
-template <int NT>
-PES_DEV int team_tau(int n)
-{
-    int tau = 32;
-    while (tau > 1 && tau * n > NT) tau >>= 1;
-    return tau >= 8 ? tau : 1;
-}
-
 // Filtering levels 2-4. elem[t] holds lane t's folded element on entry; returns
 // the Gaussian of the state before lane t's chunk.
 template <typename T, int NT>
 PES_DEV void filter_block_scan(const KParams<T>& p, FElem<T>* elem, FElem<T>* top, Gauss<T>* gs,
-                               Gauss<T>* gblock, TeamScratch<T>* scratch, unsigned& gen, Gauss<T>& out, int it)
+                               Gauss<T>* gblock, unsigned& gen, Gauss<T>& out, int it)
 {
     const int t = threadIdx.x;
     __syncthreads();
     PES_PHASE(p, it, 1);
-    // level 2: up-sweep; node (q+1) 2s - 1 combines its left child (q+1) 2s - 1 - s
 #pragma unroll 1
     for (int s = 1; s < NT; s <<= 1) {
-        const int n = NT / (2 * s);
-        const int tau = team_tau<NT>(n);
-        if (tau == 1) {
-            if (((t + 1) & (2 * s - 1)) == 0) combine_filter(elem[t - s], elem[t], elem[t]);
-        } else {
-            const int q = t / tau;
-            if (q < n) {
-                const int node = (q + 1) * 2 * s - 1;
-                team_combine_filter(elem[node - s], elem[node], elem[node], scratch[q], make_team(tau));
-            }
-        }
+        if (((t + 1) & (2 * s - 1)) == 0) combine_filter(elem[t - s], elem[t], elem[t]);
         __syncthreads();
     }
     copy_elem_to_global<T, FE>(reinterpret_cast<const T*>(&elem[NT - 1]), p.aggF + (size_t)blockIdx.x * FE);
@@ -767,24 +745,15 @@ PES_DEV void filter_block_scan(const KParams<T>& p, FElem<T>* elem, FElem<T>* to
     for (int c0 = 0; c0 < j; c0 += NT) {
         const int n = min(NT, j - c0);
         __syncthreads();
-        for (int i = t; i < n * FE; i += NT) reinterpret_cast<T*>(top)[i] = p.aggF[(size_t)c0 * FE + i];
+        for (int i = t; i < n * FE; i += NT)
+            reinterpret_cast<T*>(top)[i] = p.aggF[(size_t)c0 * FE + i];
         __syncthreads();
 #pragma unroll 1
         for (int s = 1; s < n; s <<= 1) {
-            const int pairs = (n - 1 - s) / (2 * s) + 1;
-            const int tau = team_tau<NT>(pairs);
-            if (tau == 1) {
-                if ((t & (2 * s - 1)) == 0 && t + s < n) combine_filter(top[t], top[t + s], top[t]);
-            } else {
-                const int q = t / tau;
-                if (q < pairs) {
-                    const int node = q * 2 * s;
-                    team_combine_filter(top[node], top[node + s], top[node], scratch[q], make_team(tau));
-                }
-            }
+            if ((t & (2 * s - 1)) == 0 && t + s < n) combine_filter(top[t], top[t + s], top[t]);
             __syncthreads();
         }
-        if (t < 32) team_apply_filter(*gblock, top[0], *gblock, scratch[0], make_team(32));
+        if (t == 0) apply_filter(*gblock, top[0], *gblock);
     }
     __syncthreads();
     PES_PHASE(p, it, 4);
@@ -793,26 +762,12 @@ PES_DEV void filter_block_scan(const KParams<T>& p, FElem<T>* elem, FElem<T>* to
     __syncthreads();
 #pragma unroll 1
     for (int s = NT / 2; s >= 1; s >>= 1) {
-        const int n = NT / (2 * s);
-        const int tau = team_tau<NT>(n);
-        if (tau == 1) {
-            if (((t + 1) & (2 * s - 1)) == 0) {
-                const Gauss<T> gin = gs[t];
-                Gauss<T> gr;
-                apply_filter(gin, elem[t - s], gr);
-                gs[t - s] = gin;
-                gs[t] = gr;
-            }
-        } else {
-            const int q = t / tau;
-            if (q < n) {
-                const int node = (q + 1) * 2 * s - 1;
-                const Team tm = make_team(tau);
-                for (int i = tm.r; i < GE; i += tau)
-                    reinterpret_cast<T*>(&gs[node - s])[i] = reinterpret_cast<const T*>(&gs[node])[i];
-                tm.sync();
-                team_apply_filter(gs[node - s], elem[node - s], gs[node], scratch[q], tm);
-            }
+        if (((t + 1) & (2 * s - 1)) == 0) {
+            const Gauss<T> gin = gs[t];
+            Gauss<T> gr;
+            apply_filter(gin, elem[t - s], gr);
+            gs[t - s] = gin;
+            gs[t] = gr;
         }
         __syncthreads();
     }
@@ -825,24 +780,14 @@ PES_DEV void filter_block_scan(const KParams<T>& p, FElem<T>* elem, FElem<T>* to
 // Returns the Gaussian of the state after lane t's chunk.
 template <typename T, int NT>
 PES_DEV void smoother_block_scan(const KParams<T>& p, SElem<T>* elem, SElem<T>* top, Gauss<T>* gs,
-                                 Gauss<T>* gblock, TeamScratch<T>* scratch, unsigned& gen, Gauss<T>& out, int it)
+                                 Gauss<T>* gblock, unsigned& gen, Gauss<T>& out, int it)
 {
     const int t = threadIdx.x;
     __syncthreads();
     PES_PHASE(p, it, 7);
 #pragma unroll 1
     for (int s = 1; s < NT; s <<= 1) {
-        const int n = NT / (2 * s);
-        const int tau = team_tau<NT>(n);
-        if (tau == 1) {
-            if ((t & (2 * s - 1)) == 0) combine_smoother(elem[t], elem[t + s], elem[t]);
-        } else {
-            const int q = t / tau;
-            if (q < n) {
-                const int node = q * 2 * s;
-                team_combine_smoother(elem[node], elem[node + s], elem[node], scratch[q], make_team(tau));
-            }
-        }
+        if ((t & (2 * s - 1)) == 0) combine_smoother(elem[t], elem[t + s], elem[t]);
         __syncthreads();
     }
     copy_elem_to_global<T, SE>(reinterpret_cast<const T*>(&elem[0]), p.aggS + (size_t)blockIdx.x * SE);
@@ -862,24 +807,15 @@ PES_DEV void smoother_block_scan(const KParams<T>& p, SElem<T>* elem, SElem<T>* 
         const int n = min(NT, c1 - (j + 1));
         const int c0 = c1 - n;
         __syncthreads();
-        for (int i = t; i < n * SE; i += NT) reinterpret_cast<T*>(top)[i] = p.aggS[(size_t)c0 * SE + i];
+        for (int i = t; i < n * SE; i += NT)
+            reinterpret_cast<T*>(top)[i] = p.aggS[(size_t)c0 * SE + i];
         __syncthreads();
 #pragma unroll 1
         for (int s = 1; s < n; s <<= 1) {
-            const int pairs = (n - 1 - s) / (2 * s) + 1;
-            const int tau = team_tau<NT>(pairs);
-            if (tau == 1) {
-                if ((t & (2 * s - 1)) == 0 && t + s < n) combine_smoother(top[t], top[t + s], top[t]);
-            } else {
-                const int q = t / tau;
-                if (q < pairs) {
-                    const int node = q * 2 * s;
-                    team_combine_smoother(top[node], top[node + s], top[node], scratch[q], make_team(tau));
-                }
-            }
+            if ((t & (2 * s - 1)) == 0 && t + s < n) combine_smoother(top[t], top[t + s], top[t]);
             __syncthreads();
         }
-        if (t < 32) team_apply_smoother(top[0], *gblock, *gblock, scratch[0], make_team(32));
+        if (t == 0) apply_smoother(top[0], *gblock, *gblock);
         c1 = c0;
     }
     __syncthreads();
@@ -888,26 +824,12 @@ PES_DEV void smoother_block_scan(const KParams<T>& p, SElem<T>* elem, SElem<T>* 
     __syncthreads();
 #pragma unroll 1
     for (int s = NT / 2; s >= 1; s >>= 1) {
-        const int n = NT / (2 * s);
-        const int tau = team_tau<NT>(n);
-        if (tau == 1) {
-            if ((t & (2 * s - 1)) == 0) {
-                const Gauss<T> gin = gs[t];
-                Gauss<T> gl;
-                apply_smoother(elem[t + s], gin, gl);
-                gs[t + s] = gin;
-                gs[t] = gl;
-            }
-        } else {
-            const int q = t / tau;
-            if (q < n) {
-                const int node = q * 2 * s;
-                const Team tm = make_team(tau);
-                for (int i = tm.r; i < GE; i += tau)
-                    reinterpret_cast<T*>(&gs[node + s])[i] = reinterpret_cast<const T*>(&gs[node])[i];
-                tm.sync();
-                team_apply_smoother(elem[node + s], gs[node + s], gs[node], scratch[q], tm);
-            }
+        if ((t & (2 * s - 1)) == 0) {
+            const Gauss<T> gin = gs[t];
+            Gauss<T> gl;
+            apply_smoother(elem[t + s], gin, gl);
+            gs[t + s] = gin;
+            gs[t] = gl;
         }
         __syncthreads();
     }
@@ -916,14 +838,12 @@ PES_DEV void smoother_block_scan(const KParams<T>& p, SElem<T>* elem, SElem<T>* 
     PES_PHASE(p, it, 11);
 }
 
-constexpr int TS = sizeof(TeamScratch<double>) / sizeof(double);   // scalars of one team's scratch
-
 template <int NT>
 constexpr size_t smem_bytes_for(size_t scalar)
 {
     // lane tree (filtering elements; smoothing elements alias it), top-level
-    // buffer, down-sweep Gaussians, one block Gaussian, NT/8 team scratches
-    return scalar * (size_t(NT) * FE * 2 + size_t(NT) * GE + GE + size_t(NT / 8) * TS);
+    // buffer, down-sweep Gaussians, one block Gaussian
+    return scalar * (size_t(NT) * FE * 2 + size_t(NT) * GE + GE);
 }
 
 template <typename T, int LIN, int NT>
@@ -936,7 +856,6 @@ __global__ void __launch_bounds__(NT, 1) pes_persistent_kernel(const KParams<T> 
     SElem<T>* topS = reinterpret_cast<SElem<T>*>(topF);
     Gauss<T>* gs = reinterpret_cast<Gauss<T>*>(topF + NT);
     Gauss<T>* gblock = gs + NT;
-    TeamScratch<T>* scratch = reinterpret_cast<TeamScratch<T>*>(gblock + 1);
     __shared__ int s_flag;
     __shared__ double s_red[NT];
 
@@ -964,7 +883,7 @@ __global__ void __launch_bounds__(NT, 1) pes_persistent_kernel(const KParams<T> 
             ok &= fold_filter_chunk<T, LIN>(p, a, e, lane, acc);
             elemF[t] = acc;
             Gauss<T> G;
-            filter_block_scan<T, NT>(p, elemF, topF, gs, gblock, scratch, gen, G, it);
+            filter_block_scan<T, NT>(p, elemF, topF, gs, gblock, gen, G, it);
             ok &= rerun_filter_chunk<T, LIN>(p, a, e, lane, G, accS);
             PES_PHASE(p, it, 6);
             if (track && blockIdx.x == 0) {
@@ -979,7 +898,7 @@ __global__ void __launch_bounds__(NT, 1) pes_persistent_kernel(const KParams<T> 
         if (do_smooth) {
             elemS[t] = accS;
             Gauss<T> Gs;
-            smoother_block_scan<T, NT>(p, elemS, topS, gs, gblock, scratch, gen, Gs, it);
+            smoother_block_scan<T, NT>(p, elemS, topS, gs, gblock, gen, Gs, it);
             const bool write_P = (p.mode != MODE_RUN) || (LIN == LIN_CUBATURE) || last || p.write_P_every_iter;
             int nb = -1;
             double num = 0.0, den = 0.0;
