@@ -25,6 +25,7 @@
 // they set ST_TIMEOUT and return, so the kernel always terminates.
 #pragma once
 
+#include "pes_async.cuh"
 #include "pes_ops.cuh"
 
 namespace pes {
@@ -517,76 +518,119 @@ PES_DEV void load_xP(const KParams<T>& p, int s, int lane, T* m, T* P)
 template <int LIN>
 constexpr bool kStoreElements = (LIN == LIN_CUBATURE);
 
+// Stored linearisation of step stage `i` of a lane-stream (layout of store_lin_*).
+template <typename T, class S>
+PES_DEV void obs_from_stage(const S& ws, int i, Obs<T>& ob)
+{
+#pragma unroll
+    for (int c = 0; c < 10; ++c) ob.H[c] = ws.get(i, c);
+    ob.r[0] = ws.get(i, 10);
+    ob.r[1] = ws.get(i, 11);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ob.R[c] = ws.get(i, 12 + c);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) ob.xn[c] = ws.get(i, 15 + c);
+}
+
+template <typename T, class S>
+PES_DEV void trans_from_stage(const S& ws, int i, Trans<T>& tr)
+{
+#pragma unroll
+    for (int c = 0; c < 5; ++c) tr.xn[c] = ws.get(i, 15 + c);
+#pragma unroll
+    for (int c = 0; c < 25; ++c) tr.F[c] = ws.get(i, 20 + c);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) tr.fx[c] = ws.get(i, 45 + c);
+#pragma unroll
+    for (int c = 0; c < 15; ++c) tr.Q[c] = ws.get(i, 50 + c);
+}
+
 // Filtering, level 5: re-run the chunk from the Gaussian of the state before it,
 // storing filtered moments; in MODE_RUN also build and fold the chunk's
-// smoothing elements (Eqs. 17-18) into accS.
+// smoothing elements (Eqs. 17-18) into accS. The loop runs over the L steps
+// of the chunk in every lane of the warp (lanes whose chunk is shorter idle),
+// so that a warp stream can feed it the stored linearisation.
 template <typename T, int LIN>
 PES_DEV bool rerun_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int lane, const Gauss<T>& G,
-                                SElem<T>& accS)
+                                SElem<T>& accS, T* wstage, uint64_t* wbar, uint32_t& wpar)
 {
     bool ok = true;
     selem_identity(accS);
-    if (a >= e) return ok;
     const bool smooth = (p.mode == MODE_RUN);
+    const bool any = a < e;
+    // with a stored linearisation the re-run reads it instead of linearising
+    constexpr bool stored_lin = kStoreLin<LIN>;
+    const bool use_lin = stored_lin && smooth;
     SegCursor cur;
-    cur.init(p.offsets, p.B, a);
+    if (any) cur.init(p.offsets, p.B, a);
     T m[5], P[15];
 #pragma unroll
     for (int i = 0; i < 5; ++i) m[i] = G.m[i];
 #pragma unroll
     for (int i = 0; i < 15; ++i) P[i] = G.P[i];
-    // with a stored linearisation the re-run reads it instead of linearising
-    constexpr bool stored_lin = kStoreLin<LIN>;
-    const bool use_lin = stored_lin && smooth;
     Trans<T> tr;
-    if (!cur.is_head(a)) {
+    if (any && !cur.is_head(a)) {
         if (use_lin) load_lin_trans(p, p.L - 1, lane - 1, tr);
         else ok &= get_trans<T, LIN>(p, a - 1, prev_ix(p, a, lane), tr);
     }
     const int64_t dix = p.lanes_layout ? p.NL : 1;
     int64_t ix = state_ix(p, a, a, lane);
     StateIn<T, LIN> sc, sn;
-    if (!use_lin) load_state(p, ix, sc);
+    if (!use_lin && any) load_state(p, ix, sc);
+    WarpStream<T, LINS, LINS> ws;
+    if (use_lin) {
+        ws.init(p.lin + (size_t)(lane >> 5) * p.L * (LINS * 32), wstage, wbar, wpar);
+        ws.issue(0, 0);
+    }
 #pragma unroll 1
-    for (int64_t k = a; k < e; ++k, ix += dix) {
-        cur.forward(k);
-        if (!use_lin && k + 1 < e) load_state(p, ix + dix, sn);
-        Factor<T, LIN> f;
-        if (!use_lin) ok &= factor_state(sc, f);
-        if (cur.is_head(k)) {
-            if (smooth && k > a) {
-                SElem<T> el;
-                selem_last(el, m, P);
-                combine_smoother(accS, el, accS);
-                if (kStoreElements<LIN>) store_selem(p, (int)(k - 1 - a), lane, el);
-            }
-            load_prior(p, cur.b, m, P);
-        } else {
-            T mp[5], Pp[15];
-            {
-                T FP[25];
-                predict(tr, m, P, mp, FP, Pp);
+    for (int s = 0; s < p.L; ++s, ix += dix) {
+        const int64_t k = a + s;
+        if (use_lin) {
+            if (s + 1 < p.L) ws.issue(s + 1, (s + 1) & 1);
+            ws.wait(s & 1, p.status);
+        }
+        if (k < e) {
+            cur.forward(k);
+            if (!use_lin && k + 1 < e) load_state(p, ix + dix, sn);
+            Factor<T, LIN> f;
+            if (!use_lin) ok &= factor_state(sc, f);
+            if (cur.is_head(k)) {
                 if (smooth && k > a) {
                     SElem<T> el;
-                    ok &= selem_from_prediction(m, P, FP, Pp, mp, el);
+                    selem_last(el, m, P);
                     combine_smoother(accS, el, accS);
-                    if (kStoreElements<LIN>) store_selem(p, (int)(k - 1 - a), lane, el);
+                    if (kStoreElements<LIN>) store_selem(p, s - 1, lane, el);
                 }
+                load_prior(p, cur.b, m, P);
+            } else {
+                T mp[5], Pp[15];
+                {
+                    T FP[25];
+                    predict(tr, m, P, mp, FP, Pp);
+                    if (smooth && k > a) {
+                        SElem<T> el;
+                        ok &= selem_from_prediction(m, P, FP, Pp, mp, el);
+                        combine_smoother(accS, el, accS);
+                        if (kStoreElements<LIN>) store_selem(p, s - 1, lane, el);
+                    }
+                }
+                Obs<T> ob;
+                if (use_lin) obs_from_stage<T>(ws, s & 1, ob);
+                else lin_obs(p, k, cur.b, sc, f, ob);
+                ok &= kf_update(ob, mp, Pp, m, P);
             }
-            Obs<T> ob;
-            if (use_lin) load_lin_obs(p, (int)(k - a), lane, ob);
-            else lin_obs(p, k, cur.b, sc, f, ob);
-            ok &= kf_update(ob, mp, Pp, m, P);
+            if (!smooth) store_filtered(p, k, m, P);
+            else if (!kStoreElements<LIN>) store_xP(p, s, lane, m, P);
+            if (!cur.is_tail(k) && (k + 1 < e || smooth)) {
+                if (use_lin) trans_from_stage<T>(ws, s & 1, tr);
+                else lin_trans(p, k, sc, f, tr);
+            }
+            if (!use_lin) sc = sn;
         }
-        if (!smooth) store_filtered(p, k, m, P);
-        else if (!kStoreElements<LIN>) store_xP(p, (int)(k - a), lane, m, P);
-        if (!cur.is_tail(k) && (k + 1 < e || smooth)) {
-            if (use_lin) load_lin_trans(p, (int)(k - a), lane, tr);
-            else lin_trans(p, k, sc, f, tr);
-        }
-        if (!use_lin) sc = sn;
+        if (use_lin) __syncwarp();
     }
-    if (smooth) {
+    if (use_lin) wpar = ws.parity;
+    if (smooth && any) {
         // smoothing element of the chunk's last state
         SElem<T> el;
         if (cur.is_tail(e - 1)) {
@@ -634,74 +678,111 @@ PES_DEV bool fold_smoother_chunk(const KParams<T>& p, int64_t a, int64_t e, int 
 
 // Smoothing, level 5: Rauch-Tung-Striebel re-run backwards from the Gaussian of
 // the state after the chunk: x_k ~ E_k (x_{k+1} - xr_k) + g_k with covariance
-// E P E^T + L (a last state has E = 0). In MODE_RUN the elements were stored by
-// the filtering re-run and the smoothed moments replace the nominal in place;
-// in MODE_SMOOTH the elements are rebuilt from the given filtered moments.
+// E P E^T + L (a last state has E = 0). In MODE_RUN the stored elements (or
+// the stored filtered moments, from which the elements are rebuilt) arrive
+// through a warp stream and the smoothed moments replace the nominal in
+// place; in MODE_SMOOTH the elements are rebuilt from the given arrays.
 template <typename T, int LIN>
 PES_DEV bool rts_chunk(const KParams<T>& p, int64_t a, int64_t e, int lane, const Gauss<T>& G, bool write_P,
-                       bool want_norm, double* conv, int& nb, double& num, double& den)
+                       bool want_norm, double* conv, int& nb, double& num, double& den, T* wstage, uint64_t* wbar,
+                       uint32_t& wpar)
 {
     bool ok = true;
-    if (a >= e) return ok;
+    const bool any = a < e;
     SegCursor cur;
-    cur.init(p.offsets, p.B, e - 1);
+    if (any) cur.init(p.offsets, p.B, e - 1);
     Gauss<T> s = G;
-    const bool stored = (p.mode == MODE_RUN) && kStoreElements<LIN>;
-    SElem<T> ec, en;
-    if (stored) load_selem(p, (int)(e - 1 - a), lane, ec);
-#pragma unroll 1
-    for (int64_t k = e - 1; k >= a; --k) {
-        cur.backward(k);
+    const bool run = (p.mode == MODE_RUN);
+    const bool stored = run && kStoreElements<LIN>;
+    const T* wbase = p.hand + (size_t)(lane >> 5) * p.L * (HAND * 32);
+    WarpStream<T, HAND, HAND> we;   // stored smoothing elements
+    WarpStream<T, 20, HAND> wx;     // stored filtered moments
+    if (run) {
         if (stored) {
-            if (k > a) load_selem(p, (int)(k - 1 - a), lane, en);
+            we.init(wbase, wstage, wbar, wpar);
+            we.issue(p.L - 1, 0);
         } else {
-            T m[5], P[15];
-            if (p.mode == MODE_RUN) load_xP(p, (int)(k - a), lane, m, P);
-            else load_filtered(p, k, m, P);
-            if (cur.is_tail(k)) {
-                selem_last(ec, m, P);
+            wx.init(wbase, wstage, wbar, wpar);
+            wx.issue(p.L - 1, 0);
+        }
+    }
+#pragma unroll 1
+    for (int it = 0; it < p.L; ++it) {
+        const int sidx = p.L - 1 - it;
+        const int64_t k = a + sidx;
+        const int st = it & 1;
+        if (run) {
+            if (stored) {
+                if (it + 1 < p.L) we.issue(sidx - 1, st ^ 1);
+                we.wait(st, p.status);
             } else {
-                Trans<T> tr;
-                ok &= get_trans<T, LIN>(p, k, state_ix(p, k, a, lane), tr);
-                T mp[5], FP[25], Pp[15];
-                predict(tr, m, P, mp, FP, Pp);
-                ok &= selem_from_prediction(m, P, FP, Pp, mp, ec);
+                if (it + 1 < p.L) wx.issue(sidx - 1, st ^ 1);
+                wx.wait(st, p.status);
             }
         }
-        apply_smoother(ec, s, s);
-        const int64_t ix = state_ix(p, k, a, lane);
-        T xold[5];
-        if (want_norm) load_nominal(p, ix, xold);
-        bool finite = true;
+        if (k < e) {
+            cur.backward(k);
+            SElem<T> ec;
+            if (stored) {
+                T* dst = reinterpret_cast<T*>(&ec);
 #pragma unroll
-        for (int i = 0; i < 5; ++i) {
-            finite = finite && isfinite(s.m[i]);
-            p.x[i * p.cs + ix] = s.m[i];
-        }
-        if (!finite) atomicOr(p.status, ST_NONFINITE);
-        if (write_P) {
+                for (int c = 0; c < HAND; ++c) dst[c] = we.get(st, c);
+            } else {
+                T m[5], P[15];
+                if (run) {
 #pragma unroll
-            for (int i = 0; i < 15; ++i) p.P[i * p.cs + ix] = s.P[i];
-        }
-        if (want_norm) {
-            if (cur.b != nb) {
-                if (nb >= 0) {
-                    atomicAdd(conv + 2 * nb, num);
-                    atomicAdd(conv + 2 * nb + 1, den);
+                    for (int c = 0; c < 5; ++c) m[c] = wx.get(st, c);
+#pragma unroll
+                    for (int c = 0; c < 15; ++c) P[c] = wx.get(st, 5 + c);
+                } else {
+                    load_filtered(p, k, m, P);
                 }
-                nb = cur.b;
-                num = 0.0;
-                den = 0.0;
+                if (cur.is_tail(k)) {
+                    selem_last(ec, m, P);
+                } else {
+                    Trans<T> tr;
+                    ok &= get_trans<T, LIN>(p, k, state_ix(p, k, a, lane), tr);
+                    T mp[5], FP[25], Pp[15];
+                    predict(tr, m, P, mp, FP, Pp);
+                    ok &= selem_from_prediction(m, P, FP, Pp, mp, ec);
+                }
             }
+            apply_smoother(ec, s, s);
+            const int64_t ix = state_ix(p, k, a, lane);
+            T xold[5];
+            if (want_norm) load_nominal(p, ix, xold);
+            bool finite = true;
 #pragma unroll
             for (int i = 0; i < 5; ++i) {
-                const double dv = double(s.m[i]) - double(xold[i]);
-                num += dv * dv;
-                den += double(s.m[i]) * double(s.m[i]);
+                finite = finite && isfinite(s.m[i]);
+                p.x[i * p.cs + ix] = s.m[i];
+            }
+            if (!finite) atomicOr(p.status, ST_NONFINITE);
+            if (write_P) {
+#pragma unroll
+                for (int i = 0; i < 15; ++i) p.P[i * p.cs + ix] = s.P[i];
+            }
+            if (want_norm) {
+                if (cur.b != nb) {
+                    if (nb >= 0) {
+                        atomicAdd(conv + 2 * nb, num);
+                        atomicAdd(conv + 2 * nb + 1, den);
+                    }
+                    nb = cur.b;
+                    num = 0.0;
+                    den = 0.0;
+                }
+#pragma unroll
+                for (int i = 0; i < 5; ++i) {
+                    const double dv = double(s.m[i]) - double(xold[i]);
+                    num += dv * dv;
+                    den += double(s.m[i]) * double(s.m[i]);
+                }
             }
         }
-        if (stored) ec = en;
+        if (run) __syncwarp();
     }
+    if (run) wpar = stored ? we.parity : wx.parity;
     return ok;
 }
 
@@ -842,7 +923,9 @@ template <int NT>
 constexpr size_t smem_bytes_for(size_t scalar)
 {
     // lane tree (filtering elements; smoothing elements alias it), top-level
-    // buffer, down-sweep Gaussians, one block Gaussian
+    // buffer, down-sweep Gaussians, one block Gaussian; the per-warp stream
+    // stages (2 x LINS x 32 scalars per warp) reuse this memory
+    static_assert(size_t(NT) * FE * 2 + size_t(NT) * GE + GE >= size_t(NT) * 2 * LINS, "stream stages must fit");
     return scalar * (size_t(NT) * FE * 2 + size_t(NT) * GE + GE);
 }
 
@@ -858,6 +941,17 @@ __global__ void __launch_bounds__(NT, 1) pes_persistent_kernel(const KParams<T> 
     Gauss<T>* gblock = gs + NT;
     __shared__ int s_flag;
     __shared__ double s_red[NT];
+    // per-warp stream stages reuse the tree memory during the sequential passes
+    __shared__ __align__(8) uint64_t s_bar[2 * (NT / 32)];
+    T* wstage = reinterpret_cast<T*>(smem_raw) + (size_t)(threadIdx.x >> 5) * 2 * LINS * 32;
+    uint64_t* wbar = s_bar + 2 * (threadIdx.x >> 5);
+    uint32_t wpar = 0;
+    if ((threadIdx.x & 31) == 0) {
+        mbar_init(wbar, 1);
+        mbar_init(wbar + 1, 1);
+    }
+    mbar_init_fence();
+    __syncthreads();
 
     const int t = threadIdx.x;
     const int lane = blockIdx.x * NT + t;
@@ -884,7 +978,8 @@ __global__ void __launch_bounds__(NT, 1) pes_persistent_kernel(const KParams<T> 
             elemF[t] = acc;
             Gauss<T> G;
             filter_block_scan<T, NT>(p, elemF, topF, gs, gblock, gen, G, it);
-            ok &= rerun_filter_chunk<T, LIN>(p, a, e, lane, G, accS);
+            ok &= rerun_filter_chunk<T, LIN>(p, a, e, lane, G, accS, wstage, wbar, wpar);
+            __syncthreads();   // the stream stages overlap the smoothing lane tree
             PES_PHASE(p, it, 6);
             if (track && blockIdx.x == 0) {
                 // the accumulators of the next iteration were last read before
@@ -903,7 +998,7 @@ __global__ void __launch_bounds__(NT, 1) pes_persistent_kernel(const KParams<T> 
             int nb = -1;
             double num = 0.0, den = 0.0;
             double* conv = p.conv + (size_t)(it & 1) * 2 * p.B;
-            ok &= rts_chunk<T, LIN>(p, a, e, lane, Gs, write_P, track, conv, nb, num, den);
+            ok &= rts_chunk<T, LIN>(p, a, e, lane, Gs, write_P, track, conv, nb, num, den, wstage, wbar, wpar);
             __syncthreads();
             PES_PHASE(p, it, 12);
             if (track && nb >= 0) {
