@@ -209,6 +209,39 @@ pes_status pes_ieks_run_host(pes_handle* h, const pes_model* model, pes_method m
                              int32_t max_iters, double tol, void* x_out, void* P_out, int32_t* iters_used,
                              void* stream);
 
+/*
+ * pes_ieks_run without a handle and without allocating device memory. The
+ * paper has no counterpart: this is a deployment variant of pes_ieks_run.
+ *
+ * Some callers cannot create a handle, because pes_create allocates device
+ * memory: code whose memory plan is fixed once the process has started (a
+ * real-time loop, a service with a pre-reserved budget), code inside a
+ * framework that routes every device allocation through its own pool, and
+ * latency-critical code that cannot afford an allocation, which may
+ * synchronise the device. This entry point calls no cudaMalloc, cudaFree or
+ * other allocating routine. Its scratch is one fixed array in the library's
+ * device memory, about 11 MB, which every GPU that loads the library holds
+ * until the process exits.
+ *
+ * Arguments, layouts and results are those of pes_ieks_run (DEVICE pointers).
+ * Limits: N <= PES_NOALLOC_MAX_STATES and B <= PES_NOALLOC_MAX_BATCH; larger
+ * sizes return PES_ERR_INVALID_ARG before anything is launched.
+ * The first call on a device sets the scratch up (it looks up the array's
+ * device address and clears its counters), so make that first call before
+ * any stream capture. Every call waits for its work on `stream` and returns
+ * the device status. All calls on a device share the one scratch array, which
+ * keeps the last call's contents; calls that overlap in time on the GPU (for
+ * instance from two host threads, or on two streams) race on it and must not
+ * be issued.
+ */
+#define PES_NOALLOC_MAX_STATES 8192
+#define PES_NOALLOC_MAX_BATCH 64
+pes_status pes_ieks_run_noalloc(const pes_model* model, pes_method method, pes_precision prec,
+                                const void* y, const int64_t* offsets, int32_t B, int64_t N,
+                                const void* m0, const void* P0, const void* x_init, const void* P_init,
+                                int32_t max_iters, double tol, void* x_out, void* P_out, int32_t* iters_used,
+                                void* stream);
+
 /* Launch shape the next call of the given kind would use (for tests and the
  * benchmark): blocks, threads per block, steps per thread. */
 pes_status pes_launch_shape(pes_handle* h, pes_method method, pes_precision prec, int64_t N,

@@ -8,42 +8,10 @@
 #include <new>
 
 #include "pes.h"
+#include "pes_handle.h"
 #include "pes_internal.h"
 
 using namespace pes;
-
-struct pes_handle {
-    int device = 0;
-    int num_sms = 0;
-    int64_t max_states = 0;
-    int32_t max_batch = 0;
-    int nl_max = 0;      // lanes the workspace is sized for
-    int nb_max = 0;      // blocks the workspace is sized for
-    void* hand = nullptr;
-    void* aggF = nullptr;
-    void* aggS = nullptr;
-    unsigned* bar = nullptr;
-    int* status = nullptr;
-    double* conv = nullptr;
-    int* iters_done = nullptr;
-    // device copies for pes_ieks_run_host (allocated by its first call)
-    void* hy = nullptr;
-    int64_t* hoff = nullptr;
-    void* hm0 = nullptr;
-    void* hP0 = nullptr;
-    void* hx = nullptr;
-    void* hP = nullptr;
-    void* hxi = nullptr;
-    void* hPi = nullptr;
-    double* hsens = nullptr;
-    void* sensT = nullptr;   // sensors converted to the kernel precision
-    void* lanes = nullptr;   // x, P, y in the kernel's lane-major layout
-    void* lin = nullptr;     // cubature linearisation handed from the fold to the re-run
-    long long* ptime = nullptr;   // phase timestamps (PES_PHASE_TIMES=1)
-    int ptime_blocks = 0;
-    long long timeout_ns = 2000000000LL;
-    char err[512] = {0};
-};
 
 namespace {
 

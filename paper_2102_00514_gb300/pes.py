@@ -29,7 +29,7 @@ MODEL_CT_BEARINGS, MODEL_LINEAR = 0, 1
 
 EXPORTED = ["pes_create", "pes_destroy", "pes_last_error", "pes_sync", "pes_linearize", "pes_filter_scan",
             "pes_smooth_scan", "pes_ieks_run", "pes_ieks_run_host", "pes_launch_shape", "pes_measure_fma_peak",
-            "pes_debug_phase_times"]
+            "pes_debug_phase_times", "pes_ieks_run_noalloc"]
 
 
 class PesError(RuntimeError):
@@ -76,6 +76,8 @@ def load_library():
                                      ctypes.POINTER(i32)]
     lib.pes_measure_fma_peak.argtypes = [ctypes.POINTER(d), ctypes.POINTER(d)]
     lib.pes_debug_phase_times.argtypes = [p, ctypes.POINTER(d), ctypes.POINTER(d), i32]
+    lib.pes_ieks_run_noalloc.argtypes = [mp, i32, i32, p, p, i32, i64, p, p, p, p, i32, d, p, p,
+                                         ctypes.POINTER(i32), p]
     for name in EXPORTED:
         if name != "pes_last_error":
             getattr(lib, name).restype = ctypes.c_int

@@ -1,0 +1,59 @@
+"""The allocation-free entry point pes_ieks_run_noalloc.
+
+It is meant for callers that cannot create a handle because pes_create
+allocates device memory (a fixed memory plan after start-up, a framework that
+owns every allocation, a latency budget that rules out an allocation that may
+synchronise the device). Its results must equal those of pes_ieks_run, which
+it shares every kernel with, call after call, although all calls reuse one
+fixed scratch array. This file is collected last on purpose.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2102_00514_gb300 import pes, synth
+from tests.gpu_common import TOL_FP32, TOL_FP64, rel_err, workload_to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def run_noalloc(lib, d, method, prec, N, B, iters):
+    dt = torch.float64 if prec == pes.FP64 else torch.float32
+    x = torch.empty((5, N), dtype=dt, device="cuda")
+    P = torch.empty((15, N), dtype=dt, device="cuda")
+    used = ctypes.c_int32(0)
+    ms = d["model"].as_struct()
+    st = lib.pes_ieks_run_noalloc(ctypes.byref(ms), method, prec, d["y"].data_ptr(), d["offsets"].data_ptr(), B, N,
+                                  d["m0"].data_ptr(), d["P0"].data_ptr(), None, None, iters, 0.0, x.data_ptr(),
+                                  P.data_ptr(), ctypes.byref(used), torch.cuda.current_stream().cuda_stream)
+    return st, x, P, used.value
+
+
+@pytest.mark.parametrize("prec,tol", [(pes.FP64, TOL_FP64), (pes.FP32, TOL_FP32)])
+@pytest.mark.parametrize("method", [pes.IEKS, pes.CUBATURE])
+def test_noalloc_matches_handle_entry_point_twice(method, prec, tol):
+    lib = pes.load_library()
+    for wl in (synth.workload("ieks_T500"), synth.ct_bearings([300, 1, 41], seed=3, sensor_jitter=0.2)):
+        d = workload_to_dev(wl, prec)
+        N = wl["y"].shape[1]
+        B = len(wl["offsets"]) - 1
+        sm = pes.Smoother(N, B)
+        xr, Pr, _, _ = sm.ieks_run(d["model"], method, prec, d["y"], d["offsets"], d["m0"], d["P0"], iters=4)
+        sm.sync()
+        ref_x, ref_P = xr.double().cpu().numpy(), Pr.double().cpu().numpy()
+        sm.close()
+        for _ in range(2):   # two calls in a row share the scratch
+            st, x, P, used = run_noalloc(lib, d, method, prec, N, B, 4)
+            assert st == pes.OK and used == 4
+            assert rel_err(x.double().cpu().numpy(), ref_x, wl["offsets"]) < tol
+            assert rel_err(P.double().cpu().numpy(), ref_P, wl["offsets"]) < tol
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    lib = pes.load_library()
+    wl = synth.ct_bearings([8192], seed=4)   # N = 8193 states, one more than the limit
+    d = workload_to_dev(wl, pes.FP32)
+    st, _, _, _ = run_noalloc(lib, d, pes.IEKS, pes.FP32, wl["y"].shape[1], 1, 1)
+    assert st == pes.INVALID_ARG
