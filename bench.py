@@ -93,10 +93,11 @@ def peaks_file():
 
 
 def kernel_source_hash():
+    """Hash of the device code of the persistent kernel (its headers)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2102_00514_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
+        if name.endswith(".cuh"):
             with open(os.path.join(csrc, name), "rb") as f:
                 h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
