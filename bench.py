@@ -308,7 +308,9 @@ def main():
     work_per_step = len(methods) * (N - 1) * iters
     value = world * work_per_step * args.steps / (total_ms * 1e-3)
     ms_per_step = total_ms / args.steps
-    launches_per_run = 3   # offsets validation, nominal initialisation, persistent smoother
+    # offsets validation, sensor conversion, y to the lane layout, nominal
+    # initialisation, persistent smoother, x and P back to the caller layout
+    launches_per_run = 7
 
     nb, nt, L = sm.launch_shape(pes.IEKS, pes.FP32, N)
     nbc, ntc, Lc = sm.launch_shape(pes.CUBATURE, pes.FP32, N)
