@@ -394,49 +394,58 @@ PES_DEV void load_lin_trans(const KParams<T>& p, int s, int lane, Trans<T>& tr)
     for (int i = 0; i < 15; ++i) tr.Q[i] = h[(50 + i) * 32];
 }
 
-// Filtering, level 1: fold the lane's chunk [a, e) into one element.
+// Filtering, level 1: fold the lane's chunk [a, e) into one element. Each step
+// linearises its own incoming transition (k-1 -> k, about the nominal of k-1)
+// and its observation, so no linearisation is carried from step to step.
+// With a stored linearisation (MODE_RUN, cubature) both are kept for the
+// re-run; the transition into the chunk's first state goes into the previous
+// lane's slot, where the previous lane's re-run looks for it.
 template <typename T, int LIN>
 PES_DEV bool fold_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int lane, FElem<T>& acc)
 {
     bool ok = true;
     T zero[5] = {T(0), T(0), T(0), T(0), T(0)};
-    if (a >= e) {
-        felem_identity(acc, zero);
-        return ok;
-    }
+    felem_identity(acc, zero);
+    if (a >= e) return ok;
+    const bool store_lin = kStoreLin<LIN> && p.mode == MODE_RUN;
     SegCursor cur;
     cur.init(p.offsets, p.B, a);
-    Trans<T> tr;
-    if (!cur.is_head(a)) {
-        ok &= get_trans<T, LIN>(p, a - 1, prev_ix(p, a, lane), tr);
-        felem_identity(acc, tr.xn);
-    } else {
-        felem_identity(acc, zero);
-    }
     const int64_t dix = p.lanes_layout ? p.NL : 1;
     int64_t ix = state_ix(p, a, a, lane);
-    StateIn<T, LIN> sc, sn;
+    StateIn<T, LIN> sp, sc, sn;   // inputs of states k-1, k, k+1
+    if (!cur.is_head(a)) load_state(p, prev_ix(p, a, lane), sp);
     load_state(p, ix, sc);
 #pragma unroll 1
     for (int64_t k = a; k < e; ++k, ix += dix) {
         cur.forward(k);
+        const int s = (int)(k - a);
         if (k + 1 < e) load_state(p, ix + dix, sn);
-        Factor<T, LIN> f;
-        ok &= factor_state(sc, f);
         if (cur.is_head(k)) {
             T m0[5], P0[15];
             load_prior(p, cur.b, m0, P0);
             felem_apply_prior(acc, m0, P0);
         } else {
+            Trans<T> tr;
+            {
+                Factor<T, LIN> fp;
+                ok &= factor_state(sp, fp);
+                lin_trans(p, k - 1, sp, fp, tr);
+            }
+            if (store_lin) {
+                if (s == 0) store_lin_trans(p, p.L - 1, lane - 1, tr);
+                else store_lin_trans(p, s - 1, lane, tr);
+            }
+            if (s == 0) felem_identity(acc, tr.xn);
             Obs<T> ob;
-            lin_obs(p, k, cur.b, sc, f, ob);
+            {
+                Factor<T, LIN> fc;
+                ok &= factor_state(sc, fc);
+                lin_obs(p, k, cur.b, sc, fc, ob);
+            }
+            if (store_lin) store_lin_obs(p, s, lane, ob);
             ok &= fold_filter_step(acc, tr, ob);
-            if (kStoreLin<LIN> && p.mode == MODE_RUN) store_lin_obs(p, (int)(k - a), lane, ob);
         }
-        if (!cur.is_tail(k) && (k + 1 < e || (kStoreLin<LIN> && p.mode == MODE_RUN))) {
-            lin_trans(p, k, sc, f, tr);
-            if (kStoreLin<LIN> && p.mode == MODE_RUN) store_lin_trans(p, (int)(k - a), lane, tr);
-        }
+        sp = sc;
         sc = sn;
     }
     return ok;
@@ -549,7 +558,9 @@ PES_DEV void trans_from_stage(const S& ws, int i, Trans<T>& tr)
 // storing filtered moments; in MODE_RUN also build and fold the chunk's
 // smoothing elements (Eqs. 17-18) into accS. The loop runs over the L steps
 // of the chunk in every lane of the warp (lanes whose chunk is shorter idle),
-// so that a warp stream can feed it the stored linearisation.
+// so that a warp stream can feed it the stored linearisation: step s reads
+// the transition into state s from the previous step's stage, then releases
+// that stage for the copy of step s + 1, then reads its observation.
 template <typename T, int LIN>
 PES_DEV bool rerun_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int lane, const Gauss<T>& G,
                                 SElem<T>& accS, T* wstage, uint64_t* wbar, uint32_t& wpar)
@@ -558,7 +569,6 @@ PES_DEV bool rerun_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int l
     selem_identity(accS);
     const bool smooth = (p.mode == MODE_RUN);
     const bool any = a < e;
-    // with a stored linearisation the re-run reads it instead of linearising
     constexpr bool stored_lin = kStoreLin<LIN>;
     const bool use_lin = stored_lin && smooth;
     SegCursor cur;
@@ -568,15 +578,13 @@ PES_DEV bool rerun_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int l
     for (int i = 0; i < 5; ++i) m[i] = G.m[i];
 #pragma unroll
     for (int i = 0; i < 15; ++i) P[i] = G.P[i];
-    Trans<T> tr;
-    if (any && !cur.is_head(a)) {
-        if (use_lin) load_lin_trans(p, p.L - 1, lane - 1, tr);
-        else ok &= get_trans<T, LIN>(p, a - 1, prev_ix(p, a, lane), tr);
-    }
     const int64_t dix = p.lanes_layout ? p.NL : 1;
     int64_t ix = state_ix(p, a, a, lane);
-    StateIn<T, LIN> sc, sn;
-    if (!use_lin && any) load_state(p, ix, sc);
+    StateIn<T, LIN> sp, sc, sn;   // inputs of states k-1, k, k+1 (when linearising here)
+    if (!use_lin && any) {
+        if (!cur.is_head(a)) load_state(p, prev_ix(p, a, lane), sp);
+        load_state(p, ix, sc);
+    }
     WarpStream<T, LINS, LINS> ws;
     if (use_lin) {
         ws.init(p.lin + (size_t)(lane >> 5) * p.L * (LINS * 32), wstage, wbar, wpar);
@@ -585,57 +593,84 @@ PES_DEV bool rerun_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int l
 #pragma unroll 1
     for (int s = 0; s < p.L; ++s, ix += dix) {
         const int64_t k = a + s;
-        if (use_lin) {
-            if (s + 1 < p.L) ws.issue(s + 1, (s + 1) & 1);
-            ws.wait(s & 1, p.status);
-        }
-        if (k < e) {
+        const bool act = k < e;
+        if (use_lin) ws.wait(s & 1, p.status);
+        T mp[5], Pp[15];
+        bool head = false;
+        if (act) {
             cur.forward(k);
             if (!use_lin && k + 1 < e) load_state(p, ix + dix, sn);
-            Factor<T, LIN> f;
-            if (!use_lin) ok &= factor_state(sc, f);
-            if (cur.is_head(k)) {
+            head = cur.is_head(k);
+            if (head) {
                 if (smooth && k > a) {
                     SElem<T> el;
                     selem_last(el, m, P);
                     combine_smoother(accS, el, accS);
                     if (kStoreElements<LIN>) store_selem(p, s - 1, lane, el);
                 }
+            } else {
+                Trans<T> tr;
+                if (use_lin) {
+                    if (s == 0) load_lin_trans(p, p.L - 1, lane - 1, tr);
+                    else trans_from_stage<T>(ws, (s - 1) & 1, tr);
+                } else {
+                    Factor<T, LIN> fp;
+                    ok &= factor_state(sp, fp);
+                    lin_trans(p, k - 1, sp, fp, tr);
+                }
+                T FP[25];
+                predict(tr, m, P, mp, FP, Pp);
+                if (smooth && k > a) {
+                    SElem<T> el;
+                    ok &= selem_from_prediction(m, P, FP, Pp, mp, el);
+                    combine_smoother(accS, el, accS);
+                    if (kStoreElements<LIN>) store_selem(p, s - 1, lane, el);
+                }
+            }
+        }
+        if (use_lin) {
+            // every lane is done with the previous step's stage: refill it
+            __syncwarp();
+            if (s + 1 < p.L) ws.issue(s + 1, (s + 1) & 1);
+        }
+        if (act) {
+            if (head) {
                 load_prior(p, cur.b, m, P);
             } else {
-                T mp[5], Pp[15];
-                {
-                    T FP[25];
-                    predict(tr, m, P, mp, FP, Pp);
-                    if (smooth && k > a) {
-                        SElem<T> el;
-                        ok &= selem_from_prediction(m, P, FP, Pp, mp, el);
-                        combine_smoother(accS, el, accS);
-                        if (kStoreElements<LIN>) store_selem(p, s - 1, lane, el);
-                    }
-                }
                 Obs<T> ob;
-                if (use_lin) obs_from_stage<T>(ws, s & 1, ob);
-                else lin_obs(p, k, cur.b, sc, f, ob);
+                if (use_lin) {
+                    obs_from_stage<T>(ws, s & 1, ob);
+                } else {
+                    Factor<T, LIN> fc;
+                    ok &= factor_state(sc, fc);
+                    lin_obs(p, k, cur.b, sc, fc, ob);
+                }
                 ok &= kf_update(ob, mp, Pp, m, P);
             }
             if (!smooth) store_filtered(p, k, m, P);
             else if (!kStoreElements<LIN>) store_xP(p, s, lane, m, P);
-            if (!cur.is_tail(k) && (k + 1 < e || smooth)) {
-                if (use_lin) trans_from_stage<T>(ws, s & 1, tr);
-                else lin_trans(p, k, sc, f, tr);
+            if (!use_lin) {
+                sp = sc;
+                sc = sn;
             }
-            if (!use_lin) sc = sn;
         }
-        if (use_lin) __syncwarp();
     }
     if (use_lin) wpar = ws.parity;
     if (smooth && any) {
-        // smoothing element of the chunk's last state
+        // smoothing element of the chunk's last state: the transition out of the
+        // chunk is linearised about the last state's nominal
         SElem<T> el;
         if (cur.is_tail(e - 1)) {
             selem_last(el, m, P);
         } else {
+            Trans<T> tr;
+            if (use_lin) {
+                trans_from_stage<T>(ws, (p.L - 1) & 1, tr);
+            } else {
+                Factor<T, LIN> fp;
+                ok &= factor_state(sp, fp);
+                lin_trans(p, e - 1, sp, fp, tr);
+            }
             T mp[5], FP[25], Pp[15];
             predict(tr, m, P, mp, FP, Pp);
             ok &= selem_from_prediction(m, P, FP, Pp, mp, el);
