@@ -233,9 +233,14 @@ PES_DEV void lin_obs_taylor(const DevModel<T>& m, int b, const T* xn, const T* y
 // the second being positive semi-definite by construction. Deviations
 // Z - f(xbar) are formed directly (position increments, wrapped bearings).
 
-// Deviation of the transition: f(xbar + sg) - f(xbar).
+// Deviations of the transition for the pair of sigma points xbar +- sg:
+// zp = f(xbar + sg) - f(xbar), zm = f(xbar - sg) - f(xbar). For the
+// coordinated turn the two turn angles a +- d (a = omega dt, d = sg_omega dt)
+// come from one sincos of d by angle addition with the reference's (s, c);
+// 1 - cos is formed without cancellation. inc_ref = f(xbar) - [px, py, 0, 0, 0].
 template <typename T>
-PES_DEV void dev_f(const DevModel<T>& m, const T* xbar, const T* inc_ref, const T* sg, T* out)
+PES_DEV void dev_f_pair(const DevModel<T>& m, const T* xbar, const CTCoef<T>& kr, const T* inc_ref, const T* sg,
+                        T* zp, T* zm)
 {
     if (m.kind == MODEL_LINEAR) {
 #pragma unroll
@@ -243,26 +248,51 @@ PES_DEV void dev_f(const DevModel<T>& m, const T* xbar, const T* inc_ref, const 
             T s = T(0);
 #pragma unroll
             for (int l = 0; l < 5; ++l) s = fma(m.F[i * 5 + l], sg[l], s);
-            out[i] = s;
+            zp[i] = s;
+            zm[i] = -s;
         }
-    } else {
-        T x[5];
+        return;
+    }
+    const T dt = m.dt;
+    const T thr = sizeof(T) == 4 ? T(0.05) : T(0.01);
+    T sd, cd;
+    tsincos(sg[4] * dt, &sd, &cd);
+    const T omcd = sd * sd / (T(1) + cd);
+    const T omcr = (kr.c > T(0)) ? kr.s * kr.s / (T(1) + kr.c) : T(1) - kr.c;
 #pragma unroll
-        for (int i = 0; i < 5; ++i) x[i] = xbar[i] + sg[i];
-        const CTCoef<T> k = ct_coef(x[4], m.dt);
-        T inc[5];
-        ct_increment(x, k, inc);
-        out[0] = sg[0] + (inc[0] - inc_ref[0]);
-        out[1] = sg[1] + (inc[1] - inc_ref[1]);
-        out[2] = inc[2] - inc_ref[2];
-        out[3] = inc[3] - inc_ref[3];
-        out[4] = sg[4];
+    for (int sign = 0; sign < 2; ++sign) {
+        const T sgn = sign == 0 ? T(1) : T(-1);
+        const T w = xbar[4] + sgn * sg[4];
+        const T a = w * dt;
+        const T s = kr.s * cd + sgn * kr.c * sd;
+        const T c = kr.c * cd - sgn * kr.s * sd;
+        T A1, A2;
+        if (fabs(a) < thr) {
+            const T a2 = a * a;
+            A1 = dt * (T(1) - a2 * (T(1) / T(6)) + a2 * a2 * (T(1) / T(120)));
+            A2 = dt * a * (T(0.5) - a2 * (T(1) / T(24)) + a2 * a2 * (T(1) / T(720)));
+        } else {
+            const T omc = omcr + kr.c * omcd + sgn * kr.s * sd;
+            const T iw = T(1) / w;
+            A1 = s * iw;
+            A2 = omc * iw;
+        }
+        const T vx = xbar[2] + sgn * sg[2], vy = xbar[3] + sgn * sg[3];
+        T* z = sign == 0 ? zp : zm;
+        z[0] = sgn * sg[0] + ((A1 * vx - A2 * vy) - inc_ref[0]);
+        z[1] = sgn * sg[1] + ((A2 * vx + A1 * vy) - inc_ref[1]);
+        z[2] = (c * vx - s * vy) - inc_ref[2];
+        z[3] = (s * vx + c * vy) - inc_ref[3];
+        z[4] = sgn * sg[4];
     }
 }
 
-// Deviation of the observation: h(xbar + sg) - h(xbar), bearings wrapped.
+// Deviation of the observation for the pair xbar +- sg. For bearings the angle
+// from the reference direction r = p - s to r +- sg_p is
+// atan2(+-(r x sg_p), |r|^2 +- r . sg_p): already the branch nearest h(xbar),
+// and free of cancellation for small deviations.
 template <typename T>
-PES_DEV void dev_h(const DevModel<T>& m, const T* xbar, const T* s, const T* h_ref, const T* sg, T* out)
+PES_DEV void dev_h_pair(const DevModel<T>& m, const T* xbar, const T* s, const T* sg, T* zp, T* zm)
 {
     if (m.kind == MODEL_LINEAR) {
 #pragma unroll
@@ -270,16 +300,19 @@ PES_DEV void dev_h(const DevModel<T>& m, const T* xbar, const T* s, const T* h_r
             T v = T(0);
 #pragma unroll
             for (int l = 0; l < 5; ++l) v = fma(m.H[r * 5 + l], sg[l], v);
-            out[r] = v;
+            zp[r] = v;
+            zm[r] = -v;
         }
-    } else {
-        T x[5];
+        return;
+    }
 #pragma unroll
-        for (int i = 0; i < 5; ++i) x[i] = xbar[i] + sg[i];
-        T hz[2];
-        bearings(x, s, hz);
-        out[0] = wrap_angle(hz[0] - h_ref[0]);
-        out[1] = wrap_angle(hz[1] - h_ref[1]);
+    for (int r = 0; r < 2; ++r) {
+        const T rx = xbar[0] - s[2 * r], ry = xbar[1] - s[2 * r + 1];
+        const T cross = rx * sg[1] - ry * sg[0];
+        const T rr = rx * rx + ry * ry;
+        const T rs = rx * sg[0] + ry * sg[1];
+        zp[r] = tatan2(cross, rr + rs);
+        zm[r] = tatan2(-cross, rr - rs);
     }
 }
 
@@ -310,12 +343,14 @@ PES_DEV void lin_trans_cubature(const DevModel<T>& m, const T* xbar, const T* L,
 {
     const T sq = tsqrt(T(NX));
     T inc_ref[5];
+    CTCoef<T> kr;
     if (m.kind == MODEL_LINEAR) {
 #pragma unroll
         for (int i = 0; i < 5; ++i) inc_ref[i] = T(0);
+        kr.s = kr.c = kr.A1 = kr.A2 = kr.dA1 = kr.dA2 = T(0);
     } else {
-        const CTCoef<T> k = ct_coef(xbar[4], m.dt);
-        ct_increment(xbar, k, inc_ref);
+        kr = ct_coef(xbar[4], m.dt);
+        ct_increment(xbar, kr, inc_ref);
     }
     T Dm[25];       // columns D_i (row-major: Dm[r*5 + i])
     T U[25];        // columns u_i + zdev (before centring)
@@ -325,10 +360,7 @@ PES_DEV void lin_trans_cubature(const DevModel<T>& m, const T* xbar, const T* L,
         T sg[5], zp[5], zm[5];
 #pragma unroll
         for (int r = 0; r < 5; ++r) sg[r] = sq * L[r * NX + i];
-        dev_f(m, xbar, inc_ref, sg, zp);
-#pragma unroll
-        for (int r = 0; r < 5; ++r) sg[r] = -sg[r];
-        dev_f(m, xbar, inc_ref, sg, zm);
+        dev_f_pair(m, xbar, kr, inc_ref, sg, zp, zm);
 #pragma unroll
         for (int r = 0; r < 5; ++r) {
             Dm[r * NX + i] = zp[r] - zm[r];
@@ -385,7 +417,8 @@ PES_DEV void lin_obs_cubature(const DevModel<T>& m, int b, const T* xbar, const 
     const T sq = tsqrt(T(NX));
     T s[4] = {T(0), T(0), T(0), T(0)};
     T h_ref[2];
-    if (m.kind == MODEL_LINEAR) {
+    const bool lin = (m.kind == MODEL_LINEAR);
+    if (lin) {
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             T v = m.d[r];
@@ -401,13 +434,15 @@ PES_DEV void lin_obs_cubature(const DevModel<T>& m, int b, const T* xbar, const 
     T zdev[2] = {T(0), T(0)};
 #pragma unroll
     for (int i = 0; i < NX; ++i) {
-        T sg[5], zp[2], zm[2];
+        T zp[2] = {T(0), T(0)}, zm[2] = {T(0), T(0)};
+        // bearings see only the position; chol(Pbar) is lower triangular, so
+        // sigma directions i >= 2 leave the position (and the bearing) unchanged
+        if (lin || i < 2) {
+            T sg[5];
 #pragma unroll
-        for (int r = 0; r < 5; ++r) sg[r] = sq * L[r * NX + i];
-        dev_h(m, xbar, s, h_ref, sg, zp);
-#pragma unroll
-        for (int r = 0; r < 5; ++r) sg[r] = -sg[r];
-        dev_h(m, xbar, s, h_ref, sg, zm);
+            for (int r = 0; r < 5; ++r) sg[r] = sq * L[r * NX + i];
+            dev_h_pair(m, xbar, s, sg, zp, zm);
+        }
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             Dm[r * NX + i] = zp[r] - zm[r];
@@ -436,7 +471,7 @@ PES_DEV void lin_obs_cubature(const DevModel<T>& m, int b, const T* xbar, const 
             ob.R[si2(r, q)] = m.R[si2(r, q)] + v * (T(1) / T(NX));
         }
     // residual about zbar = h(xbar) + zdev, measurement unwrapped nearest h(xbar)
-    if (m.kind == MODEL_LINEAR) {
+    if (lin) {
         ob.r[0] = y[0] - h_ref[0] - zdev[0];
         ob.r[1] = y[1] - h_ref[1] - zdev[1];
     } else {
