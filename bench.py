@@ -52,6 +52,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 17, help="states in the oracle's timed sample")
     ap.add_argument("--profile", choices=["ieks", "cubature"], default=None,
                     help="profiling case: only `warmup` + 1 FP32 runs of one method, no JSON line")
@@ -382,6 +383,26 @@ def main():
         x32[name] = (x.double().cpu().numpy(), P.double().cpu().numpy())
     sm.sync()
 
+    # PES_MIXED: the first iters-1 iterations in FP32, the final one in FP64
+    xmix = {}
+    if not args.no_mixed:
+        run_step(d32, pes.MIXED)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in methods]
+        flush.zero_()
+        run_step(d32, pes.MIXED, ev)
+        torch.cuda.synchronize()
+        per = [ev[i][0].elapsed_time(ev[i][1]) for i in range(len(methods))]
+        if rank == 0:
+            result["mixed"] = {"value": work_per_step / (sum(per) * 1e-3), "ms_per_step": sum(per),
+                               "per_method_ms": dict(zip([m for m, _ in methods], per)),
+                               "schedule": f"{iters - 1} FP32 iterations, then 1 FP64 iteration"}
+        for name, m in methods:
+            x, P, _, _ = sm.ieks_run(d32["model"], m, pes.MIXED, d32["y"], d32["offsets"], d32["m0"], d32["P0"],
+                                     iters=iters)
+            xmix[name] = (x.double().cpu().numpy(), P.double().cpu().numpy())
+        sm.sync()
+
     # end-to-end through the host-buffer entry point (copies inside the timed region)
     if not args.no_e2e:
         pin = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).pin_memory()
@@ -443,9 +464,15 @@ def main():
                 if not args.no_fp64:
                     par[name]["fp64_means"] = rel_err(x64[name][0], r["x"], wl["offsets"])
                     par[name]["fp64_covs"] = rel_err(x64[name][1], r["P"], wl["offsets"])
+                if name in xmix:
+                    par[name]["mixed_means"] = rel_err(xmix[name][0], r["x"], wl["offsets"])
+                    par[name]["mixed_covs"] = rel_err(xmix[name][1], r["P"], wl["offsets"])
             tol_ok = all(v["fp32_means"] <= 1e-4 and v["fp32_covs"] <= 1e-4 for v in par.values())
             result["parity"] = {"vs": "CPU FP64 oracle, full workload", "rel_frobenius": par,
                                 "fp32_tol": 1e-4, "fp64_tol": 1e-9, "fp32_within_tol": tol_ok}
+            if xmix:
+                result["parity"]["mixed_within_tol"] = all(v["mixed_means"] <= 1e-4 and v["mixed_covs"] <= 1e-4
+                                                           for v in par.values())
         print(json.dumps(result), flush=True)
     sm.close()
     if dist is not None:

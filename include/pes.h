@@ -36,7 +36,11 @@
  *
  * Precision. PES_FP64: every floating-point array is double. PES_FP32: every
  * floating-point array (except the model's sensors) is float.
- * PES_MIXED: not supported yet (returns PES_ERR_UNSUPPORTED).
+ * PES_MIXED (pes_ieks_run only; arrays are float): the first max_iters - 1
+ * iterations run in FP32, the final iteration — the one whose means and
+ * smoother covariances are returned — in FP64 from the FP32 nominal. Its first
+ * call on a handle allocates the FP64 copies (22 doubles per state). Other
+ * entry points return PES_ERR_UNSUPPORTED for PES_MIXED.
  *
  * Memory and ownership. Unless stated otherwise every pointer is DEVICE memory
  * owned by the caller and must stay valid until the work on `stream` has
@@ -223,8 +227,9 @@ pes_status pes_ieks_run_host(pes_handle* h, const pes_model* model, pes_method m
  * device memory, about 11 MB, which every GPU that loads the library holds
  * until the process exits.
  *
- * Arguments, layouts and results are those of pes_ieks_run (DEVICE pointers).
- * Limits: N <= PES_NOALLOC_MAX_STATES and B <= PES_NOALLOC_MAX_BATCH; larger
+ * Arguments, layouts and results are those of pes_ieks_run (DEVICE pointers),
+ * for PES_FP64 and PES_FP32; PES_MIXED, whose FP64 copies pes_ieks_run
+ * allocates, returns PES_ERR_UNSUPPORTED. Limits: N <= PES_NOALLOC_MAX_STATES and B <= PES_NOALLOC_MAX_BATCH; larger
  * sizes return PES_ERR_INVALID_ARG before anything is launched.
  * The first call on a device sets the scratch up (it looks up the array's
  * device address and clears its counters), so make that first call before

@@ -43,10 +43,12 @@ pes_status cuda_fail(pes_handle* h, cudaError_t e, const char* what)
 
 size_t scalar_size(pes_precision p) { return p == PES_FP64 ? sizeof(double) : sizeof(float); }
 
-pes_status check_common(pes_handle* h, pes_precision prec, const int64_t* offsets, int32_t B, int64_t N)
+pes_status check_common(pes_handle* h, pes_precision prec, const int64_t* offsets, int32_t B, int64_t N,
+                        bool allow_mixed = false)
 {
     if (!h) return PES_ERR_INVALID_ARG;
-    if (prec == PES_MIXED) return fail(h, PES_ERR_UNSUPPORTED, "PES_MIXED is not supported yet");
+    if (prec == PES_MIXED && !allow_mixed) return fail(h, PES_ERR_UNSUPPORTED, "PES_MIXED is only supported by pes_ieks_run");
+    if (prec == PES_MIXED) return check_common(h, PES_FP32, offsets, B, N);
     if (prec != PES_FP32 && prec != PES_FP64) return fail(h, PES_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
     if (!offsets) return fail(h, PES_ERR_INVALID_ARG, "offsets is NULL");
     if (B < 1) return fail(h, PES_ERR_INVALID_ARG, "B must be >= 1 (got %d)", (int)B);
@@ -284,6 +286,51 @@ static pes_status ieks_run_t(pes_handle* h, const pes_model* model, pes_method m
     return PES_OK;
 }
 
+// PES_MIXED: the first max_iters - 1 iterations in FP32, the last one (and so
+// the returned means and smoother covariances) in FP64 from the FP32 nominal.
+// Inputs and outputs are FP32 arrays; the FP64 copies live in h->mix.
+static pes_status ieks_run_mixed(pes_handle* h, const pes_model* model, pes_method method, const void* y,
+                                 const int64_t* offsets, int32_t B, int64_t N, const void* m0, const void* P0,
+                                 const void* x_init, const void* P_init, int32_t max_iters, double tol, void* x_out,
+                                 void* P_out, int32_t* iters_used, cudaStream_t st)
+{
+    if (!h->mix) {
+        const size_t need = sizeof(double) * (22 * (size_t)h->max_states + 20 * (size_t)h->max_batch);
+        PES_CUDA(h, cudaMalloc(&h->mix, need));
+    }
+    double* y64 = static_cast<double*>(h->mix);
+    double* x64 = y64 + 2 * N;
+    double* P64 = x64 + 5 * N;
+    double* m064 = P64 + 15 * N;
+    double* P064 = m064 + 5 * (size_t)B;
+    int32_t it32 = 0;
+    const bool cub = (method == PES_CUBATURE);
+    const void* xi32 = x_init;
+    const void* Pi32 = P_init;
+    if (max_iters > 1) {
+        pes_status r = ieks_run_t<float>(h, model, method, PES_FP32, y, offsets, B, N, m0, P0, x_init, P_init,
+                                         max_iters - 1, tol, x_out, P_out, &it32, st);
+        if (r != PES_OK && r != PES_ERR_NOT_CONVERGED) return r;
+        xi32 = x_out;
+        Pi32 = P_out;
+    }
+    PES_CUDA(h, (launch_convert_ff<float, double>((const float*)y, y64, 2 * N, st)));
+    PES_CUDA(h, (launch_convert_ff<float, double>((const float*)m0, m064, 5 * (int64_t)B, st)));
+    PES_CUDA(h, (launch_convert_ff<float, double>((const float*)P0, P064, 15 * (int64_t)B, st)));
+    if (xi32) PES_CUDA(h, (launch_convert_ff<float, double>((const float*)xi32, x64, 5 * N, st)));
+    if (cub && Pi32) PES_CUDA(h, (launch_convert_ff<float, double>((const float*)Pi32, P64, 15 * N, st)));
+    int32_t it64 = 0;
+    const pes_status r = ieks_run_t<double>(h, model, method, PES_FP64, y64, offsets, B, N, m064, P064,
+                                            xi32 ? x64 : nullptr, (cub && Pi32) ? P64 : nullptr, 1, tol, x64, P64,
+                                            &it64, st);
+    if (r != PES_OK && r != PES_ERR_NOT_CONVERGED) return r;
+    PES_CUDA(h, (launch_convert_ff<double, float>(x64, (float*)x_out, 5 * N, st)));
+    PES_CUDA(h, (launch_convert_ff<double, float>(P64, (float*)P_out, 15 * N, st)));
+    if (iters_used) *iters_used = it32 + it64;
+    PES_CUDA(h, cudaStreamSynchronize(st));
+    return r;
+}
+
 extern "C" {
 
 pes_status pes_create(pes_handle** out, int64_t max_states, int32_t max_batch)
@@ -340,7 +387,7 @@ pes_status pes_destroy(pes_handle* h)
 {
     if (!h) return PES_ERR_INVALID_ARG;
     cudaDeviceSynchronize();
-    void* ptrs[] = {h->hand, h->lanes, h->lin, h->aggF, h->aggS, h->bar, h->status, h->conv, h->iters_done, h->sensT, h->ptime,
+    void* ptrs[] = {h->hand, h->lanes, h->lin, h->mix, h->aggF, h->aggS, h->bar, h->status, h->conv, h->iters_done, h->sensT, h->ptime,
                     h->hy, h->hoff, h->hm0, h->hP0, h->hx, h->hP, h->hxi, h->hPi, h->hsens};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -470,7 +517,7 @@ pes_status pes_ieks_run(pes_handle* h, const pes_model* model, pes_method method
                         const void* x_init, const void* P_init, int32_t max_iters, double tol, void* x_out,
                         void* P_out, int32_t* iters_used, void* stream)
 {
-    pes_status r = check_common(h, prec, offsets, B, N);
+    pes_status r = check_common(h, prec, offsets, B, N, true);
     if (r != PES_OK) return r;
     if ((r = check_model(h, model)) != PES_OK) return r;
     if (method != PES_IEKS && method != PES_CUBATURE) return fail(h, PES_ERR_INVALID_ARG, "unknown method");
@@ -479,6 +526,9 @@ pes_status pes_ieks_run(pes_handle* h, const pes_model* model, pes_method method
     if (!(tol == tol)) return fail(h, PES_ERR_INVALID_ARG, "tol is NaN");
     cudaStream_t st = (cudaStream_t)stream;
     PES_CUDA(h, launch_validate_offsets(offsets, B, N, h->status, st));
+    if (prec == PES_MIXED)
+        return ieks_run_mixed(h, model, method, y, offsets, B, N, m0, P0, x_init, P_init, max_iters, tol, x_out, P_out,
+                              iters_used, st);
     if (prec == PES_FP64)
         return ieks_run_t<double>(h, model, method, prec, y, offsets, B, N, m0, P0, x_init, P_init, max_iters, tol,
                                   x_out, P_out, iters_used, st);

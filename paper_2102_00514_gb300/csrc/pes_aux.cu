@@ -54,6 +54,26 @@ cudaError_t launch_convert(const double* in, T* out, int n, cudaStream_t st)
     return cudaGetLastError();
 }
 
+template <typename Ti, typename To>
+__global__ void convert_ff_kernel(const Ti* in, To* out, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = To(in[i]);
+}
+
+template <typename Ti, typename To>
+cudaError_t launch_convert_ff(const Ti* in, To* out, int64_t n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int threads = 256;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, 152 * 16));
+    convert_ff_kernel<Ti, To><<<blocks, threads, 0, st>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_convert_ff<float, double>(const float*, double*, int64_t, cudaStream_t);
+template cudaError_t launch_convert_ff<double, float>(const double*, float*, int64_t, cudaStream_t);
+
 template cudaError_t launch_convert<float>(const double*, float*, int, cudaStream_t);
 template cudaError_t launch_convert<double>(const double*, double*, int, cudaStream_t);
 

@@ -32,6 +32,9 @@ cudaError_t launch_linearize(const KParams<T>& p, int lin, T* F, T* c, T* Qp, T*
 template <typename T>
 cudaError_t launch_init_nominal(const int64_t* offsets, int B, int64_t N, const T* m0, const T* P0, T* x, T* P,
                                 cudaStream_t st);
+// Element-wise precision conversion.
+template <typename Ti, typename To>
+cudaError_t launch_convert_ff(const Ti* in, To* out, int64_t n, cudaStream_t st);
 // Element-wise double -> T copy (model sensors into the kernel precision).
 template <typename T>
 cudaError_t launch_convert(const double* in, T* out, int n, cudaStream_t st);

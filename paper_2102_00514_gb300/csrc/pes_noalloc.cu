@@ -107,6 +107,7 @@ extern "C" pes_status pes_ieks_run_noalloc(const pes_model* model, pes_method me
                                            int32_t* iters_used, void* stream)
 {
     if (N > kMaxStates || B > kMaxBatch || N < 1 || B < 1) return PES_ERR_INVALID_ARG;
+    if (prec == PES_MIXED) return PES_ERR_UNSUPPORTED;   // its FP64 copies would be allocated
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PES_ERR_CUDA;
     const pes_status st = setup(dev);

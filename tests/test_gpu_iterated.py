@@ -106,6 +106,31 @@ def test_prior_init_equals_explicit_init(sm):
     assert torch.equal(xa, xb) and torch.equal(Pa, Pb)
 
 
+@pytest.mark.parametrize("name,method", [("ieks_T500", pes.IEKS), ("ipls_T10000", pes.CUBATURE),
+                                         ("ipls_T10000", pes.IEKS), ("ieks_T500", pes.CUBATURE)])
+def test_ieks_run_mixed_matches_oracle(sm, name, method):
+    """PES_MIXED: nine FP32 iterations, then the tenth in FP64 from the FP32
+    nominal; the result is held to the FP32 bound against the oracle's ten
+    FP64 iterations, and the final FP64 iteration equals a plain FP64 run of
+    one iteration started from the same nominal."""
+    wl = synth.workload(name)
+    ref = oracle_run(wl, method, iters=10)
+    x, P, used, _ = gpu_run(sm, wl, method, pes.MIXED, iters=10)
+    assert used == 10
+    ex = rel_err(x, ref["x"], wl["offsets"])
+    eP = rel_err(P, ref["P"], wl["offsets"])
+    print(f"{name} method {method} MIXED: means {ex:.3e} covariances {eP:.3e}")
+    assert ex < TOL_FP32 and eP < TOL_FP32
+    # the FP64 step on its own: the FP32 nominal of nine iterations, widened
+    x9, P9, _, _ = gpu_run(sm, wl, method, pes.FP32, iters=9)
+    r32 = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)
+    wl32 = dict(wl, y=r32(wl["y"]), m0=r32(wl["m0"]), P0=r32(wl["P0"]))   # the float inputs, widened
+    one = oracle_run(wl32, method, iters=1, x_init=x9, P_init=P9)
+    # the only rounding left is the final narrowing to float
+    assert rel_err(x, one["x"], wl["offsets"]) < 1e-6
+    assert rel_err(P, one["P"], wl["offsets"]) < 1e-6
+
+
 def test_host_entry_point_equals_device_entry_point(sm):
     wl = synth.workload("ieks_T500")
     d = workload_to_dev(wl, pes.FP32)
@@ -125,9 +150,11 @@ def test_invalid_arguments_rejected_before_launch(sm):
     with pytest.raises(pes.PesError) as ei:
         sm.ieks_run(d["model"], pes.IEKS, pes.FP64, d["y"], d["offsets"], d["m0"], d["P0"], iters=0)
     assert ei.value.status == pes.INVALID_ARG
+    # PES_MIXED exists for the fused iterated smoother only
+    lin = {k: torch.zeros((n, d["y"].shape[1]), dtype=torch.float32, device="cuda")
+           for k, n in (("F", 25), ("c", 5), ("Qp", 15), ("H", 10), ("d", 2), ("Rp", 3))}
     with pytest.raises(pes.PesError) as ei:
-        sm.ieks_run(d["model"], pes.IEKS, pes.MIXED, d["y"].float(), d["offsets"], d["m0"].float(),
-                    d["P0"].float(), iters=1)
+        sm.filter_scan(pes.MIXED, lin, d["y"].float(), d["m0"].float(), d["P0"].float(), d["offsets"])
     assert ei.value.status == pes.UNSUPPORTED
 
 

@@ -57,3 +57,12 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     d = workload_to_dev(wl, pes.FP32)
     st, _, _, _ = run_noalloc(lib, d, pes.IEKS, pes.FP32, wl["y"].shape[1], 1, 1)
     assert st == pes.INVALID_ARG
+
+
+def test_noalloc_rejects_mixed_precision():
+    # PES_MIXED keeps FP64 copies that pes_ieks_run allocates
+    lib = pes.load_library()
+    wl = synth.workload("ieks_T500")
+    d = workload_to_dev(wl, pes.FP32)
+    st, _, _, _ = run_noalloc(lib, d, pes.IEKS, pes.MIXED, wl["y"].shape[1], 1, 2)
+    assert st == pes.UNSUPPORTED
