@@ -48,6 +48,9 @@ def parse_args():
     ap.add_argument("--impl", choices=["pes", "reference"], default="pes")
     ap.add_argument("--T", type=int, default=1 << 20)
     ap.add_argument("--iters", type=int, default=10)
+    ap.add_argument("--batch", type=int, default=0,
+                    help="B > 0: the batched workload of B trajectories, lengths U{100..20000}, instead of one "
+                         "trajectory of length T")
     ap.add_argument("--no-parity", action="store_true", help="skip the full-size oracle parity check")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -180,11 +183,43 @@ def oracle_timed(wl_sample, iters):
     return out
 
 
-def sample_workload(wl, S):
-    """The first S states of a single-trajectory workload."""
+def one_trajectory(wl, b):
+    """Trajectory b of a workload as a workload of its own, and its state slice."""
     import numpy as np
-    return dict(wl, offsets=np.array([0, S], dtype=np.int64), y=np.ascontiguousarray(wl["y"][:, :S]),
-                x_true=np.ascontiguousarray(wl["x_true"][:, :S]))
+    off = wl["offsets"]
+    sl = slice(int(off[b]), int(off[b + 1]))
+    return dict(wl, offsets=np.array([0, off[b + 1] - off[b]], dtype=np.int64), y=wl["y"][:, sl],
+                x_true=wl["x_true"][:, sl], m0=wl["m0"][b:b + 1], P0=wl["P0"][b:b + 1],
+                sensors=wl["sensors"][b:b + 1]), sl
+
+
+def sample_workload(wl, S):
+    """A bounded sample of about S states: the first S states of a single
+    trajectory, or the first whole trajectories of a batch up to S states."""
+    import numpy as np
+    off = wl["offsets"]
+    if len(off) == 2:
+        return dict(wl, offsets=np.array([0, S], dtype=np.int64), y=np.ascontiguousarray(wl["y"][:, :S]),
+                    x_true=np.ascontiguousarray(wl["x_true"][:, :S]))
+    nb = max(1, int(np.searchsorted(off, S, side="right")) - 1)
+    n = int(off[nb])
+    return dict(wl, offsets=np.ascontiguousarray(off[:nb + 1]), y=np.ascontiguousarray(wl["y"][:, :n]),
+                x_true=np.ascontiguousarray(wl["x_true"][:, :n]), m0=wl["m0"][:nb], P0=wl["P0"][:nb],
+                sensors=wl["sensors"][:nb])
+
+
+def parity_units(wl):
+    """What the oracle checks: the whole workload for one trajectory; for a
+    batch, the first, last, shortest and longest trajectories and four seeded
+    random ones, each smoothed alone (the trajectories are independent)."""
+    import numpy as np
+    B = len(wl["offsets"]) - 1
+    if B == 1:
+        return [(wl, slice(0, int(wl["offsets"][-1])))]
+    T = np.diff(wl["offsets"]) - 1
+    pick = {0, B - 1, int(np.argmin(T)), int(np.argmax(T))}
+    pick |= set(int(b) for b in np.random.default_rng(B).choice(B, min(4, B), replace=False))
+    return [one_trajectory(wl, b) for b in sorted(pick)]
 
 
 def run_reference(args, rank, world):
@@ -248,10 +283,12 @@ def main():
             dist.barrier()
 
     T, iters = args.T, args.iters
-    wl = synth.workload(f"sweep_T{T}")
+    wl = synth.workload(f"batch{args.batch}" if args.batch > 0 else f"sweep_T{T}")
     N = wl["y"].shape[1]
+    B = len(wl["offsets"]) - 1
+    steps = N - B   # sum of T_b: every trajectory has one more state than measurements
     dev = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
-    sm = pes.Smoother(N, 1)
+    sm = pes.Smoother(N, B)
     methods = (("ieks", pes.IEKS), ("cubature", pes.CUBATURE))
 
     def device_inputs(prec):
@@ -306,7 +343,7 @@ def main():
         t = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    work_per_step = len(methods) * (N - 1) * iters
+    work_per_step = len(methods) * steps * iters
     value = world * work_per_step * args.steps / (total_ms * 1e-3)
     ms_per_step = total_ms / args.steps
     # offsets validation, sensor conversion, y to the lane layout, nominal
@@ -325,8 +362,8 @@ def main():
         per_method = {}
         for name, _ in methods:
             ms = statistics.mean(meth_ms[name])
-            flop = ALG_FLOP[name] * (N - 1) * iters
-            per_method[name] = {"ms_per_run": ms, "value": (N - 1) * iters / (ms * 1e-3),
+            flop = ALG_FLOP[name] * steps * iters
+            per_method[name] = {"ms_per_run": ms, "value": steps * iters / (ms * 1e-3),
                                 "achieved_tflops": flop / (ms * 1e-3) / 1e12}
         dom = max(per_method, key=lambda k: per_method[k]["ms_per_run"])
         achieved = per_method[dom]["achieved_tflops"]
@@ -335,7 +372,7 @@ def main():
         except Exception:
             probe32, probe64 = None, None
         roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                    "frac": achieved / fp32_peak, "traffic": traffic_for(dom, N - 1, iters),
+                    "frac": achieved / fp32_peak, "traffic": traffic_for(dom, steps, iters),
                     "kernel": f"pes_persistent_kernel<float, {dom}>",
                     "peak_source": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
                                    f"{sm_max:.0f} MHz (max SM clock)",
@@ -346,9 +383,11 @@ def main():
                   "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                   "vs_baseline": None, "dtype": "f32",
                   "data": f"synthetic coordinated-turn / bearings (seeded, seed {wl['seed']}), inputs resident in HBM",
-                  "config": {"workload": f"single trajectory T={T}, IEKS + cubature IPLS, {iters} iterations each, "
-                                         "FP32, prior initialisation",
-                             "T": T, "B": 1, "iterations": iters, "methods": ["ieks", "cubature"],
+                  "config": {"workload": (f"single trajectory T={T}" if B == 1 else
+                                          f"{B} trajectories, T_b uniform in 100..20000 (sum {steps}), turn rate "
+                                          "U(-1,1), sensors jittered by U(-0.2,0.2)") +
+                                         f", IEKS + cubature IPLS, {iters} iterations each, FP32, prior initialisation",
+                             "T": T if B == 1 else None, "B": B, "N_states": N, "iterations": iters, "methods": ["ieks", "cubature"],
                              "precision": "fp32", "l2": "flushed before every step (512 MB write)",
                              "launch": {"ieks": {"blocks": nb, "threads": nt, "steps_per_thread": L},
                                         "cubature": {"blocks": nbc, "threads": ntc, "steps_per_thread": Lc}}},
@@ -446,58 +485,67 @@ def main():
         oracle.build()
         # CPU baseline: the oracle as it stands on one host core, bounded sample
         if not args.no_cpu_baseline:
-            S = min(args.cpu_sample, N)
-            t = oracle_timed(sample_workload(wl, S), iters)
-            result["cpu_baseline"] = {"value": 2 * S * iters / (t["ieks"] + t["cubature"]), "unit": UNIT,
+            sw = sample_workload(wl, min(args.cpu_sample, N))
+            Sn, Sb = sw["y"].shape[1], len(sw["offsets"]) - 1
+            t = oracle_timed(sw, iters)
+            result["cpu_baseline"] = {"value": 2 * (Sn - Sb) * iters / (t["ieks"] + t["cubature"]), "unit": UNIT,
                                       "cores": 1, "kind": "oracle",
-                                      "sample": f"first {S} of {N} states, IEKS + cubature, {iters} iterations, "
-                                                "sequential FP64 oracle"}
-        # parity of this very run against the oracle on the full workload
+                                      "sample": f"first {Sn} of {N} states ({Sb} trajectories), IEKS + cubature, "
+                                                f"{iters} iterations, sequential FP64 oracle"}
+        # parity of this very run against the oracle: on the whole workload for
+        # one trajectory, on sampled trajectories (each smoothed alone) for a batch
         if not args.no_parity:
-            model = oracle.Model.from_workload(wl)
+            units = parity_units(wl)
+            r32 = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)
+            omethods = (("ieks", oracle.IEKS), ("cubature", oracle.CUBATURE))
 
-            def orc(m):
-                return oracle.iterated_smoother(model, m, wl["offsets"], wl["y"], wl["m0"], wl["P0"], iters=iters)
+            def orc(u, m):
+                one = u[0]
+                return oracle.iterated_smoother(oracle.Model.from_workload(one), m, one["offsets"], one["y"],
+                                                one["m0"], one["P0"], iters=iters)
 
             # the final iteration alone: one FP64 oracle iteration from the GPU's
             # own FP32 nominal, on the float inputs widened to double
-            r32 = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)
-            wl32 = dict(wl, y=r32(wl["y"]), m0=r32(wl["m0"]), P0=r32(wl["P0"]))
-
-            def orc_last(name, m):
+            def orc_last(u, name, m):
+                one, sl = u
                 if name not in nom32:
                     return None
-                return oracle.iterated_smoother(model, m, wl32["offsets"], wl32["y"], wl32["m0"], wl32["P0"],
-                                                x_init=nom32[name][0], P_init=nom32[name][1], iters=1)
+                return oracle.iterated_smoother(oracle.Model.from_workload(one), m, one["offsets"], r32(one["y"]),
+                                                r32(one["m0"]), r32(one["P0"]), x_init=nom32[name][0][:, sl],
+                                                P_init=nom32[name][1][:, sl], iters=1)
 
-            with cf.ThreadPoolExecutor(4) as ex:
-                fut = {n: ex.submit(orc, m) for n, m in (("ieks", oracle.IEKS), ("cubature", oracle.CUBATURE))}
-                fut_last = {n: ex.submit(orc_last, n, m) for n, m in (("ieks", oracle.IEKS),
-                                                                       ("cubature", oracle.CUBATURE))}
-                refs = {n: f.result() for n, f in fut.items()}
-                last = {n: f.result() for n, f in fut_last.items()}
+            with cf.ThreadPoolExecutor(min(16, os.cpu_count() or 1)) as ex:
+                fut = {(n, i): ex.submit(orc, u, m) for n, m in omethods for i, u in enumerate(units)}
+                fut_last = {(n, i): ex.submit(orc_last, u, n, m) for n, m in omethods for i, u in enumerate(units)}
+                refs = {k: f.result() for k, f in fut.items()}
+                last = {k: f.result() for k, f in fut_last.items()}
+
+            def worst(arr, ref_key, rs, key):
+                return max(rel_err(arr[:, u[1]], rs[(ref_key, i)][key], u[0]["offsets"]) for i, u in enumerate(units))
+
             par = {}
             for name, _ in methods:
-                r = refs[name]
-                par[name] = {"fp32_means": rel_err(x32[name][0], r["x"], wl["offsets"]),
-                             "fp32_covs": rel_err(x32[name][1], r["P"], wl["offsets"])}
+                par[name] = {"fp32_means": worst(x32[name][0], name, refs, "x"),
+                             "fp32_covs": worst(x32[name][1], name, refs, "P")}
                 if not args.no_fp64:
-                    par[name]["fp64_means"] = rel_err(x64[name][0], r["x"], wl["offsets"])
-                    par[name]["fp64_covs"] = rel_err(x64[name][1], r["P"], wl["offsets"])
+                    par[name]["fp64_means"] = worst(x64[name][0], name, refs, "x")
+                    par[name]["fp64_covs"] = worst(x64[name][1], name, refs, "P")
                 if name in xmix:
-                    par[name]["mixed_means"] = rel_err(xmix[name][0], r["x"], wl["offsets"])
-                    par[name]["mixed_covs"] = rel_err(xmix[name][1], r["P"], wl["offsets"])
-                par[name]["oracle_final_rel_update"] = float(r["rel_history"][-1])
-                if last.get(name) is not None:
-                    lr = last[name]
-                    par[name]["final_iteration"] = {
-                        "fp32_means": rel_err(x32[name][0], lr["x"], wl["offsets"]),
-                        "fp32_covs": rel_err(x32[name][1], lr["P"], wl["offsets"])}
+                    par[name]["mixed_means"] = worst(xmix[name][0], name, refs, "x")
+                    par[name]["mixed_covs"] = worst(xmix[name][1], name, refs, "P")
+                par[name]["oracle_final_rel_update"] = max(float(refs[(name, i)]["rel_history"][-1])
+                                                           for i in range(len(units)))
+                if name in nom32:
+                    fi = {"fp32_means": worst(x32[name][0], name, last, "x"),
+                          "fp32_covs": worst(x32[name][1], name, last, "P")}
                     if name in xmix:
-                        par[name]["final_iteration"]["mixed_means"] = rel_err(xmix[name][0], lr["x"], wl["offsets"])
-                        par[name]["final_iteration"]["mixed_covs"] = rel_err(xmix[name][1], lr["P"], wl["offsets"])
+                        fi["mixed_means"] = worst(xmix[name][0], name, last, "x")
+                        fi["mixed_covs"] = worst(xmix[name][1], name, last, "P")
+                    par[name]["final_iteration"] = fi
             tol_ok = all(v["fp32_means"] <= 1e-4 and v["fp32_covs"] <= 1e-4 for v in par.values())
-            result["parity"] = {"vs": "CPU FP64 oracle, full workload; final_iteration: one oracle iteration from "
+            scope = ("full workload" if len(units) == 1 else
+                     f"{len(units)} sampled trajectories, each smoothed alone by the oracle (worst reported)")
+            result["parity"] = {"vs": f"CPU FP64 oracle, {scope}; final_iteration: one oracle iteration from "
                                       "the GPU's own FP32 nominal of the first iters-1 iterations",
                                 "rel_frobenius": par,
                                 "fp32_tol": 1e-4, "fp64_tol": 1e-9, "fp32_within_tol": tol_ok}
