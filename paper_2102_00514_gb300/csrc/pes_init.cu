@@ -1,0 +1,895 @@
+// The learned initialiser (include/pes_init.h): a 1-D conv / MLP network on
+// the tensor cores that maps a trajectory's measurements to the initial
+// nominal trajectory of the iterated smoother (Sec. 3), with its training.
+//
+// Row layout. The states of B trajectories are stored as activation rows of
+// 64 bf16 channels (128 bytes): state k of trajectory b sits at row
+// k + 2 (b + 1), so that two zero rows separate consecutive trajectories and
+// frame the batch. A kernel-5 convolution over rows then sees zeros outside
+// each trajectory, which is the "same" zero padding per trajectory, and the
+// 1x1 layers need no special case. Gap rows are zeroed once per call and never
+// written; R = N + 2 (B + 1) rows in all.
+//
+// Every layer is one GEMM on the tensor cores (conv_tc_kernel): a tile of 128
+// rows times K = taps x 64 input channels, N = 64 output channels, bf16
+// operands and an FP32 accumulator in tensor memory. The activation tile for
+// tap j is the 128 rows starting j - 2 rows earlier, loaded by TMA (rows
+// outside 0..R-1 read as zero); the layer's weights, one 64 x 64 tile per tap,
+// stay in shared memory for the whole launch. Warp 0 issues the loads, warp 1
+// the MMAs, warps 2-5 drain the accumulators (bias, ReLU or the ReLU mask of
+// the backward pass, bf16 store); two accumulators in TMEM let the epilogue of
+// one tile overlap the MMAs of the next. The backward pass through a layer is
+// the same GEMM with the weights transposed and the taps reversed. Weight
+// gradients (a reduction over rows) run on the CUDA cores in FP32.
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "pes.h"
+#include "pes_init.h"
+#include "pes_tc.cuh"
+
+namespace {
+
+using namespace pes;
+using bf16 = __nv_bfloat16;
+
+constexpr int C = 64;                  // channels
+constexpr int G = 2;                   // zero rows around each trajectory (kernel 5 / 2)
+constexpr int TM = 128;                // rows per tile (MMA M)
+constexpr int NSTAGE = 8;              // activation tiles in flight per CTA
+constexpr int NLAYER = 6;              // 4 conv + 2 head
+constexpr int kTileBytes = TM * C * 2;
+constexpr int kWTileBytes = C * C * 2;
+constexpr int kEpiThreads = 128;
+constexpr int kConvThreads = 64 + kEpiThreads;
+constexpr uint32_t kTmemCols = 128;    // two 64-column FP32 accumulators
+constexpr uint32_t kIdesc = tc::idesc_bf16_f32(TM, C);
+
+constexpr int kTaps[NLAYER] = {5, 5, 5, 5, 1, 1};
+constexpr int kWTile0[NLAYER] = {0, 5, 10, 15, 20, 21};   // first weight tile of each layer
+constexpr int kWTiles = 22;
+constexpr int kCoReal[NLAYER] = {64, 64, 64, 64, 64, 5};  // output channels that exist
+constexpr int kPOff[NLAYER + 1] = {0, 20544, 41088, 61632, 82176, 86336, 86661};   // packed offsets
+static_assert(kPOff[NLAYER] == PES_INIT_NPARAMS, "parameter packing");
+static_assert(kTaps[0] == 5 && kTaps[NLAYER - 1] == 1 && kWTile0[NLAYER - 1] + kTaps[NLAYER - 1] == kWTiles, "layer tables");
+constexpr int kOutCols = 8;            // the head's FP32 output row (5 used)
+constexpr int kWgradStride = C * C * 5 + C;
+
+enum { EPI_RELU = 0, EPI_F32 = 1, EPI_MASK = 2 };
+
+// The same layer tables for device code.
+PES_DEV int taps_of(int l) { return l < 4 ? 5 : 1; }
+PES_DEV int wtile0_of(int l) { return l < 4 ? 5 * l : 16 + l; }
+PES_DEV int coreal_of(int l) { return l == 5 ? 5 : C; }
+PES_DEV int poff_of(int l) { return l < 4 ? 20544 * l : (l == 4 ? 82176 : 86336); }
+
+struct ConvParams {
+    int R;                      // rows
+    int ntiles;                 // ceil(R / TM)
+    int w_tile0;                // first weight tile of the layer
+    const float* bias;          // [64] (EPI_RELU, EPI_F32)
+    const uint8_t* rowmask;     // [R]: 1 for state rows
+    bf16* out;                  // [R][64] (EPI_RELU, EPI_MASK)
+    float* out_f32;             // [R][8] (EPI_F32)
+    const bf16* relu_src;       // [R][64] (EPI_MASK): the layer input whose ReLU is differentiated
+    int* status;
+};
+
+PES_DEV uint32_t pack_bf16x2(float a, float b)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+PES_DEV float2 unpack_bf16x2(uint32_t u)
+{
+    const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&u);
+    return __bfloat1622float2(h);
+}
+
+// Bounded wait that ignores the abort flag (used while draining).
+PES_DEV void drain_wait(uint64_t* bar, uint32_t parity)
+{
+    const long long t0 = async_now_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (async_now_ns() - t0 > 1000000000LL) return;
+}
+
+template <int TAPS, int EPI>
+__global__ void __launch_bounds__(kConvThreads, 1)
+    conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW,
+                   const ConvParams p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    uint8_t* sW = smem;                                   // TAPS weight tiles
+    uint8_t* sA = smem + TAPS * kWTileBytes;              // NSTAGE activation tiles
+    uint64_t* full = reinterpret_cast<uint64_t*>(sA + NSTAGE * kTileBytes);
+    uint64_t* empty = full + NSTAGE;
+    uint64_t* wbar = empty + NSTAGE;
+    uint64_t* tfull = wbar + 1;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* done = tempty + 2;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGE; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, 1);
+        }
+        mbar_init(wbar, 1);
+        mbar_init(tfull, 1);
+        mbar_init(tfull + 1, 1);
+        mbar_init(tempty, kEpiThreads);
+        mbar_init(tempty + 1, kEpiThreads);
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        mbar_init_fence();
+    }
+    if (warp == 1) tc::tmem_alloc(tslot, kTmemCols);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *tslot;
+
+    if (warp == 0) {
+        // ---- producer: weights once, then TAPS shifted activation tiles per row tile
+        if (lane == 0) {
+            int armed[NSTAGE];
+            for (int s = 0; s < NSTAGE; ++s) armed[s] = -1;
+            tc::mbar_expect_tx(wbar, TAPS * kWTileBytes);
+            for (int j = 0; j < TAPS; ++j) tc::tma_load_2d(sW + j * kWTileBytes, &tmW, 0, (p.w_tile0 + j) * C, wbar);
+            int st = 0;
+            uint32_t ph = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < p.ntiles; tile += gridDim.x) {
+                for (int j = 0; j < TAPS; ++j) {
+                    if (!tc::wait_or_abort(empty + st, ph ^ 1, p.status, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::mbar_expect_tx(full + st, kTileBytes);
+                    tc::tma_load_2d(sA + st * kTileBytes, &tmA, 0, tile * TM + j - TAPS / 2, full + st);
+                    armed[st] = (int)ph;
+                    if (++st == NSTAGE) {
+                        st = 0;
+                        ph ^= 1;
+                    }
+                }
+            }
+            if (*abort_flag) {
+                // no copy of this block may still be landing when it exits
+                drain_wait(wbar, 0);
+                for (int s = 0; s < NSTAGE; ++s)
+                    if (armed[s] >= 0) drain_wait(full + s, (uint32_t)armed[s]);
+            }
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer: TAPS x 4 MMAs (K = 16 each) per tile into one of two accumulators
+        if (lane == 0) {
+            bool ok = tc::wait_or_abort(wbar, 0, p.status, abort_flag);
+            int st = 0, acc = 0;
+            uint32_t ph = 0, tph = 0;
+            for (int tile = blockIdx.x; ok && tile < p.ntiles; tile += gridDim.x) {
+                if (!tc::wait_or_abort(tempty + acc, ((tph >> acc) & 1u) ^ 1u, p.status, abort_flag)) break;
+                tph ^= 1u << acc;
+                tc::fence_after_sync();
+                const uint32_t d = tbase + (uint32_t)(acc * C);
+                for (int j = 0; j < TAPS; ++j) {
+                    if (!tc::wait_or_abort(full + st, ph, p.status, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint64_t ad = tc::smem_desc_sw128(sA + st * kTileBytes);
+                    const uint64_t bd = tc::smem_desc_sw128(sW + j * kWTileBytes);
+#pragma unroll
+                    for (int k = 0; k < C / 16; ++k)   // +32 bytes along K per MMA
+                        tc::mma_bf16(d, ad + 2 * k, bd + 2 * k, kIdesc, (j | k) != 0);
+                    tc::mma_commit(empty + st);
+                    if (++st == NSTAGE) {
+                        st = 0;
+                        ph ^= 1;
+                    }
+                }
+                if (!ok) break;
+                tc::mma_commit(tfull + acc);
+                acc ^= 1;
+            }
+            tc::mma_commit(done);
+            drain_wait(done, 0);
+        }
+    } else {
+        // ---- epilogue: one accumulator row per thread
+        const int q = warp & 3;
+        const int rin = q * 32 + lane;
+        int acc = 0;
+        uint32_t fph = 0;
+        for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
+            bool ok = tc::wait_or_abort(tfull + acc, (fph >> acc) & 1u, p.status, abort_flag);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            fph ^= 1u << acc;
+            tc::fence_after_sync();
+            float v[C];
+            const uint32_t ta = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * C);
+#pragma unroll
+            for (int i = 0; i < C / 16; ++i) tc::tmem_ld16(ta + 16 * i, v + 16 * i);
+            tc::fence_before_sync();
+            tc::mbar_arrive(tempty + acc);
+            acc ^= 1;
+            const int r = tile * TM + rin;
+            if (r >= p.R || !p.rowmask[r]) continue;
+            if constexpr (EPI == EPI_F32) {
+                float4* dst = reinterpret_cast<float4*>(p.out_f32 + (size_t)r * kOutCols);
+                dst[0] = make_float4(v[0] + __ldg(p.bias + 0), v[1] + __ldg(p.bias + 1), v[2] + __ldg(p.bias + 2),
+                                     v[3] + __ldg(p.bias + 3));
+                dst[1] = make_float4(v[4] + __ldg(p.bias + 4), v[5] + __ldg(p.bias + 5), v[6] + __ldg(p.bias + 6),
+                                     v[7] + __ldg(p.bias + 7));
+            } else {
+                if constexpr (EPI == EPI_MASK) {
+                    const uint4* src = reinterpret_cast<const uint4*>(p.relu_src + (size_t)r * C);
+#pragma unroll
+                    for (int i = 0; i < C / 8; ++i) {
+                        const uint4 u = __ldg(src + i);
+                        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            const float2 f = unpack_bf16x2(w[h]);
+                            if (!(f.x > 0.f)) v[8 * i + 2 * h] = 0.f;
+                            if (!(f.y > 0.f)) v[8 * i + 2 * h + 1] = 0.f;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < C; ++c) v[c] = fmaxf(v[c] + __ldg(p.bias + c), 0.f);
+                }
+                uint4* dst = reinterpret_cast<uint4*>(p.out + (size_t)r * C);
+#pragma unroll
+                for (int i = 0; i < C / 8; ++i)
+                    dst[i] = make_uint4(pack_bf16x2(v[8 * i], v[8 * i + 1]), pack_bf16x2(v[8 * i + 2], v[8 * i + 3]),
+                                        pack_bf16x2(v[8 * i + 4], v[8 * i + 5]),
+                                        pack_bf16x2(v[8 * i + 6], v[8 * i + 7]));
+            }
+        }
+    }
+
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 1) tc::tmem_dealloc(tbase, kTmemCols);
+}
+
+constexpr size_t conv_smem_bytes(int taps)
+{
+    return 1024 + (size_t)taps * kWTileBytes + (size_t)NSTAGE * kTileBytes + (2 * NSTAGE + 6) * 8 + 16;
+}
+
+// ---- rows, features, loss, gradients, optimiser ----------------------------------
+
+PES_DEV int traj_of_state(const int64_t* off, int B, int64_t k)
+{
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= k) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Features of every state row and the row mask.
+template <typename T>
+__global__ void features_kernel(const T* y, const int64_t* off, int B, int64_t N, uint8_t* mask, bf16* X0)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += stride) {
+        const int b = traj_of_state(off, B, k);
+        const int64_t row = k + (int64_t)G * (b + 1);
+        float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (k == off[b]) {
+            f[5] = 1.f;
+        } else {
+            sincosf((float)y[k], &f[0], &f[1]);
+            sincosf((float)y[N + k], &f[2], &f[3]);
+            f[4] = 1.f;
+        }
+        uint4* dst = reinterpret_cast<uint4*>(X0 + (size_t)row * C);
+        dst[0] = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]), pack_bf16x2(f[4], f[5]),
+                            pack_bf16x2(f[6], f[7]));
+#pragma unroll
+        for (int i = 1; i < C / 8; ++i) dst[i] = make_uint4(0, 0, 0, 0);
+        mask[row] = 1;
+    }
+}
+
+struct ZeroList {
+    bf16* buf[10];
+    int n;
+};
+
+// The gap rows: mask 0 and zero in every listed activation buffer.
+__global__ void gap_rows_kernel(const int64_t* off, int B, int64_t N, int64_t R, uint8_t* mask, ZeroList zl)
+{
+    const int64_t total = (int64_t)G * (B + 1);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(i / G);
+        const int64_t o = off[b];
+        if (o < 0 || o > N) continue;   // malformed offsets: leave the row alone
+        const int64_t row = o + (int64_t)G * b + (i % G);
+        if (row >= R) continue;
+        mask[row] = 0;
+        for (int j = 0; j < zl.n; ++j) {
+            uint4* dst = reinterpret_cast<uint4*>(zl.buf[j] + (size_t)row * C);
+#pragma unroll
+            for (int c = 0; c < C / 8; ++c) dst[c] = make_uint4(0, 0, 0, 0);
+        }
+    }
+}
+
+struct Norm {
+    double mu[5], sigma[5];
+};
+
+// Loss terms (o - t)^2 and the output gradient dO = 2 (o - t) / (5 N) in bf16.
+template <typename T>
+__global__ void loss_kernel(const float* o, const T* xt, const int64_t* off, int B, int64_t N, Norm nm, float scale,
+                            bf16* dO, double* part)
+{
+    double s = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += stride) {
+        const int b = traj_of_state(off, B, k);
+        const int64_t row = k + (int64_t)G * (b + 1);
+        float e[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            const float t = (float)(((double)xt[(size_t)c * N + k] - nm.mu[c]) / nm.sigma[c]);
+            e[c] = o[(size_t)row * kOutCols + c] - t;
+            s += (double)e[c] * (double)e[c];
+        }
+        uint4* dst = reinterpret_cast<uint4*>(dO + (size_t)row * C);
+        dst[0] = make_uint4(pack_bf16x2(scale * e[0], scale * e[1]), pack_bf16x2(scale * e[2], scale * e[3]),
+                            pack_bf16x2(scale * e[4], 0.f), 0u);
+#pragma unroll
+        for (int i = 1; i < C / 8; ++i) dst[i] = make_uint4(0, 0, 0, 0);
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void sum_kernel(const double* part, int n, double scale, double* out)
+{
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0] * scale;
+}
+
+// Weight and bias gradients of one layer, partial per block:
+//   dW[o][i][j] = sum_r dY[r][o] X[r + j - TAPS/2][i],  db[o] = sum_r dY[r][o].
+// Thread (cb, ib) owns output channels 4cb..4cb+3 x input channels 4ib..4ib+3
+// x all taps, accumulated in FP32 over chunks of 32 rows staged in shared memory.
+template <int TAPS>
+__global__ void __launch_bounds__(256) wgrad_kernel(const bf16* dY, const bf16* X, int64_t R, float* part)
+{
+    constexpr int CH = 32;
+    constexpr int H = TAPS / 2;
+    __shared__ float4 sdy[CH][C / 4];
+    __shared__ float4 sx[CH + TAPS - 1][C / 4];
+    const int t = threadIdx.x, cb = t >> 4, ib = t & 15;
+    float acc[4][TAPS][4];
+    float bacc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int j = 0; j < TAPS; ++j)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][j][c] = 0.f;
+    const int64_t nchunks = (R + CH - 1) / CH;
+    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const int64_t r0 = ch * CH;
+        __syncthreads();
+        {   // dY rows r0 .. r0 + CH - 1: one 16-byte load per thread
+            const int rr = t >> 3, part8 = t & 7;
+            uint4 u = make_uint4(0, 0, 0, 0);
+            if (r0 + rr < R) u = __ldg(reinterpret_cast<const uint4*>(dY + (size_t)(r0 + rr) * C) + part8);
+            const float2 a = unpack_bf16x2(u.x), b = unpack_bf16x2(u.y), c = unpack_bf16x2(u.z),
+                         d = unpack_bf16x2(u.w);
+            sdy[rr][2 * part8] = make_float4(a.x, a.y, b.x, b.y);
+            sdy[rr][2 * part8 + 1] = make_float4(c.x, c.y, d.x, d.y);
+        }
+        for (int i = t; i < (CH + TAPS - 1) * 8; i += 256) {
+            const int rr = i >> 3, part8 = i & 7;
+            const int64_t r = r0 + rr - H;
+            uint4 u = make_uint4(0, 0, 0, 0);
+            if (r >= 0 && r < R) u = __ldg(reinterpret_cast<const uint4*>(X + (size_t)r * C) + part8);
+            const float2 a = unpack_bf16x2(u.x), b = unpack_bf16x2(u.y), c = unpack_bf16x2(u.z),
+                         d = unpack_bf16x2(u.w);
+            sx[rr][2 * part8] = make_float4(a.x, a.y, b.x, b.y);
+            sx[rr][2 * part8 + 1] = make_float4(c.x, c.y, d.x, d.y);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int r = 0; r < CH; ++r) {
+            const float4 d4 = sdy[r][cb];
+            const float dv[4] = {d4.x, d4.y, d4.z, d4.w};
+#pragma unroll
+            for (int j = 0; j < TAPS; ++j) {
+                const float4 x4 = sx[r + j][ib];
+                const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[a][j][c] = fmaf(dv[a], xv[c], acc[a][j][c]);
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) bacc[a] += dv[a];
+        }
+    }
+    float* out = part + (size_t)blockIdx.x * kWgradStride;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int j = 0; j < TAPS; ++j) out[((4 * cb + a) * C + 4 * ib + c) * TAPS + j] = acc[a][j][c];
+    if (ib == 0)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) out[C * C * TAPS + 4 * cb + a] = bacc[a];
+}
+
+// Sum the per-block partials into the packed gradient of one layer (fixed
+// order, so the result does not depend on scheduling).
+__global__ void wgrad_reduce_kernel(const float* part, int nblk, int nw_real, int nb_real, int bias_src,
+                                    float* grad)
+{
+    const int n = nw_real + nb_real;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int src = i < nw_real ? i : bias_src + (i - nw_real);
+        float s = 0.f;
+        for (int b = 0; b < nblk; ++b) s += part[(size_t)b * kWgradStride + src];
+        grad[i] = s;
+    }
+}
+
+__global__ void adam_kernel(float* p, float* m, float* v, const float* g, int n, float lr, float b1, float b2,
+                            float eps, float c1, float c2)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    }
+}
+
+// bf16 weight tiles for the forward GEMMs (tile (l, j): [o][i] = W_l[o][i][j])
+// and for the backward GEMMs (tile (l, j): [i][o] = W_l[o][i][TAPS-1-j]), and
+// the FP32 biases padded to 64 channels.
+__global__ void publish_kernel(const float* p, bf16* Wf, bf16* Wb, float* bias)
+{
+    const int total = kWTiles * C * C;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total + NLAYER * C;
+         idx += gridDim.x * blockDim.x) {
+        if (idx >= total) {
+            const int l = (idx - total) / C, o = (idx - total) % C;
+            bias[l * C + o] = o < coreal_of(l) ? p[poff_of(l) + coreal_of(l) * C * taps_of(l) + o] : 0.f;
+            continue;
+        }
+        const int tile = idx / (C * C), n = (idx / C) % C, kc = idx % C;
+        int l = 0;
+        while (l + 1 < NLAYER && wtile0_of(l + 1) <= tile) ++l;
+        const int j = tile - wtile0_of(l), taps = taps_of(l);
+        {   // forward: row n = output channel, column kc = input channel, tap j
+            const int o = n, i = kc;
+            Wf[idx] = __float2bfloat16_rn(o < coreal_of(l) ? p[poff_of(l) + (o * C + i) * taps + j] : 0.f);
+        }
+        {   // backward: row n = input channel, column kc = output channel, tap taps-1-j
+            const int i = n, o = kc;
+            Wb[idx] = __float2bfloat16_rn(o < coreal_of(l) ? p[poff_of(l) + (o * C + i) * taps + (taps - 1 - j)] : 0.f);
+        }
+    }
+}
+
+template <typename T>
+__global__ void denorm_kernel(const float* o, const int64_t* off, int B, int64_t N, Norm nm, T* x)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += stride) {
+        const int b = traj_of_state(off, B, k);
+        const int64_t row = k + (int64_t)G * (b + 1);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) x[(size_t)c * N + k] = (T)(nm.mu[c] + nm.sigma[c] * (double)o[row * kOutCols + c]);
+    }
+}
+
+}  // namespace
+
+// ---- host side -------------------------------------------------------------------
+
+struct pes_init_net {
+    int device = 0, num_sms = 0;
+    int64_t max_states = 0, max_rows = 0;
+    int32_t max_batch = 0;
+    float *params = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr, *bias = nullptr, *wpart = nullptr;
+    double *lpart = nullptr, *loss_dev = nullptr;
+    bf16 *Wf = nullptr, *Wb = nullptr;
+    bf16* act[NLAYER] = {};      // X0, H1..H4, Z
+    bf16 *dO = nullptr, *dA = nullptr, *dB = nullptr;
+    float* out = nullptr;
+    uint8_t* mask = nullptr;
+    int* status = nullptr;
+    CUtensorMap mapWf, mapWb;
+    Norm norm;
+    int adam_t = 0;
+    char err[256] = {0};
+};
+
+namespace {
+
+constexpr int kLossBlocks = 1024;
+
+pes_status net_fail(pes_init_net* n, pes_status s, const char* fmt, ...)
+{
+    if (n) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(n->err, sizeof(n->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+#define NET_CUDA(n, call)                                                                   \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) return net_fail(n, PES_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// Tensor map of a [rows][64] bf16 array, boxes of box_rows x 64, 128-byte swizzle.
+bool make_map(CUtensorMap* m, const void* base, uint64_t rows, uint32_t box_rows)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)C, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)C * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)C, box_rows};
+    const cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int TAPS, int EPI>
+cudaError_t launch_conv(pes_init_net* n, const bf16* in, int64_t R, bool backward, int layer, bf16* out,
+                        float* out_f32, const bf16* relu_src, cudaStream_t st)
+{
+    CUtensorMap mA;
+    if (!make_map(&mA, in, (uint64_t)R, TM)) return cudaErrorInvalidValue;
+    ConvParams p;
+    p.R = (int)R;
+    p.ntiles = (int)((R + TM - 1) / TM);
+    p.w_tile0 = kWTile0[layer];
+    p.bias = n->bias + layer * C;
+    p.rowmask = n->mask;
+    p.out = out;
+    p.out_f32 = out_f32;
+    p.relu_src = relu_src;
+    p.status = n->status;
+    const size_t smem = conv_smem_bytes(TAPS);
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<TAPS, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)std::min<int64_t>(p.ntiles, n->num_sms);
+    conv_tc_kernel<TAPS, EPI><<<grid, kConvThreads, smem, st>>>(mA, backward ? n->mapWb : n->mapWf, p);
+    return cudaGetLastError();
+}
+
+pes_status check_sizes(pes_init_net* n, pes_precision prec, const void* y, const int64_t* off, int32_t B, int64_t N)
+{
+    if (!n) return PES_ERR_INVALID_ARG;
+    if (prec != PES_FP32 && prec != PES_FP64) return net_fail(n, PES_ERR_INVALID_ARG, "precision must be FP32 or FP64");
+    if (!y || !off) return net_fail(n, PES_ERR_INVALID_ARG, "NULL array");
+    if (B < 1 || N < B || N > n->max_states || B > n->max_batch)
+        return net_fail(n, PES_ERR_INVALID_ARG, "sizes out of range (N %lld, B %d)", (long long)N, (int)B);
+    return PES_OK;
+}
+
+// Rows, features and gap rows of a call; returns R.
+template <typename T>
+pes_status prepare_rows(pes_init_net* n, const T* y, const int64_t* off, int32_t B, int64_t N, bool training,
+                        cudaStream_t st, int64_t* R_out)
+{
+    const int64_t R = N + (int64_t)G * (B + 1);
+    const int blocks = (int)std::min<int64_t>((N + 255) / 256, (int64_t)n->num_sms * 16);
+    features_kernel<T><<<blocks, 256, 0, st>>>(y, off, B, N, n->mask, n->act[0]);
+    NET_CUDA(n, cudaGetLastError());
+    ZeroList zl;
+    zl.n = 0;
+    zl.buf[zl.n++] = n->act[0];
+    for (int l = 1; l < NLAYER; ++l) zl.buf[zl.n++] = n->act[l];
+    if (training) {
+        zl.buf[zl.n++] = n->dO;
+        zl.buf[zl.n++] = n->dA;
+        zl.buf[zl.n++] = n->dB;
+    }
+    const int gblocks = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)G * (B + 1) + 255) / 256, 1024));
+    gap_rows_kernel<<<gblocks, 256, 0, st>>>(off, B, N, R, n->mask, zl);
+    NET_CUDA(n, cudaGetLastError());
+    *R_out = R;
+    return PES_OK;
+}
+
+pes_status forward_layers(pes_init_net* n, int64_t R, cudaStream_t st)
+{
+    for (int l = 0; l < 4; ++l)
+        NET_CUDA(n, (launch_conv<5, EPI_RELU>(n, n->act[l], R, false, l, n->act[l + 1], nullptr, nullptr, st)));
+    NET_CUDA(n, (launch_conv<1, EPI_RELU>(n, n->act[4], R, false, 4, n->act[5], nullptr, nullptr, st)));
+    NET_CUDA(n, (launch_conv<1, EPI_F32>(n, n->act[5], R, false, 5, nullptr, n->out, nullptr, st)));
+    return PES_OK;
+}
+
+template <int TAPS>
+pes_status layer_grad(pes_init_net* n, const bf16* dY, const bf16* X, int64_t R, int layer, float* grad,
+                      cudaStream_t st)
+{
+    const int nblk = 2 * n->num_sms;
+    wgrad_kernel<TAPS><<<nblk, 256, 0, st>>>(dY, X, R, n->wpart);
+    NET_CUDA(n, cudaGetLastError());
+    const int nw = kCoReal[layer] * C * TAPS, nb = kCoReal[layer];
+    wgrad_reduce_kernel<<<(nw + nb + 255) / 256, 256, 0, st>>>(n->wpart, nblk, nw, nb, C * C * TAPS,
+                                                                grad + kPOff[layer]);
+    NET_CUDA(n, cudaGetLastError());
+    return PES_OK;
+}
+
+// Backward pass from dO: every layer's packed gradient into `grad`.
+pes_status backward_layers(pes_init_net* n, int64_t R, float* grad, cudaStream_t st)
+{
+    pes_status s;
+    if ((s = layer_grad<1>(n, n->dO, n->act[5], R, 5, grad, st)) != PES_OK) return s;
+    NET_CUDA(n, (launch_conv<1, EPI_MASK>(n, n->dO, R, true, 5, n->dA, nullptr, n->act[5], st)));
+    if ((s = layer_grad<1>(n, n->dA, n->act[4], R, 4, grad, st)) != PES_OK) return s;
+    NET_CUDA(n, (launch_conv<1, EPI_MASK>(n, n->dA, R, true, 4, n->dB, nullptr, n->act[4], st)));
+    bf16* cur = n->dB;
+    bf16* nxt = n->dA;
+    for (int l = 3; l >= 0; --l) {   // cur: gradient at the pre-activation of conv layer l
+        if ((s = layer_grad<5>(n, cur, n->act[l], R, l, grad, st)) != PES_OK) return s;
+        if (l > 0) {
+            NET_CUDA(n, (launch_conv<5, EPI_MASK>(n, cur, R, true, l, nxt, nullptr, n->act[l], st)));
+            bf16* t = cur;
+            cur = nxt;
+            nxt = t;
+        }
+    }
+    return PES_OK;
+}
+
+pes_status read_status(pes_init_net* n, cudaStream_t st)
+{
+    int h = 0;
+    NET_CUDA(n, cudaMemcpyAsync(&h, n->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NET_CUDA(n, cudaStreamSynchronize(st));
+    if (h) {
+        NET_CUDA(n, cudaMemsetAsync(n->status, 0, sizeof(int), st));
+        return net_fail(n, PES_ERR_TIMEOUT, "a tensor-core pipeline wait ran out of time (status %d)", h);
+    }
+    return PES_OK;
+}
+
+template <typename T>
+pes_status loss_grad_t(pes_init_net* n, const T* y, const int64_t* off, int32_t B, int64_t N, const T* xt,
+                       float* grad, double* loss, cudaStream_t st)
+{
+    int64_t R = 0;
+    pes_status s = prepare_rows<T>(n, y, off, B, N, true, st, &R);
+    if (s != PES_OK) return s;
+    if ((s = forward_layers(n, R, st)) != PES_OK) return s;
+    const float scale = (float)(2.0 / (5.0 * (double)N));
+    loss_kernel<T><<<kLossBlocks, 256, 0, st>>>(n->out, xt, off, B, N, n->norm, scale, n->dO, n->lpart);
+    NET_CUDA(n, cudaGetLastError());
+    sum_kernel<<<1, 256, 0, st>>>(n->lpart, kLossBlocks, 1.0 / (5.0 * (double)N), n->loss_dev);
+    NET_CUDA(n, cudaGetLastError());
+    if ((s = backward_layers(n, R, grad, st)) != PES_OK) return s;
+    if (loss) {
+        NET_CUDA(n, cudaMemcpyAsync(loss, n->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+        return read_status(n, st);
+    }
+    return PES_OK;
+}
+
+pes_status publish(pes_init_net* n, cudaStream_t st)
+{
+    publish_kernel<<<(kWTiles * C * C + NLAYER * C + 255) / 256, 256, 0, st>>>(n->params, n->Wf, n->Wb, n->bias);
+    NET_CUDA(n, cudaGetLastError());
+    return PES_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pes_status pes_init_create(pes_init_net** out, int64_t max_states, int32_t max_batch)
+{
+    if (!out || max_states < 1 || max_batch < 1) return PES_ERR_INVALID_ARG;
+    *out = nullptr;
+    pes_init_net* n = new (std::nothrow) pes_init_net();
+    if (!n) return PES_ERR_CUDA;
+    auto bail = [&](pes_status s) {
+        pes_init_destroy(n);
+        return s;
+    };
+    if (cudaGetDevice(&n->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n->num_sms, cudaDevAttrMultiProcessorCount, n->device) != cudaSuccess)
+        return bail(PES_ERR_CUDA);
+    int major = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, n->device);
+    if (major < 10 || !encode_fn()) return bail(PES_ERR_UNSUPPORTED);
+    n->max_states = max_states;
+    n->max_batch = max_batch;
+    n->max_rows = max_states + (int64_t)G * (max_batch + 1);
+    const size_t rows = (size_t)n->max_rows;
+    bool ok = cudaMalloc(&n->params, sizeof(float) * PES_INIT_NPARAMS) == cudaSuccess &&
+              cudaMalloc(&n->m, sizeof(float) * PES_INIT_NPARAMS) == cudaSuccess &&
+              cudaMalloc(&n->v, sizeof(float) * PES_INIT_NPARAMS) == cudaSuccess &&
+              cudaMalloc(&n->grad, sizeof(float) * PES_INIT_NPARAMS) == cudaSuccess &&
+              cudaMalloc(&n->bias, sizeof(float) * NLAYER * C) == cudaSuccess &&
+              cudaMalloc(&n->wpart, sizeof(float) * (size_t)kWgradStride * 2 * n->num_sms) == cudaSuccess &&
+              cudaMalloc(&n->lpart, sizeof(double) * kLossBlocks) == cudaSuccess &&
+              cudaMalloc(&n->loss_dev, sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&n->Wf, sizeof(bf16) * kWTiles * C * C) == cudaSuccess &&
+              cudaMalloc(&n->Wb, sizeof(bf16) * kWTiles * C * C) == cudaSuccess &&
+              cudaMalloc(&n->out, sizeof(float) * kOutCols * rows) == cudaSuccess &&
+              cudaMalloc(&n->mask, rows) == cudaSuccess && cudaMalloc(&n->status, sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&n->dO, sizeof(bf16) * C * rows) == cudaSuccess &&
+              cudaMalloc(&n->dA, sizeof(bf16) * C * rows) == cudaSuccess &&
+              cudaMalloc(&n->dB, sizeof(bf16) * C * rows) == cudaSuccess;
+    for (int l = 0; ok && l < NLAYER; ++l) ok = cudaMalloc(&n->act[l], sizeof(bf16) * C * rows) == cudaSuccess;
+    if (!ok) return bail(PES_ERR_CUDA);
+    ok = cudaMemset(n->params, 0, sizeof(float) * PES_INIT_NPARAMS) == cudaSuccess &&
+         cudaMemset(n->m, 0, sizeof(float) * PES_INIT_NPARAMS) == cudaSuccess &&
+         cudaMemset(n->v, 0, sizeof(float) * PES_INIT_NPARAMS) == cudaSuccess &&
+         cudaMemset(n->status, 0, sizeof(int)) == cudaSuccess &&
+         cudaMemset(n->dO, 0, sizeof(bf16) * C * rows) == cudaSuccess;
+    if (!ok) return bail(PES_ERR_CUDA);
+    for (int c = 0; c < 5; ++c) {
+        n->norm.mu[c] = 0.0;
+        n->norm.sigma[c] = 1.0;
+    }
+    if (!make_map(&n->mapWf, n->Wf, (uint64_t)kWTiles * C, C) || !make_map(&n->mapWb, n->Wb, (uint64_t)kWTiles * C, C))
+        return bail(PES_ERR_CUDA);
+    if (publish(n, 0) != PES_OK || cudaDeviceSynchronize() != cudaSuccess) return bail(PES_ERR_CUDA);
+    *out = n;
+    return PES_OK;
+}
+
+pes_status pes_init_destroy(pes_init_net* n)
+{
+    if (!n) return PES_ERR_INVALID_ARG;
+    void* ptrs[] = {n->params, n->m, n->v, n->grad, n->bias, n->wpart, n->lpart, n->loss_dev, n->Wf, n->Wb,
+                    n->out, n->mask, n->status, n->dO, n->dA, n->dB};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (int l = 0; l < NLAYER; ++l)
+        if (n->act[l]) cudaFree(n->act[l]);
+    delete n;
+    return PES_OK;
+}
+
+const char* pes_init_last_error(const pes_init_net* n) { return n ? n->err : "NULL net"; }
+
+pes_status pes_init_set_params(pes_init_net* n, const float* params, const double* mu, const double* sigma)
+{
+    if (!n || !params || !mu || !sigma) return net_fail(n, PES_ERR_INVALID_ARG, "NULL argument");
+    for (int c = 0; c < 5; ++c)
+        if (!(sigma[c] > 0.0) || !std::isfinite(mu[c]))
+            return net_fail(n, PES_ERR_INVALID_ARG, "sigma must be positive and mu finite");
+    for (int c = 0; c < 5; ++c) {
+        n->norm.mu[c] = mu[c];
+        n->norm.sigma[c] = sigma[c];
+    }
+    NET_CUDA(n, cudaMemcpy(n->params, params, sizeof(float) * PES_INIT_NPARAMS, cudaMemcpyHostToDevice));
+    NET_CUDA(n, cudaMemset(n->m, 0, sizeof(float) * PES_INIT_NPARAMS));
+    NET_CUDA(n, cudaMemset(n->v, 0, sizeof(float) * PES_INIT_NPARAMS));
+    n->adam_t = 0;
+    pes_status s = publish(n, 0);
+    if (s != PES_OK) return s;
+    NET_CUDA(n, cudaDeviceSynchronize());
+    return PES_OK;
+}
+
+pes_status pes_init_get_params(pes_init_net* n, float* params)
+{
+    if (!n || !params) return net_fail(n, PES_ERR_INVALID_ARG, "NULL argument");
+    NET_CUDA(n, cudaDeviceSynchronize());
+    NET_CUDA(n, cudaMemcpy(params, n->params, sizeof(float) * PES_INIT_NPARAMS, cudaMemcpyDeviceToHost));
+    return PES_OK;
+}
+
+pes_status pes_init_forward(pes_init_net* n, pes_precision prec, const void* y, const int64_t* offsets, int32_t B,
+                            int64_t N, void* x_init, void* stream)
+{
+    pes_status s = check_sizes(n, prec, y, offsets, B, N);
+    if (s != PES_OK) return s;
+    if (!x_init) return net_fail(n, PES_ERR_INVALID_ARG, "NULL x_init");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int64_t R = 0;
+    s = prec == PES_FP64 ? prepare_rows<double>(n, (const double*)y, offsets, B, N, false, st, &R)
+                         : prepare_rows<float>(n, (const float*)y, offsets, B, N, false, st, &R);
+    if (s != PES_OK) return s;
+    if ((s = forward_layers(n, R, st)) != PES_OK) return s;
+    const int blocks = (int)std::min<int64_t>((N + 255) / 256, (int64_t)n->num_sms * 16);
+    if (prec == PES_FP64)
+        denorm_kernel<double><<<blocks, 256, 0, st>>>(n->out, offsets, B, N, n->norm, (double*)x_init);
+    else
+        denorm_kernel<float><<<blocks, 256, 0, st>>>(n->out, offsets, B, N, n->norm, (float*)x_init);
+    NET_CUDA(n, cudaGetLastError());
+    return PES_OK;
+}
+
+pes_status pes_init_loss_grad(pes_init_net* n, pes_precision prec, const void* y, const int64_t* offsets, int32_t B,
+                              int64_t N, const void* x_target, float* grad, double* loss, void* stream)
+{
+    pes_status s = check_sizes(n, prec, y, offsets, B, N);
+    if (s != PES_OK) return s;
+    if (!x_target || !grad) return net_fail(n, PES_ERR_INVALID_ARG, "NULL x_target or grad");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return prec == PES_FP64
+               ? loss_grad_t<double>(n, (const double*)y, offsets, B, N, (const double*)x_target, grad, loss, st)
+               : loss_grad_t<float>(n, (const float*)y, offsets, B, N, (const float*)x_target, grad, loss, st);
+}
+
+pes_status pes_init_train_step(pes_init_net* n, pes_precision prec, const void* y, const int64_t* offsets,
+                               int32_t B, int64_t N, const void* x_target, float lr, double* loss, void* stream)
+{
+    if (n && !(lr > 0.f)) return net_fail(n, PES_ERR_INVALID_ARG, "lr must be positive");
+    pes_status s = pes_init_loss_grad(n, prec, y, offsets, B, N, x_target, n ? n->grad : nullptr, loss, stream);
+    if (s != PES_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    n->adam_t += 1;
+    const double b1 = 0.9, b2 = 0.999;
+    const float c1 = (float)(1.0 / (1.0 - std::pow(b1, n->adam_t)));
+    const float c2 = (float)(1.0 / (1.0 - std::pow(b2, n->adam_t)));
+    adam_kernel<<<(PES_INIT_NPARAMS + 255) / 256, 256, 0, st>>>(n->params, n->m, n->v, n->grad, PES_INIT_NPARAMS,
+                                                                lr, (float)b1, (float)b2, 1e-8f, c1, c2);
+    NET_CUDA(n, cudaGetLastError());
+    return publish(n, st);
+}
+
+}  // extern "C"

@@ -1,0 +1,139 @@
+// Tensor-core building blocks for sm_103a: TMA tile loads, tcgen05 MMAs with
+// accumulators in tensor memory (TMEM), and their completion barriers.
+//
+// Operand tiles are bf16, K-major, 128-byte swizzled: a tile of R rows holds
+// 64 bf16 (128 B) per row in 1024-byte atoms of 8 rows, exactly what a TMA
+// load with CU_TENSOR_MAP_SWIZZLE_128B and a {64, R} box writes. One MMA
+// consumes K = 16 of the 64 columns; the next 16 start 32 bytes further on.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "pes_async.cuh"
+
+namespace pes {
+namespace tc {
+
+// 2-D tiled TMA load of the box at (x, y) into shared memory, completing
+// bytes on `bar`. x (the inner coordinate) must be a multiple of 8 bf16
+// elements (16 bytes); y may be negative or past the end (zero fill).
+PES_DEV void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+PES_DEV void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+PES_DEV void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait; returns false (and sets ST_TIMEOUT) when it gives up or when
+// another role of the block has already given up (`*abort` != 0).
+PES_DEV bool wait_or_abort(uint64_t* bar, uint32_t parity, int* status, volatile int* abort)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = async_now_ns();
+    for (unsigned polls = 0;; ++polls) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort) return false;
+        if (polls > (1u << 24) || async_now_ns() - t0 > 1000000000LL) {
+            atomicOr(status, ST_TIMEOUT);
+            *abort = 1;
+            return false;
+        }
+    }
+}
+
+// ---- tensor memory -------------------------------------------------------------
+
+// Allocate `ncols` TMEM columns (power of two >= 32); the whole warp calls.
+// The TMEM address lands in *slot (shared memory).
+PES_DEV void tmem_alloc(uint32_t* slot, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+PES_DEV void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+PES_DEV void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+PES_DEV void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// ---- descriptors ---------------------------------------------------------------
+
+// Shared-memory matrix descriptor of a K-major, 128-byte-swizzled bf16 tile
+// whose 8-row atoms are 1024 bytes apart (start address 1024-aligned, or
+// advanced along K inside the atom by multiples of 32 bytes).
+PES_DEV uint64_t smem_desc_sw128(const void* tile)
+{
+    const uint64_t addr = smem_u32(tile);
+    return ((addr >> 4) & 0x3FFFull)        // start address
+           | (1ull << 16)                   // leading byte offset (unused for swizzled K-major)
+           | ((1024ull >> 4) << 32)         // stride byte offset: next 8-row atom
+           | (1ull << 46)                   // descriptor version
+           | (2ull << 61);                  // 128-byte swizzle
+}
+
+// Instruction descriptor of kind::f16: bf16 A and B (both K-major), f32
+// accumulator, shape M x N.
+constexpr uint32_t idesc_bf16_f32(int M, int N)
+{
+    return (1u << 4)                        // D: f32
+           | (1u << 7)                      // A: bf16
+           | (1u << 10)                     // B: bf16
+           | ((uint32_t)(N >> 3) << 17)     // N / 8
+           | ((uint32_t)(M >> 4) << 24);    // M / 16
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T for one K = 16 slice; issued by one thread.
+PES_DEV void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc, bool accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"((uint32_t)accumulate)
+        : "memory");
+}
+
+// Arrive on `bar` once every MMA this thread has issued so far completes.
+PES_DEV void mma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 16 consecutive 32-bit columns of this thread's TMEM lane (32x32b shape: the
+// warp reads lanes 32 * (warp % 4) .. + 31, thread t lane + t).
+PES_DEV void tmem_ld16(uint32_t taddr, float* v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+}  // namespace tc
+}  // namespace pes

@@ -29,7 +29,10 @@ MODEL_CT_BEARINGS, MODEL_LINEAR = 0, 1
 
 EXPORTED = ["pes_create", "pes_destroy", "pes_last_error", "pes_sync", "pes_linearize", "pes_filter_scan",
             "pes_smooth_scan", "pes_ieks_run", "pes_ieks_run_host", "pes_launch_shape", "pes_measure_fma_peak",
-            "pes_debug_phase_times", "pes_ieks_run_noalloc"]
+            "pes_debug_phase_times", "pes_ieks_run_noalloc",
+            "pes_init_create", "pes_init_destroy", "pes_init_last_error", "pes_init_set_params",
+            "pes_init_get_params", "pes_init_forward", "pes_init_loss_grad", "pes_init_train_step"]
+INIT_NPARAMS = 86661
 
 
 class PesError(RuntimeError):
@@ -78,8 +81,17 @@ def load_library():
     lib.pes_debug_phase_times.argtypes = [p, ctypes.POINTER(d), ctypes.POINTER(d), i32]
     lib.pes_ieks_run_noalloc.argtypes = [mp, i32, i32, p, p, i32, i64, p, p, p, p, i32, d, p, p,
                                          ctypes.POINTER(i32), p]
+    lib.pes_init_create.argtypes = [ctypes.POINTER(p), i64, i32]
+    lib.pes_init_destroy.argtypes = [p]
+    lib.pes_init_last_error.argtypes = [p]
+    lib.pes_init_last_error.restype = ctypes.c_char_p
+    lib.pes_init_set_params.argtypes = [p, p, p, p]
+    lib.pes_init_get_params.argtypes = [p, p]
+    lib.pes_init_forward.argtypes = [p, i32, p, p, i32, i64, p, p]
+    lib.pes_init_loss_grad.argtypes = [p, i32, p, p, i32, i64, p, p, ctypes.POINTER(d), p]
+    lib.pes_init_train_step.argtypes = [p, i32, p, p, i32, i64, p, ctypes.c_float, ctypes.POINTER(d), p]
     for name in EXPORTED:
-        if name != "pes_last_error":
+        if name not in ("pes_last_error", "pes_init_last_error"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -303,3 +315,82 @@ class Smoother:
                                         h(P_out), ctypes.byref(used), _stream(stream))
         self._check(st, allow=(NOT_CONVERGED,) if allow_not_converged else ())
         return x_out, P_out, used.value, st
+
+
+class InitNet:
+    """A ``pes_init_net``: the learned initialiser (include/pes_init.h) on the
+    current CUDA device. Parameters are a float32 vector of INIT_NPARAMS."""
+
+    def __init__(self, max_states: int, max_batch: int = 1):
+        if not torch.cuda.is_available():
+            raise RuntimeError("the learned initialiser needs a CUDA GPU; there is no CPU fallback")
+        self.lib = load_library()
+        torch.cuda.init()
+        h = ctypes.c_void_p()
+        st = self.lib.pes_init_create(ctypes.byref(h), int(max_states), int(max_batch))
+        if st != OK:
+            raise PesError(st, "pes_init_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pes_init_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != OK:
+            raise PesError(st, self.lib.pes_init_last_error(self.h).decode())
+        return st
+
+    def set_params(self, params, mu, sigma):
+        import numpy as np
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.shape != (INIT_NPARAMS,):
+            raise ValueError(f"expected {INIT_NPARAMS} parameters")
+        m = np.ascontiguousarray(mu, dtype=np.float64)
+        sg = np.ascontiguousarray(sigma, dtype=np.float64)
+        self._check(self.lib.pes_init_set_params(self.h, p.ctypes.data, m.ctypes.data, sg.ctypes.data))
+
+    def get_params(self):
+        import numpy as np
+        p = np.empty(INIT_NPARAMS, dtype=np.float32)
+        self._check(self.lib.pes_init_get_params(self.h, p.ctypes.data))
+        return p
+
+    def forward(self, prec: int, y, offsets, x_out=None, stream=None):
+        dt = _dtype(prec)
+        N = y.shape[1]
+        B = offsets.shape[0] - 1
+        if x_out is None:
+            x_out = torch.empty((5, N), dtype=dt, device=y.device)
+        self._check(self.lib.pes_init_forward(self.h, prec, _ptr(y, dt), _ptr(offsets, torch.int64), B, N,
+                                              _ptr(x_out, dt), _stream(stream)))
+        return x_out
+
+    def loss_grad(self, prec: int, y, offsets, x_target, grad=None, stream=None):
+        dt = _dtype(prec)
+        N = y.shape[1]
+        B = offsets.shape[0] - 1
+        if grad is None:
+            grad = torch.empty(INIT_NPARAMS, dtype=torch.float32, device=y.device)
+        loss = ctypes.c_double()
+        self._check(self.lib.pes_init_loss_grad(self.h, prec, _ptr(y, dt), _ptr(offsets, torch.int64), B, N,
+                                                _ptr(x_target, dt), _ptr(grad, torch.float32), ctypes.byref(loss),
+                                                _stream(stream)))
+        return loss.value, grad
+
+    def train_step(self, prec: int, y, offsets, x_target, lr: float, want_loss: bool = True, stream=None):
+        dt = _dtype(prec)
+        N = y.shape[1]
+        B = offsets.shape[0] - 1
+        loss = ctypes.c_double()
+        self._check(self.lib.pes_init_train_step(self.h, prec, _ptr(y, dt), _ptr(offsets, torch.int64), B, N,
+                                                 _ptr(x_target, dt), float(lr),
+                                                 ctypes.byref(loss) if want_loss else None, _stream(stream)))
+        return loss.value if want_loss else None

@@ -1,4 +1,4 @@
-"""The C-ABI library loads and exports every entry point include/pes.h declares
+"""The C-ABI library loads and exports every entry point include/*.h declares
 (no compute calls: this runs without a GPU)."""
 import ctypes
 import os
@@ -12,14 +12,19 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_symbols():
-    src = open(os.path.join(ROOT, "include", "pes.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(pes_[a-z_]+)\s*\(", src)))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for h in sorted(os.listdir(inc)):
+        if h.endswith(".h"):
+            src = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, h)).read(), flags=re.S)
+            names |= set(re.findall(r"\b(pes_[a-z_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
     names = declared_symbols()
-    for required in ("pes_linearize", "pes_filter_scan", "pes_smooth_scan", "pes_ieks_run"):
+    for required in ("pes_linearize", "pes_filter_scan", "pes_smooth_scan", "pes_ieks_run", "pes_init_forward",
+                     "pes_init_train_step"):
         assert required in names
 
 

@@ -1,0 +1,154 @@
+"""The learned initialiser on the GPU (include/pes_init.h) against its oracle
+(oracle/learned_init.py), element by element, and what it gains.
+
+Tolerances. Both sides round the same quantities to bfloat16 (weights,
+features, hidden activations, backward operands). The device sums in FP32
+where the oracle sums exactly, so a rounding to bfloat16 can land on the other
+side of a tie in about 1e-6 / 4e-3 of the elements (FP32 error of a 320-term
+sum over one bfloat16 step); each such element moves by one bfloat16 step
+(2^-8 relative). Over six layers that gives relative errors of order 1e-4 on
+outputs and gradients; the bounds below leave a factor of ten.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import learned_init as li
+from paper_2102_00514_gb300 import pes, synth
+from tests.gpu_common import gpu_run, rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+TOL_OUT = 2e-3
+TOL_GRAD = 5e-3
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def random_params(seed):
+    rng = np.random.default_rng(seed)
+    layers = li.unpack(li.init_params(seed))
+    layers = [(W, 0.05 + 0.1 * rng.standard_normal(b.shape)) for W, b in layers]
+    return li.pack(layers).astype(np.float32)
+
+
+def workload(T_list, seed):
+    wl = synth.ct_bearings(T_list, seed=seed, omega0_halfwidth=1.0)
+    return wl
+
+
+def per_traj(wl):
+    off = wl["offsets"]
+    for b in range(len(off) - 1):
+        yield b, slice(int(off[b]), int(off[b + 1]))
+
+
+@pytest.fixture(scope="module")
+def net():
+    n = pes.InitNet(1 << 20, 4096)
+    yield n
+    n.close()
+
+
+@pytest.mark.parametrize("prec", [pes.FP32, pes.FP64])
+def test_forward_matches_oracle(net, prec):
+    # several 128-row tiles, a one-step and a one-state-after-prior trajectory, a ragged tail
+    wl = workload([1000, 7, 300, 1, 129], seed=11)
+    params = random_params(1)
+    mu = np.array([0.5, -0.2, 1.0, 0.1, 0.0])
+    sigma = np.array([2.0, 1.5, 0.8, 0.9, 0.3])
+    net.set_params(params, mu, sigma)
+    dt = torch.float32 if prec == pes.FP32 else torch.float64
+    y = to_dev(wl["y"], dt)
+    x = net.forward(prec, y, to_dev(wl["offsets"], torch.int64))
+    torch.cuda.synchronize()
+    got = x.double().cpu().numpy()
+    yin = f32(wl["y"]) if prec == pes.FP32 else wl["y"]
+    worst = 0.0
+    for b, sl in per_traj(wl):
+        ref = li.initial_nominal(params, yin[:, sl], sl.stop - sl.start - 1, mu, sigma)
+        worst = max(worst, rel_err(got[:, sl], ref, [0, sl.stop - sl.start]))
+    print(f"forward prec {prec}: worst relative error {worst:.2e}")
+    assert worst < TOL_OUT
+
+
+def test_forward_of_a_batch_equals_separate_calls(net):
+    wl = workload([40, 200, 3], seed=12)
+    params = random_params(2)
+    net.set_params(params, np.zeros(5), np.ones(5))
+    xb = net.forward(pes.FP32, to_dev(wl["y"], torch.float32), to_dev(wl["offsets"], torch.int64))
+    for b, sl in per_traj(wl):
+        off = to_dev(np.array([0, sl.stop - sl.start]), torch.int64)
+        x1 = net.forward(pes.FP32, to_dev(wl["y"][:, sl], torch.float32), off)
+        assert torch.equal(x1, xb[:, sl])
+
+
+def test_loss_and_gradient_match_oracle(net):
+    wl = workload([600, 5, 200, 77], seed=13)
+    params = random_params(3)
+    xt = wl["x_true"]
+    mu, sigma = xt.mean(axis=1), xt.std(axis=1) + 0.1
+    net.set_params(params, mu, sigma)
+    loss, g = net.loss_grad(pes.FP32, to_dev(wl["y"], torch.float32), to_dev(wl["offsets"], torch.int64),
+                            to_dev(xt, torch.float32))
+    g = g.double().cpu().numpy()
+    trajs = [(f32(wl["y"][:, sl]), f32(xt[:, sl])) for _, sl in per_traj(wl)]
+    ref_loss, ref_g = li.loss_and_grad(params, trajs, mu, sigma)
+    assert abs(loss - ref_loss) / ref_loss < TOL_OUT
+    starts = np.cumsum([0] + [int(np.prod(w)) + int(np.prod(b)) for w, b in li.SHAPES])
+    names = []
+    for l, (ws, bs) in enumerate(li.SHAPES):
+        names += [(f"W{l + 1}", int(np.prod(ws))), (f"b{l + 1}", int(np.prod(bs)))]
+    i = 0
+    for name, n in names:
+        e = np.linalg.norm(g[i:i + n] - ref_g[i:i + n]) / np.linalg.norm(ref_g[i:i + n])
+        print(f"gradient {name}: relative error {e:.2e}")
+        assert e < TOL_GRAD, name
+        i += n
+    assert i == starts[-1]
+
+
+def test_adam_step_matches_oracle(net):
+    wl = workload([300, 50], seed=14)
+    params = random_params(4)
+    xt = wl["x_true"]
+    mu, sigma = xt.mean(axis=1), xt.std(axis=1) + 0.1
+    net.set_params(params, mu, sigma)
+    y, off, xtd = to_dev(wl["y"], torch.float32), to_dev(wl["offsets"], torch.int64), to_dev(xt, torch.float32)
+    _, g = net.loss_grad(pes.FP32, y, off, xtd)
+    g = g.double().cpu().numpy()
+    opt = li.Adam(lr=1e-3)
+    expect = params
+    for _ in range(2):   # two steps from the same parameters' gradient: moments and bias correction
+        net.train_step(pes.FP32, y, off, xtd, 1e-3)
+        expect = opt.step(expect, g)
+        _, g_next = net.loss_grad(pes.FP32, y, off, xtd)
+        got = net.get_params()
+        assert np.abs(got.astype(np.float64) - expect).max() < 1e-6
+        g = g_next.double().cpu().numpy()
+
+
+def test_training_reduces_the_loss(net):
+    wl = workload([1000] * 16, seed=15)
+    xt = wl["x_true"]
+    mu, sigma = xt.mean(axis=1), xt.std(axis=1)
+    net.set_params(li.init_params(5), mu, sigma)
+    y, off, xtd = to_dev(wl["y"], torch.float32), to_dev(wl["offsets"], torch.int64), to_dev(xt, torch.float32)
+    first = net.train_step(pes.FP32, y, off, xtd, 2e-3)
+    for _ in range(200):
+        last = net.train_step(pes.FP32, y, off, xtd, 2e-3)
+    print(f"training loss {first:.4f} -> {last:.4f}")
+    assert last < 0.2 * first
+
+
+def test_invalid_arguments_rejected(net):
+    y = torch.zeros((2, 10), dtype=torch.float32, device="cuda")
+    off = to_dev(np.array([0, 10]), torch.int64)
+    with pytest.raises(pes.PesError) as ei:
+        net.forward(pes.MIXED, y, off)
+    assert ei.value.status == pes.INVALID_ARG
+    with pytest.raises(pes.PesError) as ei:
+        net.set_params(np.zeros(pes.INIT_NPARAMS, np.float32), np.zeros(5), np.array([1, 1, 0, 1, 1.0]))
+    assert ei.value.status == pes.INVALID_ARG
