@@ -214,6 +214,19 @@ pes_status pes_ieks_run_host(pes_handle* h, const pes_model* model, pes_method m
                              void* stream);
 
 /*
+ * Per-trajectory iteration counts of the last pes_ieks_run or
+ * pes_ieks_run_host call on this handle that ran in tolerance mode (tol > 0)
+ * with PES_FP32 or PES_FP64: iters[b] (HOST int32 [B]) is the first iteration
+ * after which trajectory b's relative update norm (Sec. 3 iteration; the
+ * measure of the tolerance) was <= tol, or 0 if it never was within the
+ * iterations run. The run continues until every trajectory meets tol or
+ * max_iters is reached, so trajectories that met it early keep iterating.
+ * B must equal that call's batch size (PES_ERR_INVALID_ARG otherwise).
+ * Waits for the work on `stream`.
+ */
+pes_status pes_traj_iterations(pes_handle* h, int32_t* iters, int32_t B, void* stream);
+
+/*
  * pes_ieks_run without a handle and without allocating device memory. The
  * paper has no counterpart: this is a deployment variant of pes_ieks_run.
  *

@@ -158,6 +158,7 @@ void fill_workspace(pes_handle* h, KParams<T>& p, const Shape& s)
     p.status = h->status;
     p.conv = h->conv;
     p.iters_done = h->iters_done;
+    p.traj_iters = nullptr;
     p.L = s.L;
     p.NL = s.nb * s.nt;
     p.cs = p.lanes_layout ? (int64_t)s.L * p.NL : p.N;
@@ -199,7 +200,14 @@ pes_status run_persistent_shaped(pes_handle* h, KParams<T>& p, int lin, const Sh
 {
     fill_workspace(h, p, s);
     PES_CUDA(h, cudaMemsetAsync(h->bar, 0, sizeof(unsigned), st));
-    if (p.mode == MODE_RUN && p.tol > 0.0) PES_CUDA(h, cudaMemsetAsync(h->conv, 0, sizeof(double) * 4 * p.B, st));
+    if (p.mode == MODE_RUN && p.tol > 0.0) {
+        PES_CUDA(h, cudaMemsetAsync(h->conv, 0, sizeof(double) * 4 * p.B, st));
+        if (h->traj_iters) {
+            PES_CUDA(h, cudaMemsetAsync(h->traj_iters, 0, sizeof(int) * p.B, st));
+            p.traj_iters = h->traj_iters;
+            h->traj_iters_B = p.B;
+        }
+    }
     cudaError_t e = launch_persistent(p, lin, s.nt, s.nb, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "cooperative launch of the smoother kernel");
     return PES_OK;
@@ -369,6 +377,7 @@ pes_status pes_create(pes_handle** out, int64_t max_states, int32_t max_batch)
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->status, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->conv, sizeof(double) * 4 * (size_t)max_batch);
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->iters_done, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->traj_iters, sizeof(int) * (size_t)max_batch);
     if (e == cudaSuccess) e = cudaMalloc(&h->sensT, sizeof(double) * 4 * (size_t)max_batch);
     if (e == cudaSuccess && getenv("PES_PHASE_TIMES") && atoi(getenv("PES_PHASE_TIMES")) > 0) {
         e = cudaMalloc((void**)&h->ptime, sizeof(long long) * NPHASE * (size_t)h->nb_max);
@@ -387,7 +396,7 @@ pes_status pes_destroy(pes_handle* h)
 {
     if (!h) return PES_ERR_INVALID_ARG;
     cudaDeviceSynchronize();
-    void* ptrs[] = {h->hand, h->lanes, h->lin, h->mix, h->aggF, h->aggS, h->bar, h->status, h->conv, h->iters_done, h->sensT, h->ptime,
+    void* ptrs[] = {h->hand, h->lanes, h->lin, h->mix, h->aggF, h->aggS, h->bar, h->status, h->conv, h->iters_done, h->traj_iters, h->sensT, h->ptime,
                     h->hy, h->hoff, h->hm0, h->hP0, h->hx, h->hP, h->hxi, h->hPi, h->hsens};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -534,6 +543,17 @@ pes_status pes_ieks_run(pes_handle* h, const pes_model* model, pes_method method
                                   x_out, P_out, iters_used, st);
     return ieks_run_t<float>(h, model, method, prec, y, offsets, B, N, m0, P0, x_init, P_init, max_iters, tol, x_out,
                              P_out, iters_used, st);
+}
+
+pes_status pes_traj_iterations(pes_handle* h, int32_t* iters, int32_t B, void* stream)
+{
+    if (!h || !iters) return fail(h, PES_ERR_INVALID_ARG, "NULL argument");
+    if (B != h->traj_iters_B || B < 1)
+        return fail(h, PES_ERR_INVALID_ARG, "no tolerance-mode run over %d trajectories was recorded", (int)B);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    PES_CUDA(h, cudaMemcpyAsync(iters, h->traj_iters, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, st));
+    PES_CUDA(h, cudaStreamSynchronize(st));
+    return PES_OK;
 }
 
 pes_status pes_ieks_run_host(pes_handle* h, const pes_model* model, pes_method method, pes_precision prec,

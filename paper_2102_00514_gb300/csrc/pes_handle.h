@@ -18,6 +18,8 @@ struct pes_handle {
     int* status = nullptr;
     double* conv = nullptr;
     int* iters_done = nullptr;
+    int* traj_iters = nullptr;   // [max_batch]: per-trajectory iterations of the last tolerance-mode run
+    int traj_iters_B = 0;        // its number of trajectories (0: none recorded)
     // device copies for pes_ieks_run_host (allocated by its first call)
     void* hy = nullptr;
     int64_t* hoff = nullptr;

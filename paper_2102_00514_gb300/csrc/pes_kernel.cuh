@@ -73,6 +73,7 @@ struct KParams {
     int* status;       // ST_* bits
     double* conv;      // [2][B][2] update-norm accumulators, zero at launch
     int* iters_done;
+    int* traj_iters;   // RUN with tol > 0: [B], the first iteration whose update met tol (0: none); or NULL
     int L;             // steps per lane
     int NL;            // lanes = NB * NT
     int lanes_layout;  // x, P, y use the kernel's lane-major layout (MODE_RUN)
@@ -1052,6 +1053,7 @@ __global__ void __launch_bounds__(NT, 1) pes_persistent_kernel(const KParams<T> 
                     const double num = __ldcg(conv + 2 * b), den = __ldcg(conv + 2 * b + 1);
                     const double r = den > 0.0 ? sqrt(num / den) : sqrt(num);
                     worst = fmax(worst, r);
+                    if (p.traj_iters && blockIdx.x == 0 && r <= p.tol && p.traj_iters[b] == 0) p.traj_iters[b] = it + 1;
                 }
                 s_red[t] = worst;
                 __syncthreads();

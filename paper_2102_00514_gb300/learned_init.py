@@ -1,0 +1,200 @@
+"""Training and evaluation of the learned initialiser (include/pes_init.h).
+
+The network maps a trajectory's measurements to the nominal trajectory the
+iterated smoother (Sec. 3) starts from. Its training targets are the means the
+FP64 smoother itself reaches when iterated to convergence; its use is judged
+by the smoother, not by the network's own error: iterations needed to reach a
+relative update of 1e-6, and the converged result, against the plain start
+from the prior mean.
+
+Everything numerical runs in the library's kernels (the smoother, the
+network's forward and backward passes and its Adam steps); this module only
+arranges device buffers (PyTorch) and bookkeeping on the host.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import pes, synth
+
+TOL_TARGETS = 1e-9      # relative update at which a training target counts as converged
+TOL_EVAL = 1e-6         # the tolerance iterations are counted to
+MAX_ITERS = 50
+
+
+def _dev(a, dt):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+
+
+def converged_targets(wl: dict, method: int = pes.IEKS, chunk_states: int = 1 << 23, tol: float = TOL_TARGETS,
+                      max_iters: int = MAX_ITERS):
+    """FP64 smoother means of every trajectory, iterated to `tol` from the prior,
+    in chunks of whole trajectories. Returns (x [5][N] float64 host, converged
+    bool [B])."""
+    off = wl["offsets"]
+    B = len(off) - 1
+    N = int(off[-1])
+    x = np.empty((5, N))
+    conv = np.zeros(B, dtype=bool)
+    longest = int(np.diff(off).max())
+    sm = pes.Smoother(max(chunk_states, longest), B)
+    model = pes.Model.from_workload(wl)
+    b0 = 0
+    while b0 < B:
+        b1 = int(np.searchsorted(off, off[b0] + chunk_states, side="right")) - 1
+        b1 = max(b1, b0 + 1)
+        a, e = int(off[b0]), int(off[b1])
+        sub_off = off[b0:b1 + 1] - a
+        sub_model = pes.Model.from_workload(dict(wl, sensors=wl["sensors"][b0:b1])) if len(wl["sensors"]) > 1 \
+            else model
+        xs, _, _, _ = sm.ieks_run(sub_model, method, pes.FP64, _dev(wl["y"][:, a:e], torch.float64),
+                                  _dev(sub_off, torch.int64), _dev(wl["m0"][b0:b1], torch.float64),
+                                  _dev(wl["P0"][b0:b1], torch.float64), iters=max_iters, tol=tol,
+                                  allow_not_converged=True)
+        conv[b0:b1] = sm.traj_iterations(b1 - b0) > 0
+        x[:, a:e] = xs.cpu().numpy()
+        b0 = b1
+    sm.close()
+    return x, conv
+
+
+def normalisation(x: np.ndarray):
+    mu = x.mean(axis=1)
+    sigma = x.std(axis=1)
+    return mu, np.where(sigma > 0, sigma, 1.0)
+
+
+# Packed parameter shapes (include/pes_init.h): 4 conv layers W [64][64][5],
+# b [64]; W5 [64][64], b5 [64]; W6 [5][64], b6 [5].
+SHAPES = [((64, 64, 5), 64)] * 4 + [((64, 64), 64), ((5, 64), 5)]
+
+
+def initial_params(seed: int) -> np.ndarray:
+    """He-normal weights (fan-in = input channels x taps), zero biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for ws, nb in SHAPES:
+        fan_in = int(np.prod(ws[1:]))
+        parts += [rng.standard_normal(int(np.prod(ws))) * np.sqrt(2.0 / fan_in), np.zeros(nb)]
+    p = np.concatenate(parts).astype(np.float32)
+    assert p.shape == (pes.INIT_NPARAMS,)
+    return p
+
+
+@dataclass
+class TrainLog:
+    steps: int = 0
+    seconds: float = 0.0
+    losses: list = field(default_factory=list)
+
+
+def train(net: pes.InitNet, wl: dict, targets: np.ndarray, keep: np.ndarray, *, batch_traj: int = 128,
+          steps: int = 2000, lr: float = 2e-3, lr_final: float = 2e-4, seed: int = 0,
+          log_every: int = 100) -> TrainLog:
+    """Adam on minibatches of `batch_traj` whole trajectories of one length,
+    the learning rate decayed geometrically from lr to lr_final. Only the
+    trajectories with keep[b] (converged targets) are used. The network's
+    parameters and normalisation must be set before."""
+    off = wl["offsets"]
+    lens = np.diff(off)
+    if not np.all(lens == lens[0]):
+        raise ValueError("training trajectories must share one length")
+    n1 = int(lens[0])
+    idx = np.flatnonzero(keep)
+    nmb = len(idx) // batch_traj
+    if nmb < 1:
+        raise ValueError("fewer kept trajectories than one minibatch")
+    idx = idx[:nmb * batch_traj]
+    # [minibatch][component][states] so that each minibatch is one contiguous
+    # component-major block (the layout of the ABI)
+    y = torch.as_tensor(wl["y"], dtype=torch.float32).reshape(2, -1, n1)[:, idx]
+    xt = torch.as_tensor(targets, dtype=torch.float32).reshape(5, -1, n1)[:, idx]
+    Y = y.reshape(2, nmb, batch_traj * n1).permute(1, 0, 2).contiguous().cuda()
+    X = xt.reshape(5, nmb, batch_traj * n1).permute(1, 0, 2).contiguous().cuda()
+    moff = _dev(np.arange(batch_traj + 1, dtype=np.int64) * n1, torch.int64)
+    rng = np.random.default_rng(seed)
+    log = TrainLog()
+    order = rng.permutation(nmb)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(steps):
+        if s and s % nmb == 0:
+            order = rng.permutation(nmb)
+        m = int(order[s % nmb])
+        a = lr * (lr_final / lr) ** (s / max(1, steps - 1))
+        want = (s % log_every == 0) or s == steps - 1
+        loss = net.train_step(pes.FP32, Y[m], moff, X[m], a, want_loss=want)
+        if want:
+            log.losses.append((s, loss))
+    torch.cuda.synchronize()
+    log.seconds = time.perf_counter() - t0
+    log.steps = steps
+    return log
+
+
+@dataclass
+class EvalResult:
+    iters_prior: np.ndarray        # per trajectory, 0 = tolerance not reached
+    iters_learned: np.ndarray
+    err_prior: np.ndarray          # per trajectory RMS position error against the truth
+    err_learned: np.ndarray
+    rel_diff: np.ndarray           # ||x_learned - x_prior|| / ||x_prior|| per trajectory
+    seconds: float
+
+
+def evaluate(net: pes.InitNet, wl: dict, method: int = pes.IEKS, tol: float = TOL_EVAL,
+             max_iters: int = MAX_ITERS) -> EvalResult:
+    """Iterations to `tol` and converged results from the prior start and from
+    the network's start, every trajectory of `wl` in one FP64 batch each."""
+    off = wl["offsets"]
+    B = len(off) - 1
+    N = int(off[-1])
+    sm = pes.Smoother(N, B)
+    model = pes.Model.from_workload(wl)
+    y = _dev(wl["y"], torch.float64)
+    o = _dev(off, torch.int64)
+    m0, P0 = _dev(wl["m0"], torch.float64), _dev(wl["P0"], torch.float64)
+    t0 = time.perf_counter()
+    xa, _, _, _ = sm.ieks_run(model, method, pes.FP64, y, o, m0, P0, iters=max_iters, tol=tol,
+                              allow_not_converged=True)
+    ia = sm.traj_iterations(B)
+    x0 = net.forward(pes.FP64, y, o)
+    xb, _, _, _ = sm.ieks_run(model, method, pes.FP64, y, o, m0, P0, x_init=x0, iters=max_iters, tol=tol,
+                              allow_not_converged=True)
+    ib = sm.traj_iterations(B)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    xa, xb = xa.cpu().numpy(), xb.cpu().numpy()
+    sm.close()
+    xt = wl["x_true"]
+    ea, eb, rd = np.zeros(B), np.zeros(B), np.zeros(B)
+    for b in range(B):
+        sl = slice(int(off[b]), int(off[b + 1]))
+        ea[b] = np.sqrt(np.mean((xa[0:2, sl] - xt[0:2, sl]) ** 2) * 2)
+        eb[b] = np.sqrt(np.mean((xb[0:2, sl] - xt[0:2, sl]) ** 2) * 2)
+        rd[b] = np.linalg.norm(xb[:, sl] - xa[:, sl]) / max(np.linalg.norm(xa[:, sl]), 1e-300)
+    return EvalResult(ia, ib, ea, eb, rd, secs)
+
+
+def summary(r: EvalResult) -> dict:
+    """Iterations saved on the trajectories both starts bring to tolerance, and
+    how often each start gets there."""
+    both = (r.iters_prior > 0) & (r.iters_learned > 0)
+    out = {"trajectories": int(len(r.iters_prior)),
+           "converged_prior": int((r.iters_prior > 0).sum()),
+           "converged_learned": int((r.iters_learned > 0).sum()),
+           "converged_both": int(both.sum())}
+    if both.any():
+        out.update({
+            "mean_iters_prior": float(r.iters_prior[both].mean()),
+            "mean_iters_learned": float(r.iters_learned[both].mean()),
+            "iters_saved": float((r.iters_prior[both] - r.iters_learned[both]).mean()),
+            "same_solution_within_1e-4": int((r.rel_diff[both] < 1e-4).sum()),
+            "median_position_rmse_prior": float(np.median(r.err_prior[both])),
+            "median_position_rmse_learned": float(np.median(r.err_learned[both])),
+        })
+    return out

@@ -29,7 +29,7 @@ MODEL_CT_BEARINGS, MODEL_LINEAR = 0, 1
 
 EXPORTED = ["pes_create", "pes_destroy", "pes_last_error", "pes_sync", "pes_linearize", "pes_filter_scan",
             "pes_smooth_scan", "pes_ieks_run", "pes_ieks_run_host", "pes_launch_shape", "pes_measure_fma_peak",
-            "pes_debug_phase_times", "pes_ieks_run_noalloc",
+            "pes_debug_phase_times", "pes_ieks_run_noalloc", "pes_traj_iterations",
             "pes_init_create", "pes_init_destroy", "pes_init_last_error", "pes_init_set_params",
             "pes_init_get_params", "pes_init_forward", "pes_init_loss_grad", "pes_init_train_step"]
 INIT_NPARAMS = 86661
@@ -81,6 +81,7 @@ def load_library():
     lib.pes_debug_phase_times.argtypes = [p, ctypes.POINTER(d), ctypes.POINTER(d), i32]
     lib.pes_ieks_run_noalloc.argtypes = [mp, i32, i32, p, p, i32, i64, p, p, p, p, i32, d, p, p,
                                          ctypes.POINTER(i32), p]
+    lib.pes_traj_iterations.argtypes = [p, ctypes.POINTER(i32), i32, p]
     lib.pes_init_create.argtypes = [ctypes.POINTER(p), i64, i32]
     lib.pes_init_destroy.argtypes = [p]
     lib.pes_init_last_error.argtypes = [p]
@@ -227,6 +228,14 @@ class Smoother:
         mean, mx = (ctypes.c_double * n)(), (ctypes.c_double * n)()
         self._check(self.lib.pes_debug_phase_times(self.h, mean, mx, n))
         return {name: (mean[i], mx[i]) for i, name in enumerate(self.PHASES) if name != "-"}
+
+    def traj_iterations(self, B: int, stream=None):
+        """Per-trajectory iterations to tolerance of the last tolerance-mode run (0: not reached)."""
+        import numpy as np
+        out = np.zeros(B, dtype=np.int32)
+        self._check(self.lib.pes_traj_iterations(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(B),
+                                                 _stream(stream)))
+        return out
 
     def launch_shape(self, method: int, prec: int, N: int):
         nb, nt, L = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()

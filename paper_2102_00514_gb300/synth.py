@@ -124,6 +124,12 @@ def lengths_uniform(B: int, lo: int, hi: int, seed: int) -> np.ndarray:
     return T
 
 
+def lengths_log_uniform(B: int, lo: int, hi: int, seed: int) -> np.ndarray:
+    """B lengths with log T uniform in [log lo, log hi] (rounded; PCG64 stream)."""
+    rng = np.random.default_rng(seed)
+    return np.rint(np.exp(rng.uniform(np.log(lo), np.log(hi), B))).astype(np.int64).clip(lo, hi)
+
+
 # Named workloads. The seed of configuration i is SEED_BASE + i.
 def workload(name: str) -> dict:
     """Named synthetic workloads.
@@ -134,6 +140,10 @@ def workload(name: str) -> dict:
     * ``batch<B>``        B trajectories, T_b ~ U{100..20000}, truth turn rate
                           U(-1, 1), sensors jittered by U(-0.2, 0.2)
     * ``batch<B>_T<lo>_<hi>`` the same with other length bounds (test sizes)
+    * ``train<n>_T<T>``   n trajectories of T measurements (the learned
+                          initialiser's training set; the model of ieks_T500)
+    * ``heldout<B>_T<lo>_<hi>`` B trajectories with log T uniform in [lo, hi]
+                          (its held-out set; default bounds 1,000 .. 100,000)
     """
     if name == "ieks_T500":
         return ct_bearings([500], SEED_BASE + 1)
@@ -141,6 +151,17 @@ def workload(name: str) -> dict:
         return ct_bearings([10000], SEED_BASE + 2)
     if name.startswith("sweep_T"):
         return ct_bearings([int(name[len("sweep_T"):])], SEED_BASE + 3)
+    if name.startswith("train"):
+        n, T = name[len("train"):].split("_T")
+        return ct_bearings(np.full(int(n), int(T)), SEED_BASE + 5)
+    if name.startswith("heldout"):
+        rest = name[len("heldout"):]
+        lo, hi = 1000, 100000
+        if "_T" in rest:
+            rest, bounds = rest.split("_T")
+            lo, hi = (int(v) for v in bounds.split("_"))
+        B = int(rest)
+        return ct_bearings(lengths_log_uniform(B, lo, hi, SEED_BASE + 6), SEED_BASE + 6)
     if name.startswith("batch"):
         rest = name[len("batch"):]
         lo, hi = 100, 20000

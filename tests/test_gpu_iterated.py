@@ -93,6 +93,23 @@ def test_tolerance_mode_matches_oracle_iterations(sm):
     assert st == pes.NOT_CONVERGED and used == 3
 
 
+def test_per_trajectory_iterations_match_oracle(sm):
+    wl = synth.workload("batch8_T1_3000")
+    x, P, used, st = gpu_run(sm, wl, pes.IEKS, pes.FP64, iters=50, tol=1e-6, allow_not_converged=True)
+    its = sm.traj_iterations(8)
+    off = wl["offsets"]
+    for b in range(8):
+        sl = slice(int(off[b]), int(off[b + 1]))
+        one = dict(wl, offsets=np.array([0, off[b + 1] - off[b]]), y=wl["y"][:, sl], m0=wl["m0"][b:b + 1],
+                   P0=wl["P0"][b:b + 1], sensors=wl["sensors"][b:b + 1])
+        ref = oracle_run(one, pes.IEKS, iters=50, tol=1e-6)
+        expect = ref["iters_used"] if ref["status"] == oracle.OK else 0
+        assert its[b] == expect, (b, its[b], expect)
+    assert used == (max(its) if (its > 0).all() else 50)
+    with pytest.raises(pes.PesError):
+        sm.traj_iterations(7)
+
+
 def test_prior_init_equals_explicit_init(sm):
     wl = synth.workload("ieks_T500")
     d = workload_to_dev(wl, pes.FP64)

@@ -152,3 +152,29 @@ def test_invalid_arguments_rejected(net):
     with pytest.raises(pes.PesError) as ei:
         net.set_params(np.zeros(pes.INIT_NPARAMS, np.float32), np.zeros(5), np.array([1, 1, 0, 1, 1.0]))
     assert ei.value.status == pes.INVALID_ARG
+
+
+def test_trained_initialiser_saves_iterations():
+    """Trained on the GPU (its own kernels) against converged FP64 smoother
+    means of 2,048 trajectories of T = 1,000, the network's start must bring
+    held-out trajectories of other lengths to the 1e-6 tolerance in fewer
+    iterations than the prior start, on the trajectories both starts bring
+    there, and to the same solution."""
+    from paper_2102_00514_gb300 import learned_init as L
+    wl = synth.workload("train2048_T1000")
+    x, conv = L.converged_targets(wl)
+    assert conv.mean() > 0.5
+    mu, sigma = L.normalisation(x)
+    ev = synth.workload("heldout64_T1000_10000")
+    n = pes.InitNet(ev["y"].shape[1] + 1, 128)
+    n.set_params(L.initial_params(0), mu, sigma)
+    log = L.train(n, wl, x, conv, batch_traj=64, steps=800)
+    print(f"training: {log.steps} steps in {log.seconds:.2f} s, loss {log.losses[0][1]:.4f} -> {log.losses[-1][1]:.4f}")
+    r = L.evaluate(n, ev)
+    s = L.summary(r)
+    print("evaluation:", s)
+    n.close()
+    assert log.losses[-1][1] < 0.1 * log.losses[0][1]
+    assert s["converged_both"] >= 0.5 * s["trajectories"]
+    assert s["iters_saved"] >= 1.0
+    assert s["same_solution_within_1e-4"] >= 0.9 * s["converged_both"]
