@@ -196,5 +196,7 @@ def summary(r: EvalResult) -> dict:
             "same_solution_within_1e-4": int((r.rel_diff[both] < 1e-4).sum()),
             "median_position_rmse_prior": float(np.median(r.err_prior[both])),
             "median_position_rmse_learned": float(np.median(r.err_learned[both])),
+            "mean_position_rmse_prior": float(np.mean(r.err_prior[both])),
+            "mean_position_rmse_learned": float(np.mean(r.err_learned[both])),
         })
     return out
