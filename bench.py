@@ -56,6 +56,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-learned-init", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 17, help="states in the oracle's timed sample")
     ap.add_argument("--profile", choices=["ieks", "cubature"], default=None,
                     help="profiling case: only `warmup` + 1 FP32 runs of one method, no JSON line")
@@ -479,6 +480,14 @@ def main():
             result["e2e"] = {"value": world * work_per_step * args.steps / e2e_s, "unit": UNIT,
                              "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                              "ms_per_step": 1e3 * e2e_s / args.steps}
+
+    # iterations saved by the learned initialiser (a reduced run of the full
+    # experiment: 8,192 training trajectories, 256 held-out ones)
+    if rank == 0 and not args.no_learned_init:
+        from paper_2102_00514_gb300 import learned_init as LI
+        li = LI.run(n_train=8192, T_train=1000, n_heldout=256, steps=3000, batch_traj=128)
+        result["iters_saved"] = li["ieks"].get("iters_saved")
+        result["learned_init"] = li
 
     if rank == 0:
         import oracle

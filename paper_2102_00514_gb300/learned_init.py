@@ -200,3 +200,63 @@ def summary(r: EvalResult) -> dict:
             "mean_position_rmse_learned": float(np.mean(r.err_learned[both])),
         })
     return out
+
+
+def run(n_train: int = 100_000, T_train: int = 1000, n_heldout: int = 1024, heldout_lo: int = 1000,
+        heldout_hi: int = 100_000, steps: int = 8000, batch_traj: int = 128, methods=("ieks", "cubature"),
+        seed: int = 0) -> dict:
+    """The whole experiment: targets, training, evaluation of both methods.
+    The defaults are the full-size configuration (10^5 training trajectories
+    of T = 1,000; 1,024 held-out trajectories with log T uniform in
+    [1,000, 100,000])."""
+    out = {"n_train": n_train, "T_train": T_train, "n_heldout": n_heldout,
+           "heldout_T": [heldout_lo, heldout_hi], "steps": steps, "batch_traj": batch_traj}
+    t0 = time.perf_counter()
+    wl = synth.workload(f"train{n_train}_T{T_train}")
+    ev = synth.workload(f"heldout{n_heldout}_T{heldout_lo}_{heldout_hi}")
+    out["synth_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    x, conv = converged_targets(wl)
+    out["targets_s"] = time.perf_counter() - t0
+    out["targets_converged"] = float(conv.mean())
+    mu, sigma = normalisation(x[:, np.repeat(conv, T_train + 1)])
+    net = pes.InitNet(max(ev["y"].shape[1], batch_traj * (T_train + 1)), max(n_heldout, batch_traj))
+    net.set_params(initial_params(seed), mu, sigma)
+    log = train(net, wl, x, conv, batch_traj=batch_traj, steps=steps, lr=2e-3, lr_final=1e-4, seed=seed)
+    out["train_s"] = log.seconds
+    out["train_states_per_s"] = steps * batch_traj * (T_train + 1) / log.seconds
+    out["loss_first_last"] = [log.losses[0][1], log.losses[-1][1]]
+    del x, wl
+    # inference throughput on the held-out set (forward pass only)
+    y = _dev(ev["y"], torch.float64)
+    o = _dev(ev["offsets"], torch.int64)
+    net.forward(pes.FP64, y, o)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    net.forward(pes.FP64, y, o)
+    e1.record()
+    torch.cuda.synchronize()
+    out["inference_states_per_s"] = ev["y"].shape[1] / (e0.elapsed_time(e1) * 1e-3)
+    for name in methods:
+        m = pes.IEKS if name == "ieks" else pes.CUBATURE
+        r = evaluate(net, ev, method=m)
+        out[name] = summary(r)
+        out[name]["seconds"] = r.seconds
+    net.close()
+    return out
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="train and evaluate the learned initialiser")
+    ap.add_argument("--n-train", type=int, default=100_000)
+    ap.add_argument("--T-train", type=int, default=1000)
+    ap.add_argument("--n-heldout", type=int, default=1024)
+    ap.add_argument("--steps", type=int, default=8000)
+    ap.add_argument("--batch-traj", type=int, default=128)
+    a = ap.parse_args()
+    from . import build
+    build.build_all()
+    print(json.dumps(run(a.n_train, a.T_train, a.n_heldout, steps=a.steps, batch_traj=a.batch_traj)), flush=True)
