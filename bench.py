@@ -188,6 +188,22 @@ def oracle_timed(wl_sample, iters):
     return out
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest value of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, work_per_step: float, steps: int, seconds: float) -> float:
+    """Units all ranks processed per second: every rank does the same work
+    (replicas, weak scaling) and the slowest rank's time counts."""
+    return world * work_per_step * steps / seconds
+
+
 def one_trajectory(wl, b):
     """Trajectory b of a workload as a workload of its own, and its state slice."""
     import numpy as np
@@ -343,13 +359,9 @@ def main():
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     clk = clocks.stop(int(vis.split(",")[local]) if vis and vis.split(",")[local].isdigit() else local)
 
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
     work_per_step = len(methods) * steps * iters
-    value = world * work_per_step * args.steps / (total_ms * 1e-3)
+    value = whole_job_rate(world, work_per_step, args.steps, total_ms * 1e-3)
     ms_per_step = total_ms / args.steps
     # offsets validation, sensor conversion, y to the lane layout, nominal
     # initialisation, persistent smoother, x and P back to the caller layout
@@ -472,16 +484,12 @@ def main():
         t0 = time.perf_counter()
         for _ in range(args.steps):
             e2e_step()
-        e2e_s = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
         if rank == 0:
             h2d = len(methods) * (hy.numel() * 4 + hoff.numel() * 8 + hm0.numel() * 4 + hP0.numel() * 4 +
                                   hs.numel() * 8)
             d2h = len(methods) * (hx.numel() * 4 + hP.numel() * 4)
-            result["e2e"] = {"value": world * work_per_step * args.steps / e2e_s, "unit": UNIT,
+            result["e2e"] = {"value": whole_job_rate(world, work_per_step, args.steps, e2e_s), "unit": UNIT,
                              "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                              "ms_per_step": 1e3 * e2e_s / args.steps}
 
