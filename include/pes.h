@@ -165,6 +165,21 @@ pes_status pes_filter_scan(pes_handle* h, pes_precision prec,
                            void* xf, void* Pf, void* stream);
 
 /*
+ * pes_filter_scan plus the log-likelihood of each trajectory's measurements
+ * under the affine model, loglik[b] = log p(y_1..y_{T_b}) (DEVICE double [B];
+ * 0 for a trajectory without measurements). The paper notes (Sec. 2) that the
+ * filtering elements can carry this marginal likelihood; here it comes from
+ * the same pass, as the sum over steps of log N(y_k; H_k m_k^- + d_k, S_k),
+ * with m_k^-, S_k the exact one-step predictions that the scan's re-run
+ * produces, terms accumulated in double for either precision.
+ */
+pes_status pes_filter_loglik(pes_handle* h, pes_precision prec,
+                             const void* F, const void* c, const void* Qp,
+                             const void* H, const void* d, const void* Rp, const void* y,
+                             const void* m0, const void* P0, const int64_t* offsets, int32_t B, int64_t N,
+                             void* xf, void* Pf, double* loglik, void* stream);
+
+/*
  * Smoothing by the reverse associative scan of Sec. 4 (elements Eqs. 17-18,
  * operator Eq. 19, suffix products as in Sec. 2) from filtered moments
  * xf [5][N], Pf [15][N] and the transitions F, c, Qp: smoothed means

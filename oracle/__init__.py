@@ -109,6 +109,8 @@ def _load():
         lib.orc_linearize.restype = i
         lib.orc_kf_rts.argtypes = [i64, p, i64] + [p] * 13
         lib.orc_kf_rts.restype = i
+        lib.orc_kf_loglik.argtypes = [i64, p, i64] + [p] * 10
+        lib.orc_kf_loglik.restype = i
         lib.orc_iterated_smoother.argtypes = [mp, i, i64, p, i64, p, p, p, p, p, i, d, p, p, p, p]
         lib.orc_iterated_smoother.restype = i
         lib.orc_filter_element.argtypes = [p] * 7 + [ctypes.POINTER(FElem)]
@@ -316,6 +318,25 @@ def kf_rts(offsets, lin: dict, y, m0, P0) -> dict:
         raise np.linalg.LinAlgError(f"orc_kf_rts status {st}")
     return dict(xf=np.ascontiguousarray(xf.T), Pf=_sym_soa(Pf, 5),
                 xs=np.ascontiguousarray(xs.T), Ps=_sym_soa(Ps, 5))
+
+
+def kf_loglik(offsets, lin: dict, y, m0, P0) -> np.ndarray:
+    """log p(y_{1:T_b}) per trajectory under the affine model given by ``lin``
+    (prediction error decomposition of the Kalman filter)."""
+    lib = _load()
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    N = int(offsets[-1])
+    B = len(offsets) - 1
+    F, c, Qp, H, d, Rp = _lin_aos(lin)
+    ya = _aos(y)
+    m0a = _f64(m0).reshape(B, 5)
+    P0a = np.ascontiguousarray(sym_full(_f64(P0).reshape(B, 15), 5).reshape(B, 25))
+    out = np.zeros(B)
+    st = lib.orc_kf_loglik(N, _p(offsets), B, _p(F), _p(c), _p(Qp), _p(H), _p(d), _p(Rp), _p(ya), _p(m0a), _p(P0a),
+                           _p(out))
+    if st != OK:
+        raise np.linalg.LinAlgError(f"orc_kf_loglik status {st}")
+    return out
 
 
 def by_elements(offsets, lin: dict, y, m0, P0) -> dict:

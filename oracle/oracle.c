@@ -565,6 +565,56 @@ int orc_kf_rts(int64_t N, const int64_t* offsets, int64_t B,
 /* the iteration (Sec. 3): re-linearise about the previous smoothed moments   */
 /* ------------------------------------------------------------------------- */
 
+int orc_kf_loglik(int64_t N, const int64_t* offsets, int64_t B,
+                  const double* F, const double* c, const double* Qp,
+                  const double* H, const double* d, const double* Rp, const double* y,
+                  const double* m0, const double* P0, double* loglik)
+{
+    (void)N;
+    const double log_2pi = log(2.0 * 3.14159265358979323846);
+    for (int64_t b = 0; b < B; ++b) {
+        double m[5], P[25];
+        memcpy(m, m0 + 5 * b, sizeof m);
+        memcpy(P, P0 + 25 * b, sizeof P);
+        double ll = 0.0;
+        for (int64_t k = offsets[b] + 1; k < offsets[b + 1]; ++k) {
+            /* one-step prediction of x_k and of y_k */
+            double mp[5], FP[25], Pp[25];
+            mv(NX, NX, F + 25 * (k - 1), m, mp);
+            for (int i = 0; i < NX; ++i) mp[i] += c[5 * (k - 1) + i];
+            mm(NX, NX, NX, F + 25 * (k - 1), P, FP);
+            mmt(NX, NX, NX, FP, F + 25 * (k - 1), Pp);
+            for (int i = 0; i < 25; ++i) Pp[i] += Qp[25 * (k - 1) + i];
+            const double* Hk = H + 10 * k;
+            double HP[10], S[4], Sinv[4], Hm[2], v[2];
+            mm(NY, NX, NX, Hk, Pp, HP);
+            mmt(NY, NX, NY, HP, Hk, S);
+            for (int i = 0; i < 4; ++i) S[i] += Rp[4 * k + i];
+            if (!inverse(NY, S, Sinv)) return ORC_NOT_PD;
+            const double det = S[0] * S[3] - S[1] * S[2];
+            if (!(det > 0.0)) return ORC_NOT_PD;
+            mv(NY, NX, Hk, mp, Hm);
+            for (int r = 0; r < NY; ++r) v[r] = y[2 * k + r] - Hm[r] - d[2 * k + r];
+            double q = 0.0;
+            for (int r = 0; r < NY; ++r)
+                for (int s = 0; s < NY; ++s) q += v[r] * Sinv[r * 2 + s] * v[s];
+            ll += -0.5 * (q + log(det)) - 0.5 * NY * log_2pi;
+            /* the update, as in the filter */
+            double PHt[10], K[10], Kv[5], KS[10], KSK[25];
+            mmt(NX, NX, NY, Pp, Hk, PHt);
+            mm(NX, NY, NY, PHt, Sinv, K);
+            mv(NX, NY, K, v, Kv);
+            for (int i = 0; i < NX; ++i) m[i] = mp[i] + Kv[i];
+            mm(NX, NY, NY, K, S, KS);
+            mmt(NX, NY, NX, KS, K, KSK);
+            for (int i = 0; i < 25; ++i) P[i] = Pp[i] - KSK[i];
+            symmetrize(NX, P);
+        }
+        loglik[b] = ll;
+    }
+    return ORC_OK;
+}
+
 int orc_iterated_smoother(const orc_model* m, int method, int64_t N, const int64_t* offsets, int64_t B,
                           const double* y, const double* m0, const double* P0,
                           const double* x_init, const double* P_init, int max_iters, double tol,

@@ -54,6 +54,13 @@ int orc_kf_rts(int64_t N, const int64_t* offsets, int64_t B,
                const double* H, const double* d, const double* Rp, const double* y,
                const double* m0, const double* P0,
                double* xf, double* Pf, double* xs, double* Ps);
+/* log p(y_1..y_T) of each trajectory under the affine model (Sec. 2: the
+ * marginal likelihood the filtering recursion carries), by the prediction
+ * error decomposition: sum over k of log N(y_k; H_k m_k^- + d_k, S_k). */
+int orc_kf_loglik(int64_t N, const int64_t* offsets, int64_t B,
+                  const double* F, const double* c, const double* Qp,
+                  const double* H, const double* d, const double* Rp, const double* y,
+                  const double* m0, const double* P0, double* loglik);
 int orc_iterated_smoother(const orc_model* m, int method, int64_t N, const int64_t* offsets, int64_t B,
                           const double* y, const double* m0, const double* P0,
                           const double* x_init, const double* P_init, int max_iters, double tol,

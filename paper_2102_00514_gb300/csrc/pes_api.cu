@@ -228,10 +228,12 @@ template <typename T>
 static pes_status filter_scan_t(pes_handle* h, const void* F, const void* c, const void* Qp, const void* H,
                                 const void* d, const void* Rp, const void* y, const void* m0, const void* P0,
                                 const int64_t* offsets, int32_t B, int64_t N, void* xf, void* Pf, pes_precision prec,
-                                cudaStream_t st)
+                                cudaStream_t st, double* loglik = nullptr)
 {
     KParams<T> p{};
     p.N = N; p.offsets = offsets; p.B = B; p.mode = MODE_FILTER; p.iters = 1;
+    if (loglik) PES_CUDA(h, cudaMemsetAsync(loglik, 0, sizeof(double) * B, st));
+    p.loglik = loglik;
     p.F = (const T*)F; p.c = (const T*)c; p.Qp = (const T*)Qp; p.H = (const T*)H; p.d = (const T*)d;
     p.Rp = (const T*)Rp; p.y = (const T*)y; p.m0 = (const T*)m0; p.P0 = (const T*)P0;
     p.xf = (T*)xf; p.Pf = (T*)Pf;
@@ -506,6 +508,22 @@ pes_status pes_filter_scan(pes_handle* h, pes_precision prec, const void* F, con
     return filter_scan_t<float>(h, F, c, Qp, H, d, Rp, y, m0, P0, offsets, B, N, xf, Pf, prec, st);
 }
 
+
+pes_status pes_filter_loglik(pes_handle* h, pes_precision prec, const void* F, const void* c, const void* Qp,
+                             const void* H, const void* d, const void* Rp, const void* y, const void* m0,
+                             const void* P0, const int64_t* offsets, int32_t B, int64_t N, void* xf, void* Pf,
+                             double* loglik, void* stream)
+{
+    pes_status r = check_common(h, prec, offsets, B, N);
+    if (r != PES_OK) return r;
+    if (!F || !c || !Qp || !H || !d || !Rp || !y || !m0 || !P0 || !xf || !Pf || !loglik)
+        return fail(h, PES_ERR_INVALID_ARG, "NULL array");
+    cudaStream_t st = (cudaStream_t)stream;
+    PES_CUDA(h, launch_validate_offsets(offsets, B, N, h->status, st));
+    if (prec == PES_FP64)
+        return filter_scan_t<double>(h, F, c, Qp, H, d, Rp, y, m0, P0, offsets, B, N, xf, Pf, prec, st, loglik);
+    return filter_scan_t<float>(h, F, c, Qp, H, d, Rp, y, m0, P0, offsets, B, N, xf, Pf, prec, st, loglik);
+}
 
 pes_status pes_smooth_scan(pes_handle* h, pes_precision prec, const void* F, const void* c, const void* Qp,
                            const void* xf, const void* Pf, const int64_t* offsets, int32_t B, int64_t N, void* xs,

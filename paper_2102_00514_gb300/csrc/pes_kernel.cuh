@@ -74,6 +74,7 @@ struct KParams {
     double* conv;      // [2][B][2] update-norm accumulators, zero at launch
     int* iters_done;
     int* traj_iters;   // RUN with tol > 0: [B], the first iteration whose update met tol (0: none); or NULL
+    double* loglik;    // FILTER: [B] log p(y_{1:T_b}) accumulated (zero at launch), or NULL
     int L;             // steps per lane
     int NL;            // lanes = NB * NT
     int lanes_layout;  // x, P, y use the kernel's lane-major layout (MODE_RUN)
@@ -569,6 +570,8 @@ PES_DEV bool rerun_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int l
     bool ok = true;
     selem_identity(accS);
     const bool smooth = (p.mode == MODE_RUN);
+    double ll = 0.0;   // log-likelihood terms of trajectory llb (filter scan with given arrays only)
+    int llb = -1;
     const bool any = a < e;
     constexpr bool stored_lin = kStoreLin<LIN>;
     const bool use_lin = stored_lin && smooth;
@@ -646,7 +649,22 @@ PES_DEV bool rerun_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int l
                     ok &= factor_state(sc, fc);
                     lin_obs(p, k, cur.b, sc, fc, ob);
                 }
-                ok &= kf_update(ob, mp, Pp, m, P);
+                if constexpr (LIN == LIN_ARRAYS) {
+                    if (p.loglik) {
+                        double term;
+                        ok &= kf_update(ob, mp, Pp, m, P, &term);
+                        if (cur.b != llb) {
+                            if (llb >= 0) atomicAdd(p.loglik + llb, ll);
+                            ll = 0.0;
+                            llb = cur.b;
+                        }
+                        ll += term;
+                    } else {
+                        ok &= kf_update(ob, mp, Pp, m, P);
+                    }
+                } else {
+                    ok &= kf_update(ob, mp, Pp, m, P);
+                }
             }
             if (!smooth) store_filtered(p, k, m, P);
             else if (!kStoreElements<LIN>) store_xP(p, s, lane, m, P);
@@ -657,6 +675,7 @@ PES_DEV bool rerun_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int l
         }
     }
     if (use_lin) wpar = ws.parity;
+    if (llb >= 0) atomicAdd(p.loglik + llb, ll);
     if (smooth && any) {
         // smoothing element of the chunk's last state: the transition out of the
         // chunk is linearised about the last state's nominal

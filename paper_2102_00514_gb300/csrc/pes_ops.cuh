@@ -362,7 +362,7 @@ PES_DEV void predict(const Trans<T>& tr, const T* m, const T* P, T* mp, T* FP, T
 
 // Kalman update of (mp, Pp) with the observation ob: (m, P).
 template <typename T>
-PES_DEV bool kf_update(const Obs<T>& ob, const T* mp, const T* Pp, T* m, T* P)
+PES_DEV bool kf_update(const Obs<T>& ob, const T* mp, const T* Pp, T* m, T* P, double* loglik_term = nullptr)
 {
     T HP[10];
 #pragma unroll
@@ -395,6 +395,14 @@ PES_DEV bool kf_update(const Obs<T>& ob, const T* mp, const T* Pp, T* m, T* P)
 #pragma unroll
         for (int l = 0; l < 5; ++l) hv = fma(-ob.H[r * 5 + l], mp[l] - ob.xn[l], hv);
         v[r] = hv;
+    }
+    if (loglik_term) {
+        // log N(v; 0, S): the term of step k in log p(y_{1:T}) = sum_k log p(y_k | y_{1:k-1})
+        const double s00 = S[si2(0, 0)], s01 = S[si2(0, 1)], s11 = S[si2(1, 1)];
+        const double det = s00 * s11 - s01 * s01;
+        const double v0 = v[0], v1 = v[1];
+        const double q = (s11 * v0 * v0 - 2.0 * s01 * v0 * v1 + s00 * v1 * v1) / det;
+        *loglik_term = -0.5 * (q + log(det)) - 1.8378770664093454836;   // log(2 pi)
     }
 #pragma unroll
     for (int i = 0; i < 5; ++i) m[i] = fma(KT[5 + i], v[1], fma(KT[i], v[0], mp[i]));

@@ -29,7 +29,7 @@ MODEL_CT_BEARINGS, MODEL_LINEAR = 0, 1
 
 EXPORTED = ["pes_create", "pes_destroy", "pes_last_error", "pes_sync", "pes_linearize", "pes_filter_scan",
             "pes_smooth_scan", "pes_ieks_run", "pes_ieks_run_host", "pes_launch_shape", "pes_measure_fma_peak",
-            "pes_debug_phase_times", "pes_ieks_run_noalloc", "pes_traj_iterations",
+            "pes_debug_phase_times", "pes_ieks_run_noalloc", "pes_traj_iterations", "pes_filter_loglik",
             "pes_init_create", "pes_init_destroy", "pes_init_last_error", "pes_init_set_params",
             "pes_init_get_params", "pes_init_forward", "pes_init_loss_grad", "pes_init_train_step"]
 INIT_NPARAMS = 86661
@@ -71,6 +71,7 @@ def load_library():
     lib.pes_sync.argtypes = [p, p]
     lib.pes_linearize.argtypes = [p, mp, i32, i32, p, p, p, p, i32, i64, p, p, p, p, p, p, p, p]
     lib.pes_filter_scan.argtypes = [p, i32, p, p, p, p, p, p, p, p, p, p, i32, i64, p, p, p]
+    lib.pes_filter_loglik.argtypes = [p, i32, p, p, p, p, p, p, p, p, p, p, i32, i64, p, p, p, p]
     lib.pes_smooth_scan.argtypes = [p, i32, p, p, p, p, p, p, i32, i64, p, p, p]
     lib.pes_ieks_run.argtypes = [p, mp, i32, i32, p, p, i32, i64, p, p, p, p, i32, d, p, p,
                                  ctypes.POINTER(i32), p]
@@ -269,6 +270,20 @@ class Smoother:
                                       _ptr(xf), _ptr(Pf), _stream(stream))
         self._check(st)
         return xf, Pf
+
+    def filter_loglik(self, prec: int, lin: dict, y, m0, P0, offsets, stream=None):
+        """Filtered moments and per-trajectory log-likelihoods (float64 [B], device)."""
+        dt = _dtype(prec)
+        N = y.shape[1]
+        B = offsets.shape[0] - 1
+        xf = torch.empty((5, N), dtype=dt, device=y.device)
+        Pf = torch.empty((15, N), dtype=dt, device=y.device)
+        ll = torch.empty(B, dtype=torch.float64, device=y.device)
+        st = self.lib.pes_filter_loglik(self.h, prec, *[_ptr(lin[k], dt) for k in ("F", "c", "Qp", "H", "d", "Rp")],
+                                        _ptr(y, dt), _ptr(m0, dt), _ptr(P0, dt), _ptr(offsets, torch.int64), B, N,
+                                        _ptr(xf), _ptr(Pf), _ptr(ll), _stream(stream))
+        self._check(st)
+        return xf, Pf, ll
 
     def smooth_scan(self, prec: int, lin: dict, xf, Pf, offsets, stream=None):
         dt = _dtype(prec)

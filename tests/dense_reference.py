@@ -58,6 +58,31 @@ def condition(mu, S, H, d, R, y, upto=None):
     return mpost, 0.5 * (Spost + Spost.T)
 
 
+def dense_log_evidence(F, c, Qp, H, d, R, y, m0, P0):
+    """log p(y_1..y_T) of the stacked affine model: y stacked is Gaussian with
+    mean Hs mu + ds and covariance Hs S Hs^T + Rs."""
+    mu, S = stacked_prior(F, c, Qp, m0, P0)
+    n, m = 5, 2
+    T = len(H) - 1
+    if T == 0:
+        return 0.0
+    Hs = np.zeros((T * m, (T + 1) * n))
+    ds = np.zeros(T * m)
+    ys = np.zeros(T * m)
+    Rs = np.zeros((T * m, T * m))
+    for k in range(1, T + 1):
+        r = slice((k - 1) * m, k * m)
+        Hs[r, k * n:(k + 1) * n] = H[k]
+        ds[r] = d[k]
+        ys[r] = y[k]
+        Rs[r, r] = R[k]
+    G = Hs @ S @ Hs.T + Rs
+    e = ys - Hs @ mu - ds
+    sign, logdet = np.linalg.slogdet(G)
+    assert sign > 0
+    return float(-0.5 * (e @ np.linalg.solve(G, e) + logdet + T * m * np.log(2 * np.pi)))
+
+
 def dense_smoother(F, c, Qp, H, d, R, y, m0, P0):
     """Smoothed means [T+1][5] and covariances [T+1][5][5]."""
     mu, S = stacked_prior(F, c, Qp, m0, P0)

@@ -79,3 +79,24 @@ def test_malformed_offsets_rejected(sm):
     # the handle keeps working afterwards
     xf, Pf = sm.filter_scan(pes.FP64, dlin, to_dev(y), to_dev(m0), to_dev(P0), to_dev(off, torch.int64))
     sm.sync()
+
+
+@pytest.mark.parametrize("name,T_list", CASES)
+@pytest.mark.parametrize("prec,tol", [(pes.FP64, TOL_FP64), (pes.FP32, TOL_FP32)])
+def test_filter_loglik_matches_oracle(sm, name, T_list, prec, tol):
+    lin, y, m0, P0, off = random_linear_workload(T_list, zlib.crc32(name.encode()) % 1000 + 2)
+    ref = oracle.kf_loglik(off, lin, y, m0, P0)
+    refx = oracle.kf_rts(off, lin, y, m0, P0)
+    dt = torch.float64 if prec == pes.FP64 else torch.float32
+    dlin = {k: to_dev(v, dt) for k, v in lin.items()}
+    xf, Pf, ll = sm.filter_loglik(prec, dlin, to_dev(y, dt), to_dev(m0, dt), to_dev(P0, dt),
+                                  to_dev(off, torch.int64))
+    sm.sync()
+    ll = ll.cpu().numpy()
+    for b in range(len(T_list)):
+        assert abs(ll[b] - ref[b]) <= tol * max(1.0, abs(ref[b])), (b, ll[b], ref[b])
+        if T_list[b] == 0:
+            assert ll[b] == 0.0
+    # the filtered moments are those of pes_filter_scan
+    assert rel_err(xf.double().cpu().numpy(), refx["xf"], off) < tol
+    assert rel_err(Pf.double().cpu().numpy(), refx["Pf"], off) < tol

@@ -6,12 +6,14 @@
 * The paper's elements and operators (Eqs. 13-19), folded sequentially, equal
   the definition; the operators are associative and have identities.
 * For a linear-Gaussian model one iteration is exact and a second changes nothing.
+* The filter's log-likelihood equals the log-density of the stacked measurement
+  vector (brute force), and its increments are the one-step predictive densities.
 """
 import numpy as np
 import pytest
 
 import oracle
-from tests.dense_reference import dense_filter, dense_smoother
+from tests.dense_reference import dense_filter, dense_log_evidence, dense_smoother
 
 RNG = np.random.default_rng(20210201)
 
@@ -58,6 +60,44 @@ def test_kf_rts_equals_dense_conditioning(T, singular_q):
     np.testing.assert_allclose(oracle.sym_full(out["Ps"].T, 5), Ps, rtol=1e-9, atol=1e-9)
     np.testing.assert_allclose(out["xf"].T, xf, rtol=1e-9, atol=1e-9)
     np.testing.assert_allclose(oracle.sym_full(out["Pf"].T, 5), Pf, rtol=1e-9, atol=1e-9)
+
+
+@pytest.mark.parametrize("singular_q", [False, True])
+@pytest.mark.parametrize("T", [1, 2, 7, 25])
+def test_loglik_equals_dense_log_evidence(T, singular_q):
+    lin, y, m0, P0, (F, c, Q, H, d, R, yy) = random_linear_lin(T, RNG, singular_q)
+    ll = oracle.kf_loglik(np.array([0, T + 1]), lin, y, m0, P0)
+    ref = dense_log_evidence(F[:T], c[:T], Q[:T], H, d, R, yy, m0[0], oracle.sym_full(P0[0], 5))
+    assert abs(ll[0] - ref) < 1e-9 * max(1.0, abs(ref))
+
+
+def test_loglik_increment_is_the_predictive_density():
+    # log p(y_{1:T}) - log p(y_{1:T-1}) = log N(y_T; H m_T^- + d, H P_T^- H^T + R)
+    T = 9
+    lin, y, m0, P0, (F, c, Q, H, d, R, yy) = random_linear_lin(T, RNG)
+    full = oracle.kf_loglik(np.array([0, T + 1]), lin, y, m0, P0)[0]
+    cut = {k: v[:, :T].copy() for k, v in lin.items()}
+    short = oracle.kf_loglik(np.array([0, T]), cut, y[:, :T].copy(), m0, P0)[0]
+    out = oracle.kf_rts(np.array([0, T]), cut, y[:, :T].copy(), m0, P0)
+    m = out["xf"][:, T - 1]
+    P = oracle.sym_full(out["Pf"][:, T - 1], 5)
+    mp = F[T - 1] @ m + c[T - 1]
+    Pp = F[T - 1] @ P @ F[T - 1].T + Q[T - 1]
+    S = H[T] @ Pp @ H[T].T + R[T]
+    e = yy[T] - H[T] @ mp - d[T]
+    dens = -0.5 * (e @ np.linalg.solve(S, e) + np.log(np.linalg.det(S)) + 2 * np.log(2 * np.pi))
+    assert abs((full - short) - dens) < 1e-10 * max(1.0, abs(dens))
+
+
+def test_loglik_of_a_batch_is_per_trajectory():
+    parts = [random_linear_lin(T, RNG) for T in (3, 1, 6)]
+    lls = [oracle.kf_loglik(np.array([0, T + 1]), p[0], p[1], p[2], p[3])[0] for T, p in zip((3, 1, 6), parts)]
+    lin = {k: np.concatenate([p[0][k] for p in parts], axis=1) for k in parts[0][0]}
+    y = np.concatenate([p[1] for p in parts], axis=1)
+    m0 = np.concatenate([p[2] for p in parts])
+    P0 = np.concatenate([p[3] for p in parts])
+    got = oracle.kf_loglik(np.array([0, 4, 6, 13]), lin, y, m0, P0)
+    np.testing.assert_allclose(got, lls, rtol=1e-13)
 
 
 @pytest.mark.parametrize("singular_q", [False, True])
