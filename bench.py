@@ -57,6 +57,8 @@ def parse_args():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-learned-init", action="store_true")
+    ap.add_argument("--sequential", action="store_true",
+                    help="also time the sequential counterpart (one GPU thread per trajectory) on the workload")
     ap.add_argument("--cpu-sample", type=int, default=1 << 17, help="states in the oracle's timed sample")
     ap.add_argument("--profile", choices=["ieks", "cubature"], default=None,
                     help="profiling case: only `warmup` + 1 FP32 runs of one method, no JSON line")
@@ -443,6 +445,23 @@ def main():
                                      iters=iters - 1)
             nom32[name] = (x.double().cpu().numpy(), P.double().cpu().numpy())
     sm.sync()
+
+    # the sequential counterpart on the same GPU: one thread per trajectory
+    if args.sequential:
+        seq = {}
+        for name, m in methods:
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sm.ieks_run_sequential(d32["model"], m, pes.FP32, d32["y"], d32["offsets"], d32["m0"], d32["P0"],
+                                   iters=iters, x_out=d32["x"], P_out=d32["P"])
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            seq[name] = {"ms_per_run": ms, "value": steps * iters / (ms * 1e-3)}
+        if rank == 0:
+            result["sequential"] = {"impl": "one GPU thread per trajectory, FP32", "per_method": seq,
+                                    "value": work_per_step / (sum(v["ms_per_run"] for v in seq.values()) * 1e-3)}
 
     # PES_MIXED: the first iters-1 iterations in FP32, the final one in FP64
     xmix = {}

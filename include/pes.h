@@ -229,9 +229,27 @@ pes_status pes_ieks_run_host(pes_handle* h, const pes_model* model, pes_method m
                              void* stream);
 
 /*
- * Per-trajectory iteration counts of the last pes_ieks_run or
- * pes_ieks_run_host call on this handle that ran in tolerance mode (tol > 0)
- * with PES_FP32 or PES_FP64: iters[b] (HOST int32 [B]) is the first iteration
+ * The sequential counterpart of pes_ieks_run on the GPU, with the same
+ * arguments, layouts and results: one thread per trajectory runs the extended
+ * (PES_IEKS) or cubature (PES_CUBATURE) Kalman filter and RTS smoother of the
+ * Sec. 3 iteration over its whole trajectory, the form the paper's parallel
+ * method is measured against. It suits many short trajectories; with few
+ * trajectories most of the GPU idles. In tolerance mode each trajectory stops
+ * at its own first iteration whose relative update is <= tol (recorded for
+ * pes_traj_iterations), and *iters_used is the largest count. Uses the
+ * handle's workspace; PES_MIXED returns PES_ERR_UNSUPPORTED. x_out / P_out
+ * hold the nominal between iterations (they may equal x_init / P_init).
+ */
+pes_status pes_ieks_run_sequential(pes_handle* h, const pes_model* model, pes_method method, pes_precision prec,
+                                   const void* y, const int64_t* offsets, int32_t B, int64_t N,
+                                   const void* m0, const void* P0, const void* x_init, const void* P_init,
+                                   int32_t max_iters, double tol, void* x_out, void* P_out, int32_t* iters_used,
+                                   void* stream);
+
+/*
+ * Per-trajectory iteration counts of the last pes_ieks_run,
+ * pes_ieks_run_host or pes_ieks_run_sequential call on this handle that ran in
+ * tolerance mode (tol > 0) with PES_FP32 or PES_FP64: iters[b] (HOST int32 [B]) is the first iteration
  * after which trajectory b's relative update norm (Sec. 3 iteration; the
  * measure of the tolerance) was <= tol, or 0 if it never was within the
  * iterations run. The run continues until every trajectory meets tol or

@@ -296,6 +296,50 @@ static pes_status ieks_run_t(pes_handle* h, const pes_model* model, pes_method m
     return PES_OK;
 }
 
+// The sequential counterpart: one thread per trajectory over the caller's
+// layout, the nominal held in x_out / P_out, smoothing elements in h->hand.
+template <typename T>
+static pes_status ieks_run_sequential_t(pes_handle* h, const pes_model* model, pes_method method, const void* y,
+                                        const int64_t* offsets, int32_t B, int64_t N, const void* m0, const void* P0,
+                                        const void* x_init, const void* P_init, int32_t max_iters, double tol,
+                                        void* x_out, void* P_out, int32_t* iters_used, cudaStream_t st)
+{
+    const bool cub = (method == PES_CUBATURE);
+    if (x_init && x_init != x_out) PES_CUDA(h, cudaMemcpyAsync(x_out, x_init, sizeof(T) * 5 * N, cudaMemcpyDeviceToDevice, st));
+    if (cub && P_init && P_init != P_out)
+        PES_CUDA(h, cudaMemcpyAsync(P_out, P_init, sizeof(T) * 15 * N, cudaMemcpyDeviceToDevice, st));
+    if (!x_init || (cub && !P_init))
+        PES_CUDA(h, launch_init_nominal<T>(offsets, B, N, (const T*)m0, (const T*)P0, x_init ? nullptr : (T*)x_out,
+                                           (cub && !P_init) ? (T*)P_out : nullptr, st));
+    KParams<T> p{};
+    p.N = N; p.offsets = offsets; p.B = B; p.mode = MODE_RUN; p.iters = max_iters; p.tol = tol;
+    pes_status rm = device_model<T>(h, *model, B, st, p.model);
+    if (rm != PES_OK) return rm;
+    p.y = (const T*)y; p.m0 = (const T*)m0; p.P0 = (const T*)P0;
+    p.x = (T*)x_out; p.P = (T*)P_out;
+    p.lanes_layout = 0;
+    p.cs = N;
+    p.hand = static_cast<T*>(h->hand);
+    p.status = h->status;
+    p.iters_done = h->iters_done;
+    p.traj_iters = nullptr;
+    PES_CUDA(h, cudaMemsetAsync(h->iters_done, 0, sizeof(int), st));
+    if (tol > 0.0 && h->traj_iters) {
+        PES_CUDA(h, cudaMemsetAsync(h->traj_iters, 0, sizeof(int) * B, st));
+        p.traj_iters = h->traj_iters;
+        h->traj_iters_B = B;
+    }
+    const cudaError_t e = cub ? launch_sequential<T, LIN_CUBATURE>(p, st) : launch_sequential<T, LIN_IEKS>(p, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "launch of the sequential smoother");
+    if (tol > 0.0 || iters_used) {
+        int it = 0;
+        pes_status r = read_status(h, st, &it);
+        if (iters_used) *iters_used = it;
+        return r;
+    }
+    return PES_OK;
+}
+
 // PES_MIXED: the first max_iters - 1 iterations in FP32, the last one (and so
 // the returned means and smoother covariances) in FP64 from the FP32 nominal.
 // Inputs and outputs are FP32 arrays; the FP64 copies live in h->mix.
@@ -561,6 +605,27 @@ pes_status pes_ieks_run(pes_handle* h, const pes_model* model, pes_method method
                                   x_out, P_out, iters_used, st);
     return ieks_run_t<float>(h, model, method, prec, y, offsets, B, N, m0, P0, x_init, P_init, max_iters, tol, x_out,
                              P_out, iters_used, st);
+}
+
+pes_status pes_ieks_run_sequential(pes_handle* h, const pes_model* model, pes_method method, pes_precision prec,
+                                   const void* y, const int64_t* offsets, int32_t B, int64_t N, const void* m0,
+                                   const void* P0, const void* x_init, const void* P_init, int32_t max_iters,
+                                   double tol, void* x_out, void* P_out, int32_t* iters_used, void* stream)
+{
+    pes_status r = check_common(h, prec, offsets, B, N);
+    if (r != PES_OK) return r;
+    if ((r = check_model(h, model)) != PES_OK) return r;
+    if (method != PES_IEKS && method != PES_CUBATURE) return fail(h, PES_ERR_INVALID_ARG, "unknown method");
+    if (!y || !m0 || !P0 || !x_out || !P_out) return fail(h, PES_ERR_INVALID_ARG, "NULL array");
+    if (max_iters < 1) return fail(h, PES_ERR_INVALID_ARG, "max_iters must be >= 1");
+    if (!(tol == tol)) return fail(h, PES_ERR_INVALID_ARG, "tol is NaN");
+    cudaStream_t st = (cudaStream_t)stream;
+    PES_CUDA(h, launch_validate_offsets(offsets, B, N, h->status, st));
+    if (prec == PES_FP64)
+        return ieks_run_sequential_t<double>(h, model, method, y, offsets, B, N, m0, P0, x_init, P_init, max_iters,
+                                             tol, x_out, P_out, iters_used, st);
+    return ieks_run_sequential_t<float>(h, model, method, y, offsets, B, N, m0, P0, x_init, P_init, max_iters, tol,
+                                        x_out, P_out, iters_used, st);
 }
 
 pes_status pes_traj_iterations(pes_handle* h, int32_t* iters, int32_t B, void* stream)

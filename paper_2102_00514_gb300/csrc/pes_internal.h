@@ -45,6 +45,9 @@ cudaError_t launch_lanes_transpose(const T* src, T* dst, int nc, int64_t N, int 
 template <typename T>
 cudaError_t launch_init_nominal_lanes(const int64_t* offsets, int B, int64_t N, int L, int NL, const T* m0,
                                       const T* P0, T* x, T* P, cudaStream_t st);
+template <typename T, int LIN>
+cudaError_t launch_sequential(const KParams<T>& p, cudaStream_t st);
+
 cudaError_t launch_validate_offsets(const int64_t* offsets, int B, int64_t N, int* status, cudaStream_t st);
 
 }  // namespace pes

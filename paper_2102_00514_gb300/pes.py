@@ -29,7 +29,7 @@ MODEL_CT_BEARINGS, MODEL_LINEAR = 0, 1
 
 EXPORTED = ["pes_create", "pes_destroy", "pes_last_error", "pes_sync", "pes_linearize", "pes_filter_scan",
             "pes_smooth_scan", "pes_ieks_run", "pes_ieks_run_host", "pes_launch_shape", "pes_measure_fma_peak",
-            "pes_debug_phase_times", "pes_ieks_run_noalloc", "pes_traj_iterations", "pes_filter_loglik",
+            "pes_debug_phase_times", "pes_ieks_run_noalloc", "pes_traj_iterations", "pes_filter_loglik", "pes_ieks_run_sequential",
             "pes_init_create", "pes_init_destroy", "pes_init_last_error", "pes_init_set_params",
             "pes_init_get_params", "pes_init_forward", "pes_init_loss_grad", "pes_init_train_step"]
 INIT_NPARAMS = 86661
@@ -76,6 +76,7 @@ def load_library():
     lib.pes_ieks_run.argtypes = [p, mp, i32, i32, p, p, i32, i64, p, p, p, p, i32, d, p, p,
                                  ctypes.POINTER(i32), p]
     lib.pes_ieks_run_host.argtypes = lib.pes_ieks_run.argtypes
+    lib.pes_ieks_run_sequential.argtypes = lib.pes_ieks_run.argtypes
     lib.pes_launch_shape.argtypes = [p, i32, i32, i64, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                      ctypes.POINTER(i32)]
     lib.pes_measure_fma_peak.argtypes = [ctypes.POINTER(d), ctypes.POINTER(d)]
@@ -313,6 +314,26 @@ class Smoother:
                                    B, N, _ptr(m0, dt), _ptr(P0, dt), _ptr(x_init, dt), _ptr(P_init, dt), int(iters),
                                    float(tol), _ptr(x_out, dt), _ptr(P_out, dt),
                                    ctypes.byref(used) if (want_iters or tol > 0) else None, _stream(stream))
+        self._check(st, allow=(NOT_CONVERGED,) if allow_not_converged else ())
+        return x_out, P_out, used.value, st
+
+    def ieks_run_sequential(self, model: Model, method: int, prec: int, y, offsets, m0, P0, x_init=None,
+                            P_init=None, iters: int = 10, tol: float = 0.0, x_out=None, P_out=None, stream=None,
+                            allow_not_converged: bool = False):
+        """One thread per trajectory (the sequential method on the GPU); same results as ieks_run."""
+        dt = _dtype(prec)
+        N = y.shape[1]
+        B = offsets.shape[0] - 1
+        if x_out is None:
+            x_out = torch.empty((5, N), dtype=dt, device=y.device)
+        if P_out is None:
+            P_out = torch.empty((15, N), dtype=dt, device=y.device)
+        used = ctypes.c_int32(0)
+        ms = model.as_struct()
+        st = self.lib.pes_ieks_run_sequential(self.h, ctypes.byref(ms), method, prec, _ptr(y, dt),
+                                              _ptr(offsets, torch.int64), B, N, _ptr(m0, dt), _ptr(P0, dt),
+                                              _ptr(x_init, dt), _ptr(P_init, dt), int(iters), float(tol),
+                                              _ptr(x_out, dt), _ptr(P_out, dt), ctypes.byref(used), _stream(stream))
         self._check(st, allow=(NOT_CONVERGED,) if allow_not_converged else ())
         return x_out, P_out, used.value, st
 
