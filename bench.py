@@ -453,12 +453,16 @@ def main():
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            sm.ieks_run_sequential(d32["model"], m, pes.FP32, d32["y"], d32["offsets"], d32["m0"], d32["P0"],
-                                   iters=iters, x_out=d32["x"], P_out=d32["P"])
+            status = "ok"
+            try:
+                sm.ieks_run_sequential(d32["model"], m, pes.FP32, d32["y"], d32["offsets"], d32["m0"], d32["P0"],
+                                       iters=iters, x_out=d32["x"], P_out=d32["P"])
+            except pes.PesError as err:   # the run completed; a trajectory's result is flagged
+                status = str(err)
             e1.record()
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
-            seq[name] = {"ms_per_run": ms, "value": steps * iters / (ms * 1e-3)}
+            seq[name] = {"ms_per_run": ms, "value": steps * iters / (ms * 1e-3), "status": status}
         if rank == 0:
             result["sequential"] = {"impl": "one GPU thread per trajectory, FP32", "per_method": seq,
                                     "value": work_per_step / (sum(v["ms_per_run"] for v in seq.values()) * 1e-3)}
