@@ -26,6 +26,7 @@ _lib = None
 
 IEKS = 0
 CUBATURE = 1
+UNSCENTED = 2
 MODEL_CT_BEARINGS = 0
 MODEL_LINEAR = 1
 OK, NOT_PD, NOT_CONVERGED = 0, 2, 4
@@ -48,7 +49,8 @@ class _Model(ctypes.Structure):
                 ("r_std", ctypes.c_double),
                 ("sensors", ctypes.c_void_p), ("sensors_per_traj", ctypes.c_int),
                 ("F", ctypes.c_double * 25), ("c", ctypes.c_double * 5), ("Q", ctypes.c_double * 25),
-                ("H", ctypes.c_double * 10), ("d", ctypes.c_double * 2), ("R", ctypes.c_double * 4)]
+                ("H", ctypes.c_double * 10), ("d", ctypes.c_double * 2), ("R", ctypes.c_double * 4),
+                ("ut_alpha", ctypes.c_double), ("ut_beta", ctypes.c_double), ("ut_kappa", ctypes.c_double)]
 
 
 class FElem(ctypes.Structure):
@@ -105,6 +107,8 @@ def _load():
         lib.orc_measurement_noise.argtypes = [mp, p]
         lib.orc_slr.argtypes = [mp, i, i64, p, p, p, p, p]
         lib.orc_slr.restype = i
+        lib.orc_slr_unscented.argtypes = [mp, i, i64, p, p, p, p, p]
+        lib.orc_slr_unscented.restype = i
         lib.orc_linearize.argtypes = [mp, i, i64, p, i64, p, p, p, p, p, p, p, p, p, p]
         lib.orc_linearize.restype = i
         lib.orc_kf_rts.argtypes = [i64, p, i64] + [p] * 13
@@ -174,6 +178,15 @@ class Model:
     def __init__(self, s: _Model, keep=()):
         self.s = s
         self._keep = keep
+        if s.ut_alpha == 0.0:   # the unscented rule's parameters default to the cubature rule's
+            s.ut_alpha, s.ut_beta, s.ut_kappa = 1.0, 0.0, 0.0
+
+    def unscented(self, alpha: float, beta: float, kappa: float) -> "Model":
+        """The same model with the unscented rule's parameters set."""
+        s = _Model()
+        ctypes.pointer(s)[0] = self.s
+        s.ut_alpha, s.ut_beta, s.ut_kappa = alpha, beta, kappa
+        return Model(s, self._keep)
 
     @classmethod
     def ct_bearings(cls, dt, q_c, q_w, r_std, sensors, q_form=0):
@@ -247,14 +260,16 @@ def bearings_jacobian(x, s):
     return out.reshape(2, 5)
 
 
-def slr(model: Model, which: int, b: int, xbar, Pbar):
-    """Cubature SLR (Eqs. 7-9) of f (which=0) or h of trajectory b (which=1)."""
+def slr(model: Model, which: int, b: int, xbar, Pbar, method: int = CUBATURE):
+    """Sigma-point SLR (Eqs. 7-9) of f (which=0) or h of trajectory b (which=1),
+    with the cubature rule or (method=UNSCENTED) the model's unscented rule."""
     nz = 5 if which == 0 else 2
     xbar, Pbar = _f64(xbar), _f64(Pbar)
     G = np.zeros(nz * 5)
     off = np.zeros(nz)
     Lam = np.zeros(nz * nz)
-    st = _load().orc_slr(ctypes.byref(model.s), which, b, _p(xbar), _p(Pbar), _p(G), _p(off), _p(Lam))
+    fn = _load().orc_slr_unscented if method == UNSCENTED else _load().orc_slr
+    st = fn(ctypes.byref(model.s), which, b, _p(xbar), _p(Pbar), _p(G), _p(off), _p(Lam))
     if st != OK:
         raise np.linalg.LinAlgError(f"orc_slr status {st}")
     return G.reshape(nz, 5), off, Lam.reshape(nz, nz)

@@ -418,6 +418,65 @@ int orc_slr(const orc_model* m, int which, int64_t b, const double xbar[5], cons
     return ORC_OK;
 }
 
+int orc_slr_unscented(const orc_model* m, int which, int64_t b, const double xbar[5], const double Pbar[25],
+                      double* G, double* offset, double* Lam)
+{
+    const int nz = which == 0 ? NX : NY;
+    const double a = m->ut_alpha, n = (double)NX;
+    const double lambda = a * a * (n + m->ut_kappa) - n;
+    if (!(n + lambda > 0.0)) return ORC_NOT_PD;
+    double Lc[25];
+    if (!cholesky(NX, Pbar, Lc)) return ORC_NOT_PD;
+    /* point 0 is the centre; points 1..n and n+1..2n the two sides */
+    double X[2 * NX + 1][NX], Z[2 * NX + 1][NX], Wm[2 * NX + 1], Wc[2 * NX + 1];
+    const double scale = sqrt(n + lambda);
+    for (int r = 0; r < NX; ++r) X[0][r] = xbar[r];
+    for (int i = 0; i < NX; ++i)
+        for (int r = 0; r < NX; ++r) {
+            X[1 + i][r] = xbar[r] + scale * Lc[r * NX + i];
+            X[1 + NX + i][r] = xbar[r] - scale * Lc[r * NX + i];
+        }
+    Wm[0] = lambda / (n + lambda);
+    Wc[0] = Wm[0] + 1.0 - a * a + m->ut_beta;
+    for (int j = 1; j < 2 * NX + 1; ++j) Wm[j] = Wc[j] = 1.0 / (2.0 * (n + lambda));
+    double ref[NX];
+    for (int j = 0; j < 2 * NX + 1; ++j) {
+        if (which == 0) model_f(m, X[j], Z[j]);
+        else model_h(m, b, X[j], Z[j]);
+    }
+    if (which == 1 && angles(m)) {
+        model_h(m, b, xbar, ref);
+        for (int j = 0; j < 2 * NX + 1; ++j)
+            for (int r = 0; r < nz; ++r) Z[j][r] = ref[r] + orc_wrap(Z[j][r] - ref[r]);
+    }
+    double zbar[NX] = {0};
+    for (int j = 0; j < 2 * NX + 1; ++j)
+        for (int r = 0; r < nz; ++r) zbar[r] += Wm[j] * Z[j][r];
+    double Psi[NX * NX] = {0}; /* NX x nz */
+    double Phi[NX * NX] = {0}; /* nz x nz */
+    for (int j = 0; j < 2 * NX + 1; ++j) {
+        for (int i = 0; i < NX; ++i)
+            for (int r = 0; r < nz; ++r)
+                Psi[i * nz + r] += Wc[j] * (X[j][i] - xbar[i]) * (Z[j][r] - zbar[r]);
+        for (int r = 0; r < nz; ++r)
+            for (int s = 0; s < nz; ++s)
+                Phi[r * nz + s] += Wc[j] * (Z[j][r] - zbar[r]) * (Z[j][s] - zbar[s]);
+    }
+    double Gt[NX * NX];
+    chol_solve(NX, nz, Lc, Psi, Gt);
+    for (int r = 0; r < nz; ++r)
+        for (int i = 0; i < NX; ++i) G[r * NX + i] = Gt[i * nz + r];
+    double Gx[NX];
+    mv(nz, NX, G, xbar, Gx);
+    for (int r = 0; r < nz; ++r) offset[r] = zbar[r] - Gx[r];
+    double GP[NX * NX], GPG[NX * NX];
+    mm(nz, NX, NX, G, Pbar, GP);
+    mmt(nz, NX, nz, GP, G, GPG);
+    for (int r = 0; r < nz * nz; ++r) Lam[r] = Phi[r] - GPG[r];
+    symmetrize(nz, Lam);
+    return ORC_OK;
+}
+
 int orc_linearize(const orc_model* m, int method, int64_t N, const int64_t* offsets, int64_t B,
                   const double* xbar, const double* Pbar, const double* y,
                   double* F, double* c, double* Qp, double* H, double* d, double* Rp, double* y_used)
@@ -442,7 +501,9 @@ int orc_linearize(const orc_model* m, int method, int64_t N, const int64_t* offs
                     memcpy(Qp + 25 * k, Q, sizeof(Q));
                 } else {
                     double Lam[25];
-                    int st = orc_slr(m, 0, b, xk, Pbar + 25 * k, F + 25 * k, c + 5 * k, Lam);
+                    int st = method == ORC_UNSCENTED
+                                 ? orc_slr_unscented(m, 0, b, xk, Pbar + 25 * k, F + 25 * k, c + 5 * k, Lam)
+                                 : orc_slr(m, 0, b, xk, Pbar + 25 * k, F + 25 * k, c + 5 * k, Lam);
                     if (st != ORC_OK) return st;
                     for (int i = 0; i < 25; ++i) Qp[25 * k + i] = Q[i] + Lam[i];
                 }
@@ -463,7 +524,9 @@ int orc_linearize(const orc_model* m, int method, int64_t N, const int64_t* offs
                     memcpy(Rp + 4 * k, R, sizeof(R));
                 } else {
                     double Om[4];
-                    int st = orc_slr(m, 1, b, xk, Pbar + 25 * k, H + 10 * k, d + 2 * k, Om);
+                    int st = method == ORC_UNSCENTED
+                                 ? orc_slr_unscented(m, 1, b, xk, Pbar + 25 * k, H + 10 * k, d + 2 * k, Om)
+                                 : orc_slr(m, 1, b, xk, Pbar + 25 * k, H + 10 * k, d + 2 * k, Om);
                     if (st != ORC_OK) return st;
                     for (int i = 0; i < 4; ++i) Rp[4 * k + i] = R[i] + Om[i];
                 }

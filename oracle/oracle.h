@@ -14,6 +14,7 @@
 
 #define ORC_IEKS 0
 #define ORC_CUBATURE 1
+#define ORC_UNSCENTED 2
 
 #define ORC_MODEL_CT_BEARINGS 0
 #define ORC_MODEL_LINEAR 1
@@ -31,6 +32,8 @@ typedef struct {
     int sensors_per_traj;
     /* linear model x' = F x + c + q, y = H x + d + r (full matrices, row-major) */
     double F[25], c[5], Q[25], H[10], d[2], R[4];
+    /* unscented rule (ORC_UNSCENTED): spread alpha, prior-knowledge beta, kappa */
+    double ut_alpha, ut_beta, ut_kappa;
 } orc_model;
 
 typedef struct { double A[25], b[5], C[25], eta[5], J[25]; } orc_felem;
@@ -46,6 +49,13 @@ void orc_measurement_noise(const orc_model* m, double R[4]);
 
 int orc_slr(const orc_model* m, int which, int64_t b, const double xbar[5], const double Pbar[25],
             double* G, double* offset, double* Lam);
+/* The same regression with the unscented rule of parameters (alpha, beta,
+ * kappa): lambda = alpha^2 (n + kappa) - n, points xbar and
+ * xbar +- sqrt(n + lambda) (chol Pbar) e_i, mean weights lambda / (n + lambda)
+ * (centre) and 1 / (2 (n + lambda)), covariance weights the same except
+ * lambda / (n + lambda) + 1 - alpha^2 + beta at the centre. */
+int orc_slr_unscented(const orc_model* m, int which, int64_t b, const double xbar[5], const double Pbar[25],
+                      double* G, double* offset, double* Lam);
 int orc_linearize(const orc_model* m, int method, int64_t N, const int64_t* offsets, int64_t B,
                   const double* xbar, const double* Pbar, const double* y,
                   double* F, double* c, double* Qp, double* H, double* d, double* Rp, double* y_used);

@@ -4,6 +4,9 @@ bearings model (Secs. 3 and 5).
 * Cubature SLR (Eqs. 7-9) is exact for affine functions, recovers the
   Jacobian of the coordinates in which f is affine, and tends to the Taylor
   linearisation (Eq. 10) as the covariance shrinks.
+* The unscented rule with alpha = 1, beta = 0, kappa = 0 is the cubature rule
+  (a separate code path); for other parameters it is exact for affine
+  functions and gives the exact mean of quadratic functions.
 * Every IEKS iteration is one Gauss-Newton step of the MAP problem (checked
   against a dense Gauss-Newton solve, positive-definite Q), and at
   convergence the MAP gradient vanishes.
@@ -68,6 +71,56 @@ def test_slr_small_covariance_tends_to_taylor(which):
         assert np.all(np.linalg.eigvalsh(Lam) > -1e-15)
     # second-order convergence in the sigma-point spread
     assert errs[1] < 0.02 * errs[0] + 1e-12 and errs[2] < 0.02 * errs[1] + 1e-12
+
+
+UT_PARAMS = [(1.0, 2.0, 1.0), (0.8, 2.0, 0.5), (1.0, 0.0, -2.0)]
+
+
+def test_unscented_with_cubature_parameters_is_the_cubature_rule():
+    m = ct_model().unscented(1.0, 0.0, 0.0)
+    xbar = np.array([0.4, -0.2, 1.1, 0.3, 0.8])
+    A = np.random.default_rng(5).standard_normal((5, 5))
+    P = 0.05 * (A @ A.T) + 0.01 * np.eye(5)
+    for which in (0, 1):
+        a = oracle.slr(m, which, 0, xbar, P, method=oracle.UNSCENTED)
+        c = oracle.slr(m, which, 0, xbar, P, method=oracle.CUBATURE)
+        for u, v in zip(a, c):
+            np.testing.assert_allclose(u, v, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("alpha,beta,kappa", UT_PARAMS)
+def test_unscented_exact_for_linear_model(alpha, beta, kappa):
+    rng = np.random.default_rng(4)
+    F = rng.standard_normal((5, 5)); c = rng.standard_normal(5)
+    H = rng.standard_normal((2, 5)); d = rng.standard_normal(2)
+    m = oracle.Model.linear(F, c, np.eye(5), H, d, np.eye(2)).unscented(alpha, beta, kappa)
+    xbar = rng.standard_normal(5)
+    A = rng.standard_normal((5, 5)); P = A @ A.T + np.eye(5)
+    for which, (Gt, ot) in ((0, (F, c)), (1, (H, d))):
+        G, off, Lam = oracle.slr(m, which, 0, xbar, P, method=oracle.UNSCENTED)
+        np.testing.assert_allclose(G, Gt, atol=1e-11)
+        np.testing.assert_allclose(off, ot, atol=1e-11)
+        np.testing.assert_allclose(Lam, 0, atol=1e-11)
+
+
+@pytest.mark.parametrize("alpha,beta,kappa", UT_PARAMS)
+def test_unscented_mean_exact_for_quadratics(alpha, beta, kappa):
+    """The symmetric rule integrates polynomials of degree 2 (and odd ones)
+    exactly, so its mean of a function that is quadratic up to a tiny quartic
+    remainder must match the Gaussian expectation: the coordinated turn with
+    only the turn rate uncertain, N(0.8, 0.3^2), over dt = 0.01 (remainder of
+    order (0.3 dt)^4). The expectation is integrated by 40-node Gauss-Hermite.
+    A wrong centre or side weight moves the mean by O(1)."""
+    m = ct_model().unscented(alpha, beta, kappa)
+    xbar = np.array([0.4, -0.2, 1.1, 0.3, 0.8])
+    P = np.diag([0.0, 0.0, 0.0, 0.0, 0.3 ** 2])
+    P[:4, :4] = 1e-30 * np.eye(4)   # (p, v) fixed: f depends on omega alone
+    G, off, Lam = oracle.slr(m, 0, 0, xbar, P, method=oracle.UNSCENTED)
+    zbar = G @ xbar + off
+    t, w = np.polynomial.hermite_e.hermegauss(40)
+    exact = sum(wi * oracle.ct_f(xbar + np.array([0, 0, 0, 0, 0.3 * ti]), synth.DT) for ti, wi in zip(t, w))
+    exact = exact / w.sum()
+    np.testing.assert_allclose(zbar, exact, atol=1e-9)
 
 
 def test_slr_unwraps_bearings_across_branch_cut():
