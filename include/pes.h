@@ -77,7 +77,17 @@ typedef enum {
     PES_ERR_TIMEOUT = 7        /* an internal grid-wide wait exceeded its time limit */
 } pes_status;
 
-typedef enum { PES_IEKS = 0, PES_CUBATURE = 1 } pes_method;
+/* Linearisation of Sec. 3: PES_IEKS, first-order Taylor expansion (Eq. 10);
+ * PES_CUBATURE, statistical linear regression (Eqs. 7-9) over the third-degree
+ * spherical-radial cubature points xbar +- sqrt(n) chol(Pbar) e_i, weights
+ * 1/(2n); PES_UNSCENTED, the same regression over the unscented points of
+ * parameters (ut_alpha, ut_beta, ut_kappa) of pes_model: lambda =
+ * alpha^2 (n + kappa) - n, points xbar and xbar +- sqrt(n + lambda) chol(Pbar) e_i,
+ * mean weights lambda/(n + lambda) (centre) and 1/(2(n + lambda)), the
+ * centre's covariance weight lambda/(n + lambda) + 1 - alpha^2 + beta
+ * (n + lambda > 0 required). The paper names sigma-point rules generally
+ * (Sec. 3); the unscented rule is one of them. */
+typedef enum { PES_IEKS = 0, PES_CUBATURE = 1, PES_UNSCENTED = 2 } pes_method;
 typedef enum { PES_FP64 = 0, PES_FP32 = 1, PES_MIXED = 2 } pes_precision;
 typedef enum { PES_MODEL_CT_BEARINGS = 0, PES_MODEL_LINEAR = 1 } pes_model_kind;
 
@@ -113,6 +123,9 @@ typedef struct {
     double H[10];
     double d[2];
     double R[3];
+    double ut_alpha;   /* PES_UNSCENTED only: spread, prior-knowledge and secondary scaling parameters */
+    double ut_beta;
+    double ut_kappa;
 } pes_model;
 
 typedef struct pes_handle pes_handle;

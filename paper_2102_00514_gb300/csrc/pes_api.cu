@@ -61,11 +61,34 @@ pes_status check_common(pes_handle* h, pes_precision prec, const int64_t* offset
     return PES_OK;
 }
 
+// Sigma-point rule of a method: the spread of the side points, twice a side
+// point's weight, and the centre's covariance weight (pes.h, pes_method).
+void sigma_rule(const pes_model& m, pes_method method, double& scale, double& w, double& w0c)
+{
+    const double n = 5.0;
+    if (method == PES_UNSCENTED) {
+        const double a = m.ut_alpha;
+        const double lam = a * a * (n + m.ut_kappa) - n;
+        scale = sqrt(n + lam);
+        w = 1.0 / (n + lam);
+        w0c = lam / (n + lam) + 1.0 - a * a + m.ut_beta;
+    } else {
+        scale = sqrt(n);
+        w = 1.0 / n;
+        w0c = 0.0;
+    }
+}
+
 template <typename T>
-DevModel<T> to_dev_model(const pes_model& m, const T* sensors_T)
+DevModel<T> to_dev_model(const pes_model& m, const T* sensors_T, pes_method method)
 {
     DevModel<T> d;
     memset(&d, 0, sizeof(d));
+    double sc, w, w0c;
+    sigma_rule(m, method, sc, w, w0c);
+    d.sp_scale = T(sc);
+    d.sp_w = T(w);
+    d.sp_w0c = T(w0c);
     d.kind = m.kind;
     d.sensors_per_traj = m.sensors_per_traj;
     d.dt = T(m.dt);
@@ -103,6 +126,20 @@ DevModel<T> to_dev_model(const pes_model& m, const T* sensors_T)
 // The model's sensors in the kernel precision, in the handle's workspace.
 template <typename T>
 pes_status device_model(pes_handle* h, const pes_model& m, int32_t B, cudaStream_t st, DevModel<T>& out);
+
+pes_status check_method(pes_handle* h, pes_method method, const pes_model* m)
+{
+    if (method != PES_IEKS && method != PES_CUBATURE && method != PES_UNSCENTED)
+        return fail(h, PES_ERR_INVALID_ARG, "unknown method");
+    if (method == PES_UNSCENTED) {
+        if (!std::isfinite(m->ut_alpha) || m->ut_alpha == 0.0 || !std::isfinite(m->ut_beta) ||
+            !std::isfinite(m->ut_kappa))
+            return fail(h, PES_ERR_INVALID_ARG, "unscented parameters must be finite, alpha non-zero");
+        const double lam = m->ut_alpha * m->ut_alpha * (5.0 + m->ut_kappa) - 5.0;
+        if (!(5.0 + lam > 0.0)) return fail(h, PES_ERR_INVALID_ARG, "unscented rule needs n + lambda > 0");
+    }
+    return PES_OK;
+}
 
 pes_status check_model(pes_handle* h, const pes_model* m)
 {
@@ -184,10 +221,11 @@ pes_status read_status(pes_handle* h, cudaStream_t st, int* iters = nullptr)
 }
 
 template <typename T>
-pes_status device_model(pes_handle* h, const pes_model& m, int32_t B, cudaStream_t st, DevModel<T>& out)
+pes_status device_model(pes_handle* h, const pes_model& m, int32_t B, cudaStream_t st, DevModel<T>& out,
+                        pes_method method)
 {
     T* sensT = static_cast<T*>(h->sensT);
-    out = to_dev_model<T>(m, sensT);
+    out = to_dev_model<T>(m, sensT, method);
     if (m.kind == PES_MODEL_CT_BEARINGS) {
         const int n = 4 * (m.sensors_per_traj ? (int)B : 1);
         PES_CUDA(h, launch_convert<T>(m.sensors, sensT, n, st));
@@ -258,7 +296,7 @@ static pes_status ieks_run_t(pes_handle* h, const pes_model* model, pes_method m
                              const void* P0, const void* x_init, const void* P_init, int32_t max_iters, double tol,
                              void* x_out, void* P_out, int32_t* iters_used, cudaStream_t st)
 {
-    const int lin = method == PES_CUBATURE ? LIN_CUBATURE : LIN_IEKS;
+    const int lin = method == PES_IEKS ? LIN_IEKS : LIN_CUBATURE;
     Shape s;
     pes_status r = make_shape<T>(h, lin, prec, N, s);
     if (r != PES_OK) return r;
@@ -269,7 +307,7 @@ static pes_status ieks_run_t(pes_handle* h, const pes_model* model, pes_method m
     T* lP = lx + 5 * cs;
     T* ly = lP + 15 * cs;
     PES_CUDA(h, launch_lanes_transpose<T>((const T*)y, ly, 2, N, s.L, NL, true, st));
-    const bool cub = (method == PES_CUBATURE);
+    const bool cub = (method != PES_IEKS);
     if (x_init) PES_CUDA(h, launch_lanes_transpose<T>((const T*)x_init, lx, 5, N, s.L, NL, true, st));
     if (cub && P_init) PES_CUDA(h, launch_lanes_transpose<T>((const T*)P_init, lP, 15, N, s.L, NL, true, st));
     if (!x_init || (cub && !P_init))
@@ -278,7 +316,7 @@ static pes_status ieks_run_t(pes_handle* h, const pes_model* model, pes_method m
     KParams<T> p{};
     p.N = N; p.offsets = offsets; p.B = B; p.mode = MODE_RUN; p.iters = max_iters; p.tol = tol;
     p.write_P_every_iter = tol > 0.0 ? 1 : 0;
-    pes_status rm = device_model<T>(h, *model, B, st, p.model);
+    pes_status rm = device_model<T>(h, *model, B, st, p.model, method);
     if (rm != PES_OK) return rm;
     p.y = ly; p.m0 = (const T*)m0; p.P0 = (const T*)P0;
     p.x = lx; p.P = lP;
@@ -304,7 +342,7 @@ static pes_status ieks_run_sequential_t(pes_handle* h, const pes_model* model, p
                                         const void* x_init, const void* P_init, int32_t max_iters, double tol,
                                         void* x_out, void* P_out, int32_t* iters_used, cudaStream_t st)
 {
-    const bool cub = (method == PES_CUBATURE);
+    const bool cub = (method != PES_IEKS);
     if (x_init && x_init != x_out) PES_CUDA(h, cudaMemcpyAsync(x_out, x_init, sizeof(T) * 5 * N, cudaMemcpyDeviceToDevice, st));
     if (cub && P_init && P_init != P_out)
         PES_CUDA(h, cudaMemcpyAsync(P_out, P_init, sizeof(T) * 15 * N, cudaMemcpyDeviceToDevice, st));
@@ -313,7 +351,7 @@ static pes_status ieks_run_sequential_t(pes_handle* h, const pes_model* model, p
                                            (cub && !P_init) ? (T*)P_out : nullptr, st));
     KParams<T> p{};
     p.N = N; p.offsets = offsets; p.B = B; p.mode = MODE_RUN; p.iters = max_iters; p.tol = tol;
-    pes_status rm = device_model<T>(h, *model, B, st, p.model);
+    pes_status rm = device_model<T>(h, *model, B, st, p.model, method);
     if (rm != PES_OK) return rm;
     p.y = (const T*)y; p.m0 = (const T*)m0; p.P0 = (const T*)P0;
     p.x = (T*)x_out; p.P = (T*)P_out;
@@ -358,7 +396,7 @@ static pes_status ieks_run_mixed(pes_handle* h, const pes_model* model, pes_meth
     double* m064 = P64 + 15 * N;
     double* P064 = m064 + 5 * (size_t)B;
     int32_t it32 = 0;
-    const bool cub = (method == PES_CUBATURE);
+    const bool cub = (method != PES_IEKS);
     const void* xi32 = x_init;
     const void* Pi32 = P_init;
     if (max_iters > 1) {
@@ -494,7 +532,7 @@ pes_status pes_launch_shape(pes_handle* h, pes_method method, pes_precision prec
 {
     if (!h || N < 1) return PES_ERR_INVALID_ARG;
     if (prec == PES_MIXED) return PES_ERR_UNSUPPORTED;
-    const int lin = method == PES_CUBATURE ? LIN_CUBATURE : LIN_IEKS;
+    const int lin = method == PES_IEKS ? LIN_IEKS : LIN_CUBATURE;
     Shape s;
     pes_status r = (prec == PES_FP64) ? make_shape<double>(h, lin, prec, N, s) : make_shape<float>(h, lin, prec, N, s);
     if (r != PES_OK) return r;
@@ -512,23 +550,23 @@ pes_status pes_linearize(pes_handle* h, const pes_model* model, pes_method metho
     pes_status r = check_common(h, prec, offsets, B, N);
     if (r != PES_OK) return r;
     if ((r = check_model(h, model)) != PES_OK) return r;
-    if (method != PES_IEKS && method != PES_CUBATURE) return fail(h, PES_ERR_INVALID_ARG, "unknown method");
+    if ((r = check_method(h, method, model)) != PES_OK) return r;
     if (!x_nom || !y || !F || !c || !Qp || !H || !d || !Rp) return fail(h, PES_ERR_INVALID_ARG, "NULL array");
-    if (method == PES_CUBATURE && !P_nom) return fail(h, PES_ERR_INVALID_ARG, "cubature needs P_nom");
+    if (method != PES_IEKS && !P_nom) return fail(h, PES_ERR_INVALID_ARG, "sigma-point methods need P_nom");
     cudaStream_t st = (cudaStream_t)stream;
     PES_CUDA(h, launch_validate_offsets(offsets, B, N, h->status, st));
-    const int lin = method == PES_CUBATURE ? LIN_CUBATURE : LIN_IEKS;
+    const int lin = method == PES_IEKS ? LIN_IEKS : LIN_CUBATURE;
     if (prec == PES_FP64) {
         KParams<double> p{};
         p.N = N; p.offsets = offsets; p.B = B;
-        if ((r = device_model<double>(h, *model, B, st, p.model)) != PES_OK) return r;
+        if ((r = device_model<double>(h, *model, B, st, p.model, method)) != PES_OK) return r;
         p.x = (double*)x_nom; p.P = (double*)P_nom; p.y = (const double*)y; p.status = h->status; p.cs = N;
         PES_CUDA(h, launch_linearize<double>(p, lin, (double*)F, (double*)c, (double*)Qp, (double*)H, (double*)d,
                                              (double*)Rp, (double*)y_used, st));
     } else {
         KParams<float> p{};
         p.N = N; p.offsets = offsets; p.B = B;
-        if ((r = device_model<float>(h, *model, B, st, p.model)) != PES_OK) return r;
+        if ((r = device_model<float>(h, *model, B, st, p.model, method)) != PES_OK) return r;
         p.x = (float*)x_nom; p.P = (float*)P_nom; p.y = (const float*)y; p.status = h->status; p.cs = N;
         PES_CUDA(h, launch_linearize<float>(p, lin, (float*)F, (float*)c, (float*)Qp, (float*)H, (float*)d,
                                             (float*)Rp, (float*)y_used, st));
@@ -591,7 +629,7 @@ pes_status pes_ieks_run(pes_handle* h, const pes_model* model, pes_method method
     pes_status r = check_common(h, prec, offsets, B, N, true);
     if (r != PES_OK) return r;
     if ((r = check_model(h, model)) != PES_OK) return r;
-    if (method != PES_IEKS && method != PES_CUBATURE) return fail(h, PES_ERR_INVALID_ARG, "unknown method");
+    if ((r = check_method(h, method, model)) != PES_OK) return r;
     if (!y || !m0 || !P0 || !x_out || !P_out) return fail(h, PES_ERR_INVALID_ARG, "NULL array");
     if (max_iters < 1) return fail(h, PES_ERR_INVALID_ARG, "max_iters must be >= 1");
     if (!(tol == tol)) return fail(h, PES_ERR_INVALID_ARG, "tol is NaN");
@@ -615,7 +653,7 @@ pes_status pes_ieks_run_sequential(pes_handle* h, const pes_model* model, pes_me
     pes_status r = check_common(h, prec, offsets, B, N);
     if (r != PES_OK) return r;
     if ((r = check_model(h, model)) != PES_OK) return r;
-    if (method != PES_IEKS && method != PES_CUBATURE) return fail(h, PES_ERR_INVALID_ARG, "unknown method");
+    if ((r = check_method(h, method, model)) != PES_OK) return r;
     if (!y || !m0 || !P0 || !x_out || !P_out) return fail(h, PES_ERR_INVALID_ARG, "NULL array");
     if (max_iters < 1) return fail(h, PES_ERR_INVALID_ARG, "max_iters must be >= 1");
     if (!(tol == tol)) return fail(h, PES_ERR_INVALID_ARG, "tol is NaN");
@@ -679,11 +717,11 @@ pes_status pes_ieks_run_host(pes_handle* h, const pes_model* model, pes_method m
     PES_CUDA(h, cudaMemcpyAsync(h->hm0, m0, ts * 5 * B, cudaMemcpyHostToDevice, st));
     PES_CUDA(h, cudaMemcpyAsync(h->hP0, P0, ts * 15 * B, cudaMemcpyHostToDevice, st));
     if (x_init) PES_CUDA(h, cudaMemcpyAsync(h->hx, x_init, ts * 5 * N, cudaMemcpyHostToDevice, st));
-    if (P_init && method == PES_CUBATURE)
+    if (P_init && method != PES_IEKS)
         PES_CUDA(h, cudaMemcpyAsync(h->hP, P_init, ts * 15 * N, cudaMemcpyHostToDevice, st));
     int32_t it = 0;
     pes_status r = pes_ieks_run(h, &dm, method, prec, h->hy, h->hoff, B, N, h->hm0, h->hP0, x_init ? h->hx : nullptr,
-                                (P_init && method == PES_CUBATURE) ? h->hP : nullptr, max_iters, tol, h->hx, h->hP,
+                                (P_init && method != PES_IEKS) ? h->hP : nullptr, max_iters, tol, h->hx, h->hP,
                                 &it, stream);
     if (iters_used) *iters_used = it;
     if (r != PES_OK && r != PES_ERR_NOT_CONVERGED) return r;

@@ -30,6 +30,11 @@ struct DevModel {
     T Q[15];
     T R[3];
     T F[25], c[5], H[10], d[2];   // linear model
+    // sigma-point rule of the regression (Eqs. 7-9) over symmetric points
+    // xbar +- sp_scale chol(Pbar) e_i: sp_w = 1 / sp_scale^2 is twice a side
+    // point's weight, sp_w0c the centre's covariance weight (cubature:
+    // sqrt(n), 1/n, 0)
+    T sp_scale, sp_w, sp_w0c;
 };
 
 // Transition k -> k+1 linearised about xn = xbar_k: x_{k+1} ~ fx + F (x_k - xn) + N(0, Q')
@@ -341,7 +346,7 @@ PES_DEV bool cub_factor(const T* Pbar, T* L, T* rdiag)
 template <typename T>
 PES_DEV void lin_trans_cubature(const DevModel<T>& m, const T* xbar, const T* L, const T* rdiag, Trans<T>& tr)
 {
-    const T sq = tsqrt(T(NX));
+    const T sq = m.sp_scale;
     T inc_ref[5];
     CTCoef<T> kr;
     if (m.kind == MODEL_LINEAR) {
@@ -369,14 +374,16 @@ PES_DEV void lin_trans_cubature(const DevModel<T>& m, const T* xbar, const T* L,
             zdev[r] += h;
         }
     }
+    // zbar - f(xbar): the side points' mean deviation (the centre's is zero)
 #pragma unroll
-    for (int r = 0; r < 5; ++r) zdev[r] *= T(1) / T(NX);
-    // F = D L^{-1} / (2 sqrt(n))
+    for (int r = 0; r < 5; ++r) zdev[r] *= m.sp_w;
+    // F = D L^{-1} / (2 scale)
     const T sc = T(0.5) / sq;
 #pragma unroll
     for (int i = 0; i < 25; ++i) Dm[i] *= sc;
     solve_rows_lower_t<T, 5>(L, rdiag, Dm, tr.F);
-    // Lambda = (1/n) sum_i u_i u_i^T with u_i = U_i - zdev
+    // Lambda = w sum_i u_i u_i^T + w0c zdev zdev^T with u_i = U_i - zdev (the
+    // side points' D D^T part cancels against F Pbar F^T)
 #pragma unroll
     for (int r = 0; r < 5; ++r)
 #pragma unroll
@@ -388,7 +395,7 @@ PES_DEV void lin_trans_cubature(const DevModel<T>& m, const T* xbar, const T* L,
             T s = T(0);
 #pragma unroll
             for (int i = 0; i < NX; ++i) s = fma(U[r * NX + i], U[q * NX + i], s);
-            tr.Q[si(r, q)] = m.Q[si(r, q)] + s * (T(1) / T(NX));
+            tr.Q[si(r, q)] = m.Q[si(r, q)] + s * m.sp_w + m.sp_w0c * zdev[r] * zdev[q];
         }
     // fx = zbar = f(xbar) + zdev
     if (m.kind == MODEL_LINEAR) {
@@ -414,7 +421,7 @@ template <typename T>
 PES_DEV void lin_obs_cubature(const DevModel<T>& m, int b, const T* xbar, const T* L, const T* rdiag, const T* y,
                               Obs<T>& ob)
 {
-    const T sq = tsqrt(T(NX));
+    const T sq = m.sp_scale;
     T s[4] = {T(0), T(0), T(0), T(0)};
     T h_ref[2];
     const bool lin = (m.kind == MODEL_LINEAR);
@@ -452,7 +459,7 @@ PES_DEV void lin_obs_cubature(const DevModel<T>& m, int b, const T* xbar, const 
         }
     }
 #pragma unroll
-    for (int r = 0; r < 2; ++r) zdev[r] *= T(1) / T(NX);
+    for (int r = 0; r < 2; ++r) zdev[r] *= m.sp_w;
     const T sc = T(0.5) / sq;
 #pragma unroll
     for (int i = 0; i < 10; ++i) Dm[i] *= sc;
@@ -468,7 +475,7 @@ PES_DEV void lin_obs_cubature(const DevModel<T>& m, int b, const T* xbar, const 
             T v = T(0);
 #pragma unroll
             for (int i = 0; i < NX; ++i) v = fma(U[r * NX + i], U[q * NX + i], v);
-            ob.R[si2(r, q)] = m.R[si2(r, q)] + v * (T(1) / T(NX));
+            ob.R[si2(r, q)] = m.R[si2(r, q)] + v * m.sp_w + m.sp_w0c * zdev[r] * zdev[q];
         }
     // residual about zbar = h(xbar) + zdev, measurement unwrapped nearest h(xbar)
     if (lin) {

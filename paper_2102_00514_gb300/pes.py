@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libpes.so")
 OK, INVALID_ARG, NOT_PD, NONFINITE, NOT_CONVERGED, CUDA, UNSUPPORTED, TIMEOUT = range(8)
 STATUS_NAMES = {0: "PES_OK", 1: "PES_ERR_INVALID_ARG", 2: "PES_ERR_NOT_PD", 3: "PES_ERR_NONFINITE",
                 4: "PES_ERR_NOT_CONVERGED", 5: "PES_ERR_CUDA", 6: "PES_ERR_UNSUPPORTED", 7: "PES_ERR_TIMEOUT"}
-IEKS, CUBATURE = 0, 1
+IEKS, CUBATURE, UNSCENTED = 0, 1, 2
 FP64, FP32, MIXED = 0, 1, 2
 MODEL_CT_BEARINGS, MODEL_LINEAR = 0, 1
 
@@ -46,7 +46,8 @@ class _Model(ctypes.Structure):
                 ("q_c", ctypes.c_double), ("q_w", ctypes.c_double), ("r_std", ctypes.c_double),
                 ("sensors", ctypes.c_void_p), ("sensors_per_traj", ctypes.c_int32),
                 ("F", ctypes.c_double * 25), ("c", ctypes.c_double * 5), ("Q", ctypes.c_double * 15),
-                ("H", ctypes.c_double * 10), ("d", ctypes.c_double * 2), ("R", ctypes.c_double * 3)]
+                ("H", ctypes.c_double * 10), ("d", ctypes.c_double * 2), ("R", ctypes.c_double * 3),
+                ("ut_alpha", ctypes.c_double), ("ut_beta", ctypes.c_double), ("ut_kappa", ctypes.c_double)]
 
 
 _lib = None
@@ -117,10 +118,14 @@ class Model:
     H: tuple = ()
     d: tuple = ()
     R: tuple = ()
+    ut_alpha: float = 1.0   # the unscented rule (UNSCENTED); these values give the cubature rule
+    ut_beta: float = 0.0
+    ut_kappa: float = 0.0
 
     def as_struct(self) -> _Model:
         s = _Model()
         s.kind, s.q_form = self.kind, self.q_form
+        s.ut_alpha, s.ut_beta, s.ut_kappa = self.ut_alpha, self.ut_beta, self.ut_kappa
         s.dt, s.q_c, s.q_w, s.r_std = self.dt, self.q_c, self.q_w, self.r_std
         if self.sensors is not None:
             if self.sensors.dtype != torch.float64:

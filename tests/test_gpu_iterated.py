@@ -6,7 +6,8 @@ import torch
 
 import oracle
 from paper_2102_00514_gb300 import pes, synth
-from tests.gpu_common import (TOL_FP32, TOL_FP64, gpu_run, oracle_run, rel_err, to_dev, workload_to_dev)
+from tests.gpu_common import (ORACLE_METHOD, TOL_FP32, TOL_FP64, gpu_run, oracle_run, rel_err, to_dev,
+                               workload_to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -18,17 +19,19 @@ def sm():
     s.close()
 
 
-@pytest.mark.parametrize("method", [pes.IEKS, pes.CUBATURE])
+@pytest.mark.parametrize("method", [pes.IEKS, pes.CUBATURE, pes.UNSCENTED])
 @pytest.mark.parametrize("prec", [pes.FP64, pes.FP32])
 def test_linearize_matches_oracle(sm, method, prec):
     wl = synth.ct_bearings([40, 1, 300], seed=21, sensor_jitter=0.2, omega0_halfwidth=1.0)
     # a non-trivial nominal: one oracle iteration from the prior
-    out = oracle_run(wl, method, iters=1)
+    ut = (0.8, 2.0, 0.5) if method == pes.UNSCENTED else None
+    out = oracle_run(wl, method, iters=1, ut=ut)
     om = oracle.Model.from_workload(wl)
-    ref = oracle.linearize(om, oracle.IEKS if method == pes.IEKS else oracle.CUBATURE, wl["offsets"],
-                           out["x"], out["P"], wl["y"])
+    if ut is not None:
+        om = om.unscented(*ut)
+    ref = oracle.linearize(om, ORACLE_METHOD[method], wl["offsets"], out["x"], out["P"], wl["y"])
     dt = torch.float64 if prec == pes.FP64 else torch.float32
-    d = workload_to_dev(wl, prec)
+    d = workload_to_dev(wl, prec, ut)
     got = sm.linearize(d["model"], method, prec, to_dev(out["x"], dt), to_dev(out["P"], dt), d["y"], d["offsets"])
     sm.sync()
     tol = 1e-10 if prec == pes.FP64 else 2e-4
@@ -47,6 +50,54 @@ def test_ieks_run_fp64_matches_oracle(sm, name, method):
     assert used == 10
     assert rel_err(x, ref["x"], wl["offsets"]) < TOL_FP64
     assert rel_err(P, ref["P"], wl["offsets"]) < TOL_FP64
+
+
+UT = [(1.0, 2.0, 1.0), (0.8, 2.0, 0.5)]
+
+
+@pytest.mark.parametrize("ut", UT)
+@pytest.mark.parametrize("name", ["ieks_T500", "ipls_T10000"])
+def test_unscented_fp64_matches_oracle(sm, name, ut):
+    wl = synth.workload(name)
+    ref = oracle_run(wl, pes.UNSCENTED, iters=10, ut=ut)
+    x, P, used, _ = gpu_run(sm, wl, pes.UNSCENTED, pes.FP64, iters=10, ut=ut)
+    assert used == 10
+    assert rel_err(x, ref["x"], wl["offsets"]) < TOL_FP64
+    assert rel_err(P, ref["P"], wl["offsets"]) < TOL_FP64
+
+
+def test_unscented_fp32_matches_oracle(sm):
+    wl = synth.workload("ipls_T10000")
+    ref = oracle_run(wl, pes.UNSCENTED, iters=10, ut=UT[0])
+    x, P, _, _ = gpu_run(sm, wl, pes.UNSCENTED, pes.FP32, iters=10, ut=UT[0])
+    assert rel_err(x, ref["x"], wl["offsets"]) < TOL_FP32
+    assert rel_err(P, ref["P"], wl["offsets"]) < TOL_FP32
+
+
+def test_unscented_with_cubature_parameters_equals_cubature(sm):
+    wl = synth.workload("batch8_T1_3000")
+    xa, Pa, _, _ = gpu_run(sm, wl, pes.UNSCENTED, pes.FP64, iters=3, ut=(1.0, 0.0, 0.0))
+    xb, Pb, _, _ = gpu_run(sm, wl, pes.CUBATURE, pes.FP64, iters=3)
+    assert rel_err(xa, xb, wl["offsets"]) < 1e-12
+    assert rel_err(Pa, Pb, wl["offsets"]) < 1e-12
+
+
+def test_unscented_sequential_matches_oracle(sm):
+    wl = synth.workload("batch8_T1_3000")
+    ref = oracle_run(wl, pes.UNSCENTED, iters=5, ut=UT[1])
+    d = workload_to_dev(wl, pes.FP64, UT[1])
+    x, P, _, _ = sm.ieks_run_sequential(d["model"], pes.UNSCENTED, pes.FP64, d["y"], d["offsets"], d["m0"], d["P0"],
+                                        iters=5)
+    assert rel_err(x.cpu().numpy(), ref["x"], wl["offsets"]) < TOL_FP64
+    assert rel_err(P.cpu().numpy(), ref["P"], wl["offsets"]) < TOL_FP64
+
+
+def test_unscented_parameters_validated(sm):
+    wl = synth.workload("ieks_T500")
+    for bad in ((1.0, 0.0, -5.0), (0.0, 2.0, 1.0)):   # n + lambda = 0; alpha = 0
+        with pytest.raises(pes.PesError) as ei:
+            gpu_run(sm, wl, pes.UNSCENTED, pes.FP64, iters=1, ut=bad)
+        assert ei.value.status == pes.INVALID_ARG
 
 
 @pytest.mark.parametrize("name,method", [("ieks_T500", pes.IEKS), ("ipls_T10000", pes.CUBATURE),
