@@ -446,6 +446,31 @@ def main():
             nom32[name] = (x.double().cpu().numpy(), P.double().cpu().numpy())
     sm.sync()
 
+    # the same step replayed from CUDA graphs (one captured run per method)
+    graphs = [sm.graph(d32["model"], m, pes.FP32, d32["y"], d32["offsets"], d32["m0"], d32["P0"], iters=iters,
+                       x_out=d32["x"], P_out=d32["P"]) for _, m in methods]
+    for g in graphs:
+        g.launch()
+    sm.sync()
+    gms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for g in graphs:
+            g.launch()
+        e1.record()
+        torch.cuda.synchronize()
+        gms.append(e0.elapsed_time(e1))
+    sm.sync()
+    for g in graphs:
+        g.close()
+    if rank == 0:
+        gt = max_over_ranks(sum(gms), None, "cuda")
+        result["graph"] = {"value": whole_job_rate(world, work_per_step, args.steps, gt * 1e-3),
+                           "ms_per_step": gt / args.steps,
+                           "note": "each method's pes_ieks_run captured once (pes_ieks_graph_create), replayed"}
+
     # the sequential counterpart on the same GPU: one thread per trajectory
     if args.sequential:
         seq = {}

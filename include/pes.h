@@ -306,6 +306,43 @@ pes_status pes_ieks_run_noalloc(const pes_model* model, pes_method method, pes_p
                                 int32_t max_iters, double tol, void* x_out, void* P_out, int32_t* iters_used,
                                 void* stream);
 
+/*
+ * A pes_ieks_run of fixed arguments (fixed iterations: no tolerance, no
+ * iteration count read back) captured once into a CUDA graph: offsets
+ * validation, sensor conversion, the layout transposes, the nominal
+ * initialisation and the persistent launch that runs every iteration. The
+ * graph keeps the pointers; replay it with pes_graph_launch after changing the
+ * arrays' contents (not their addresses or sizes). Replays use the handle's
+ * workspace, so they must not overlap other calls on the handle; device-side
+ * faults reach the handle's status word (pes_sync). PES_MIXED synchronises and
+ * returns PES_ERR_UNSUPPORTED.
+ */
+typedef struct pes_graph pes_graph;
+pes_status pes_ieks_graph_create(pes_handle* h, const pes_model* model, pes_method method, pes_precision prec,
+                                 const void* y, const int64_t* offsets, int32_t B, int64_t N, const void* m0,
+                                 const void* P0, const void* x_init, const void* P_init, int32_t iters,
+                                 void* x_out, void* P_out, pes_graph** out);
+pes_status pes_graph_launch(pes_graph* g, void* stream);
+pes_status pes_graph_destroy(pes_graph* g);
+
+/*
+ * Autotuner of the launch shape (the paper runs its scans through JAX; here
+ * the shape is this library's choice): times pes_ieks_run of the given
+ * workload with `iters` iterations for every distinct launch the candidates
+ * give (threads per block 128 or 256 for FP32, 128 for FP64; at least
+ * 4 .. 128 steps per lane, which sets the number of blocks when N is small)
+ * and keeps the fastest for this handle, method and precision: later calls
+ * of any size use it (pes_launch_shape reports it). x_scratch [5][N] and
+ * P_scratch [15][N] (DEVICE, the precision's type) receive the runs' outputs.
+ * Outputs (HOST, may be NULL): the chosen threads per block and minimum
+ * steps per lane, and its time per run in ms. Synchronous; on an error the
+ * previous choice stays.
+ */
+pes_status pes_autotune(pes_handle* h, const pes_model* model, pes_method method, pes_precision prec,
+                        const void* y, const int64_t* offsets, int32_t B, int64_t N, const void* m0,
+                        const void* P0, int32_t iters, void* x_scratch, void* P_scratch, int32_t* threads,
+                        int32_t* min_steps, float* ms_per_run, void* stream);
+
 /* Launch shape the next call of the given kind would use (for tests and the
  * benchmark): blocks, threads per block, steps per thread. */
 pes_status pes_launch_shape(pes_handle* h, pes_method method, pes_precision prec, int64_t N,

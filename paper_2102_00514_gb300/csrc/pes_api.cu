@@ -157,14 +157,20 @@ pes_status check_model(pes_handle* h, const pes_model* m)
 
 // Block size per precision. PES_FP32_THREADS (128 or 256) overrides the FP32
 // choice, for tuning.
-int choose_nt(pes_precision prec)
+// Threads per block and minimum steps per lane: the autotuned values of the
+// handle if pes_autotune set them, else the defaults (256 threads for FP32,
+// the 128 that the FP64 kernel is compiled for).
+int choose_nt(const pes_handle* h, int lin, pes_precision prec)
 {
-    if (prec == PES_FP64) return 128;
-    if (const char* env = getenv("PES_FP32_THREADS")) {
-        const int v = atoi(env);
-        if (v == 128 || v == 256) return v;
-    }
-    return 256;
+    const pes_tune& t = h->tune[lin][prec == PES_FP64 ? 1 : 0];
+    if (t.nt) return t.nt;
+    return prec == PES_FP64 ? 128 : 256;
+}
+
+int choose_min_steps(const pes_handle* h, int lin, pes_precision prec)
+{
+    const pes_tune& t = h->tune[lin][prec == PES_FP64 ? 1 : 0];
+    return t.min_steps ? t.min_steps : kMinStepsPerThread;
 }
 
 struct Shape {
@@ -174,10 +180,11 @@ struct Shape {
 template <typename T>
 pes_status make_shape(pes_handle* h, int lin, pes_precision prec, int64_t N, Shape& s)
 {
-    s.nt = choose_nt(prec);
+    s.nt = choose_nt(h, lin, prec);
+    const int min_steps = choose_min_steps(h, lin, prec);
     const int cap = coop_capacity(T(0), lin, s.nt, h->device);
     if (cap <= 0) return fail(h, PES_ERR_CUDA, "the smoother kernel cannot be made co-resident on this device");
-    const int64_t want = (N + (int64_t)s.nt * kMinStepsPerThread - 1) / ((int64_t)s.nt * kMinStepsPerThread);
+    const int64_t want = (N + (int64_t)s.nt * min_steps - 1) / ((int64_t)s.nt * min_steps);
     s.nb = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)cap, want, (int64_t)h->nb_max}));
     const int64_t lanes = (int64_t)s.nb * s.nt;
     s.L = (int)((N + lanes - 1) / lanes);
@@ -423,6 +430,11 @@ static pes_status ieks_run_mixed(pes_handle* h, const pes_model* model, pes_meth
     return r;
 }
 
+struct pes_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
 extern "C" {
 
 pes_status pes_create(pes_handle** out, int64_t max_states, int32_t max_batch)
@@ -539,6 +551,129 @@ pes_status pes_launch_shape(pes_handle* h, pes_method method, pes_precision prec
     if (blocks) *blocks = s.nb;
     if (threads) *threads = s.nt;
     if (steps_per_thread) *steps_per_thread = s.L;
+    return PES_OK;
+}
+
+pes_status pes_ieks_graph_create(pes_handle* h, const pes_model* model, pes_method method, pes_precision prec,
+                                 const void* y, const int64_t* offsets, int32_t B, int64_t N, const void* m0,
+                                 const void* P0, const void* x_init, const void* P_init, int32_t iters, void* x_out,
+                                 void* P_out, pes_graph** out)
+{
+    if (!h || !out) return PES_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (prec == PES_MIXED) return fail(h, PES_ERR_UNSUPPORTED, "PES_MIXED synchronises and cannot be captured");
+    cudaStream_t cs = nullptr;
+    PES_CUDA(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    pes_status r = PES_OK;
+    if (e == cudaSuccess) {
+        r = pes_ieks_run(h, model, method, prec, y, offsets, B, N, m0, P0, x_init, P_init, iters, 0.0, x_out, P_out,
+                         nullptr, cs);
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);   // ends the capture whatever happened
+        if (r == PES_OK && e2 != cudaSuccess) r = cuda_fail(h, e2, "stream capture of the smoother");
+    } else {
+        r = cuda_fail(h, e, "cudaStreamBeginCapture");
+    }
+    cudaStreamDestroy(cs);
+    cudaGraphExec_t exec = nullptr;
+    if (r == PES_OK) {
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e != cudaSuccess) r = cuda_fail(h, e, "cudaGraphInstantiate");
+    }
+    if (r != PES_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return r;
+    }
+    pes_graph* g = new (std::nothrow) pes_graph();
+    if (!g) {
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        return fail(h, PES_ERR_CUDA, "out of host memory");
+    }
+    g->graph = graph;
+    g->exec = exec;
+    *out = g;
+    return PES_OK;
+}
+
+pes_status pes_graph_launch(pes_graph* g, void* stream)
+{
+    if (!g) return PES_ERR_INVALID_ARG;
+    return cudaGraphLaunch(g->exec, (cudaStream_t)stream) == cudaSuccess ? PES_OK : PES_ERR_CUDA;
+}
+
+pes_status pes_graph_destroy(pes_graph* g)
+{
+    if (!g) return PES_ERR_INVALID_ARG;
+    cudaGraphExecDestroy(g->exec);
+    cudaGraphDestroy(g->graph);
+    delete g;
+    return PES_OK;
+}
+
+pes_status pes_autotune(pes_handle* h, const pes_model* model, pes_method method, pes_precision prec, const void* y,
+                        const int64_t* offsets, int32_t B, int64_t N, const void* m0, const void* P0,
+                        int32_t iters, void* x_scratch, void* P_scratch, int32_t* threads, int32_t* min_steps,
+                        float* ms_per_run, void* stream)
+{
+    if (!h) return PES_ERR_INVALID_ARG;
+    if (prec != PES_FP32 && prec != PES_FP64) return fail(h, PES_ERR_INVALID_ARG, "autotune FP32 or FP64");
+    if (iters < 1 || !x_scratch || !P_scratch) return fail(h, PES_ERR_INVALID_ARG, "iters >= 1 and scratch needed");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int lin = method == PES_IEKS ? LIN_IEKS : LIN_CUBATURE;
+    pes_tune& slot = h->tune[lin][prec == PES_FP64 ? 1 : 0];
+    const pes_tune saved = slot;
+    const int nts32[] = {128, 256}, nts64[] = {128};
+    const int* nts = prec == PES_FP64 ? nts64 : nts32;
+    const int n_nt = prec == PES_FP64 ? 1 : 2;
+    const int steps[] = {4, 8, 16, 32, 64, 128};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PES_CUDA(h, cudaEventCreate(&e0));
+    PES_CUDA(h, cudaEventCreate(&e1));
+    float best = 1e30f;
+    pes_tune best_t;
+    int seen_nb[16], seen_nt[16], n_seen = 0;
+    pes_status r = PES_OK;
+    for (int a = 0; a < n_nt && r == PES_OK; ++a) {
+        for (int b = 0; b < 6 && r == PES_OK; ++b) {
+            slot.nt = nts[a];
+            slot.min_steps = steps[b];
+            Shape s;
+            r = (prec == PES_FP64) ? make_shape<double>(h, lin, prec, N, s) : make_shape<float>(h, lin, prec, N, s);
+            if (r != PES_OK) break;
+            bool dup = false;   // candidates that give the same launch are timed once
+            for (int q = 0; q < n_seen; ++q) dup |= (seen_nb[q] == s.nb && seen_nt[q] == s.nt);
+            if (dup) continue;
+            seen_nb[n_seen] = s.nb;
+            seen_nt[n_seen++] = s.nt;
+            float ms = 1e30f;
+            for (int rep = 0; rep < 2 && r == PES_OK; ++rep) {   // the first run warms up
+                cudaEventRecord(e0, st);
+                r = pes_ieks_run(h, model, method, prec, y, offsets, B, N, m0, P0, nullptr, nullptr, iters, 0.0,
+                                 x_scratch, P_scratch, nullptr, stream);
+                cudaEventRecord(e1, st);
+                if (r == PES_OK) r = pes_sync(h, stream);
+                float t = 0.f;
+                if (r == PES_OK && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess && rep == 1) ms = t;
+            }
+            if (r == PES_OK && ms < best) {
+                best = ms;
+                best_t = slot;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r != PES_OK) {
+        slot = saved;
+        return r;
+    }
+    slot = best_t;
+    if (threads) *threads = best_t.nt;
+    if (min_steps) *min_steps = best_t.min_steps;
+    if (ms_per_run) *ms_per_run = best;
     return PES_OK;
 }
 

@@ -4,6 +4,13 @@
 
 #include <stdint.h>
 
+// Launch shape chosen by pes_autotune for one (linearisation, precision):
+// threads per block and the minimum steps per lane (0: the defaults).
+struct pes_tune {
+    int nt = 0;
+    int min_steps = 0;
+};
+
 struct pes_handle {
     int device = 0;
     int num_sms = 0;
@@ -20,6 +27,7 @@ struct pes_handle {
     int* iters_done = nullptr;
     int* traj_iters = nullptr;   // [max_batch]: per-trajectory iterations of the last tolerance-mode run
     int traj_iters_B = 0;        // its number of trajectories (0: none recorded)
+    pes_tune tune[3][2];         // [linearisation][FP32, FP64]
     // device copies for pes_ieks_run_host (allocated by its first call)
     void* hy = nullptr;
     int64_t* hoff = nullptr;

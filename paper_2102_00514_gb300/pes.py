@@ -29,7 +29,7 @@ MODEL_CT_BEARINGS, MODEL_LINEAR = 0, 1
 
 EXPORTED = ["pes_create", "pes_destroy", "pes_last_error", "pes_sync", "pes_linearize", "pes_filter_scan",
             "pes_smooth_scan", "pes_ieks_run", "pes_ieks_run_host", "pes_launch_shape", "pes_measure_fma_peak",
-            "pes_debug_phase_times", "pes_ieks_run_noalloc", "pes_traj_iterations", "pes_filter_loglik", "pes_ieks_run_sequential",
+            "pes_debug_phase_times", "pes_ieks_run_noalloc", "pes_traj_iterations", "pes_filter_loglik", "pes_ieks_run_sequential", "pes_autotune", "pes_ieks_graph_create", "pes_graph_launch", "pes_graph_destroy",
             "pes_init_create", "pes_init_destroy", "pes_init_last_error", "pes_init_set_params",
             "pes_init_get_params", "pes_init_forward", "pes_init_loss_grad", "pes_init_train_step"]
 INIT_NPARAMS = 86661
@@ -78,6 +78,11 @@ def load_library():
                                  ctypes.POINTER(i32), p]
     lib.pes_ieks_run_host.argtypes = lib.pes_ieks_run.argtypes
     lib.pes_ieks_run_sequential.argtypes = lib.pes_ieks_run.argtypes
+    lib.pes_ieks_graph_create.argtypes = [p, mp, i32, i32, p, p, i32, i64, p, p, p, p, i32, p, p, ctypes.POINTER(p)]
+    lib.pes_graph_launch.argtypes = [p, p]
+    lib.pes_graph_destroy.argtypes = [p]
+    lib.pes_autotune.argtypes = [p, mp, i32, i32, p, p, i32, i64, p, p, i32, p, p, ctypes.POINTER(i32),
+                                 ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float), p]
     lib.pes_launch_shape.argtypes = [p, i32, i32, i64, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                      ctypes.POINTER(i32)]
     lib.pes_measure_fma_peak.argtypes = [ctypes.POINTER(d), ctypes.POINTER(d)]
@@ -244,6 +249,40 @@ class Smoother:
                                                  _stream(stream)))
         return out
 
+    def autotune(self, model: Model, method: int, prec: int, y, offsets, m0, P0, iters: int = 2, stream=None):
+        """Time the candidate launch shapes on this workload and keep the fastest
+        for (method, precision); returns (threads, min_steps, ms_per_run)."""
+        dt = _dtype(prec)
+        N = y.shape[1]
+        B = offsets.shape[0] - 1
+        xs = torch.empty((5, N), dtype=dt, device=y.device)
+        Ps = torch.empty((15, N), dtype=dt, device=y.device)
+        nt, ms_, t = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+        st = self.lib.pes_autotune(self.h, ctypes.byref(model.as_struct()), method, prec, _ptr(y, dt),
+                                   _ptr(offsets, torch.int64), B, N, _ptr(m0, dt), _ptr(P0, dt), int(iters),
+                                   _ptr(xs), _ptr(Ps), ctypes.byref(nt), ctypes.byref(ms_), ctypes.byref(t),
+                                   _stream(stream))
+        self._check(st)
+        return nt.value, ms_.value, t.value
+
+    def graph(self, model: Model, method: int, prec: int, y, offsets, m0, P0, x_init=None, P_init=None,
+              iters: int = 10, x_out=None, P_out=None):
+        """Capture one ieks_run of these arguments into a CUDA graph (see Graph)."""
+        dt = _dtype(prec)
+        N = y.shape[1]
+        B = offsets.shape[0] - 1
+        if x_out is None:
+            x_out = torch.empty((5, N), dtype=dt, device=y.device)
+        if P_out is None:
+            P_out = torch.empty((15, N), dtype=dt, device=y.device)
+        g = ctypes.c_void_p()
+        ms = model.as_struct()
+        self._check(self.lib.pes_ieks_graph_create(self.h, ctypes.byref(ms), method, prec, _ptr(y, dt),
+                                                   _ptr(offsets, torch.int64), B, N, _ptr(m0, dt), _ptr(P0, dt),
+                                                   _ptr(x_init, dt), _ptr(P_init, dt), int(iters), _ptr(x_out, dt),
+                                                   _ptr(P_out, dt), ctypes.byref(g)))
+        return Graph(self, g, (model, y, offsets, m0, P0, x_init, P_init), x_out, P_out)
+
     def launch_shape(self, method: int, prec: int, N: int):
         nb, nt, L = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         self._check(self.lib.pes_launch_shape(self.h, method, prec, int(N), ctypes.byref(nb), ctypes.byref(nt),
@@ -365,6 +404,30 @@ class Smoother:
                                         h(P_out), ctypes.byref(used), _stream(stream))
         self._check(st, allow=(NOT_CONVERGED,) if allow_not_converged else ())
         return x_out, P_out, used.value, st
+
+
+class Graph:
+    """A captured smoother run (pes_graph); ``launch()`` replays it and the
+    results land in ``x`` and ``P``. Keeps the captured tensors alive."""
+
+    def __init__(self, sm: "Smoother", g, keep, x, P):
+        self.sm, self.g, self._keep, self.x, self.P = sm, g, keep, x, P
+
+    def launch(self, stream=None):
+        st = self.sm.lib.pes_graph_launch(self.g, _stream(stream))
+        if st != OK:
+            raise PesError(st, "pes_graph_launch failed")
+
+    def close(self):
+        if getattr(self, "g", None):
+            self.sm.lib.pes_graph_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class InitNet:

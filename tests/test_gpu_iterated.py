@@ -245,3 +245,43 @@ def test_not_positive_definite_prior_reported(sm):
     with pytest.raises(pes.PesError) as ei:
         gpu_run(sm, wl, pes.CUBATURE, pes.FP64, iters=2)
     assert ei.value.status in (pes.NOT_PD, pes.NONFINITE)
+
+
+def test_autotune_keeps_a_valid_shape_and_results():
+    s = pes.Smoother(1 << 16, 64)
+    wl = synth.workload("batch16_T100_3000")
+    d = workload_to_dev(wl, pes.FP32)
+    N = wl["y"].shape[1]
+    before = s.launch_shape(pes.CUBATURE, pes.FP32, N)
+    nt, min_steps, ms = s.autotune(d["model"], pes.CUBATURE, pes.FP32, d["y"], d["offsets"], d["m0"], d["P0"], iters=2)
+    assert nt in (128, 256) and min_steps in (4, 8, 16, 32, 64, 128) and ms > 0
+    nb, nt2, L = s.launch_shape(pes.CUBATURE, pes.FP32, N)
+    assert nt2 == nt and nb * nt * L >= N
+    print(f"autotune: {before} -> {(nb, nt2, L)}, {ms:.3f} ms per run")
+    # the other method and precision keep their defaults
+    assert s.launch_shape(pes.IEKS, pes.FP32, N)[1] == 256
+    ref = oracle_run(wl, pes.CUBATURE, iters=4)
+    x, P, _, _ = gpu_run(s, wl, pes.CUBATURE, pes.FP32, iters=4)
+    assert rel_err(x, ref["x"], wl["offsets"]) < TOL_FP32
+    assert rel_err(P, ref["P"], wl["offsets"]) < TOL_FP32
+    s.close()
+
+
+def test_graph_replay_equals_direct_call(sm):
+    wl = synth.workload("batch8_T1_3000")
+    for method in (pes.IEKS, pes.CUBATURE):
+        d = workload_to_dev(wl, pes.FP32)
+        x, P, _, _ = sm.ieks_run(d["model"], method, pes.FP32, d["y"], d["offsets"], d["m0"], d["P0"], iters=3)
+        sm.sync()
+        g = sm.graph(d["model"], method, pes.FP32, d["y"], d["offsets"], d["m0"], d["P0"], iters=3)
+        g.launch()
+        sm.sync()
+        assert torch.equal(g.x, x) and torch.equal(g.P, P)
+        # new contents at the same addresses: the replay follows them
+        d["y"].mul_(1.0001)
+        x2, P2, _, _ = sm.ieks_run(d["model"], method, pes.FP32, d["y"], d["offsets"], d["m0"], d["P0"], iters=3)
+        sm.sync()
+        g.launch()
+        sm.sync()
+        assert torch.equal(g.x, x2) and torch.equal(g.P, P2) and not torch.equal(x2, x)
+        g.close()
