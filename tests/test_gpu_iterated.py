@@ -260,10 +260,14 @@ def test_autotune_keeps_a_valid_shape_and_results():
     print(f"autotune: {before} -> {(nb, nt2, L)}, {ms:.3f} ms per run")
     # the other method and precision keep their defaults
     assert s.launch_shape(pes.IEKS, pes.FP32, N)[1] == 256
+    # a tuned shape changes only the partition into lanes: FP64 results stay
+    # within rounding of the oracle
+    d64 = workload_to_dev(wl, pes.FP64)
+    s.autotune(d64["model"], pes.CUBATURE, pes.FP64, d64["y"], d64["offsets"], d64["m0"], d64["P0"], iters=2)
     ref = oracle_run(wl, pes.CUBATURE, iters=4)
-    x, P, _, _ = gpu_run(s, wl, pes.CUBATURE, pes.FP32, iters=4)
-    assert rel_err(x, ref["x"], wl["offsets"]) < TOL_FP32
-    assert rel_err(P, ref["P"], wl["offsets"]) < TOL_FP32
+    x, P, _, _ = gpu_run(s, wl, pes.CUBATURE, pes.FP64, iters=4)
+    assert rel_err(x, ref["x"], wl["offsets"]) < TOL_FP64
+    assert rel_err(P, ref["P"], wl["offsets"]) < TOL_FP64
     s.close()
 
 
