@@ -57,6 +57,7 @@ def parse_args():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-learned-init", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--sequential", action="store_true",
                     help="also time the sequential counterpart (one GPU thread per trajectory) on the workload")
     ap.add_argument("--cpu-sample", type=int, default=1 << 17, help="states in the oracle's timed sample")
@@ -335,6 +336,13 @@ def main():
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     d32 = device_inputs(pes.FP32)
+    # launch shapes chosen by the library's autotuner on this workload
+    tuned = {}
+    if not args.no_autotune:
+        for name, m in methods:
+            nt_, steps_, ms_ = sm.autotune(d32["model"], m, pes.FP32, d32["y"], d32["offsets"], d32["m0"], d32["P0"],
+                                           iters=2)
+            tuned[name] = {"threads": nt_, "min_steps_per_lane": steps_, "ms_per_2_iterations": ms_}
     for _ in range(args.warmup):
         run_step(d32, pes.FP32)
     sm.sync()
@@ -409,7 +417,8 @@ def main():
                              "T": T if B == 1 else None, "B": B, "N_states": N, "iterations": iters, "methods": ["ieks", "cubature"],
                              "precision": "fp32", "l2": "flushed before every step (512 MB write)",
                              "launch": {"ieks": {"blocks": nb, "threads": nt, "steps_per_thread": L},
-                                        "cubature": {"blocks": nbc, "threads": ntc, "steps_per_thread": Lc}}},
+                                        "cubature": {"blocks": nbc, "threads": ntc, "steps_per_thread": Lc},
+                                        "autotuned": tuned or None}},
                   "roofline": roofline, "per_method": per_method,
                   "gpu_launches": launches_per_run * len(methods) * args.steps, "clocks": clk}
 
