@@ -50,7 +50,8 @@ class _Model(ctypes.Structure):
                 ("sensors", ctypes.c_void_p), ("sensors_per_traj", ctypes.c_int),
                 ("F", ctypes.c_double * 25), ("c", ctypes.c_double * 5), ("Q", ctypes.c_double * 25),
                 ("H", ctypes.c_double * 10), ("d", ctypes.c_double * 2), ("R", ctypes.c_double * 4),
-                ("ut_alpha", ctypes.c_double), ("ut_beta", ctypes.c_double), ("ut_kappa", ctypes.c_double)]
+                ("ut_alpha", ctypes.c_double), ("ut_beta", ctypes.c_double), ("ut_kappa", ctypes.c_double),
+                ("lm_lambda", ctypes.c_double)]
 
 
 class FElem(ctypes.Structure):
@@ -180,6 +181,13 @@ class Model:
         self._keep = keep
         if s.ut_alpha == 0.0:   # the unscented rule's parameters default to the cubature rule's
             s.ut_alpha, s.ut_beta, s.ut_kappa = 1.0, 0.0, 0.0
+
+    def damped(self, lm_lambda: float) -> "Model":
+        """The same model with Levenberg-Marquardt damping lm_lambda of the iteration."""
+        s = _Model()
+        ctypes.pointer(s)[0] = self.s
+        s.lm_lambda = lm_lambda
+        return Model(s, self._keep)
 
     def unscented(self, alpha: float, beta: float, kappa: float) -> "Model":
         """The same model with the unscented rule's parameters set."""

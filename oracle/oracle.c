@@ -548,11 +548,39 @@ int orc_linearize(const orc_model* m, int method, int64_t N, const int64_t* offs
 /* the definition: sequential Kalman filter + RTS smoother of Eq. 11          */
 /* ------------------------------------------------------------------------- */
 
+/* The Levenberg-Marquardt pseudo-measurement of state k: a Kalman update of
+ * (m, P) with H = I, R = I / lambda and measurement xbar_k. */
+static int damp_update(double* m, double* P, const double* xbar, double lambda)
+{
+    double S[25], Sinv[25], K[25], KP[25];
+    memcpy(S, P, sizeof S);
+    for (int i = 0; i < NX; ++i) S[i * NX + i] += 1.0 / lambda;
+    if (!inverse(NX, S, Sinv)) return ORC_NOT_PD;
+    mm(NX, NX, NX, P, Sinv, K);
+    double v[NX], Kv[NX];
+    for (int i = 0; i < NX; ++i) v[i] = xbar[i] - m[i];
+    mv(NX, NX, K, v, Kv);
+    for (int i = 0; i < NX; ++i) m[i] += Kv[i];
+    mm(NX, NX, NX, K, P, KP);
+    for (int i = 0; i < 25; ++i) P[i] -= KP[i];
+    symmetrize(NX, P);
+    return ORC_OK;
+}
+
 int orc_kf_rts(int64_t N, const int64_t* offsets, int64_t B,
                const double* F, const double* c, const double* Qp,
                const double* H, const double* d, const double* Rp, const double* y,
                const double* m0, const double* P0,
                double* xf, double* Pf, double* xs, double* Ps)
+{
+    return orc_kf_rts_damped(N, offsets, B, F, c, Qp, H, d, Rp, y, m0, P0, NULL, 0.0, xf, Pf, xs, Ps);
+}
+
+int orc_kf_rts_damped(int64_t N, const int64_t* offsets, int64_t B,
+                      const double* F, const double* c, const double* Qp,
+                      const double* H, const double* d, const double* Rp, const double* y,
+                      const double* m0, const double* P0, const double* xbar, double lambda,
+                      double* xf, double* Pf, double* xs, double* Ps)
 {
     double* xp = (double*)malloc(sizeof(double) * 5 * N);
     double* Pp = (double*)malloc(sizeof(double) * 25 * N);
@@ -561,6 +589,7 @@ int orc_kf_rts(int64_t N, const int64_t* offsets, int64_t B,
         int64_t k0 = offsets[b], k1 = offsets[b + 1];
         memcpy(xf + 5 * k0, m0 + 5 * b, sizeof(double) * 5);
         memcpy(Pf + 25 * k0, P0 + 25 * b, sizeof(double) * 25);
+        if (lambda > 0.0 && (status = damp_update(xf + 5 * k0, Pf + 25 * k0, xbar + 5 * k0, lambda)) != ORC_OK) break;
         for (int64_t k = k0 + 1; k < k1; ++k) {
             /* predict with the transition k-1 -> k */
             const double* Fk = F + 25 * (k - 1);
@@ -593,6 +622,7 @@ int orc_kf_rts(int64_t N, const int64_t* offsets, int64_t B,
             mmt(NX, NY, NX, KS, K, KSK);
             for (int i = 0; i < 25; ++i) Pf[25 * k + i] = P_[i] - KSK[i];
             symmetrize(NX, Pf + 25 * k);
+            if (lambda > 0.0 && (status = damp_update(xf + 5 * k, Pf + 25 * k, xbar + 5 * k, lambda)) != ORC_OK) break;
         }
         if (status != ORC_OK) break;
         /* Rauch-Tung-Striebel backward pass */
@@ -708,7 +738,8 @@ int orc_iterated_smoother(const orc_model* m, int method, int64_t N, const int64
     for (it = 1; it <= max_iters; ++it) {
         status = orc_linearize(m, method, N, offsets, B, x_out, P_out, y, F, c, Qp, H, d, Rp, yu);
         if (status != ORC_OK) break;
-        status = orc_kf_rts(N, offsets, B, F, c, Qp, H, d, Rp, yu, m0, P0, xf, Pf, xs, Ps);
+        status = orc_kf_rts_damped(N, offsets, B, F, c, Qp, H, d, Rp, yu, m0, P0, x_out, m->lm_lambda, xf, Pf, xs,
+                                   Ps);
         if (status != ORC_OK) break;
         /* relative update norm, worst trajectory */
         double rel = 0.0;

@@ -34,6 +34,9 @@ typedef struct {
     double F[25], c[5], Q[25], H[10], d[2], R[4];
     /* unscented rule (ORC_UNSCENTED): spread alpha, prior-knowledge beta, kappa */
     double ut_alpha, ut_beta, ut_kappa;
+    /* Levenberg-Marquardt damping of the iteration (0: none): every state gets
+     * the pseudo-measurement xbar_k = x_k + e, e ~ N(0, I / lm_lambda) */
+    double lm_lambda;
 } orc_model;
 
 typedef struct { double A[25], b[5], C[25], eta[5], J[25]; } orc_felem;
@@ -71,6 +74,14 @@ int orc_kf_loglik(int64_t N, const int64_t* offsets, int64_t B,
                   const double* F, const double* c, const double* Qp,
                   const double* H, const double* d, const double* Rp, const double* y,
                   const double* m0, const double* P0, double* loglik);
+/* orc_kf_rts with the Levenberg-Marquardt pseudo-measurements of the nominal
+ * xbar [N][5] (covariance I / lambda) applied after each state's update
+ * (lambda = 0: orc_kf_rts). */
+int orc_kf_rts_damped(int64_t N, const int64_t* offsets, int64_t B,
+                      const double* F, const double* c, const double* Qp,
+                      const double* H, const double* d, const double* Rp, const double* y,
+                      const double* m0, const double* P0, const double* xbar, double lambda,
+                      double* xf, double* Pf, double* xs, double* Ps);
 int orc_iterated_smoother(const orc_model* m, int method, int64_t N, const int64_t* offsets, int64_t B,
                           const double* y, const double* m0, const double* P0,
                           const double* x_init, const double* P_init, int max_iters, double tol,

@@ -106,11 +106,12 @@ def dense_filter(F, c, Qp, H, d, R, y, m0, P0):
     return xf, Pf
 
 
-def gauss_newton_step(x, f, fjac, h, hjac, Q, R, y, m0, P0):
+def gauss_newton_step(x, f, fjac, h, hjac, Q, R, y, m0, P0, damping=0.0):
     """One Gauss-Newton step of the MAP problem
         |x_0 - m0|^2_{P0^-1} + sum_k |x_k - f(x_{k-1})|^2_{Q^-1} + sum_k |y_k - h(x_k)|^2_{R^-1}
-    about the trajectory x [T+1][5] (Q positive definite). Returns the new
-    trajectory and the gradient of the objective at x."""
+    about the trajectory x [T+1][5] (Q positive definite); with damping > 0 the
+    Levenberg-Marquardt step (J^T W J + damping I) dx = -J^T W r. Returns the
+    new trajectory and the gradient of the objective at x."""
     T = len(x) - 1
     n, m = 5, 2
     nv = (T + 1) * n
@@ -141,5 +142,5 @@ def gauss_newton_step(x, f, fjac, h, hjac, Q, R, y, m0, P0):
         o += s
     A = Jm.T @ W @ Jm
     g = Jm.T @ W @ r
-    dx = -np.linalg.solve(A, g)
+    dx = -np.linalg.solve(A + damping * np.eye(nv), g)
     return x + dx.reshape(T + 1, n), 2.0 * g

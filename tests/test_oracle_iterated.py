@@ -135,6 +135,15 @@ def test_slr_unwraps_bearings_across_branch_cut():
     assert np.abs(Om).max() < 1e-6
 
 
+def _ct_gn_damped(wl, model, x, lam):
+    Q = model.Q(); R = model.R()
+    s = wl["sensors"][0]
+    return gauss_newton_step(
+        x, lambda v: oracle.ct_f(v, wl["dt"]), lambda v: oracle.ct_jacobian(v, wl["dt"]),
+        lambda v: oracle.bearings_h(v, s), lambda v: oracle.bearings_jacobian(v, s),
+        Q, R, wl["y"].T, wl["m0"][0], oracle.sym_full(wl["P0"][0], 5), damping=lam)
+
+
 def _ct_gn(wl, model, x):
     Q = model.Q(); R = model.R()
     s = wl["sensors"][0]
@@ -142,6 +151,36 @@ def _ct_gn(wl, model, x):
         x, lambda v: oracle.ct_f(v, wl["dt"]), lambda v: oracle.ct_jacobian(v, wl["dt"]),
         lambda v: oracle.bearings_h(v, s), lambda v: oracle.bearings_jacobian(v, s),
         Q, R, wl["y"].T, wl["m0"][0], oracle.sym_full(wl["P0"][0], 5))
+
+
+@pytest.mark.parametrize("lam", [0.3, 5.0, 200.0])
+def test_damped_iterations_are_levenberg_marquardt_steps(lam):
+    """With damping lambda every IEKS iteration is the Levenberg-Marquardt
+    step of the MAP problem about the current nominal (positive-definite Q;
+    a trajectory whose bearings stay clear of the branch cut, which the dense
+    step does not unwrap)."""
+    wl = synth.ct_bearings([15], seed=11, q_form=1)
+    model = oracle.Model.from_workload(wl)
+    dm = model.damped(lam)
+    x = np.tile(wl["m0"][0], (16, 1))
+    for it in range(3):
+        out = oracle.iterated_smoother(dm, oracle.IEKS, wl["offsets"], wl["y"], wl["m0"], wl["P0"], x_init=x.T,
+                                       iters=1)
+        x_gn, _ = _ct_gn_damped(wl, model, x, lam)
+        np.testing.assert_allclose(out["x"].T, x_gn, rtol=1e-8, atol=1e-9)
+        x = out["x"].T.copy()
+
+
+def test_heavy_damping_shrinks_the_step():
+    wl = synth.ct_bearings([15], seed=13, q_form=1)
+    model = oracle.Model.from_workload(wl)
+    x0 = np.tile(wl["m0"][0], (16, 1))
+    steps = []
+    for lam in (1e2, 1e4, 1e6):
+        out = oracle.iterated_smoother(model.damped(lam), oracle.IEKS, wl["offsets"], wl["y"], wl["m0"], wl["P0"],
+                                       x_init=x0.T, iters=1)
+        steps.append(np.abs(out["x"].T - x0).max())
+    assert steps[1] < 0.02 * steps[0] and steps[2] < 0.02 * steps[1]
 
 
 def test_ieks_iterations_are_gauss_newton_steps():
