@@ -176,11 +176,13 @@ def test_heavy_damping_shrinks_the_step():
     model = oracle.Model.from_workload(wl)
     x0 = np.tile(wl["m0"][0], (16, 1))
     steps = []
-    for lam in (1e2, 1e4, 1e6):
+    # the step falls like 1 / lambda once lambda dominates the curvature
+    # (Q^-1 of the positive-definite Q reaches ~1e8 here)
+    for lam in (1e10, 1e12, 1e14):
         out = oracle.iterated_smoother(model.damped(lam), oracle.IEKS, wl["offsets"], wl["y"], wl["m0"], wl["P0"],
                                        x_init=x0.T, iters=1)
         steps.append(np.abs(out["x"].T - x0).max())
-    assert steps[1] < 0.02 * steps[0] and steps[2] < 0.02 * steps[1]
+    assert 0.005 < steps[1] / steps[0] < 0.02 and 0.005 < steps[2] / steps[1] < 0.02
 
 
 def test_ieks_iterations_are_gauss_newton_steps():
