@@ -126,6 +126,12 @@ typedef struct {
     double ut_alpha;   /* PES_UNSCENTED only: spread, prior-knowledge and secondary scaling parameters */
     double ut_beta;
     double ut_kappa;
+    /* Levenberg-Marquardt damping of the iteration (Sec. 3 names it as a
+     * variant; 0 = none): each iteration adds at every state the
+     * pseudo-measurement xbar_k = x_k + e, e ~ N(0, I / lm_lambda), of the
+     * previous nominal, which turns the Gauss-Newton step of the IEKS into a
+     * Levenberg-Marquardt step (any method; pes_ieks_run and its variants). */
+    double lm_lambda;
 } pes_model;
 
 typedef struct pes_handle pes_handle;

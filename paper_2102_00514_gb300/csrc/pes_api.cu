@@ -89,6 +89,7 @@ DevModel<T> to_dev_model(const pes_model& m, const T* sensors_T, pes_method meth
     d.sp_scale = T(sc);
     d.sp_w = T(w);
     d.sp_w0c = T(w0c);
+    d.lm = T(m.lm_lambda);
     d.kind = m.kind;
     d.sensors_per_traj = m.sensors_per_traj;
     d.dt = T(m.dt);
@@ -143,6 +144,8 @@ pes_status check_method(pes_handle* h, pes_method method, const pes_model* m)
 
 pes_status check_model(pes_handle* h, const pes_model* m)
 {
+    if (m && !(m->lm_lambda >= 0.0 && std::isfinite(m->lm_lambda)))
+        return fail(h, PES_ERR_INVALID_ARG, "lm_lambda must be finite and >= 0");
     if (!m) return fail(h, PES_ERR_INVALID_ARG, "model is NULL");
     if (m->kind == PES_MODEL_CT_BEARINGS) {
         if (!m->sensors) return fail(h, PES_ERR_INVALID_ARG, "model.sensors is NULL");

@@ -447,6 +447,12 @@ PES_DEV bool fold_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int la
             if (store_lin) store_lin_obs(p, s, lane, ob);
             ok &= fold_filter_step(acc, tr, ob);
         }
+        if (LIN != LIN_ARRAYS && p.model.lm > T(0)) {
+            // Levenberg-Marquardt pseudo-measurement of this state's nominal
+            FElem<T> dmp;
+            felem_damping(dmp, sc.x, p.model.lm);
+            combine_filter(acc, dmp, acc);
+        }
         sp = sc;
         sc = sn;
     }
@@ -668,6 +674,23 @@ PES_DEV bool rerun_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int l
                 } else {
                     ok &= kf_update(ob, mp, Pp, m, P);
                 }
+            }
+            if (LIN != LIN_ARRAYS && p.model.lm > T(0)) {
+                // Levenberg-Marquardt pseudo-measurement of this state's nominal
+                T xb[5];
+                load_nominal(p, ix, xb);
+                FElem<T> dmp;
+                felem_damping(dmp, xb, p.model.lm);
+                Gauss<T> g, gd;
+#pragma unroll
+                for (int i = 0; i < 5; ++i) g.m[i] = m[i];
+#pragma unroll
+                for (int i = 0; i < 15; ++i) g.P[i] = P[i];
+                apply_filter(g, dmp, gd);
+#pragma unroll
+                for (int i = 0; i < 5; ++i) m[i] = gd.m[i];
+#pragma unroll
+                for (int i = 0; i < 15; ++i) P[i] = gd.P[i];
             }
             if (!smooth) store_filtered(p, k, m, P);
             else if (!kStoreElements<LIN>) store_xP(p, s, lane, m, P);

@@ -35,6 +35,7 @@ struct DevModel {
     // point's weight, sp_w0c the centre's covariance weight (cubature:
     // sqrt(n), 1/n, 0)
     T sp_scale, sp_w, sp_w0c;
+    T lm;   // Levenberg-Marquardt damping lambda (0: none)
 };
 
 // Transition k -> k+1 linearised about xn = xbar_k: x_{k+1} ~ fx + F (x_k - xn) + N(0, Q')

@@ -61,6 +61,29 @@ PES_DEV void felem_identity(FElem<T>& a, const T* xr)
     }
 }
 
+// The Levenberg-Marquardt damping of state k as a filtering element: the
+// pseudo-measurement xbar = x_k + e, e ~ N(0, I / lambda), through an identity
+// transition, about the reference xr = xbar: A = I, b = xbar, C = 0, eta = 0,
+// J = lambda I. acc (x) damping adds the damping to the state acc ends at.
+template <typename T>
+PES_DEV void felem_damping(FElem<T>& a, const T* xbar, T lambda)
+{
+    set_identity(a.A);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        a.b[i] = xbar[i];
+        a.eta[i] = T(0);
+        a.xr[i] = xbar[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 15; ++i) {
+        a.C[i] = T(0);
+        a.J[i] = T(0);
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) a.J[si(i, i)] = lambda;
+}
+
 // a (x) a_0 where a_0 is the prior element (A = 0, b = m0, C = P0, eta = J = 0):
 // the conditional density forgets its input; the likelihood stays.
 template <typename T>

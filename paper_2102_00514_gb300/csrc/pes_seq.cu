@@ -50,6 +50,27 @@ PES_DEV void seq_write(const KParams<T>& p, int64_t k, const Gauss<T>& g, double
     for (int i = 0; i < 15; ++i) p.P[(size_t)i * p.N + k] = g.P[i];
 }
 
+// The Levenberg-Marquardt pseudo-measurement of state k's nominal (if any).
+template <typename T>
+PES_DEV void seq_damp(const KParams<T>& p, int64_t k, T* m, T* P)
+{
+    if (!(p.model.lm > T(0))) return;
+    T xb[5];
+    load_nominal(p, k, xb);
+    FElem<T> dmp;
+    felem_damping(dmp, xb, p.model.lm);
+    Gauss<T> g, gd;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) g.m[i] = m[i];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) g.P[i] = P[i];
+    apply_filter(g, dmp, gd);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) m[i] = gd.m[i];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) P[i] = gd.P[i];
+}
+
 template <typename T, int LIN>
 __global__ void __launch_bounds__(64) sequential_smoother_kernel(const KParams<T> p)
 {
@@ -67,6 +88,7 @@ __global__ void __launch_bounds__(64) sequential_smoother_kernel(const KParams<T
         // forward: filter, and the smoothing element of every state but the last
         T m[5], P[15];
         load_prior(p, b, m, P);
+        seq_damp(p, a, m, P);
         for (int64_t k = a + 1; k < e; ++k) {
             Trans<T> tr;
             ok &= get_trans<T, LIN>(p, k - 1, k - 1, tr);
@@ -78,6 +100,7 @@ __global__ void __launch_bounds__(64) sequential_smoother_kernel(const KParams<T
             Obs<T> ob;
             ok &= get_obs<T, LIN>(p, k, k, b, ob);
             ok &= kf_update(ob, mp, Pp, m, P);
+            seq_damp(p, k, m, P);
         }
         // backward: the last state's smoothed moments are its filtered ones
         Gauss<T> g;

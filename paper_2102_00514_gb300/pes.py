@@ -47,7 +47,8 @@ class _Model(ctypes.Structure):
                 ("sensors", ctypes.c_void_p), ("sensors_per_traj", ctypes.c_int32),
                 ("F", ctypes.c_double * 25), ("c", ctypes.c_double * 5), ("Q", ctypes.c_double * 15),
                 ("H", ctypes.c_double * 10), ("d", ctypes.c_double * 2), ("R", ctypes.c_double * 3),
-                ("ut_alpha", ctypes.c_double), ("ut_beta", ctypes.c_double), ("ut_kappa", ctypes.c_double)]
+                ("ut_alpha", ctypes.c_double), ("ut_beta", ctypes.c_double), ("ut_kappa", ctypes.c_double),
+                ("lm_lambda", ctypes.c_double)]
 
 
 _lib = None
@@ -126,11 +127,13 @@ class Model:
     ut_alpha: float = 1.0   # the unscented rule (UNSCENTED); these values give the cubature rule
     ut_beta: float = 0.0
     ut_kappa: float = 0.0
+    lm_lambda: float = 0.0   # Levenberg-Marquardt damping of the iteration (0: none)
 
     def as_struct(self) -> _Model:
         s = _Model()
         s.kind, s.q_form = self.kind, self.q_form
         s.ut_alpha, s.ut_beta, s.ut_kappa = self.ut_alpha, self.ut_beta, self.ut_kappa
+        s.lm_lambda = self.lm_lambda
         s.dt, s.q_c, s.q_w, s.r_std = self.dt, self.q_c, self.q_w, self.r_std
         if self.sensors is not None:
             if self.sensors.dtype != torch.float64:

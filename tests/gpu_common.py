@@ -33,10 +33,12 @@ def to_dev(a, dtype=torch.float64):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda").contiguous()
 
 
-def workload_to_dev(wl: dict, prec: int, ut=None):
-    """Device copies of a workload; ut = (alpha, beta, kappa) of the unscented rule."""
+def workload_to_dev(wl: dict, prec: int, ut=None, lm: float = 0.0):
+    """Device copies of a workload; ut = (alpha, beta, kappa) of the unscented
+    rule, lm the Levenberg-Marquardt damping."""
     dt = torch.float64 if prec == pes.FP64 else torch.float32
     model = pes.Model.from_workload(wl)
+    model.lm_lambda = lm
     if ut is not None:
         model.ut_alpha, model.ut_beta, model.ut_kappa = ut
     return dict(y=to_dev(wl["y"], dt), offsets=to_dev(wl["offsets"], torch.int64), m0=to_dev(wl["m0"], dt),
@@ -46,18 +48,21 @@ def workload_to_dev(wl: dict, prec: int, ut=None):
 ORACLE_METHOD = {pes.IEKS: oracle.IEKS, pes.CUBATURE: oracle.CUBATURE, pes.UNSCENTED: oracle.UNSCENTED}
 
 
-def oracle_run(wl: dict, method: int, iters: int = 10, tol: float = 0.0, x_init=None, P_init=None, ut=None):
+def oracle_run(wl: dict, method: int, iters: int = 10, tol: float = 0.0, x_init=None, P_init=None, ut=None,
+               lm: float = 0.0):
     model = oracle.Model.from_workload(wl)
     if ut is not None:
         model = model.unscented(*ut)
+    if lm:
+        model = model.damped(lm)
     om = ORACLE_METHOD[method]
     return oracle.iterated_smoother(model, om, wl["offsets"], wl["y"], wl["m0"], wl["P0"], x_init=x_init,
                                     P_init=P_init, iters=iters, tol=tol)
 
 
 def gpu_run(sm: pes.Smoother, wl: dict, method: int, prec: int, iters: int = 10, tol: float = 0.0,
-            allow_not_converged: bool = False, ut=None):
-    d = workload_to_dev(wl, prec, ut)
+            allow_not_converged: bool = False, ut=None, lm: float = 0.0):
+    d = workload_to_dev(wl, prec, ut, lm)
     x, P, used, st = sm.ieks_run(d["model"], method, prec, d["y"], d["offsets"], d["m0"], d["P0"], iters=iters,
                                  tol=tol, want_iters=True, allow_not_converged=allow_not_converged)
     torch.cuda.synchronize()

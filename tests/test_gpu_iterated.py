@@ -289,3 +289,36 @@ def test_graph_replay_equals_direct_call(sm):
         sm.sync()
         assert torch.equal(g.x, x2) and torch.equal(g.P, P2) and not torch.equal(x2, x)
         g.close()
+
+
+@pytest.mark.parametrize("lm", [1.0, 50.0])
+@pytest.mark.parametrize("name,method", [("ieks_T500", pes.IEKS), ("ipls_T10000", pes.CUBATURE),
+                                         ("batch64_T1_400", pes.IEKS)])
+def test_damped_fp64_matches_oracle(sm, name, method, lm):
+    wl = synth.workload(name)
+    ref = oracle_run(wl, method, iters=10, lm=lm)
+    x, P, used, _ = gpu_run(sm, wl, method, pes.FP64, iters=10, lm=lm)
+    assert rel_err(x, ref["x"], wl["offsets"]) < TOL_FP64
+    assert rel_err(P, ref["P"], wl["offsets"]) < TOL_FP64
+
+
+def test_damped_fp32_and_sequential_match_oracle(sm):
+    wl = synth.workload("ipls_T10000")
+    ref = oracle_run(wl, pes.IEKS, iters=10, lm=10.0)
+    x, P, _, _ = gpu_run(sm, wl, pes.IEKS, pes.FP32, iters=10, lm=10.0)
+    assert rel_err(x, ref["x"], wl["offsets"]) < TOL_FP32
+    assert rel_err(P, ref["P"], wl["offsets"]) < TOL_FP32
+    wl = synth.workload("batch8_T1_3000")
+    ref = oracle_run(wl, pes.CUBATURE, iters=5, lm=3.0)
+    d = workload_to_dev(wl, pes.FP64, lm=3.0)
+    x, P, _, _ = sm.ieks_run_sequential(d["model"], pes.CUBATURE, pes.FP64, d["y"], d["offsets"], d["m0"], d["P0"],
+                                        iters=5)
+    assert rel_err(x.cpu().numpy(), ref["x"], wl["offsets"]) < TOL_FP64
+    assert rel_err(P.cpu().numpy(), ref["P"], wl["offsets"]) < TOL_FP64
+
+
+def test_damping_rejects_negative_lambda(sm):
+    wl = synth.workload("ieks_T500")
+    with pytest.raises(pes.PesError) as ei:
+        gpu_run(sm, wl, pes.IEKS, pes.FP64, iters=1, lm=-1.0)
+    assert ei.value.status == pes.INVALID_ARG
