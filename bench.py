@@ -61,19 +61,37 @@ def parse_args():
     ap.add_argument("--sequential", action="store_true",
                     help="also time the sequential counterpart (one GPU thread per trajectory) on the workload")
     ap.add_argument("--cpu-sample", type=int, default=1 << 17, help="states in the oracle's timed sample")
-    ap.add_argument("--profile", choices=["ieks", "cubature"], default=None,
+    ap.add_argument("--profile", choices=["ieks", "cubature", "init"], default=None,
                     help="profiling case: only `warmup` + 1 FP32 runs of one method, no JSON line")
     ap.add_argument("--prec", choices=["fp32", "fp64"], default="fp32", help="precision of --profile")
     return ap.parse_args()
 
 
 def run_profile_case(args):
-    """A short, single-method case for ncu captures: `warmup` launches, then one."""
+    """A short, single-method case for ncu captures: `warmup` launches, then one.
+    --profile init: forward passes of the learned initialiser on 64 held-out
+    trajectories (log T uniform in 1,000 .. 100,000), six GEMM launches each."""
     import numpy as np
     import torch
 
     from paper_2102_00514_gb300 import build, pes, synth
     build.build_all()
+    if args.profile == "init":
+        from paper_2102_00514_gb300 import learned_init as LI
+        wl = synth.workload("heldout64_T1000_100000")
+        N = wl["y"].shape[1]
+        net = pes.InitNet(N, 64)
+        net.set_params(LI.initial_params(0), np.zeros(5), np.ones(5))
+        y = torch.as_tensor(wl["y"], dtype=torch.float32, device="cuda")
+        o = torch.as_tensor(wl["offsets"], dtype=torch.int64, device="cuda")
+        for i in range(args.warmup + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            net.forward(pes.FP32, y, o)
+            torch.cuda.synchronize()
+            print(f"forward {i}: {N} states, {1e3 * (time.perf_counter() - t0):.3f} ms", flush=True)
+        net.close()
+        return
     wl = synth.workload(f"sweep_T{args.T}")
     N = wl["y"].shape[1]
     prec = pes.FP32 if args.prec == "fp32" else pes.FP64
