@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     uint64_t* done = tempty + 2;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+    float* sbias = reinterpret_cast<float*>(tslot + 4);   // 16-byte aligned, 64 floats
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -135,6 +136,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         mbar_init_fence();
     }
     if (warp == 1) tc::tmem_alloc(tslot, kTmemCols);
+    if (EPI != EPI_MASK && threadIdx.x >= 64 && threadIdx.x < 64 + C) sbias[threadIdx.x - 64] = p.bias[threadIdx.x - 64];
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -229,10 +231,8 @@ __global__ void __launch_bounds__(kConvThreads, 1)
             if (r >= p.R || !p.rowmask[r]) continue;
             if constexpr (EPI == EPI_F32) {
                 float4* dst = reinterpret_cast<float4*>(p.out_f32 + (size_t)r * kOutCols);
-                dst[0] = make_float4(v[0] + __ldg(p.bias + 0), v[1] + __ldg(p.bias + 1), v[2] + __ldg(p.bias + 2),
-                                     v[3] + __ldg(p.bias + 3));
-                dst[1] = make_float4(v[4] + __ldg(p.bias + 4), v[5] + __ldg(p.bias + 5), v[6] + __ldg(p.bias + 6),
-                                     v[7] + __ldg(p.bias + 7));
+                dst[0] = make_float4(v[0] + sbias[0], v[1] + sbias[1], v[2] + sbias[2], v[3] + sbias[3]);
+                dst[1] = make_float4(v[4] + sbias[4], v[5] + sbias[5], v[6] + sbias[6], v[7] + sbias[7]);
             } else {
                 if constexpr (EPI == EPI_MASK) {
                     const uint4* src = reinterpret_cast<const uint4*>(p.relu_src + (size_t)r * C);
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                     }
                 } else {
 #pragma unroll
-                    for (int c = 0; c < C; ++c) v[c] = fmaxf(v[c] + __ldg(p.bias + c), 0.f);
+                    for (int c = 0; c < C; ++c) v[c] = fmaxf(v[c] + sbias[c], 0.f);
                 }
                 uint4* dst = reinterpret_cast<uint4*>(p.out + (size_t)r * C);
 #pragma unroll
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
 
 constexpr size_t conv_smem_bytes(int taps)
 {
-    return 1024 + (size_t)taps * kWTileBytes + (size_t)NSTAGE * kTileBytes + (2 * NSTAGE + 6) * 8 + 16;
+    return 1024 + (size_t)taps * kWTileBytes + (size_t)NSTAGE * kTileBytes + (2 * NSTAGE + 6) * 8 + 16 + C * 4;
 }
 
 // ---- rows, features, loss, gradients, optimiser ----------------------------------
