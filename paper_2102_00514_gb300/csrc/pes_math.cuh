@@ -29,6 +29,16 @@ template <typename T> PES_DEV T tsqrt(T x);
 template <> PES_DEV float tsqrt<float>(float x) { return sqrtf(x); }
 template <> PES_DEV double tsqrt<double>(double x) { return sqrt(x); }
 
+// Reciprocal square root and reciprocal on the pivot chains of the
+// factorisations: FP32 takes the hardware approximations (rsqrtf, and
+// __fdividef for the reciprocal: a few ulp), FP64 the correctly rounded forms.
+template <typename T> PES_DEV T trsqrt(T x);
+template <> PES_DEV float trsqrt<float>(float x) { return rsqrtf(x); }
+template <> PES_DEV double trsqrt<double>(double x) { return 1.0 / sqrt(x); }
+template <typename T> PES_DEV T trcp(T x);
+template <> PES_DEV float trcp<float>(float x) { return __fdividef(1.0f, x); }
+template <> PES_DEV double trcp<double>(double x) { return 1.0 / x; }
+
 // ---- products -------------------------------------------------------------
 
 // C = A B (5x5)
@@ -177,8 +187,8 @@ PES_DEV int chol_psd(const T* S, T* L)
         for (int l = 0; l < j; ++l) s = fma(-L[j * NX + l], L[j * NX + l], s);
         const bool ok = s > T(0);
         zero_pivots += ok ? 0 : 1;
-        const T d = ok ? tsqrt(s) : T(0);
-        const T inv = ok ? T(1) / d : T(0);
+        const T inv = ok ? trsqrt(s) : T(0);
+        const T d = s * inv;
         L[j * NX + j] = d;
 #pragma unroll
         for (int i = j + 1; i < NX; ++i) {
@@ -206,8 +216,8 @@ PES_DEV bool chol_pd(const T* S, T* L, T* rdiag)
         for (int l = 0; l < j; ++l) s = fma(-L[j * NX + l], L[j * NX + l], s);
         const bool ok = s > T(0);
         ok_all = ok_all && ok;
-        const T d = ok ? tsqrt(s) : T(1);
-        const T inv = T(1) / d;
+        const T inv = ok ? trsqrt(s) : T(1);
+        const T d = ok ? s * inv : T(1);
         L[j * NX + j] = d;
         rdiag[j] = inv;
 #pragma unroll
@@ -299,7 +309,7 @@ PES_DEV bool inv2_spd(const T* S, T* Si)
 {
     const T det = S[0] * S[2] - S[1] * S[1];
     const bool ok = (det > T(0)) && (S[0] > T(0));
-    const T r = ok ? T(1) / det : T(0);
+    const T r = ok ? trcp(det) : T(0);
     Si[0] = S[2] * r;
     Si[1] = -S[1] * r;
     Si[2] = S[0] * r;

@@ -98,8 +98,8 @@ PES_DEV CTCoef<T> ct_coef(T w, T dt)
         k.dA2 = dt * dt * (T(0.5) - a2 * T(0.125) + a2 * a2 * (T(1) / T(144)));
     } else {
         // 1 - cos a without cancellation for cos a > 0
-        const T omc = (k.c > T(0)) ? k.s * k.s / (T(1) + k.c) : T(1) - k.c;
-        const T iw = T(1) / w;
+        const T omc = (k.c > T(0)) ? k.s * k.s * trcp(T(1) + k.c) : T(1) - k.c;
+        const T iw = trcp(w);
         k.A1 = k.s * iw;
         k.A2 = omc * iw;
         k.dA1 = (a * k.c - k.s) * iw * iw;
@@ -166,7 +166,7 @@ PES_DEV void bearings_jacobian(const T* x, const T* s, T* H)
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const T dx = x[0] - s[2 * r], dy = x[1] - s[2 * r + 1];
-        const T ir2 = T(1) / (dx * dx + dy * dy);
+        const T ir2 = trcp(dx * dx + dy * dy);
         H[r * 5 + 0] = -dy * ir2;
         H[r * 5 + 1] = dx * ir2;
     }
@@ -263,8 +263,8 @@ PES_DEV void dev_f_pair(const DevModel<T>& m, const T* xbar, const CTCoef<T>& kr
     const T thr = sizeof(T) == 4 ? T(0.05) : T(0.01);
     T sd, cd;
     tsincos(sg[4] * dt, &sd, &cd);
-    const T omcd = sd * sd / (T(1) + cd);
-    const T omcr = (kr.c > T(0)) ? kr.s * kr.s / (T(1) + kr.c) : T(1) - kr.c;
+    const T omcd = sd * sd * trcp(T(1) + cd);
+    const T omcr = (kr.c > T(0)) ? kr.s * kr.s * trcp(T(1) + kr.c) : T(1) - kr.c;
 #pragma unroll
     for (int sign = 0; sign < 2; ++sign) {
         const T sgn = sign == 0 ? T(1) : T(-1);
@@ -279,7 +279,7 @@ PES_DEV void dev_f_pair(const DevModel<T>& m, const T* xbar, const CTCoef<T>& kr
             A2 = dt * a * (T(0.5) - a2 * (T(1) / T(24)) + a2 * a2 * (T(1) / T(720)));
         } else {
             const T omc = omcr + kr.c * omcd + sgn * kr.s * sd;
-            const T iw = T(1) / w;
+            const T iw = trcp(w);
             A1 = s * iw;
             A2 = omc * iw;
         }
@@ -379,7 +379,7 @@ PES_DEV void lin_trans_cubature(const DevModel<T>& m, const T* xbar, const T* L,
 #pragma unroll
     for (int r = 0; r < 5; ++r) zdev[r] *= m.sp_w;
     // F = D L^{-1} / (2 scale)
-    const T sc = T(0.5) / sq;
+    const T sc = T(0.5) * trcp(sq);
 #pragma unroll
     for (int i = 0; i < 25; ++i) Dm[i] *= sc;
     solve_rows_lower_t<T, 5>(L, rdiag, Dm, tr.F);
@@ -461,7 +461,7 @@ PES_DEV void lin_obs_cubature(const DevModel<T>& m, int b, const T* xbar, const 
     }
 #pragma unroll
     for (int r = 0; r < 2; ++r) zdev[r] *= m.sp_w;
-    const T sc = T(0.5) / sq;
+    const T sc = T(0.5) * trcp(sq);
 #pragma unroll
     for (int i = 0; i < 10; ++i) Dm[i] *= sc;
     solve_rows_lower_t<T, 2>(L, rdiag, Dm, ob.H);
