@@ -396,12 +396,15 @@ PES_DEV void load_lin_trans(const KParams<T>& p, int s, int lane, Trans<T>& tr)
     for (int i = 0; i < 15; ++i) tr.Q[i] = h[(50 + i) * 32];
 }
 
-// Filtering, level 1: fold the lane's chunk [a, e) into one element. Each step
-// linearises its own incoming transition (k-1 -> k, about the nominal of k-1)
-// and its observation, so no linearisation is carried from step to step.
+// Filtering, level 1: fold the lane's chunk [a, e) into one element. Step k
+// folds the update with its own observation and then the prediction through
+// its outgoing transition (k -> k+1), both linearised about the nominal of k,
+// so the state's sigma-point factor serves both and no earlier state's inputs
+// stay live. The transition into the chunk's first state is linearised once
+// before the loop; the outgoing transition of the chunk's last state is
+// linearised only to be stored for the re-run (the next lane folds it itself).
 // With a stored linearisation (MODE_RUN, cubature) both are kept for the
-// re-run; the transition into the chunk's first state goes into the previous
-// lane's slot, where the previous lane's re-run looks for it.
+// re-run, the transition at the slot of its source state.
 template <typename T, int LIN>
 PES_DEV bool fold_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int lane, FElem<T>& acc)
 {
@@ -414,38 +417,34 @@ PES_DEV bool fold_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int la
     cur.init(p.offsets, p.B, a);
     const int64_t dix = p.lanes_layout ? p.NL : 1;
     int64_t ix = state_ix(p, a, a, lane);
-    StateIn<T, LIN> sp, sc, sn;   // inputs of states k-1, k, k+1
-    if (!cur.is_head(a)) load_state(p, prev_ix(p, a, lane), sp);
+    StateIn<T, LIN> sc, sn;   // inputs of states k, k+1
+    if (!cur.is_head(a)) {
+        StateIn<T, LIN> sp;
+        load_state(p, prev_ix(p, a, lane), sp);
+        Trans<T> tr;
+        Factor<T, LIN> fp;
+        ok &= factor_state(sp, fp);
+        lin_trans(p, a - 1, sp, fp, tr);
+        felem_identity(acc, tr.xn);
+        fold_predict(acc, tr);
+    }
     load_state(p, ix, sc);
 #pragma unroll 1
     for (int64_t k = a; k < e; ++k, ix += dix) {
         cur.forward(k);
         const int s = (int)(k - a);
         if (k + 1 < e) load_state(p, ix + dix, sn);
+        Factor<T, LIN> fc;
+        ok &= factor_state(sc, fc);
         if (cur.is_head(k)) {
             T m0[5], P0[15];
             load_prior(p, cur.b, m0, P0);
             felem_apply_prior(acc, m0, P0);
         } else {
-            Trans<T> tr;
-            {
-                Factor<T, LIN> fp;
-                ok &= factor_state(sp, fp);
-                lin_trans(p, k - 1, sp, fp, tr);
-            }
-            if (store_lin) {
-                if (s == 0) store_lin_trans(p, p.L - 1, lane - 1, tr);
-                else store_lin_trans(p, s - 1, lane, tr);
-            }
-            if (s == 0) felem_identity(acc, tr.xn);
             Obs<T> ob;
-            {
-                Factor<T, LIN> fc;
-                ok &= factor_state(sc, fc);
-                lin_obs(p, k, cur.b, sc, fc, ob);
-            }
+            lin_obs(p, k, cur.b, sc, fc, ob);
             if (store_lin) store_lin_obs(p, s, lane, ob);
-            ok &= fold_filter_step(acc, tr, ob);
+            ok &= fold_update(acc, ob);
         }
         if (LIN != LIN_ARRAYS && p.model.lm > T(0)) {
             // Levenberg-Marquardt pseudo-measurement of this state's nominal
@@ -453,7 +452,12 @@ PES_DEV bool fold_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int la
             felem_damping(dmp, sc.x, p.model.lm);
             combine_filter(acc, dmp, acc);
         }
-        sp = sc;
+        if (!cur.is_tail(k) && (k + 1 < e || store_lin)) {
+            Trans<T> tr;
+            lin_trans(p, k, sc, fc, tr);
+            if (store_lin) store_lin_trans(p, s, lane, tr);
+            if (k + 1 < e) fold_predict(acc, tr);
+        }
         sc = sn;
     }
     return ok;

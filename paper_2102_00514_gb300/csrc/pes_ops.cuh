@@ -108,8 +108,12 @@ PES_DEV void felem_apply_prior(FElem<T>& a, const T* m0, const T* P0)
 //   A = A- - K G,  b = b- + K v,  C = C- - K H C-,
 // and the likelihood of y_k given the input accumulates
 //   J += G^T S^{-1} G,  eta += G^T S^{-1} v.
+// The two halves of fold_filter_step: the prediction through the transition,
+// after which a describes x_k given the input, then the update with the
+// observation at k. Folding them separately keeps the transition and the
+// observation from being live together.
 template <typename T>
-PES_DEV bool fold_filter_step(FElem<T>& a, const Trans<T>& tr, const Obs<T>& ob)
+PES_DEV void fold_predict(FElem<T>& a, const Trans<T>& tr)
 {
     T Am[25];
     mm(tr.F, a.A, Am);
@@ -122,6 +126,20 @@ PES_DEV bool fold_filter_step(FElem<T>& a, const Trans<T>& tr, const Obs<T>& ob)
     T FC[25], Cm[15];
     m_s(tr.F, a.C, FC);
     abt_sym_add(FC, tr.F, tr.Q, Cm);
+#pragma unroll
+    for (int i = 0; i < 25; ++i) a.A[i] = Am[i];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) a.b[i] = bm[i];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) a.C[i] = Cm[i];
+}
+
+template <typename T>
+PES_DEV bool fold_update(FElem<T>& a, const Obs<T>& ob)
+{
+    const T* Am = a.A;
+    const T* bm = a.b;
+    const T* Cm = a.C;
     // H C-
     T HC[10];
 #pragma unroll
@@ -162,18 +180,25 @@ PES_DEV bool fold_filter_step(FElem<T>& a, const Trans<T>& tr, const Obs<T>& ob)
         for (int l = 0; l < 5; ++l) hv = fma(-ob.H[r * 5 + l], bm[l] - ob.xn[l], hv);
         v[r] = hv;
     }
+    T Anew[25], bnew[5], Cnew[15];
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
 #pragma unroll
         for (int j = 0; j < 5; ++j)
-            a.A[i * 5 + j] = fma(-KT[5 + i], G[5 + j], fma(-KT[i], G[j], Am[i * 5 + j]));
-        a.b[i] = fma(KT[5 + i], v[1], fma(KT[i], v[0], bm[i]));
+            Anew[i * 5 + j] = fma(-KT[5 + i], G[5 + j], fma(-KT[i], G[j], Am[i * 5 + j]));
+        bnew[i] = fma(KT[5 + i], v[1], fma(KT[i], v[0], bm[i]));
     }
 #pragma unroll
     for (int i = 0; i < 5; ++i)
 #pragma unroll
         for (int j = i; j < 5; ++j)
-            a.C[si(i, j)] = fma(-KT[5 + i], HC[5 + j], fma(-KT[i], HC[j], Cm[si(i, j)]));
+            Cnew[si(i, j)] = fma(-KT[5 + i], HC[5 + j], fma(-KT[i], HC[j], Cm[si(i, j)]));
+#pragma unroll
+    for (int i = 0; i < 25; ++i) a.A[i] = Anew[i];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) a.b[i] = bnew[i];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) a.C[i] = Cnew[i];
     // likelihood of y_k given the input
     T SiG[10], Siv[2];
 #pragma unroll
@@ -190,6 +215,13 @@ PES_DEV bool fold_filter_step(FElem<T>& a, const Trans<T>& tr, const Obs<T>& ob)
         a.eta[i] = fma(G[5 + i], Siv[1], fma(G[i], Siv[0], a.eta[i]));
     }
     return ok;
+}
+
+template <typename T>
+PES_DEV bool fold_filter_step(FElem<T>& a, const Trans<T>& tr, const Obs<T>& ob)
+{
+    fold_predict(a, tr);
+    return fold_update(a, ob);
 }
 
 // out = ai (x) aj, Eq. 15 (ai earlier in time). aj's input reference is the
