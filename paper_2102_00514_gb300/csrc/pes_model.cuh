@@ -261,9 +261,20 @@ PES_DEV void dev_f_pair(const DevModel<T>& m, const T* xbar, const CTCoef<T>& kr
     }
     const T dt = m.dt;
     const T thr = sizeof(T) == 4 ? T(0.05) : T(0.01);
-    T sd, cd;
-    tsincos(sg[4] * dt, &sd, &cd);
-    const T omcd = sd * sd * trcp(T(1) + cd);
+    // the turn-angle offset d = sg_omega dt of a sigma point is small: below
+    // 0.05 its sine and 1 - cos by their Taylor series through d^7 and d^8
+    // (remainders below d^9/9! < 6e-18), else by sincos
+    T sd, cd, omcd;
+    const T d = sg[4] * dt;
+    if (fabs(d) < T(0.05)) {
+        const T d2 = d * d;
+        sd = d * (T(1) - d2 * (T(1) / T(6)) * (T(1) - d2 * (T(1) / T(20)) * (T(1) - d2 * (T(1) / T(42)))));
+        omcd = d2 * T(0.5) * (T(1) - d2 * (T(1) / T(12)) * (T(1) - d2 * (T(1) / T(30)) * (T(1) - d2 * (T(1) / T(56)))));
+        cd = T(1) - omcd;
+    } else {
+        tsincos(d, &sd, &cd);
+        omcd = sd * sd * trcp(T(1) + cd);
+    }
     const T omcr = (kr.c > T(0)) ? kr.s * kr.s * trcp(T(1) + kr.c) : T(1) - kr.c;
 #pragma unroll
     for (int sign = 0; sign < 2; ++sign) {
