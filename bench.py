@@ -453,6 +453,16 @@ def main():
         if rank == 0:
             result["fp64"] = {"value": work_per_step / (sum(per) * 1e-3), "ms_per_step": sum(per),
                               "per_method_ms": dict(zip([m for m, _ in methods], per))}
+            # the FP64 path is bound by the FP64 pipe: its roofline is the
+            # measured FP64 FMA rate (pes_measure_fma_peak)
+            p64 = roofline.get("fma_probe_tflops", {}).get("fp64")
+            if p64:
+                r64 = {}
+                for (name, _), ms in zip(methods, per):
+                    ach = ALG_FLOP[name] * steps * iters / (ms * 1e-3) / 1e12
+                    r64[name] = {"achieved_tflops": ach, "frac": ach / p64}
+                result["fp64"]["roofline"] = {"bound": "fp64", "peak_tflops": p64,
+                                              "peak_source": "measured FP64 FMA probe", "per_method": r64}
         x64 = {}
         for name, m in methods:
             x, P, _, _ = sm.ieks_run(d64["model"], m, pes.FP64, d64["y"], d64["offsets"], d64["m0"], d64["P0"],
