@@ -328,3 +328,16 @@ def test_damping_rejects_negative_lambda(sm):
     with pytest.raises(pes.PesError) as ei:
         gpu_run(sm, wl, pes.IEKS, pes.FP64, iters=1, lm=-1.0)
     assert ei.value.status == pes.INVALID_ARG
+
+
+def test_mixed_tolerance_mode(sm):
+    """PES_MIXED in tolerance mode: FP32 iterations until the tolerance (or
+    max_iters - 1), then one FP64 iteration; the result matches the FP64
+    oracle iterated to the same tolerance within the FP32 bound."""
+    wl = synth.workload("ieks_T500")
+    ref = oracle_run(wl, pes.IEKS, iters=50, tol=1e-6)
+    x, P, used, st = gpu_run(sm, wl, pes.IEKS, pes.MIXED, iters=50, tol=1e-6, allow_not_converged=True)
+    assert st == pes.OK
+    assert 2 <= used <= ref["iters_used"] + 3
+    assert rel_err(x, ref["x"], wl["offsets"]) < TOL_FP32
+    assert rel_err(P, ref["P"], wl["offsets"]) < TOL_FP32

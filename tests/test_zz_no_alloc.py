@@ -66,3 +66,21 @@ def test_noalloc_rejects_mixed_precision():
     d = workload_to_dev(wl, pes.FP32)
     st, _, _, _ = run_noalloc(lib, d, pes.IEKS, pes.MIXED, wl["y"].shape[1], 1, 2)
     assert st == pes.UNSUPPORTED
+
+
+def test_noalloc_unscented_and_damped_match_handle_entry_point():
+    lib = pes.load_library()
+    wl = synth.ct_bearings([300, 41], seed=5, sensor_jitter=0.2)
+    N, B = wl["y"].shape[1], 2
+    d = workload_to_dev(wl, pes.FP64)
+    d["model"].ut_alpha, d["model"].ut_beta, d["model"].ut_kappa = 1.0, 2.0, 1.0
+    d["model"].lm_lambda = 2.0
+    sm = pes.Smoother(N, B)
+    xr, Pr, _, _ = sm.ieks_run(d["model"], pes.UNSCENTED, pes.FP64, d["y"], d["offsets"], d["m0"], d["P0"], iters=3)
+    sm.sync()
+    ref_x, ref_P = xr.cpu().numpy(), Pr.cpu().numpy()
+    sm.close()
+    st, x, P, used = run_noalloc(lib, d, pes.UNSCENTED, pes.FP64, N, B, 3)
+    assert st == pes.OK and used == 3
+    assert rel_err(x.cpu().numpy(), ref_x, wl["offsets"]) < 1e-12
+    assert rel_err(P.cpu().numpy(), ref_P, wl["offsets"]) < 1e-12
