@@ -27,6 +27,7 @@ _lib = None
 IEKS = 0
 CUBATURE = 1
 UNSCENTED = 2
+GAUSS_HERMITE = 3
 MODEL_CT_BEARINGS = 0
 MODEL_LINEAR = 1
 OK, NOT_PD, NOT_CONVERGED = 0, 2, 4
@@ -110,6 +111,8 @@ def _load():
         lib.orc_slr.restype = i
         lib.orc_slr_unscented.argtypes = [mp, i, i64, p, p, p, p, p]
         lib.orc_slr_unscented.restype = i
+        lib.orc_slr_gauss_hermite.argtypes = [mp, i, i64, p, p, p, p, p]
+        lib.orc_slr_gauss_hermite.restype = i
         lib.orc_linearize.argtypes = [mp, i, i64, p, i64, p, p, p, p, p, p, p, p, p, p]
         lib.orc_linearize.restype = i
         lib.orc_kf_rts.argtypes = [i64, p, i64] + [p] * 13
@@ -276,7 +279,8 @@ def slr(model: Model, which: int, b: int, xbar, Pbar, method: int = CUBATURE):
     G = np.zeros(nz * 5)
     off = np.zeros(nz)
     Lam = np.zeros(nz * nz)
-    fn = _load().orc_slr_unscented if method == UNSCENTED else _load().orc_slr
+    fn = {UNSCENTED: _load().orc_slr_unscented, GAUSS_HERMITE: _load().orc_slr_gauss_hermite}.get(method,
+                                                                                              _load().orc_slr)
     st = fn(ctypes.byref(model.s), which, b, _p(xbar), _p(Pbar), _p(G), _p(off), _p(Lam))
     if st != OK:
         raise np.linalg.LinAlgError(f"orc_slr status {st}")

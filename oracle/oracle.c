@@ -477,6 +477,65 @@ int orc_slr_unscented(const orc_model* m, int which, int64_t b, const double xba
     return ORC_OK;
 }
 
+int orc_slr_gauss_hermite(const orc_model* m, int which, int64_t b, const double xbar[5], const double Pbar[25],
+                          double* G, double* offset, double* Lam)
+{
+    const int nz = which == 0 ? NX : NY;
+    double Lc[25];
+    if (!cholesky(NX, Pbar, Lc)) return ORC_NOT_PD;
+    const double node[3] = {-sqrt(3.0), 0.0, sqrt(3.0)};
+    const double wt[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};
+    enum { NP = 243 };   /* 3^5 */
+    static __thread double X[NP][NX], Z[NP][NX], W[NP];
+    for (int p = 0; p < NP; ++p) {
+        double xi[NX];
+        int q = p;
+        W[p] = 1.0;
+        for (int d = 0; d < NX; ++d) {
+            xi[d] = node[q % 3];
+            W[p] *= wt[q % 3];
+            q /= 3;
+        }
+        for (int r = 0; r < NX; ++r) {
+            double v = xbar[r];
+            for (int d = 0; d < NX; ++d) v += Lc[r * NX + d] * xi[d];
+            X[p][r] = v;
+        }
+        if (which == 0) model_f(m, X[p], Z[p]);
+        else model_h(m, b, X[p], Z[p]);
+    }
+    if (which == 1 && angles(m)) {
+        double ref[NX];
+        model_h(m, b, xbar, ref);
+        for (int p = 0; p < NP; ++p)
+            for (int r = 0; r < nz; ++r) Z[p][r] = ref[r] + orc_wrap(Z[p][r] - ref[r]);
+    }
+    double zbar[NX] = {0};
+    for (int p = 0; p < NP; ++p)
+        for (int r = 0; r < nz; ++r) zbar[r] += W[p] * Z[p][r];
+    double Psi[NX * NX] = {0}; /* NX x nz */
+    double Phi[NX * NX] = {0}; /* nz x nz */
+    for (int p = 0; p < NP; ++p) {
+        for (int i = 0; i < NX; ++i)
+            for (int r = 0; r < nz; ++r) Psi[i * nz + r] += W[p] * (X[p][i] - xbar[i]) * (Z[p][r] - zbar[r]);
+        for (int r = 0; r < nz; ++r)
+            for (int t = 0; t < nz; ++t) Phi[r * nz + t] += W[p] * (Z[p][r] - zbar[r]) * (Z[p][t] - zbar[t]);
+    }
+    double Gt[NX * NX];
+    chol_solve(NX, nz, Lc, Psi, Gt);
+    for (int r = 0; r < nz; ++r)
+        for (int i = 0; i < NX; ++i) G[r * NX + i] = Gt[i * nz + r];
+    double Gx[NX];
+    mv(nz, NX, G, xbar, Gx);
+    for (int r = 0; r < nz; ++r) offset[r] = zbar[r] - Gx[r];
+    double GP[NX * NX], GPG[NX * NX];
+    mm(nz, NX, NX, G, Pbar, GP);
+    mmt(nz, NX, nz, GP, G, GPG);
+    for (int r = 0; r < nz * nz; ++r) Lam[r] = Phi[r] - GPG[r];
+    symmetrize(nz, Lam);
+    return ORC_OK;
+}
+
 int orc_linearize(const orc_model* m, int method, int64_t N, const int64_t* offsets, int64_t B,
                   const double* xbar, const double* Pbar, const double* y,
                   double* F, double* c, double* Qp, double* H, double* d, double* Rp, double* y_used)
@@ -503,6 +562,8 @@ int orc_linearize(const orc_model* m, int method, int64_t N, const int64_t* offs
                     double Lam[25];
                     int st = method == ORC_UNSCENTED
                                  ? orc_slr_unscented(m, 0, b, xk, Pbar + 25 * k, F + 25 * k, c + 5 * k, Lam)
+                             : method == ORC_GAUSS_HERMITE
+                                 ? orc_slr_gauss_hermite(m, 0, b, xk, Pbar + 25 * k, F + 25 * k, c + 5 * k, Lam)
                                  : orc_slr(m, 0, b, xk, Pbar + 25 * k, F + 25 * k, c + 5 * k, Lam);
                     if (st != ORC_OK) return st;
                     for (int i = 0; i < 25; ++i) Qp[25 * k + i] = Q[i] + Lam[i];
@@ -526,6 +587,8 @@ int orc_linearize(const orc_model* m, int method, int64_t N, const int64_t* offs
                     double Om[4];
                     int st = method == ORC_UNSCENTED
                                  ? orc_slr_unscented(m, 1, b, xk, Pbar + 25 * k, H + 10 * k, d + 2 * k, Om)
+                             : method == ORC_GAUSS_HERMITE
+                                 ? orc_slr_gauss_hermite(m, 1, b, xk, Pbar + 25 * k, H + 10 * k, d + 2 * k, Om)
                                  : orc_slr(m, 1, b, xk, Pbar + 25 * k, H + 10 * k, d + 2 * k, Om);
                     if (st != ORC_OK) return st;
                     for (int i = 0; i < 4; ++i) Rp[4 * k + i] = R[i] + Om[i];

@@ -15,6 +15,7 @@
 #define ORC_IEKS 0
 #define ORC_CUBATURE 1
 #define ORC_UNSCENTED 2
+#define ORC_GAUSS_HERMITE 3
 
 #define ORC_MODEL_CT_BEARINGS 0
 #define ORC_MODEL_LINEAR 1
@@ -59,6 +60,12 @@ int orc_slr(const orc_model* m, int which, int64_t b, const double xbar[5], cons
  * lambda / (n + lambda) + 1 - alpha^2 + beta at the centre. */
 int orc_slr_unscented(const orc_model* m, int which, int64_t b, const double xbar[5], const double Pbar[25],
                       double* G, double* offset, double* Lam);
+/* The same regression with the third-order Gauss-Hermite product rule:
+ * 3^n points xbar + chol(Pbar) xi, xi in {-sqrt 3, 0, sqrt 3}^n, weights the
+ * products of 1/6, 2/3, 1/6 (exact for polynomials of degree 5 in each
+ * coordinate of a standard Gaussian). */
+int orc_slr_gauss_hermite(const orc_model* m, int which, int64_t b, const double xbar[5], const double Pbar[25],
+                          double* G, double* offset, double* Lam);
 int orc_linearize(const orc_model* m, int method, int64_t N, const int64_t* offsets, int64_t B,
                   const double* xbar, const double* Pbar, const double* y,
                   double* F, double* c, double* Qp, double* H, double* d, double* Rp, double* y_used);
