@@ -61,6 +61,13 @@ pes_status check_common(pes_handle* h, pes_precision prec, const int64_t* offset
     return PES_OK;
 }
 
+// Kernel linearisation of a method: Taylor, the symmetric sigma-point rules
+// (cubature, unscented: one kernel, parameterised), Gauss-Hermite.
+int lin_of(pes_method method)
+{
+    return method == PES_IEKS ? LIN_IEKS : (method == PES_GAUSS_HERMITE ? LIN_GH : LIN_CUBATURE);
+}
+
 // Sigma-point rule of a method: the spread of the side points, twice a side
 // point's weight, and the centre's covariance weight (pes.h, pes_method).
 void sigma_rule(const pes_model& m, pes_method method, double& scale, double& w, double& w0c)
@@ -130,7 +137,7 @@ pes_status device_model(pes_handle* h, const pes_model& m, int32_t B, cudaStream
 
 pes_status check_method(pes_handle* h, pes_method method, const pes_model* m)
 {
-    if (method != PES_IEKS && method != PES_CUBATURE && method != PES_UNSCENTED)
+    if (method != PES_IEKS && method != PES_CUBATURE && method != PES_UNSCENTED && method != PES_GAUSS_HERMITE)
         return fail(h, PES_ERR_INVALID_ARG, "unknown method");
     if (method == PES_UNSCENTED) {
         if (!std::isfinite(m->ut_alpha) || m->ut_alpha == 0.0 || !std::isfinite(m->ut_beta) ||
@@ -306,7 +313,7 @@ static pes_status ieks_run_t(pes_handle* h, const pes_model* model, pes_method m
                              const void* P0, const void* x_init, const void* P_init, int32_t max_iters, double tol,
                              void* x_out, void* P_out, int32_t* iters_used, cudaStream_t st)
 {
-    const int lin = method == PES_IEKS ? LIN_IEKS : LIN_CUBATURE;
+    const int lin = lin_of(method);
     Shape s;
     pes_status r = make_shape<T>(h, lin, prec, N, s);
     if (r != PES_OK) return r;
@@ -377,7 +384,9 @@ static pes_status ieks_run_sequential_t(pes_handle* h, const pes_model* model, p
         p.traj_iters = h->traj_iters;
         h->traj_iters_B = B;
     }
-    const cudaError_t e = cub ? launch_sequential<T, LIN_CUBATURE>(p, st) : launch_sequential<T, LIN_IEKS>(p, st);
+    const cudaError_t e = !cub                           ? launch_sequential<T, LIN_IEKS>(p, st)
+                          : method == PES_GAUSS_HERMITE ? launch_sequential<T, LIN_GH>(p, st)
+                                                        : launch_sequential<T, LIN_CUBATURE>(p, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "launch of the sequential smoother");
     if (tol > 0.0 || iters_used) {
         int it = 0;
@@ -547,7 +556,7 @@ pes_status pes_launch_shape(pes_handle* h, pes_method method, pes_precision prec
 {
     if (!h || N < 1) return PES_ERR_INVALID_ARG;
     if (prec == PES_MIXED) return PES_ERR_UNSUPPORTED;
-    const int lin = method == PES_IEKS ? LIN_IEKS : LIN_CUBATURE;
+    const int lin = lin_of(method);
     Shape s;
     pes_status r = (prec == PES_FP64) ? make_shape<double>(h, lin, prec, N, s) : make_shape<float>(h, lin, prec, N, s);
     if (r != PES_OK) return r;
@@ -625,7 +634,7 @@ pes_status pes_autotune(pes_handle* h, const pes_model* model, pes_method method
     if (prec != PES_FP32 && prec != PES_FP64) return fail(h, PES_ERR_INVALID_ARG, "autotune FP32 or FP64");
     if (iters < 1 || !x_scratch || !P_scratch) return fail(h, PES_ERR_INVALID_ARG, "iters >= 1 and scratch needed");
     cudaStream_t st = (cudaStream_t)stream;
-    const int lin = method == PES_IEKS ? LIN_IEKS : LIN_CUBATURE;
+    const int lin = lin_of(method);
     pes_tune& slot = h->tune[lin][prec == PES_FP64 ? 1 : 0];
     const pes_tune saved = slot;
     const int nts32[] = {128, 256}, nts64[] = {128};
@@ -693,7 +702,7 @@ pes_status pes_linearize(pes_handle* h, const pes_model* model, pes_method metho
     if (method != PES_IEKS && !P_nom) return fail(h, PES_ERR_INVALID_ARG, "sigma-point methods need P_nom");
     cudaStream_t st = (cudaStream_t)stream;
     PES_CUDA(h, launch_validate_offsets(offsets, B, N, h->status, st));
-    const int lin = method == PES_IEKS ? LIN_IEKS : LIN_CUBATURE;
+    const int lin = lin_of(method);
     if (prec == PES_FP64) {
         KParams<double> p{};
         p.N = N; p.offsets = offsets; p.B = B;

@@ -278,6 +278,8 @@ cudaError_t launch_linearize(const KParams<T>& p, int lin, T* F, T* c, T* Qp, T*
     const int blocks = (int)std::min<int64_t>((p.N + threads - 1) / threads, 152 * 16);
     if (lin == LIN_IEKS)
         linearize_kernel<T, LIN_IEKS><<<blocks, threads, 0, st>>>(p, F, c, Qp, H, d, Rp, y_used);
+    else if (lin == LIN_GH)
+        linearize_kernel<T, LIN_GH><<<blocks, threads, 0, st>>>(p, F, c, Qp, H, d, Rp, y_used);
     else
         linearize_kernel<T, LIN_CUBATURE><<<blocks, threads, 0, st>>>(p, F, c, Qp, H, d, Rp, y_used);
     return cudaGetLastError();

@@ -9,6 +9,7 @@ static cudaError_t launch_nt(const KParams<T>& p, int lin, int nb, cudaStream_t 
 {
     if (lin == LIN_ARRAYS) return launch_cfg<T, LIN_ARRAYS, NT>(p, nb, st);
     if (lin == LIN_IEKS) return launch_cfg<T, LIN_IEKS, NT>(p, nb, st);
+    if (lin == LIN_GH) return launch_cfg<T, LIN_GH, NT>(p, nb, st);
     return launch_cfg<T, LIN_CUBATURE, NT>(p, nb, st);
 }
 
@@ -17,6 +18,7 @@ static int capacity_nt(int lin, int device)
 {
     if (lin == LIN_ARRAYS) return capacity_cfg<T, LIN_ARRAYS, NT>(device);
     if (lin == LIN_IEKS) return capacity_cfg<T, LIN_IEKS, NT>(device);
+    if (lin == LIN_GH) return capacity_cfg<T, LIN_GH, NT>(device);
     return capacity_cfg<T, LIN_CUBATURE, NT>(device);
 }
 

@@ -1,0 +1,3 @@
+// Persistent smoother kernel: float, LIN_GH (Gauss-Hermite product rule), 256 threads per block.
+#include "pes_launch_impl.cuh"
+PES_INSTANTIATE(float, pes::LIN_GH, 256)

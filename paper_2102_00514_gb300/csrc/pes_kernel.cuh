@@ -239,21 +239,21 @@ template <typename T, int LIN>
 PES_DEV void load_state(const KParams<T>& p, int64_t ix, StateIn<T, LIN>& s)
 {
     if (LIN != LIN_ARRAYS) load_nominal(p, ix, s.x);
-    if (LIN == LIN_CUBATURE) load_nominal_cov(p, ix, s.P);
+    if (kSigma<LIN>) load_nominal_cov(p, ix, s.P);
     load_y(p, ix, s.y);
 }
 
 // Sigma-point factor of the state's nominal covariance (cubature only).
 template <typename T, int LIN>
 struct Factor {
-    T L[LIN == LIN_CUBATURE ? 25 : 1];
-    T rd[LIN == LIN_CUBATURE ? 5 : 1];
+    T L[kSigma<LIN> ? 25 : 1];
+    T rd[kSigma<LIN> ? 5 : 1];
 };
 
 template <typename T, int LIN>
 PES_DEV bool factor_state(const StateIn<T, LIN>& s, Factor<T, LIN>& f)
 {
-    if (LIN == LIN_CUBATURE) return cub_factor(s.P, f.L, f.rd);
+    if (kSigma<LIN>) return cub_factor(s.P, f.L, f.rd);
     return true;
 }
 
@@ -274,6 +274,8 @@ PES_DEV void lin_trans(const KParams<T>& p, int64_t k, const StateIn<T, LIN>& s,
         for (int i = 0; i < 15; ++i) tr.Q[i] = __ldg(p.Qp + i * p.N + k);
     } else if (LIN == LIN_IEKS) {
         lin_trans_taylor(p.model, s.x, tr);
+    } else if (LIN == LIN_GH) {
+        lin_trans_gh(p.model, s.x, f.L, f.rd, tr);
     } else {
         lin_trans_cubature(p.model, s.x, f.L, f.rd, tr);
     }
@@ -295,6 +297,8 @@ PES_DEV void lin_obs(const KParams<T>& p, int64_t k, int b, const StateIn<T, LIN
         for (int i = 0; i < 3; ++i) ob.R[i] = __ldg(p.Rp + i * p.N + k);
     } else if (LIN == LIN_IEKS) {
         lin_obs_taylor(p.model, b, s.x, s.y, ob);
+    } else if (LIN == LIN_GH) {
+        lin_obs_gh(p.model, b, s.x, f.L, f.rd, s.y, ob);
     } else {
         lin_obs_cubature(p.model, b, s.x, f.L, f.rd, s.y, ob);
     }
@@ -330,7 +334,7 @@ PES_DEV bool get_obs(const KParams<T>& p, int64_t k, int64_t ix, int b, Obs<T>& 
 // cubature linearisation (2 n_x sigma points through f and h) costs far more
 // than the traffic; the Taylor one does not.
 template <int LIN>
-constexpr bool kStoreLin = (LIN == LIN_CUBATURE);
+constexpr bool kStoreLin = kSigma<LIN>;
 
 // Layout [warp][s][LINS][32 lanes]; per state: H (10), r (2), R' (3), xn (5),
 // F (25), fx (5), Q' (15).
@@ -431,7 +435,7 @@ PES_DEV bool fold_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int la
     // the next state's inputs are loaded a step ahead, except for cubature,
     // whose register pressure makes the prefetch cost more in spills than it
     // hides (measured: fold 202 -> 194 us per iteration at T = 2^20 without it)
-    constexpr bool prefetch = (LIN != LIN_CUBATURE);
+    constexpr bool prefetch = !kSigma<LIN>;
     if (prefetch) load_state(p, ix, sc);
 #pragma unroll 1
     for (int64_t k = a; k < e; ++k, ix += dix) {
@@ -1087,7 +1091,7 @@ __global__ void __launch_bounds__(NT, 1) pes_persistent_kernel(const KParams<T> 
             elemS[t] = accS;
             Gauss<T> Gs;
             smoother_block_scan<T, NT>(p, elemS, topS, gs, gblock, gen, Gs, it);
-            const bool write_P = (p.mode != MODE_RUN) || (LIN == LIN_CUBATURE) || last || p.write_P_every_iter;
+            const bool write_P = (p.mode != MODE_RUN) || kSigma<LIN> || last || p.write_P_every_iter;
             int nb = -1;
             double num = 0.0, den = 0.0;
             double* conv = p.conv + (size_t)(it & 1) * 2 * p.B;

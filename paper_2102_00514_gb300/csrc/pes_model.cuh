@@ -16,7 +16,12 @@
 namespace pes {
 
 enum { MODEL_CT_BEARINGS = 0, MODEL_LINEAR = 1 };
-enum { LIN_ARRAYS = 0, LIN_IEKS = 1, LIN_CUBATURE = 2 };
+enum { LIN_ARRAYS = 0, LIN_IEKS = 1, LIN_CUBATURE = 2, LIN_GH = 3 };
+
+// Linearisations by statistical linear regression over sigma points (Eqs. 7-9),
+// which need the nominal covariance and its factor.
+template <int LIN>
+constexpr bool kSigma = (LIN == LIN_CUBATURE || LIN == LIN_GH);
 enum { ST_NOT_PD = 1, ST_NONFINITE = 2, ST_TIMEOUT = 4, ST_NOT_CONVERGED = 8, ST_BADARG = 16 };
 
 // Model parameters as passed to the kernels, already in the kernel's
@@ -497,6 +502,190 @@ PES_DEV void lin_obs_cubature(const DevModel<T>& m, int b, const T* xbar, const 
         ob.r[0] = wrap_angle(y[0] - h_ref[0]) - zdev[0];
         ob.r[1] = wrap_angle(y[1] - h_ref[1]) - zdev[1];
     }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) ob.xn[i] = xbar[i];
+}
+
+// ---- third-order Gauss-Hermite product rule -------------------------------------
+//
+// The regression of Eqs. 7-9 over the 3^5 points xbar + L xi, L = chol(Pbar),
+// xi in {-sqrt 3, 0, sqrt 3}^5, weights the products of 1/6, 2/3, 1/6. With the
+// deviations dz = g(xbar + L xi) - g(xbar) and sum_i w_i xi_i = 0:
+//   zbar - g(xbar) = sum w dz,   G = sum w dz xi^T,   F = Psi^T Pbar^{-1} = G L^{-1},
+//   Lambda = sum w dz dz^T - (zbar - g)(zbar - g)^T - G G^T.
+
+// Node and weight of digit q (0, 1, 2) of the product rule.
+template <typename T>
+PES_DEV void gh_node(int q, T& xi, T& w)
+{
+    const T r3 = T(1.7320508075688772935);
+    xi = q == 0 ? -r3 : (q == 1 ? T(0) : r3);
+    w = q == 1 ? T(2) / T(3) : T(1) / T(6);
+}
+
+// f(xbar + dx) - f(xbar) of the coordinated turn (the one-sided form of
+// dev_f_pair).
+template <typename T>
+PES_DEV void ct_deviation(const DevModel<T>& m, const T* xbar, const CTCoef<T>& kr, const T* inc_ref, const T* dx,
+                          T* dz)
+{
+    const T dt = m.dt;
+    const T thr = sizeof(T) == 4 ? T(0.05) : T(0.01);
+    T sd, cd, omcd;
+    const T d = dx[4] * dt;
+    if (fabs(d) < T(0.05)) {
+        const T d2 = d * d;
+        sd = d * (T(1) - d2 * (T(1) / T(6)) * (T(1) - d2 * (T(1) / T(20)) * (T(1) - d2 * (T(1) / T(42)))));
+        omcd = d2 * T(0.5) * (T(1) - d2 * (T(1) / T(12)) * (T(1) - d2 * (T(1) / T(30)) * (T(1) - d2 * (T(1) / T(56)))));
+        cd = T(1) - omcd;
+    } else {
+        tsincos(d, &sd, &cd);
+        omcd = sd * sd * trcp(T(1) + cd);
+    }
+    const T omcr = (kr.c > T(0)) ? kr.s * kr.s * trcp(T(1) + kr.c) : T(1) - kr.c;
+    const T w = xbar[4] + dx[4];
+    const T a = w * dt;
+    const T sn = kr.s * cd + kr.c * sd;
+    const T cs = kr.c * cd - kr.s * sd;
+    T A1, A2;
+    if (fabs(a) < thr) {
+        const T a2 = a * a;
+        A1 = dt * (T(1) - a2 * (T(1) / T(6)) + a2 * a2 * (T(1) / T(120)));
+        A2 = dt * a * (T(0.5) - a2 * (T(1) / T(24)) + a2 * a2 * (T(1) / T(720)));
+    } else {
+        const T omc = omcr + kr.c * omcd + kr.s * sd;
+        const T iw = trcp(w);
+        A1 = sn * iw;
+        A2 = omc * iw;
+    }
+    const T vx = xbar[2] + dx[2], vy = xbar[3] + dx[3];
+    dz[0] = dx[0] + ((A1 * vx - A2 * vy) - inc_ref[0]);
+    dz[1] = dx[1] + ((A2 * vx + A1 * vy) - inc_ref[1]);
+    dz[2] = (cs * vx - sn * vy) - inc_ref[2];
+    dz[3] = (sn * vx + cs * vy) - inc_ref[3];
+    dz[4] = dx[4];
+}
+
+template <typename T>
+PES_DEV void lin_trans_gh(const DevModel<T>& m, const T* xbar, const T* L, const T* rdiag, Trans<T>& tr)
+{
+    if (m.kind == MODEL_LINEAR) {   // the regression of an affine map is the map
+        lin_trans_taylor(m, xbar, tr);
+        return;
+    }
+    const CTCoef<T> kr = ct_coef(xbar[4], m.dt);
+    T inc_ref[5];
+    ct_increment(xbar, kr, inc_ref);
+    T zd[5] = {T(0), T(0), T(0), T(0), T(0)}, G[25], Phi[15];
+#pragma unroll
+    for (int i = 0; i < 25; ++i) G[i] = T(0);
+#pragma unroll
+    for (int i = 0; i < 15; ++i) Phi[i] = T(0);
+#pragma unroll 1
+    for (int pnt = 0; pnt < 243; ++pnt) {
+        T xi[5], w = T(1);
+        int q = pnt;
+#pragma unroll
+        for (int d = 0; d < 5; ++d) {
+            T wd;
+            gh_node<T>(q % 3, xi[d], wd);
+            w *= wd;
+            q /= 3;
+        }
+        T dx[5];
+#pragma unroll
+        for (int r = 0; r < 5; ++r) {
+            T v = T(0);
+#pragma unroll
+            for (int d = 0; d <= r; ++d) v = fma(L[r * NX + d], xi[d], v);
+            dx[r] = v;
+        }
+        T dz[5];
+        ct_deviation(m, xbar, kr, inc_ref, dx, dz);
+#pragma unroll
+        for (int r = 0; r < 5; ++r) {
+            const T wz = w * dz[r];
+            zd[r] += wz;
+#pragma unroll
+            for (int d = 0; d < 5; ++d) G[r * 5 + d] = fma(wz, xi[d], G[r * 5 + d]);
+#pragma unroll
+            for (int c = r; c < 5; ++c) Phi[si(r, c)] = fma(wz, dz[c], Phi[si(r, c)]);
+        }
+    }
+    solve_rows_lower_t<T, 5>(L, rdiag, G, tr.F);
+#pragma unroll
+    for (int r = 0; r < 5; ++r)
+#pragma unroll
+        for (int c = r; c < 5; ++c) {
+            T v = Phi[si(r, c)] - zd[r] * zd[c];
+#pragma unroll
+            for (int d = 0; d < 5; ++d) v = fma(-G[r * 5 + d], G[c * 5 + d], v);
+            tr.Q[si(r, c)] = m.Q[si(r, c)] + v;
+        }
+    tr.fx[0] = xbar[0] + inc_ref[0] + zd[0];
+    tr.fx[1] = xbar[1] + inc_ref[1] + zd[1];
+    tr.fx[2] = inc_ref[2] + zd[2];
+    tr.fx[3] = inc_ref[3] + zd[3];
+    tr.fx[4] = inc_ref[4] + zd[4];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) tr.xn[i] = xbar[i];
+}
+
+// Bearings see only the position, and with L lower triangular the position of
+// xbar + L xi depends on xi_0 and xi_1 alone: the 243-point rule reduces to
+// the 9 points of (xi_0, xi_1), the other coordinates' weights summing to 1.
+template <typename T>
+PES_DEV void lin_obs_gh(const DevModel<T>& m, int b, const T* xbar, const T* L, const T* rdiag, const T* y,
+                        Obs<T>& ob)
+{
+    if (m.kind == MODEL_LINEAR) {
+        lin_obs_taylor(m, b, xbar, y, ob);
+        return;
+    }
+    T s[4];
+    load_sensors(m, b, s);
+    T h_ref[2];
+    bearings(xbar, s, h_ref);
+    T zd[2] = {T(0), T(0)}, G[10], Phi[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int i = 0; i < 10; ++i) G[i] = T(0);
+#pragma unroll
+    for (int q0 = 0; q0 < 3; ++q0)
+#pragma unroll
+        for (int q1 = 0; q1 < 3; ++q1) {
+            T x0, w0, x1, w1;
+            gh_node<T>(q0, x0, w0);
+            gh_node<T>(q1, x1, w1);
+            const T w = w0 * w1;
+            const T dpx = L[0] * x0, dpy = L[NX] * x0 + L[NX + 1] * x1;
+            T dz[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const T rx = xbar[0] - s[2 * r], ry = xbar[1] - s[2 * r + 1];
+                const T cross = rx * dpy - ry * dpx;
+                const T rr = rx * rx + ry * ry;
+                const T rs = rx * dpx + ry * dpy;
+                dz[r] = tatan2(cross, rr + rs);
+            }
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const T wz = w * dz[r];
+                zd[r] += wz;
+                G[r * 5 + 0] = fma(wz, x0, G[r * 5 + 0]);
+                G[r * 5 + 1] = fma(wz, x1, G[r * 5 + 1]);
+#pragma unroll
+                for (int c = r; c < 2; ++c) Phi[si2(r, c)] = fma(wz, dz[c], Phi[si2(r, c)]);
+            }
+        }
+    solve_rows_lower_t<T, 2>(L, rdiag, G, ob.H);
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = r; c < 2; ++c)
+            ob.R[si2(r, c)] = m.R[si2(r, c)] + Phi[si2(r, c)] - zd[r] * zd[c] - G[r * 5] * G[c * 5] -
+                              G[r * 5 + 1] * G[c * 5 + 1];
+    ob.r[0] = wrap_angle(y[0] - h_ref[0]) - zd[0];
+    ob.r[1] = wrap_angle(y[1] - h_ref[1]) - zd[1];
 #pragma unroll
     for (int i = 0; i < 5; ++i) ob.xn[i] = xbar[i];
 }

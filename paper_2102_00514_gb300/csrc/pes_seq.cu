@@ -153,5 +153,7 @@ template cudaError_t launch_sequential<float, LIN_IEKS>(const KParams<float>&, c
 template cudaError_t launch_sequential<float, LIN_CUBATURE>(const KParams<float>&, cudaStream_t);
 template cudaError_t launch_sequential<double, LIN_IEKS>(const KParams<double>&, cudaStream_t);
 template cudaError_t launch_sequential<double, LIN_CUBATURE>(const KParams<double>&, cudaStream_t);
+template cudaError_t launch_sequential<float, LIN_GH>(const KParams<float>&, cudaStream_t);
+template cudaError_t launch_sequential<double, LIN_GH>(const KParams<double>&, cudaStream_t);
 
 }  // namespace pes

@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libpes.so")
 OK, INVALID_ARG, NOT_PD, NONFINITE, NOT_CONVERGED, CUDA, UNSUPPORTED, TIMEOUT = range(8)
 STATUS_NAMES = {0: "PES_OK", 1: "PES_ERR_INVALID_ARG", 2: "PES_ERR_NOT_PD", 3: "PES_ERR_NONFINITE",
                 4: "PES_ERR_NOT_CONVERGED", 5: "PES_ERR_CUDA", 6: "PES_ERR_UNSUPPORTED", 7: "PES_ERR_TIMEOUT"}
-IEKS, CUBATURE, UNSCENTED = 0, 1, 2
+IEKS, CUBATURE, UNSCENTED, GAUSS_HERMITE = 0, 1, 2, 3
 FP64, FP32, MIXED = 0, 1, 2
 MODEL_CT_BEARINGS, MODEL_LINEAR = 0, 1
 

@@ -45,7 +45,8 @@ def workload_to_dev(wl: dict, prec: int, ut=None, lm: float = 0.0):
                 P0=to_dev(wl["P0"], dt), model=model)
 
 
-ORACLE_METHOD = {pes.IEKS: oracle.IEKS, pes.CUBATURE: oracle.CUBATURE, pes.UNSCENTED: oracle.UNSCENTED}
+ORACLE_METHOD = {pes.IEKS: oracle.IEKS, pes.CUBATURE: oracle.CUBATURE, pes.UNSCENTED: oracle.UNSCENTED,
+                 pes.GAUSS_HERMITE: oracle.GAUSS_HERMITE}
 
 
 def oracle_run(wl: dict, method: int, iters: int = 10, tol: float = 0.0, x_init=None, P_init=None, ut=None,

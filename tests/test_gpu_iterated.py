@@ -19,7 +19,7 @@ def sm():
     s.close()
 
 
-@pytest.mark.parametrize("method", [pes.IEKS, pes.CUBATURE, pes.UNSCENTED])
+@pytest.mark.parametrize("method", [pes.IEKS, pes.CUBATURE, pes.UNSCENTED, pes.GAUSS_HERMITE])
 @pytest.mark.parametrize("prec", [pes.FP64, pes.FP32])
 def test_linearize_matches_oracle(sm, method, prec):
     wl = synth.ct_bearings([40, 1, 300], seed=21, sensor_jitter=0.2, omega0_halfwidth=1.0)
@@ -341,3 +341,30 @@ def test_mixed_tolerance_mode(sm):
     assert 2 <= used <= ref["iters_used"] + 3
     assert rel_err(x, ref["x"], wl["offsets"]) < TOL_FP32
     assert rel_err(P, ref["P"], wl["offsets"]) < TOL_FP32
+
+
+@pytest.mark.parametrize("name", ["ieks_T500", "ipls_T10000", "batch64_T1_400"])
+def test_gauss_hermite_fp64_matches_oracle(sm, name):
+    wl = synth.workload(name)
+    ref = oracle_run(wl, pes.GAUSS_HERMITE, iters=10)
+    x, P, used, _ = gpu_run(sm, wl, pes.GAUSS_HERMITE, pes.FP64, iters=10)
+    assert used == 10
+    assert rel_err(x, ref["x"], wl["offsets"]) < TOL_FP64
+    assert rel_err(P, ref["P"], wl["offsets"]) < TOL_FP64
+
+
+def test_gauss_hermite_fp32_and_sequential_match_oracle(sm):
+    wl = synth.workload("ipls_T10000")
+    ref = oracle_run(wl, pes.GAUSS_HERMITE, iters=10)
+    x, P, _, _ = gpu_run(sm, wl, pes.GAUSS_HERMITE, pes.FP32, iters=10)
+    print(f"Gauss-Hermite FP32: means {rel_err(x, ref['x'], wl['offsets']):.2e} "
+          f"covariances {rel_err(P, ref['P'], wl['offsets']):.2e}")
+    assert rel_err(x, ref["x"], wl["offsets"]) < TOL_FP32
+    assert rel_err(P, ref["P"], wl["offsets"]) < TOL_FP32
+    wl = synth.workload("batch8_T1_3000")
+    ref = oracle_run(wl, pes.GAUSS_HERMITE, iters=4)
+    d = workload_to_dev(wl, pes.FP64)
+    x, P, _, _ = sm.ieks_run_sequential(d["model"], pes.GAUSS_HERMITE, pes.FP64, d["y"], d["offsets"], d["m0"],
+                                        d["P0"], iters=4)
+    assert rel_err(x.cpu().numpy(), ref["x"], wl["offsets"]) < TOL_FP64
+    assert rel_err(P.cpu().numpy(), ref["P"], wl["offsets"]) < TOL_FP64
