@@ -566,6 +566,33 @@ PES_DEV void ct_deviation(const DevModel<T>& m, const T* xbar, const CTCoef<T>& 
     dz[4] = dx[4];
 }
 
+// The point xbar + L xi of index pnt (base-3 digits) and its weight.
+template <typename T>
+PES_DEV T gh_point(int pnt, const T* L, T* xi, T* dx)
+{
+    T w = T(1);
+    int q = pnt;
+#pragma unroll
+    for (int d = 0; d < 5; ++d) {
+        T wd;
+        gh_node<T>(q % 3, xi[d], wd);
+        w *= wd;
+        q /= 3;
+    }
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+        T v = T(0);
+#pragma unroll
+        for (int d = 0; d <= r; ++d) v = fma(L[r * NX + d], xi[d], v);
+        dx[r] = v;
+    }
+    return w;
+}
+
+// Two passes over the points: the first sums zbar - f(xbar) and G; the second
+// sums Lambda as the weighted second moment of the regression's residuals
+// dz - (zbar - f) - G xi, which equals the moment form above without its
+// cancellation (the residuals are the small, nonlinear part).
 template <typename T>
 PES_DEV void lin_trans_gh(const DevModel<T>& m, const T* xbar, const T* L, const T* rdiag, Trans<T>& tr)
 {
@@ -576,31 +603,13 @@ PES_DEV void lin_trans_gh(const DevModel<T>& m, const T* xbar, const T* L, const
     const CTCoef<T> kr = ct_coef(xbar[4], m.dt);
     T inc_ref[5];
     ct_increment(xbar, kr, inc_ref);
-    T zd[5] = {T(0), T(0), T(0), T(0), T(0)}, G[25], Phi[15];
+    T zd[5] = {T(0), T(0), T(0), T(0), T(0)}, G[25];
 #pragma unroll
     for (int i = 0; i < 25; ++i) G[i] = T(0);
-#pragma unroll
-    for (int i = 0; i < 15; ++i) Phi[i] = T(0);
 #pragma unroll 1
     for (int pnt = 0; pnt < 243; ++pnt) {
-        T xi[5], w = T(1);
-        int q = pnt;
-#pragma unroll
-        for (int d = 0; d < 5; ++d) {
-            T wd;
-            gh_node<T>(q % 3, xi[d], wd);
-            w *= wd;
-            q /= 3;
-        }
-        T dx[5];
-#pragma unroll
-        for (int r = 0; r < 5; ++r) {
-            T v = T(0);
-#pragma unroll
-            for (int d = 0; d <= r; ++d) v = fma(L[r * NX + d], xi[d], v);
-            dx[r] = v;
-        }
-        T dz[5];
+        T xi[5], dx[5], dz[5];
+        const T w = gh_point(pnt, L, xi, dx);
         ct_deviation(m, xbar, kr, inc_ref, dx, dz);
 #pragma unroll
         for (int r = 0; r < 5; ++r) {
@@ -608,20 +617,32 @@ PES_DEV void lin_trans_gh(const DevModel<T>& m, const T* xbar, const T* L, const
             zd[r] += wz;
 #pragma unroll
             for (int d = 0; d < 5; ++d) G[r * 5 + d] = fma(wz, xi[d], G[r * 5 + d]);
-#pragma unroll
-            for (int c = r; c < 5; ++c) Phi[si(r, c)] = fma(wz, dz[c], Phi[si(r, c)]);
         }
+    }
+    T Lam[15];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) Lam[i] = T(0);
+#pragma unroll 1
+    for (int pnt = 0; pnt < 243; ++pnt) {
+        T xi[5], dx[5], dz[5];
+        const T w = gh_point(pnt, L, xi, dx);
+        ct_deviation(m, xbar, kr, inc_ref, dx, dz);
+        T e[5];
+#pragma unroll
+        for (int r = 0; r < 5; ++r) {
+            T v = dz[r] - zd[r];
+#pragma unroll
+            for (int d = 0; d < 5; ++d) v = fma(-G[r * 5 + d], xi[d], v);
+            e[r] = v;
+        }
+#pragma unroll
+        for (int r = 0; r < 5; ++r)
+#pragma unroll
+            for (int c = r; c < 5; ++c) Lam[si(r, c)] = fma(w * e[r], e[c], Lam[si(r, c)]);
     }
     solve_rows_lower_t<T, 5>(L, rdiag, G, tr.F);
 #pragma unroll
-    for (int r = 0; r < 5; ++r)
-#pragma unroll
-        for (int c = r; c < 5; ++c) {
-            T v = Phi[si(r, c)] - zd[r] * zd[c];
-#pragma unroll
-            for (int d = 0; d < 5; ++d) v = fma(-G[r * 5 + d], G[c * 5 + d], v);
-            tr.Q[si(r, c)] = m.Q[si(r, c)] + v;
-        }
+    for (int i = 0; i < 15; ++i) tr.Q[i] = m.Q[i] + Lam[i];
     tr.fx[0] = xbar[0] + inc_ref[0] + zd[0];
     tr.fx[1] = xbar[1] + inc_ref[1] + zd[1];
     tr.fx[2] = inc_ref[2] + zd[2];
@@ -646,44 +667,49 @@ PES_DEV void lin_obs_gh(const DevModel<T>& m, int b, const T* xbar, const T* L, 
     load_sensors(m, b, s);
     T h_ref[2];
     bearings(xbar, s, h_ref);
-    T zd[2] = {T(0), T(0)}, G[10], Phi[3] = {T(0), T(0), T(0)};
+    T dzs[9][2], xs[9][2], ws[9];
+    T zd[2] = {T(0), T(0)}, G[10];
 #pragma unroll
     for (int i = 0; i < 10; ++i) G[i] = T(0);
 #pragma unroll
     for (int q0 = 0; q0 < 3; ++q0)
 #pragma unroll
         for (int q1 = 0; q1 < 3; ++q1) {
+            const int j = q0 * 3 + q1;
             T x0, w0, x1, w1;
             gh_node<T>(q0, x0, w0);
             gh_node<T>(q1, x1, w1);
-            const T w = w0 * w1;
+            ws[j] = w0 * w1;
+            xs[j][0] = x0;
+            xs[j][1] = x1;
             const T dpx = L[0] * x0, dpy = L[NX] * x0 + L[NX + 1] * x1;
-            T dz[2];
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 const T rx = xbar[0] - s[2 * r], ry = xbar[1] - s[2 * r + 1];
                 const T cross = rx * dpy - ry * dpx;
                 const T rr = rx * rx + ry * ry;
                 const T rs = rx * dpx + ry * dpy;
-                dz[r] = tatan2(cross, rr + rs);
-            }
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const T wz = w * dz[r];
+                dzs[j][r] = tatan2(cross, rr + rs);
+                const T wz = ws[j] * dzs[j][r];
                 zd[r] += wz;
                 G[r * 5 + 0] = fma(wz, x0, G[r * 5 + 0]);
                 G[r * 5 + 1] = fma(wz, x1, G[r * 5 + 1]);
-#pragma unroll
-                for (int c = r; c < 2; ++c) Phi[si2(r, c)] = fma(wz, dz[c], Phi[si2(r, c)]);
             }
         }
+    T Om[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        T e[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) e[r] = dzs[j][r] - zd[r] - G[r * 5] * xs[j][0] - G[r * 5 + 1] * xs[j][1];
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int c = r; c < 2; ++c) Om[si2(r, c)] = fma(ws[j] * e[r], e[c], Om[si2(r, c)]);
+    }
     solve_rows_lower_t<T, 2>(L, rdiag, G, ob.H);
 #pragma unroll
-    for (int r = 0; r < 2; ++r)
-#pragma unroll
-        for (int c = r; c < 2; ++c)
-            ob.R[si2(r, c)] = m.R[si2(r, c)] + Phi[si2(r, c)] - zd[r] * zd[c] - G[r * 5] * G[c * 5] -
-                              G[r * 5 + 1] * G[c * 5 + 1];
+    for (int i = 0; i < 3; ++i) ob.R[i] = m.R[i] + Om[i];
     ob.r[0] = wrap_angle(y[0] - h_ref[0]) - zd[0];
     ob.r[1] = wrap_angle(y[1] - h_ref[1]) - zd[1];
 #pragma unroll
