@@ -343,12 +343,14 @@ def test_mixed_tolerance_mode(sm):
     assert rel_err(P, ref["P"], wl["offsets"]) < TOL_FP32
 
 
-@pytest.mark.parametrize("name", ["ieks_T500", "ipls_T10000", "batch64_T1_400"])
-def test_gauss_hermite_fp64_matches_oracle(sm, name):
+@pytest.mark.parametrize("name,iters", [("ieks_T500", 10), ("ipls_T10000", 10), ("batch64_T1_400", 5)])
+def test_gauss_hermite_fp64_matches_oracle(sm, name, iters):
+    # the batch holds short trajectories whose iteration has not converged:
+    # five iterations, as for the other rules' batched checks
     wl = synth.workload(name)
-    ref = oracle_run(wl, pes.GAUSS_HERMITE, iters=10)
-    x, P, used, _ = gpu_run(sm, wl, pes.GAUSS_HERMITE, pes.FP64, iters=10)
-    assert used == 10
+    ref = oracle_run(wl, pes.GAUSS_HERMITE, iters=iters)
+    x, P, used, _ = gpu_run(sm, wl, pes.GAUSS_HERMITE, pes.FP64, iters=iters)
+    assert used == iters
     assert rel_err(x, ref["x"], wl["offsets"]) < TOL_FP64
     assert rel_err(P, ref["P"], wl["offsets"]) < TOL_FP64
 
