@@ -193,7 +193,12 @@ pes_status make_shape(pes_handle* h, int lin, pes_precision prec, int64_t N, Sha
     s.nt = choose_nt(h, lin, prec);
     const int min_steps = choose_min_steps(h, lin, prec);
     const int cap = coop_capacity(T(0), lin, s.nt, h->device);
-    if (cap <= 0) return fail(h, PES_ERR_CUDA, "the smoother kernel cannot be made co-resident on this device");
+    if (cap < 0) {
+        cudaGetLastError();   // clear a sticky launch-configuration error
+        return fail(h, PES_ERR_CUDA, "the smoother kernel's occupancy query failed: %s",
+                    cudaGetErrorString((cudaError_t)(-cap)));
+    }
+    if (cap == 0) return fail(h, PES_ERR_CUDA, "the smoother kernel cannot be made co-resident on this device");
     const int64_t want = (N + (int64_t)s.nt * min_steps - 1) / ((int64_t)s.nt * min_steps);
     s.nb = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)cap, want, (int64_t)h->nb_max}));
     const int64_t lanes = (int64_t)s.nb * s.nt;

@@ -22,12 +22,14 @@ cudaError_t launch_cfg(const KParams<T>& p, int nb, cudaStream_t st)
 template <typename T, int LIN, int NT>
 int capacity_cfg(int device)
 {
+    // a failing call returns its negated error code (the caller reports it)
     auto kern = pes_persistent_kernel<T, LIN, NT>;
     const size_t smem = smem_bytes_for<NT>(sizeof(T));
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return -(int)e;
     int per_sm = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess) return 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem)) != cudaSuccess) return -(int)e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) return -(int)e;
     return per_sm * sms;
 }
 
