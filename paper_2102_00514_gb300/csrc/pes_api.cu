@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <type_traits>
 
 #include "pes.h"
 #include "pes_handle.h"
@@ -170,6 +171,8 @@ pes_status check_model(pes_handle* h, const pes_model* m)
 // Threads per block and minimum steps per lane: the autotuned values of the
 // handle if pes_autotune set them, else the defaults (256 threads for FP32,
 // the 128 that the FP64 kernel is compiled for).
+static_assert(std::extent<decltype(pes_handle::tune)>::value > LIN_GH, "one tuning slot per linearisation");
+
 int choose_nt(const pes_handle* h, int lin, pes_precision prec)
 {
     const pes_tune& t = h->tune[lin][prec == PES_FP64 ? 1 : 0];

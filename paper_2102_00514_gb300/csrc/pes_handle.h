@@ -27,7 +27,7 @@ struct pes_handle {
     int* iters_done = nullptr;
     int* traj_iters = nullptr;   // [max_batch]: per-trajectory iterations of the last tolerance-mode run
     int traj_iters_B = 0;        // its number of trajectories (0: none recorded)
-    pes_tune tune[3][2];         // [linearisation][FP32, FP64]
+    pes_tune tune[4][2];         // [linearisation (LIN_*)][FP32, FP64]
     // device copies for pes_ieks_run_host (allocated by its first call)
     void* hy = nullptr;
     int64_t* hoff = nullptr;
