@@ -44,7 +44,11 @@ constexpr int G = 2;                   // zero rows around each trajectory (kern
 constexpr int TM = 128;                // rows per tile (MMA M)
 constexpr int NSTAGE = 8;              // activation tiles in flight per CTA
 constexpr int NLAYER = 6;              // 4 conv + 2 head
-constexpr int kTileBytes = TM * C * 2;
+// A convolution with TAPS > 1 loads one halo tile of TM + TAPS - 1 rows per row
+// tile (tap j reads its rows j .. j + TM - 1); a stage is rounded up to the
+// 1024-byte swizzle pattern.
+constexpr int halo_rows(int taps) { return TM + taps - 1; }
+constexpr int stage_bytes(int taps) { return (halo_rows(taps) * C * 2 + 1023) / 1024 * 1024; }
 constexpr int kWTileBytes = C * C * 2;
 constexpr int kEpiThreads = 128;
 constexpr int kConvThreads = 64 + kEpiThreads;
@@ -60,6 +64,8 @@ static_assert(kPOff[NLAYER] == PES_INIT_NPARAMS, "parameter packing");
 static_assert(kTaps[0] == 5 && kTaps[NLAYER - 1] == 1 && kWTile0[NLAYER - 1] + kTaps[NLAYER - 1] == kWTiles, "layer tables");
 constexpr int kOutCols = 8;            // the head's FP32 output row (5 used)
 constexpr int kWgradStride = C * C * 5 + C;
+constexpr int kOutWarpBytes = 32 * C * 2;                  // 32 bf16 rows of one epilogue warp
+constexpr int kOutStageOffset = 1024;                       // after the barriers and the bias (1024-aligned)
 
 enum { EPI_RELU = 0, EPI_F32 = 1, EPI_MASK = 2 };
 
@@ -104,13 +110,14 @@ PES_DEV void drain_wait(uint64_t* bar, uint32_t parity)
 template <int TAPS, int EPI>
 __global__ void __launch_bounds__(kConvThreads, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW,
-                   const ConvParams p)
+                   const __grid_constant__ CUtensorMap tmOut, const ConvParams p)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     uint8_t* sW = smem;                                   // TAPS weight tiles
-    uint8_t* sA = smem + TAPS * kWTileBytes;              // NSTAGE activation tiles
-    uint64_t* full = reinterpret_cast<uint64_t*>(sA + NSTAGE * kTileBytes);
+    constexpr int kStage = stage_bytes(TAPS);
+    uint8_t* sA = smem + TAPS * kWTileBytes;              // NSTAGE activation (halo) tiles
+    uint64_t* full = reinterpret_cast<uint64_t*>(sA + NSTAGE * kStage);
     uint64_t* empty = full + NSTAGE;
     uint64_t* wbar = empty + NSTAGE;
     uint64_t* tfull = wbar + 1;
@@ -119,6 +126,9 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
     float* sbias = reinterpret_cast<float*>(tslot + 4);   // 16-byte aligned, 64 floats
+    // bf16 outputs leave through TMA stores: per epilogue warp two 32-row
+    // staging tiles (4 KB each, 128-byte swizzled like the tensor map)
+    uint8_t* sOut = sA + NSTAGE * kStage + kOutStageOffset;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -143,7 +153,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     const uint32_t tbase = *tslot;
 
     if (warp == 0) {
-        // ---- producer: weights once, then TAPS shifted activation tiles per row tile
+        // ---- producer: weights once, then one halo tile per row tile
         if (lane == 0) {
             int armed[NSTAGE];
             for (int s = 0; s < NSTAGE; ++s) armed[s] = -1;
@@ -153,18 +163,14 @@ __global__ void __launch_bounds__(kConvThreads, 1)
             uint32_t ph = 0;
             bool ok = true;
             for (int tile = blockIdx.x; ok && tile < p.ntiles; tile += gridDim.x) {
-                for (int j = 0; j < TAPS; ++j) {
-                    if (!tc::wait_or_abort(empty + st, ph ^ 1, p.status, abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    tc::mbar_expect_tx(full + st, kTileBytes);
-                    tc::tma_load_2d(sA + st * kTileBytes, &tmA, 0, tile * TM + j - TAPS / 2, full + st);
-                    armed[st] = (int)ph;
-                    if (++st == NSTAGE) {
-                        st = 0;
-                        ph ^= 1;
-                    }
+                if (!tc::wait_or_abort(empty + st, ph ^ 1, p.status, abort_flag)) break;
+                // rows before 0 or past the end arrive as zeros and count in full
+                tc::mbar_expect_tx(full + st, halo_rows(TAPS) * C * 2);
+                tc::tma_load_2d(sA + st * kStage, &tmA, 0, tile * TM - TAPS / 2, full + st);
+                armed[st] = (int)ph;
+                if (++st == NSTAGE) {
+                    st = 0;
+                    ph ^= 1;
                 }
             }
             if (*abort_flag) {
@@ -185,24 +191,22 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                 tph ^= 1u << acc;
                 tc::fence_after_sync();
                 const uint32_t d = tbase + (uint32_t)(acc * C);
+                if (!tc::wait_or_abort(full + st, ph, p.status, abort_flag)) break;
+                tc::fence_after_sync();
+#pragma unroll
                 for (int j = 0; j < TAPS; ++j) {
-                    if (!tc::wait_or_abort(full + st, ph, p.status, abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    tc::fence_after_sync();
-                    const uint64_t ad = tc::smem_desc_sw128(sA + st * kTileBytes);
+                    // tap j: the TM rows starting at row j of the halo tile
+                    const uint64_t ad = tc::smem_desc_sw128(sA + st * kStage + j * C * 2);
                     const uint64_t bd = tc::smem_desc_sw128(sW + j * kWTileBytes);
 #pragma unroll
                     for (int k = 0; k < C / 16; ++k)   // +32 bytes along K per MMA
                         tc::mma_bf16(d, ad + 2 * k, bd + 2 * k, kIdesc, (j | k) != 0);
-                    tc::mma_commit(empty + st);
-                    if (++st == NSTAGE) {
-                        st = 0;
-                        ph ^= 1;
-                    }
                 }
-                if (!ok) break;
+                tc::mma_commit(empty + st);
+                if (++st == NSTAGE) {
+                    st = 0;
+                    ph ^= 1;
+                }
                 tc::mma_commit(tfull + acc);
                 acc ^= 1;
             }
@@ -213,9 +217,20 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         // ---- epilogue: one accumulator row per thread
         const int q = warp & 3;
         const int rin = q * 32 + lane;
-        int acc = 0;
+        uint8_t* wout = sOut + (warp - 2) * 2 * kOutWarpBytes;
+        int acc = 0, buf = 0;
         uint32_t fph = 0;
         for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
+            // the row's mask (and, backward, its ReLU source) are read before
+            // the accumulator is waited for, so their latency overlaps the MMAs
+            const int r = tile * TM + rin;
+            const bool live = r < p.R && p.rowmask[r];
+            uint4 src[EPI == EPI_MASK ? C / 8 : 1];
+            if constexpr (EPI == EPI_MASK) {
+                const uint4* s = reinterpret_cast<const uint4*>(p.relu_src + (size_t)r * C);
+#pragma unroll
+                for (int i = 0; i < C / 8; ++i) src[i] = live ? __ldg(s + i) : make_uint4(0, 0, 0, 0);
+            }
             bool ok = tc::wait_or_abort(tfull + acc, (fph >> acc) & 1u, p.status, abort_flag);
             if (!__all_sync(0xffffffffu, ok)) break;
             fph ^= 1u << acc;
@@ -227,19 +242,17 @@ __global__ void __launch_bounds__(kConvThreads, 1)
             tc::fence_before_sync();
             tc::mbar_arrive(tempty + acc);
             acc ^= 1;
-            const int r = tile * TM + rin;
-            if (r >= p.R || !p.rowmask[r]) continue;
             if constexpr (EPI == EPI_F32) {
-                float4* dst = reinterpret_cast<float4*>(p.out_f32 + (size_t)r * kOutCols);
-                dst[0] = make_float4(v[0] + sbias[0], v[1] + sbias[1], v[2] + sbias[2], v[3] + sbias[3]);
-                dst[1] = make_float4(v[4] + sbias[4], v[5] + sbias[5], v[6] + sbias[6], v[7] + sbias[7]);
+                if (live) {
+                    float4* dst = reinterpret_cast<float4*>(p.out_f32 + (size_t)r * kOutCols);
+                    dst[0] = make_float4(v[0] + sbias[0], v[1] + sbias[1], v[2] + sbias[2], v[3] + sbias[3]);
+                    dst[1] = make_float4(v[4] + sbias[4], v[5] + sbias[5], v[6] + sbias[6], v[7] + sbias[7]);
+                }
             } else {
                 if constexpr (EPI == EPI_MASK) {
-                    const uint4* src = reinterpret_cast<const uint4*>(p.relu_src + (size_t)r * C);
 #pragma unroll
                     for (int i = 0; i < C / 8; ++i) {
-                        const uint4 u = __ldg(src + i);
-                        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+                        const uint32_t w[4] = {src[i].x, src[i].y, src[i].z, src[i].w};
 #pragma unroll
                         for (int h = 0; h < 4; ++h) {
                             const float2 f = unpack_bf16x2(w[h]);
@@ -251,14 +264,31 @@ __global__ void __launch_bounds__(kConvThreads, 1)
 #pragma unroll
                     for (int c = 0; c < C; ++c) v[c] = fmaxf(v[c] + sbias[c], 0.f);
                 }
-                uint4* dst = reinterpret_cast<uint4*>(p.out + (size_t)r * C);
+                // stage the warp's 32 rows (gap rows as zeros, which they stay)
+                // and store them with one TMA box; the buffer used two tiles
+                // ago must have been read out first
+                uint8_t* stg = wout + buf * kOutWarpBytes;
+                if (lane == 0) tc::bulk_wait_read<1>();
+                __syncwarp();
 #pragma unroll
-                for (int i = 0; i < C / 8; ++i)
-                    dst[i] = make_uint4(pack_bf16x2(v[8 * i], v[8 * i + 1]), pack_bf16x2(v[8 * i + 2], v[8 * i + 3]),
-                                        pack_bf16x2(v[8 * i + 4], v[8 * i + 5]),
-                                        pack_bf16x2(v[8 * i + 6], v[8 * i + 7]));
+                for (int i = 0; i < C / 8; ++i) {
+                    const uint4 u = live ? make_uint4(pack_bf16x2(v[8 * i], v[8 * i + 1]),
+                                                      pack_bf16x2(v[8 * i + 2], v[8 * i + 3]),
+                                                      pack_bf16x2(v[8 * i + 4], v[8 * i + 5]),
+                                                      pack_bf16x2(v[8 * i + 6], v[8 * i + 7]))
+                                         : make_uint4(0, 0, 0, 0);
+                    *reinterpret_cast<uint4*>(stg + lane * 128 + ((i ^ (lane & 7)) << 4)) = u;
+                }
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) {
+                    tc::tma_store_2d(&tmOut, 0, tile * TM + q * 32, stg);
+                    tc::bulk_commit();
+                }
+                buf ^= 1;
             }
         }
+        if (EPI != EPI_F32 && lane == 0) tc::bulk_wait_all();
     }
 
     tc::fence_before_sync();
@@ -269,8 +299,12 @@ __global__ void __launch_bounds__(kConvThreads, 1)
 
 constexpr size_t conv_smem_bytes(int taps)
 {
-    return 1024 + (size_t)taps * kWTileBytes + (size_t)NSTAGE * kTileBytes + (2 * NSTAGE + 6) * 8 + 16 + C * 4;
+    return 1024 + (size_t)taps * kWTileBytes + (size_t)NSTAGE * stage_bytes(taps) + kOutStageOffset +
+           (size_t)4 * 2 * kOutWarpBytes;
 }
+static_assert(conv_smem_bytes(5) <= 227 * 1024 && conv_smem_bytes(1) <= 227 * 1024, "shared memory per CTA");
+// tap j of a halo tile ends at row j + TM, inside its stage
+static_assert(halo_rows(5) * C * 2 <= stage_bytes(5) && stage_bytes(1) == TM * C * 2, "halo stages");
 
 // ---- rows, features, loss, gradients, optimiser ----------------------------------
 
@@ -286,27 +320,60 @@ PES_DEV int traj_of_state(const int64_t* off, int B, int64_t k)
 }
 
 // Features of every state row and the row mask.
-template <typename T>
-__global__ void features_kernel(const T* y, const int64_t* off, int B, int64_t N, uint8_t* mask, bf16* X0)
+// Trajectory owning row r (0 .. B; B is the trailing gap): the last b whose
+// leading gap starts at or before r (trajectory b's rows begin at off[b] + G b).
+PES_DEV int traj_of_row(const int64_t* off, int B, int64_t r)
 {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += stride) {
-        const int b = traj_of_state(off, B, k);
-        const int64_t row = k + (int64_t)G * (b + 1);
-        float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (k == off[b]) {
-            f[5] = 1.f;
-        } else {
-            sincosf((float)y[k], &f[0], &f[1]);
-            sincosf((float)y[N + k], &f[2], &f[3]);
-            f[4] = 1.f;
+    int lo = 0, hi = B;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] + (int64_t)G * mid <= r) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Input features of every row (Sec. 5's initialiser input): a state's
+// (sin y1, cos y1, sin y2, cos y2, 1, 0) or the prior row's (0, 0, 0, 0, 0, 1),
+// zeros on the gap rows, and the row mask. A warp owns 32 consecutive rows, one
+// lane each; it then stores them as eight 512-byte runs (four rows each), the
+// first 16 bytes of a row taken from its lane by shuffles.
+template <typename T>
+__global__ void features_kernel(const T* y, const int64_t* off, int B, int64_t N, int64_t R, uint8_t* mask, bf16* X0)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (R + 31) / 32;
+    const int64_t wstride = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; w < nw; w += wstride) {
+        const int64_t r = w * 32 + lane;
+        uint4 u = make_uint4(0, 0, 0, 0);
+        if (r < R) {
+            const int b = traj_of_row(off, B, r);
+            const int64_t k = r - (int64_t)G * (b + 1);
+            const bool state = b < B && r - (off[b] + (int64_t)G * b) >= G && k >= 0 && k < N;
+            if (state) {
+                float f[4] = {0.f, 0.f, 0.f, 0.f};
+                const bool prior = k == off[b];
+                if (!prior) {
+                    sincosf((float)y[k], &f[0], &f[1]);
+                    sincosf((float)y[N + k], &f[2], &f[3]);
+                }
+                u = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]),
+                               pack_bf16x2(prior ? 0.f : 1.f, prior ? 1.f : 0.f), 0u);
+            }
+            mask[r] = state ? 1 : 0;
         }
-        uint4* dst = reinterpret_cast<uint4*>(X0 + (size_t)row * C);
-        dst[0] = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]), pack_bf16x2(f[4], f[5]),
-                            pack_bf16x2(f[6], f[7]));
+        uint4* dst = reinterpret_cast<uint4*>(X0) + (size_t)w * 32 * (C / 8);
 #pragma unroll
-        for (int i = 1; i < C / 8; ++i) dst[i] = make_uint4(0, 0, 0, 0);
-        mask[row] = 1;
+        for (int i = 0; i < C / 8; ++i) {
+            const int src = 4 * i + (lane >> 3);   // row w * 32 + src, chunk lane & 7
+            uint4 v;
+            v.x = __shfl_sync(0xffffffffu, u.x, src);
+            v.y = __shfl_sync(0xffffffffu, u.y, src);
+            v.z = __shfl_sync(0xffffffffu, u.z, src);
+            v.w = __shfl_sync(0xffffffffu, u.w, src);
+            if (w * 32 + src < R) dst[32 * i + lane] = (lane & 7) == 0 ? v : make_uint4(0, 0, 0, 0);
+        }
     }
 }
 
@@ -315,8 +382,8 @@ struct ZeroList {
     int n;
 };
 
-// The gap rows: mask 0 and zero in every listed activation buffer.
-__global__ void gap_rows_kernel(const int64_t* off, int B, int64_t N, int64_t R, uint8_t* mask, ZeroList zl)
+// Zero the gap rows of every listed buffer.
+__global__ void gap_rows_kernel(const int64_t* off, int B, int64_t N, int64_t R, ZeroList zl)
 {
     const int64_t total = (int64_t)G * (B + 1);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
@@ -325,7 +392,6 @@ __global__ void gap_rows_kernel(const int64_t* off, int B, int64_t N, int64_t R,
         if (o < 0 || o > N) continue;   // malformed offsets: leave the row alone
         const int64_t row = o + (int64_t)G * b + (i % G);
         if (row >= R) continue;
-        mask[row] = 0;
         for (int j = 0; j < zl.n; ++j) {
             uint4* dst = reinterpret_cast<uint4*>(zl.buf[j] + (size_t)row * C);
 #pragma unroll
@@ -513,15 +579,25 @@ __global__ void publish_kernel(const float* p, bf16* Wf, bf16* Wb, float* bias)
     }
 }
 
+// x = mu + sigma * output, in FP32 (the output is a bf16 network's; FP64 is a
+// slow pipe on this GPU) and stored in the caller's precision.
 template <typename T>
 __global__ void denorm_kernel(const float* o, const int64_t* off, int B, int64_t N, Norm nm, T* x)
 {
+    float mu[5], sg[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        mu[c] = (float)nm.mu[c];
+        sg[c] = (float)nm.sigma[c];
+    }
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += stride) {
         const int b = traj_of_state(off, B, k);
-        const int64_t row = k + (int64_t)G * (b + 1);
+        const float4* row = reinterpret_cast<const float4*>(o + (size_t)(k + (int64_t)G * (b + 1)) * kOutCols);
+        const float4 lo = __ldg(row), hi = __ldg(row + 1);
+        const float v[5] = {lo.x, lo.y, lo.z, lo.w, hi.x};
 #pragma unroll
-        for (int c = 0; c < 5; ++c) x[(size_t)c * N + k] = (T)(nm.mu[c] + nm.sigma[c] * (double)o[row * kOutCols + c]);
+        for (int c = 0; c < 5; ++c) x[(size_t)c * N + k] = (T)fmaf(sg[c], v[c], mu[c]);
     }
 }
 
@@ -600,8 +676,11 @@ template <int TAPS, int EPI>
 cudaError_t launch_conv(pes_init_net* n, const bf16* in, int64_t R, bool backward, int layer, bf16* out,
                         float* out_f32, const bf16* relu_src, cudaStream_t st)
 {
-    CUtensorMap mA;
-    if (!make_map(&mA, in, (uint64_t)R, TM)) return cudaErrorInvalidValue;
+    CUtensorMap mA, mOut;
+    if (!make_map(&mA, in, (uint64_t)R, halo_rows(TAPS))) return cudaErrorInvalidValue;
+    // bf16 outputs: boxes of the 32 rows of one epilogue warp (the head's FP32
+    // output is stored directly; its map is a placeholder)
+    if (!make_map(&mOut, out ? (const void*)out : (const void*)in, (uint64_t)R, 32)) return cudaErrorInvalidValue;
     ConvParams p;
     p.R = (int)R;
     p.ntiles = (int)((R + TM - 1) / TM);
@@ -617,7 +696,7 @@ cudaError_t launch_conv(pes_init_net* n, const bf16* in, int64_t R, bool backwar
                                          (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = (int)std::min<int64_t>(p.ntiles, n->num_sms);
-    conv_tc_kernel<TAPS, EPI><<<grid, kConvThreads, smem, st>>>(mA, backward ? n->mapWb : n->mapWf, p);
+    conv_tc_kernel<TAPS, EPI><<<grid, kConvThreads, smem, st>>>(mA, backward ? n->mapWb : n->mapWf, mOut, p);
     return cudaGetLastError();
 }
 
@@ -637,21 +716,19 @@ pes_status prepare_rows(pes_init_net* n, const T* y, const int64_t* off, int32_t
                         cudaStream_t st, int64_t* R_out)
 {
     const int64_t R = N + (int64_t)G * (B + 1);
-    const int blocks = (int)std::min<int64_t>((N + 255) / 256, (int64_t)n->num_sms * 16);
-    features_kernel<T><<<blocks, 256, 0, st>>>(y, off, B, N, n->mask, n->act[0]);
+    const int blocks = (int)std::min<int64_t>((R + 255) / 256, (int64_t)n->num_sms * 16);
+    features_kernel<T><<<blocks, 256, 0, st>>>(y, off, B, N, R, n->mask, n->act[0]);
     NET_CUDA(n, cudaGetLastError());
-    ZeroList zl;
-    zl.n = 0;
-    zl.buf[zl.n++] = n->act[0];
-    for (int l = 1; l < NLAYER; ++l) zl.buf[zl.n++] = n->act[l];
+    // Every convolution writes zeros on the gap rows of its output; the loss
+    // gradient does not, and the weight gradients sum over all rows.
     if (training) {
+        ZeroList zl;
+        zl.n = 0;
         zl.buf[zl.n++] = n->dO;
-        zl.buf[zl.n++] = n->dA;
-        zl.buf[zl.n++] = n->dB;
+        const int gblocks = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)G * (B + 1) + 255) / 256, 1024));
+        gap_rows_kernel<<<gblocks, 256, 0, st>>>(off, B, N, R, zl);
+        NET_CUDA(n, cudaGetLastError());
     }
-    const int gblocks = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)G * (B + 1) + 255) / 256, 1024));
-    gap_rows_kernel<<<gblocks, 256, 0, st>>>(off, B, N, R, n->mask, zl);
-    NET_CUDA(n, cudaGetLastError());
     *R_out = R;
     return PES_OK;
 }

@@ -27,6 +27,27 @@ PES_DEV void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64
         : "memory");
 }
 
+// 2-D tiled TMA store of the shared-memory box at (x, y) (both >= 0; rows past
+// the end are not written), in the issuing thread's bulk async-group.
+PES_DEV void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src)
+{
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map), "r"(x),
+                 "r"(y), "r"(smem_u32(src))
+                 : "memory");
+}
+
+PES_DEV void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+// Wait until at most N of this thread's bulk groups still read shared memory.
+template <int N>
+PES_DEV void bulk_wait_read()
+{
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+
+// Wait until all of this thread's bulk groups have completed.
+PES_DEV void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 PES_DEV void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
@@ -78,8 +99,10 @@ PES_DEV void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync
 // ---- descriptors ---------------------------------------------------------------
 
 // Shared-memory matrix descriptor of a K-major, 128-byte-swizzled bf16 tile
-// whose 8-row atoms are 1024 bytes apart (start address 1024-aligned, or
-// advanced along K inside the atom by multiples of 32 bytes).
+// whose 8-row atoms are 1024 bytes apart, inside a swizzled region that begins
+// 1024-aligned. The tile may start at any 128-byte row of that region: the
+// swizzle follows the shared-memory address itself, so the base offset stays
+// 0. Advancing along K inside the row adds multiples of 32 bytes.
 PES_DEV uint64_t smem_desc_sw128(const void* tile)
 {
     const uint64_t addr = smem_u32(tile);
