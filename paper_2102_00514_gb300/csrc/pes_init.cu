@@ -50,8 +50,8 @@ constexpr int NLAYER = 6;              // 4 conv + 2 head
 constexpr int halo_rows(int taps) { return TM + taps - 1; }
 constexpr int stage_bytes(int taps) { return (halo_rows(taps) * C * 2 + 1023) / 1024 * 1024; }
 constexpr int kWTileBytes = C * C * 2;
-constexpr int kEpiThreads = 128;
-constexpr int kConvThreads = 64 + kEpiThreads;
+constexpr int kEpiThreads = 128;      // one epilogue warpgroup (per accumulator)
+constexpr int kConvThreads = 64 + 2 * kEpiThreads;
 constexpr uint32_t kTmemCols = 128;    // two 64-column FP32 accumulators
 constexpr uint32_t kIdesc = tc::idesc_bf16_f32(TM, C);
 
@@ -126,8 +126,8 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
     float* sbias = reinterpret_cast<float*>(tslot + 4);   // 16-byte aligned, 64 floats
-    // bf16 outputs leave through TMA stores: per epilogue warp two 32-row
-    // staging tiles (4 KB each, 128-byte swizzled like the tensor map)
+    // bf16 outputs leave through TMA stores: per epilogue warp one 32-row
+    // staging tile (4 KB, 128-byte swizzled like the tensor map)
     uint8_t* sOut = sA + NSTAGE * kStage + kOutStageOffset;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -214,13 +214,14 @@ __global__ void __launch_bounds__(kConvThreads, 1)
             drain_wait(done, 0);
         }
     } else {
-        // ---- epilogue: one accumulator row per thread
-        const int q = warp & 3;
+        // ---- epilogue: two warpgroups, group g drains accumulator g (the
+        // CTA's tiles alternate between them), one accumulator row per thread
+        const int g = (warp - 2) >> 2;
+        const int q = warp & 3;   // TMEM lane quadrant this warp may read
         const int rin = q * 32 + lane;
-        uint8_t* wout = sOut + (warp - 2) * 2 * kOutWarpBytes;
-        int acc = 0, buf = 0;
+        uint8_t* stg = sOut + (warp - 2) * kOutWarpBytes;
         uint32_t fph = 0;
-        for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
+        for (int tile = blockIdx.x + g * gridDim.x; tile < p.ntiles; tile += 2 * gridDim.x) {
             // the row's mask (and, backward, its ReLU source) are read before
             // the accumulator is waited for, so their latency overlaps the MMAs
             const int r = tile * TM + rin;
@@ -231,17 +232,14 @@ __global__ void __launch_bounds__(kConvThreads, 1)
 #pragma unroll
                 for (int i = 0; i < C / 8; ++i) src[i] = live ? __ldg(s + i) : make_uint4(0, 0, 0, 0);
             }
-            bool ok = tc::wait_or_abort(tfull + acc, (fph >> acc) & 1u, p.status, abort_flag);
+            bool ok = tc::wait_or_abort(tfull + g, fph, p.status, abort_flag);
             if (!__all_sync(0xffffffffu, ok)) break;
-            fph ^= 1u << acc;
+            fph ^= 1u;
             tc::fence_after_sync();
             float v[C];
-            const uint32_t ta = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * C);
-#pragma unroll
-            for (int i = 0; i < C / 16; ++i) tc::tmem_ld16(ta + 16 * i, v + 16 * i);
+            tc::tmem_ld64(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * C), v);
             tc::fence_before_sync();
-            tc::mbar_arrive(tempty + acc);
-            acc ^= 1;
+            tc::mbar_arrive(tempty + g);
             if constexpr (EPI == EPI_F32) {
                 if (live) {
                     float4* dst = reinterpret_cast<float4*>(p.out_f32 + (size_t)r * kOutCols);
@@ -265,10 +263,9 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                     for (int c = 0; c < C; ++c) v[c] = fmaxf(v[c] + sbias[c], 0.f);
                 }
                 // stage the warp's 32 rows (gap rows as zeros, which they stay)
-                // and store them with one TMA box; the buffer used two tiles
-                // ago must have been read out first
-                uint8_t* stg = wout + buf * kOutWarpBytes;
-                if (lane == 0) tc::bulk_wait_read<1>();
+                // and store them with one TMA box; the store of the group's
+                // previous tile must have read the buffer out first
+                if (lane == 0) tc::bulk_wait_read<0>();
                 __syncwarp();
 #pragma unroll
                 for (int i = 0; i < C / 8; ++i) {
@@ -285,7 +282,6 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                     tc::tma_store_2d(&tmOut, 0, tile * TM + q * 32, stg);
                     tc::bulk_commit();
                 }
-                buf ^= 1;
             }
         }
         if (EPI != EPI_F32 && lane == 0) tc::bulk_wait_all();
@@ -300,7 +296,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
 constexpr size_t conv_smem_bytes(int taps)
 {
     return 1024 + (size_t)taps * kWTileBytes + (size_t)NSTAGE * stage_bytes(taps) + kOutStageOffset +
-           (size_t)4 * 2 * kOutWarpBytes;
+           (size_t)2 * 4 * kOutWarpBytes;
 }
 static_assert(conv_smem_bytes(5) <= 227 * 1024 && conv_smem_bytes(1) <= 227 * 1024, "shared memory per CTA");
 // tap j of a halo tile ends at row j + TM, inside its stage
