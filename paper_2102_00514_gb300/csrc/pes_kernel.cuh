@@ -891,20 +891,51 @@ PES_DEV void copy_elem_to_global(const T* src, T* dst)
     for (int i = threadIdx.x; i < NE; i += blockDim.x) dst[i] = src[i];
 }
 
+// n blocks' aggregates (NE scalars each) from global into shared memory, eight
+// loads in flight per thread before their stores (one L2 round trip per eight
+// scalars instead of one per scalar).
+template <typename T, int NT, int NE>
+PES_DEV void load_aggregates(const T* src, T* dst, int n)
+{
+    constexpr int U = 8;
+    const int total = n * NE;
+#pragma unroll 1
+    for (int i0 = threadIdx.x; i0 < total; i0 += U * NT) {
+        T v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * NT;
+            v[u] = i < total ? src[i] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * NT;
+            if (i < total) dst[i] = v[u];
+        }
+    }
+}
+
 // Filtering levels 2-4. elem[t] holds lane t's folded element on entry; returns
 // the Gaussian of the state before lane t's chunk.
-// Filtering levels 2-4. elem[t] holds lane t's folded element on entry; returns
-// the Gaussian of the state before lane t's chunk.
+//
+// The operators of a tree level are issue-bound, one thread's instruction
+// stream each: a level costs one operator's time only while no SM
+// sub-partition runs two warps of it. So the operator at element 2t + 1 (or
+// 2t) runs on thread t < NT / 2: a level's active threads then sit in at most
+// NT / 64 warps, one per sub-partition, where the element's own thread would
+// spread them over all NT / 32 warps.
 template <typename T, int NT>
 PES_DEV void filter_block_scan(const KParams<T>& p, FElem<T>* elem, FElem<T>* top, Gauss<T>* gs,
                                Gauss<T>* gblock, unsigned& gen, Gauss<T>& out, int it)
 {
     const int t = threadIdx.x;
+    const bool half = t < NT / 2;
+    const int to = 2 * t + 1, te = 2 * t;   // the odd and the even element of thread t
     __syncthreads();
     PES_PHASE(p, it, 1);
 #pragma unroll 1
     for (int s = 1; s < NT; s <<= 1) {
-        if (((t + 1) & (2 * s - 1)) == 0) combine_filter(elem[t - s], elem[t], elem[t]);
+        if (half && ((to + 1) & (2 * s - 1)) == 0) combine_filter(elem[to - s], elem[to], elem[to]);
         __syncthreads();
     }
     copy_elem_to_global<T, FE>(reinterpret_cast<const T*>(&elem[NT - 1]), p.aggF + (size_t)blockIdx.x * FE);
@@ -923,12 +954,11 @@ PES_DEV void filter_block_scan(const KParams<T>& p, FElem<T>* elem, FElem<T>* to
     for (int c0 = 0; c0 < j; c0 += NT) {
         const int n = min(NT, j - c0);
         __syncthreads();
-        for (int i = t; i < n * FE; i += NT)
-            reinterpret_cast<T*>(top)[i] = p.aggF[(size_t)c0 * FE + i];
+        load_aggregates<T, NT, FE>(p.aggF + (size_t)c0 * FE, reinterpret_cast<T*>(top), n);
         __syncthreads();
 #pragma unroll 1
         for (int s = 1; s < n; s <<= 1) {
-            if ((t & (2 * s - 1)) == 0 && t + s < n) combine_filter(top[t], top[t + s], top[t]);
+            if (half && (te & (2 * s - 1)) == 0 && te + s < n) combine_filter(top[te], top[te + s], top[te]);
             __syncthreads();
         }
         if (t == 0) apply_filter(*gblock, top[0], *gblock);
@@ -940,12 +970,12 @@ PES_DEV void filter_block_scan(const KParams<T>& p, FElem<T>* elem, FElem<T>* to
     __syncthreads();
 #pragma unroll 1
     for (int s = NT / 2; s >= 1; s >>= 1) {
-        if (((t + 1) & (2 * s - 1)) == 0) {
-            const Gauss<T> gin = gs[t];
+        if (half && ((to + 1) & (2 * s - 1)) == 0) {
+            const Gauss<T> gin = gs[to];
             Gauss<T> gr;
-            apply_filter(gin, elem[t - s], gr);
-            gs[t - s] = gin;
-            gs[t] = gr;
+            apply_filter(gin, elem[to - s], gr);
+            gs[to - s] = gin;
+            gs[to] = gr;
         }
         __syncthreads();
     }
@@ -961,11 +991,13 @@ PES_DEV void smoother_block_scan(const KParams<T>& p, SElem<T>* elem, SElem<T>* 
                                  Gauss<T>* gblock, unsigned& gen, Gauss<T>& out, int it)
 {
     const int t = threadIdx.x;
+    const bool half = t < NT / 2;
+    const int te = 2 * t;   // the operators run as in filter_block_scan
     __syncthreads();
     PES_PHASE(p, it, 7);
 #pragma unroll 1
     for (int s = 1; s < NT; s <<= 1) {
-        if ((t & (2 * s - 1)) == 0) combine_smoother(elem[t], elem[t + s], elem[t]);
+        if (half && (te & (2 * s - 1)) == 0) combine_smoother(elem[te], elem[te + s], elem[te]);
         __syncthreads();
     }
     copy_elem_to_global<T, SE>(reinterpret_cast<const T*>(&elem[0]), p.aggS + (size_t)blockIdx.x * SE);
@@ -985,12 +1017,11 @@ PES_DEV void smoother_block_scan(const KParams<T>& p, SElem<T>* elem, SElem<T>* 
         const int n = min(NT, c1 - (j + 1));
         const int c0 = c1 - n;
         __syncthreads();
-        for (int i = t; i < n * SE; i += NT)
-            reinterpret_cast<T*>(top)[i] = p.aggS[(size_t)c0 * SE + i];
+        load_aggregates<T, NT, SE>(p.aggS + (size_t)c0 * SE, reinterpret_cast<T*>(top), n);
         __syncthreads();
 #pragma unroll 1
         for (int s = 1; s < n; s <<= 1) {
-            if ((t & (2 * s - 1)) == 0 && t + s < n) combine_smoother(top[t], top[t + s], top[t]);
+            if (half && (te & (2 * s - 1)) == 0 && te + s < n) combine_smoother(top[te], top[te + s], top[te]);
             __syncthreads();
         }
         if (t == 0) apply_smoother(top[0], *gblock, *gblock);
@@ -1002,12 +1033,12 @@ PES_DEV void smoother_block_scan(const KParams<T>& p, SElem<T>* elem, SElem<T>* 
     __syncthreads();
 #pragma unroll 1
     for (int s = NT / 2; s >= 1; s >>= 1) {
-        if ((t & (2 * s - 1)) == 0) {
-            const Gauss<T> gin = gs[t];
+        if (half && (te & (2 * s - 1)) == 0) {
+            const Gauss<T> gin = gs[te];
             Gauss<T> gl;
-            apply_smoother(elem[t + s], gin, gl);
-            gs[t + s] = gin;
-            gs[t] = gl;
+            apply_smoother(elem[te + s], gin, gl);
+            gs[te + s] = gin;
+            gs[te] = gl;
         }
         __syncthreads();
     }
