@@ -885,6 +885,16 @@ PES_DEV bool rts_chunk(const KParams<T>& p, int64_t a, int64_t e, int lane, cons
 
 // ---- block and grid levels -------------------------------------------------------------
 
+// The filtering operator of the tree levels as one out-of-line function: the
+// lane and top-level trees then run the same copy of its ~2,000 instructions,
+// which stays in the instruction cache from level to level, where two inlined
+// copies were each fetched afresh (the smaller operators stay inline).
+template <typename T>
+__device__ __noinline__ void tree_combine_filter(const FElem<T>& a, const FElem<T>& b, FElem<T>& o)
+{
+    combine_filter(a, b, o);
+}
+
 template <typename T, int NE>
 PES_DEV void copy_elem_to_global(const T* src, T* dst)
 {
@@ -935,7 +945,7 @@ PES_DEV void filter_block_scan(const KParams<T>& p, FElem<T>* elem, FElem<T>* to
     PES_PHASE(p, it, 1);
 #pragma unroll 1
     for (int s = 1; s < NT; s <<= 1) {
-        if (half && ((to + 1) & (2 * s - 1)) == 0) combine_filter(elem[to - s], elem[to], elem[to]);
+        if (half && ((to + 1) & (2 * s - 1)) == 0) tree_combine_filter(elem[to - s], elem[to], elem[to]);
         __syncthreads();
     }
     copy_elem_to_global<T, FE>(reinterpret_cast<const T*>(&elem[NT - 1]), p.aggF + (size_t)blockIdx.x * FE);
@@ -958,7 +968,7 @@ PES_DEV void filter_block_scan(const KParams<T>& p, FElem<T>* elem, FElem<T>* to
         __syncthreads();
 #pragma unroll 1
         for (int s = 1; s < n; s <<= 1) {
-            if (half && (te & (2 * s - 1)) == 0 && te + s < n) combine_filter(top[te], top[te + s], top[te]);
+            if (half && (te & (2 * s - 1)) == 0 && te + s < n) tree_combine_filter(top[te], top[te + s], top[te]);
             __syncthreads();
         }
         if (t == 0) apply_filter(*gblock, top[0], *gblock);
