@@ -648,16 +648,27 @@ def main():
                         fi["mixed_means"] = worst(xmix[name][0], name, last, "x")
                         fi["mixed_covs"] = worst(xmix[name][1], name, last, "P")
                     par[name]["final_iteration"] = fi
-            tol_ok = all(v["fp32_means"] <= 1e-4 and v["fp32_covs"] <= 1e-4 for v in par.values())
             scope = ("full workload" if len(units) == 1 else
                      f"{len(units)} sampled trajectories, each smoothed alone by the oracle (worst reported)")
+
+            def within(rows, prefix, tol):
+                keys = (prefix + "_means", prefix + "_covs")
+                got = [r for r in rows if all(k in r for k in keys)]
+                return all(r[k] <= tol for r in got for k in keys) if got else None
+
+            finals = [v["final_iteration"] for v in par.values() if "final_iteration" in v]
+            # one verdict per check: the final iteration from a given nominal is what
+            # the kernel's precision decides; all iterations also carry the
+            # iteration's own amplification wherever the oracle has not converged
             result["parity"] = {"vs": f"CPU FP64 oracle, {scope}; final_iteration: one oracle iteration from "
                                       "the GPU's own FP32 nominal of the first iters-1 iterations",
                                 "rel_frobenius": par,
-                                "fp32_tol": 1e-4, "fp64_tol": 1e-9, "fp32_within_tol": tol_ok}
-            if xmix:
-                result["parity"]["mixed_within_tol"] = all(v["mixed_means"] <= 1e-4 and v["mixed_covs"] <= 1e-4
-                                                           for v in par.values())
+                                "tol": {"fp32": 1e-4, "fp64": 1e-9},
+                                "within_tol": {"fp64_all_iterations": within(par.values(), "fp64", 1e-9),
+                                               "fp32_final_iteration": within(finals, "fp32", 1e-4),
+                                               "mixed_final_iteration": within(finals, "mixed", 1e-4),
+                                               "fp32_all_iterations": within(par.values(), "fp32", 1e-4),
+                                               "mixed_all_iterations": within(par.values(), "mixed", 1e-4)}}
         print(json.dumps(result), flush=True)
     sm.close()
     if dist is not None:
