@@ -12,9 +12,9 @@ import torch
 import oracle
 from paper_2102_00514_gb300 import pes, synth
 
-# FP64: rounding-order differences only (the benchmark spec's bound for FP64).
+# FP64: rounding-order differences only (1e-9 relative).
 TOL_FP64 = 1e-9
-# FP32 means and covariances after the final iteration (the benchmark spec's bound).
+# FP32 means and covariances after the final iteration (1e-4 relative).
 TOL_FP32 = 1e-4
 
 
