@@ -186,6 +186,73 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+class NvmlPoller:
+    """SM clock and clock-event reasons read through NVML every millisecond on a
+    host thread (read-only queries), so that a timed region of a few tens of
+    milliseconds still holds samples."""
+    # clock-event reason bits of nvml.h
+    REASONS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown",
+               0x4: "sw_power_cap", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, device: int, fallback_index: int):
+        import ctypes
+        import threading
+        self.ctypes, self.threading = ctypes, threading
+        self.lib, self.h, self.thread, self.samples = None, None, None, []
+        self.stop_flag = False
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return
+            h = ctypes.c_void_p()
+            found = False
+            try:
+                import torch
+                pr = torch.cuda.get_device_properties(device)
+                for fmt in ("%08x:%02x:%02x.0", "%04x:%02x:%02x.0"):
+                    bus = (fmt % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)).encode()
+                    if lib.nvmlDeviceGetHandleByPciBusId_v2(bus, ctypes.byref(h)) == 0:
+                        found = True
+                        break
+            except Exception:
+                found = False
+            if not found and lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(fallback_index), ctypes.byref(h)) != 0:
+                return
+            self.lib, self.h = lib, h
+        except OSError:
+            self.lib = None
+
+    def _run(self):
+        ct = self.ctypes
+        clk, mx, rs = ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        reasons = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None)
+        while not self.stop_flag:
+            ok = self.lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(clk)) == 0   # NVML_CLOCK_SM
+            ok = ok and self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ct.byref(mx)) == 0
+            ok = ok and reasons is not None and reasons(self.h, ct.byref(rs)) == 0
+            if ok:
+                self.samples.append((clk.value, mx.value, rs.value))
+            time.sleep(0.001)
+
+    def start(self):
+        if self.lib is None:
+            return
+        self.thread = self.threading.Thread(target=self._run, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        if self.thread is None:
+            return None
+        self.stop_flag = True
+        self.thread.join()
+        if not self.samples:
+            return None
+        sm = [c for c, _, _ in self.samples]
+        reasons = sorted({name for _, _, r in self.samples for bit, name in self.REASONS.items() if r & bit})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(m for _, m, _ in self.samples),
+                "reasons": reasons, "samples": len(self.samples), "source": "NVML, every 1 ms during the timed region"}
+
+
 def rel_err(a, b, offsets):
     import numpy as np
     worst = 0.0
@@ -368,8 +435,12 @@ def main():
     barrier()
     torch.cuda.synchronize()
 
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    smi_index = int(vis.split(",")[local]) if vis and vis.split(",")[local].isdigit() else local
     clocks = ClockSampler()
     clocks.start()
+    poller = NvmlPoller(torch.cuda.current_device(), smi_index)
+    poller.start()
     step_ms, meth_ms = [], {name: [] for name, _ in methods}
     for _ in range(args.steps):
         flush.zero_()
@@ -382,10 +453,15 @@ def main():
         step_ms.append(sum(per))
     sm.sync()
     torch.cuda.synchronize()
+    polled = poller.stop()
     barrier()
     torch.cuda.synchronize()
-    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
-    clk = clocks.stop(int(vis.split(",")[local]) if vis and vis.split(",")[local].isdigit() else local)
+    smi = clocks.stop(smi_index)
+    # the NVML poll is the one with samples inside a short timed region;
+    # nvidia-smi (200 ms interval) is kept beside it
+    clk = polled if polled is not None else smi
+    if clk is not None and polled is not None and smi is not None:
+        clk = dict(clk, nvidia_smi=smi)
 
     total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
     work_per_step = len(methods) * steps * iters
