@@ -745,6 +745,15 @@ def main():
                                                "mixed_final_iteration": within(finals, "mixed", 1e-4),
                                                "fp32_all_iterations": within(par.values(), "fp32", 1e-4),
                                                "mixed_all_iterations": within(par.values(), "mixed", 1e-4)}}
+            # the rate of this run's fastest precision whose final iteration meets
+            # the tolerance (FP32, else MIXED), beside the FP32 `value`
+            wt = result["parity"]["within_tol"]
+            if wt["fp32_final_iteration"]:
+                result["at_oracle_tol"] = {"precision": "fp32", "value": result["value"], "unit": UNIT}
+            elif wt["mixed_final_iteration"] and "mixed" in result:
+                result["at_oracle_tol"] = {"precision": "mixed", "value": result["mixed"]["value"], "unit": UNIT}
+            else:
+                result["at_oracle_tol"] = None
         print(json.dumps(result), flush=True)
     sm.close()
     if dist is not None:
