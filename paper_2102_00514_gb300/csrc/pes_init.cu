@@ -7,20 +7,25 @@
 // k + 2 (b + 1), so that two zero rows separate consecutive trajectories and
 // frame the batch. A kernel-5 convolution over rows then sees zeros outside
 // each trajectory, which is the "same" zero padding per trajectory, and the
-// 1x1 layers need no special case. Gap rows are zeroed once per call and never
-// written; R = N + 2 (B + 1) rows in all.
+// 1x1 layers need no special case. The features kernel writes every row of the
+// input (zeros on the gap rows), every bf16 layer writes zeros on the gap rows
+// of its output (the FP32 head writes the state rows only) and the loss
+// gradient's gap rows are zeroed apart; R = N + 2 (B + 1) rows in all.
 //
 // Every layer is one GEMM on the tensor cores (conv_tc_kernel): a tile of 128
 // rows times K = taps x 64 input channels, N = 64 output channels, bf16
-// operands and an FP32 accumulator in tensor memory. The activation tile for
-// tap j is the 128 rows starting j - 2 rows earlier, loaded by TMA (rows
-// outside 0..R-1 read as zero); the layer's weights, one 64 x 64 tile per tap,
-// stay in shared memory for the whole launch. Warp 0 issues the loads, warp 1
-// the MMAs, warps 2-5 drain the accumulators (bias, ReLU or the ReLU mask of
-// the backward pass, bf16 store); two accumulators in TMEM let the epilogue of
-// one tile overlap the MMAs of the next. The backward pass through a layer is
-// the same GEMM with the weights transposed and the taps reversed. Weight
-// gradients (a reduction over rows) run on the CUDA cores in FP32.
+// operands and an FP32 accumulator in tensor memory. Per row tile one TMA load
+// brings the 128 + taps - 1 rows starting taps / 2 rows earlier (rows outside
+// 0..R-1 read as zero), and tap j's MMAs read them from row j on; the layer's
+// weights, one 64 x 64 tile per tap, stay in shared memory for the whole
+// launch. Warp 0 issues the loads, warp 1 the MMAs; two accumulators in TMEM,
+// drained by two epilogue warpgroups (warps 2-5 and 6-9), let the epilogues of
+// consecutive tiles run at once and overlap the MMAs of the next. An epilogue
+// applies bias and ReLU (or the ReLU mask of the backward pass), stages its
+// warp's 32 bf16 rows in shared memory and writes them with one TMA store. The
+// backward pass through a layer is the same GEMM with the weights transposed
+// and the taps reversed. Weight gradients (a reduction over rows) run on the
+// CUDA cores in FP32.
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
