@@ -64,6 +64,8 @@ def parse_args():
     ap.add_argument("--profile", choices=["ieks", "cubature", "init"], default=None,
                     help="profiling case: only `warmup` + 1 FP32 runs of one method, no JSON line")
     ap.add_argument("--prec", choices=["fp32", "fp64"], default="fp32", help="precision of --profile")
+    ap.add_argument("--sweep", action="store_true",
+                    help="the length sweep T = 2^10 .. 2^20: one JSON line per length, no benchmark line")
     return ap.parse_args()
 
 
@@ -108,6 +110,72 @@ def run_profile_case(args):
         sm.sync()
         print(f"run {i}: {1e3 * (time.perf_counter() - t0):.3f} ms", flush=True)
     sm.close()
+
+
+def run_sweep(args):
+    """--sweep: one trajectory of each length T = 2^10 .. 2^20, both methods,
+    `iters` iterations: milliseconds per run in FP32, MIXED and FP64 (CUDA events,
+    median of 5 after 2 warm-up runs, autotuned launch shapes, L2 not flushed),
+    and the error of the final iteration (FP32 and MIXED) against one oracle
+    iteration from the GPU's own FP32 nominal of the first iters - 1 iterations.
+    One JSON line per length."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2102_00514_gb300 import build, pes, synth
+    build.build_all()
+    iters = args.iters
+    r32 = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)
+    methods = (("ieks", pes.IEKS, oracle.IEKS), ("cubature", pes.CUBATURE, oracle.CUBATURE))
+    for e in range(10, 21):
+        T = 1 << e
+        wl = synth.workload(f"sweep_T{T}")
+        N = wl["y"].shape[1]
+        sm = pes.Smoother(N, 1)
+        model = pes.Model.from_workload(wl)
+        dev = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+        ins = {prec: (dev(wl["y"], dt), dev(wl["offsets"], torch.int64), dev(wl["m0"], dt), dev(wl["P0"], dt))
+               for prec, dt in ((pes.FP32, torch.float32), (pes.FP64, torch.float64))}
+        ins[pes.MIXED] = ins[pes.FP32]
+        line = {"T": T, "iterations": iters, "l2": "not flushed (the sweep is a diagnostic, not the benchmark)"}
+        for name, m, om in methods:
+            rec = {}
+            for prec in (pes.FP32, pes.FP64):
+                y, off, m0, P0 = ins[prec]
+                sm.autotune(model, m, prec, y, off, m0, P0, iters=2)
+            for key, prec in (("fp32", pes.FP32), ("mixed", pes.MIXED), ("fp64", pes.FP64)):
+                y, off, m0, P0 = ins[prec]
+                ms = []
+                for rep_ in range(7):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    sm.ieks_run(model, m, prec, y, off, m0, P0, iters=iters)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    if rep_ >= 2:
+                        ms.append(e0.elapsed_time(e1))
+                ms_run = statistics.median(ms)
+                rec[key] = {"ms_per_run": ms_run, "us_per_iteration": 1e3 * ms_run / iters,
+                            "value": T * iters / (ms_run * 1e-3)}
+            y, off, m0, P0 = ins[pes.FP32]
+            x9, P9 = sm.ieks_run(model, m, pes.FP32, y, off, m0, P0, iters=iters - 1)[:2]
+            x, P = sm.ieks_run(model, m, pes.FP32, y, off, m0, P0, iters=iters)[:2]
+            xm, Pm = sm.ieks_run(model, m, pes.MIXED, y, off, m0, P0, iters=iters)[:2]
+            torch.cuda.synchronize()
+            last = oracle.iterated_smoother(oracle.Model.from_workload(wl), om, wl["offsets"], r32(wl["y"]),
+                                            r32(wl["m0"]), r32(wl["P0"]), x_init=x9.double().cpu().numpy(),
+                                            P_init=P9.double().cpu().numpy(), iters=1)
+            o = wl["offsets"]
+            rec["final_iteration"] = {
+                "fp32_means": rel_err(x.double().cpu().numpy(), last["x"], o),
+                "fp32_covs": rel_err(P.double().cpu().numpy(), last["P"], o),
+                "mixed_means": rel_err(xm.double().cpu().numpy(), last["x"], o),
+                "mixed_covs": rel_err(Pm.double().cpu().numpy(), last["P"], o)}
+            rec["launch_fp32"] = dict(zip(("blocks", "threads", "steps_per_thread"), sm.launch_shape(m, pes.FP32, N)))
+            line[name] = rec
+        print(json.dumps(line), flush=True)
+        sm.close()
 
 
 def peaks_file():
@@ -373,6 +441,9 @@ def main():
         return
     if args.profile:
         run_profile_case(args)
+        return
+    if args.sweep:
+        run_sweep(args)
         return
 
     import numpy as np
