@@ -513,7 +513,7 @@ pes_status pes_destroy(pes_handle* h)
     if (!h) return PES_ERR_INVALID_ARG;
     cudaDeviceSynchronize();
     void* ptrs[] = {h->hand, h->lanes, h->lin, h->mix, h->aggF, h->aggS, h->bar, h->status, h->conv, h->iters_done, h->traj_iters, h->sensT, h->ptime,
-                    h->hy, h->hoff, h->hm0, h->hP0, h->hx, h->hP, h->hxi, h->hPi, h->hsens};
+                    h->hy, h->hoff, h->hm0, h->hP0, h->hx, h->hP, h->hsens};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete h;
@@ -857,7 +857,15 @@ pes_status pes_ieks_run_host(pes_handle* h, const pes_model* model, pes_method m
         if (e == cudaSuccess) e = cudaMalloc(&h->hx, sizeof(double) * 5 * Nmax);
         if (e == cudaSuccess) e = cudaMalloc(&h->hP, sizeof(double) * 15 * Nmax);
         if (e == cudaSuccess) e = cudaMalloc((void**)&h->hsens, sizeof(double) * 4 * Bmax);
-        if (e != cudaSuccess) return cuda_fail(h, e, "allocating the host-path buffers");
+        if (e != cudaSuccess) {
+            // leave none of them set, so that a later call allocates them all again
+            void** bufs[] = {&h->hy, (void**)&h->hoff, &h->hm0, &h->hP0, &h->hx, &h->hP, (void**)&h->hsens};
+            for (void** b : bufs) {
+                if (*b) cudaFree(*b);
+                *b = nullptr;
+            }
+            return cuda_fail(h, e, "allocating the host-path buffers");
+        }
     }
     cudaStream_t st = (cudaStream_t)stream;
     pes_model dm = *model;

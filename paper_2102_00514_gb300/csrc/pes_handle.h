@@ -35,8 +35,6 @@ struct pes_handle {
     void* hP0 = nullptr;
     void* hx = nullptr;
     void* hP = nullptr;
-    void* hxi = nullptr;
-    void* hPi = nullptr;
     double* hsens = nullptr;
     void* sensT = nullptr;   // sensors converted to the kernel precision
     void* lanes = nullptr;   // x, P, y in the kernel's lane-major layout
