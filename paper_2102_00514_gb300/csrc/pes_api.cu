@@ -11,6 +11,7 @@
 #include "pes.h"
 #include "pes_handle.h"
 #include "pes_internal.h"
+#include "pes_refine.cuh"
 
 using namespace pes;
 
@@ -48,8 +49,10 @@ pes_status check_common(pes_handle* h, pes_precision prec, const int64_t* offset
                         bool allow_mixed = false)
 {
     if (!h) return PES_ERR_INVALID_ARG;
-    if (prec == PES_MIXED && !allow_mixed) return fail(h, PES_ERR_UNSUPPORTED, "PES_MIXED is only supported by pes_ieks_run");
-    if (prec == PES_MIXED) return check_common(h, PES_FP32, offsets, B, N);
+    const bool two_stage = (prec == PES_MIXED || prec == PES_REFINED);
+    if (two_stage && !allow_mixed)
+        return fail(h, PES_ERR_UNSUPPORTED, "PES_MIXED and PES_REFINED are only supported by pes_ieks_run");
+    if (two_stage) return check_common(h, PES_FP32, offsets, B, N);
     if (prec != PES_FP32 && prec != PES_FP64) return fail(h, PES_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
     if (!offsets) return fail(h, PES_ERR_INVALID_ARG, "offsets is NULL");
     if (B < 1) return fail(h, PES_ERR_INVALID_ARG, "B must be >= 1 (got %d)", (int)B);
@@ -450,6 +453,117 @@ static pes_status ieks_run_mixed(pes_handle* h, const pes_model* model, pes_meth
     return r;
 }
 
+// The refinement workspace: nominal and filtered moments (20 + 20 floats per
+// slot), residual elements (RE), stored transitions (RT), the filter's
+// correction (RD), for every lane-major slot the handle can hold.
+static pes_status ensure_refine_workspace(pes_handle* h)
+{
+    if (h->refw) return PES_OK;
+    const size_t slots = (size_t)h->max_states + (size_t)h->nl_max;
+    PES_CUDA(h, cudaMalloc(&h->refw, sizeof(float) * (20 + 20 + RE + RT + RD) * slots));
+    return PES_OK;
+}
+
+// PES_REFINED: the first max_iters - 1 iterations in FP32, then the final
+// iteration in FP32 and its Newton refinement (pes_refine.cuh): float-float
+// residuals of the filter and RTS recursions about the FP32 solution, and the
+// corrections from two FP32 scans. Everything stays in the lane-major layout
+// of the smoother kernel; the refinement workspace (155 floats per slot) is
+// allocated by the first call on the handle.
+static pes_status ieks_run_refined(pes_handle* h, const pes_model* model, pes_method method, const void* y,
+                                   const int64_t* offsets, int32_t B, int64_t N, const void* m0, const void* P0,
+                                   const void* x_init, const void* P_init, int32_t max_iters, double tol, void* x_out,
+                                   void* P_out, int32_t* iters_used, cudaStream_t st)
+{
+    if (method == PES_GAUSS_HERMITE)
+        return fail(h, PES_ERR_UNSUPPORTED, "PES_REFINED supports PES_IEKS, PES_CUBATURE and PES_UNSCENTED");
+    if (model->lm_lambda > 0.0)
+        return fail(h, PES_ERR_UNSUPPORTED, "PES_REFINED does not support Levenberg-Marquardt damping");
+    const int lin = lin_of(method);
+    Shape s;
+    pes_status r = make_shape<float>(h, lin, PES_FP32, N, s);
+    if (r != PES_OK) return r;
+    const int cap = refine_scan_capacity(s.nt, h->device);
+    if (cap < 0) {
+        cudaGetLastError();
+        return fail(h, PES_ERR_CUDA, "the refinement scan's occupancy query failed: %s",
+                    cudaGetErrorString((cudaError_t)(-cap)));
+    }
+    if (cap < s.nb)
+        return fail(h, PES_ERR_CUDA, "the refinement scan cannot be made co-resident (%d of %d blocks)", cap, s.nb);
+    if ((r = ensure_refine_workspace(h)) != PES_OK) return r;
+    const int NL = s.nb * s.nt;
+    const int64_t cs = (int64_t)s.L * NL;
+    float* lx = static_cast<float*>(h->lanes);
+    float* lP = lx + 5 * cs;
+    float* ly = lP + 15 * cs;
+    float* nom = static_cast<float*>(h->refw);
+    float* filt = nom + 20 * cs;
+    float* elem = filt + 20 * cs;
+    float* trans = elem + RE * cs;
+    float* dlt = trans + RT * cs;
+    PES_CUDA(h, launch_lanes_transpose<float>((const float*)y, ly, 2, N, s.L, NL, true, st));
+    const bool cub = (method != PES_IEKS);
+    if (x_init) PES_CUDA(h, launch_lanes_transpose<float>((const float*)x_init, lx, 5, N, s.L, NL, true, st));
+    if (cub && P_init) PES_CUDA(h, launch_lanes_transpose<float>((const float*)P_init, lP, 15, N, s.L, NL, true, st));
+    if (!x_init || (cub && !P_init))
+        PES_CUDA(h, launch_init_nominal_lanes<float>(offsets, B, N, s.L, NL, (const float*)m0, (const float*)P0,
+                                                     x_init ? nullptr : lx, (cub && !P_init) ? lP : nullptr, st));
+    KParams<float> p{};
+    p.N = N; p.offsets = offsets; p.B = B; p.mode = MODE_RUN;
+    if ((r = device_model<float>(h, *model, B, st, p.model, method)) != PES_OK) return r;
+    p.y = ly; p.m0 = (const float*)m0; p.P0 = (const float*)P0;
+    p.x = lx; p.P = lP;
+    p.lanes_layout = 1;
+    int32_t it32 = 0;
+    pes_status r32 = PES_OK;
+    if (max_iters > 1) {
+        p.iters = max_iters - 1;
+        p.tol = tol;
+        p.write_P_every_iter = tol > 0.0 ? 1 : 0;
+        if ((r = run_persistent_shaped<float>(h, p, lin, s, st)) != PES_OK) return r;
+        if (tol > 0.0) {
+            r32 = read_status(h, st, &it32);
+            if (r32 != PES_OK && r32 != PES_ERR_NOT_CONVERGED) return r32;
+        } else {
+            it32 = max_iters - 1;
+        }
+    }
+    // the final iteration's nominal, then the iteration itself with its filtered moments kept
+    PES_CUDA(h, cudaMemcpyAsync(nom, lx, sizeof(float) * 20 * cs, cudaMemcpyDeviceToDevice, st));
+    p.iters = 1;
+    p.tol = 0.0;
+    p.write_P_every_iter = 1;
+    p.fstore = filt;
+    if ((r = run_persistent_shaped<float>(h, p, lin, s, st)) != PES_OK) return r;
+    RefineParams rp{};
+    rp.N = N; rp.offsets = offsets; rp.B = B; rp.L = s.L; rp.NL = NL; rp.cs = cs;
+    rp.model = p.model;
+    rp.y = ly; rp.m0 = (const float*)m0; rp.P0 = (const float*)P0;
+    rp.nom = nom; rp.filt = filt; rp.xs = lx;
+    rp.elem = elem; rp.trans = trans; rp.dlt = dlt;
+    rp.agg = static_cast<float*>(h->aggF);
+    rp.bar = h->bar;
+    rp.status = h->status;
+    rp.timeout_ns = h->timeout_ns;
+    PES_CUDA(h, launch_refine_fwd(rp, lin, st));
+    PES_CUDA(h, cudaMemsetAsync(h->bar, 0, sizeof(unsigned), st));
+    cudaError_t e = launch_refine_scan(rp, true, s.nt, s.nb, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cooperative launch of the refinement scan");
+    PES_CUDA(h, launch_refine_bwd(rp, st));
+    PES_CUDA(h, cudaMemsetAsync(h->bar, 0, sizeof(unsigned), st));
+    e = launch_refine_scan(rp, false, s.nt, s.nb, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cooperative launch of the refinement scan");
+    PES_CUDA(h, launch_lanes_transpose<float>(lx, (float*)x_out, 5, N, s.L, NL, false, st));
+    PES_CUDA(h, launch_lanes_transpose<float>(lP, (float*)P_out, 15, N, s.L, NL, false, st));
+    if (tol > 0.0 || iters_used) {
+        r = read_status(h, st);
+        if (iters_used) *iters_used = it32 + 1;
+        return r != PES_OK ? r : r32;
+    }
+    return PES_OK;
+}
+
 struct pes_graph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -512,7 +626,7 @@ pes_status pes_destroy(pes_handle* h)
 {
     if (!h) return PES_ERR_INVALID_ARG;
     cudaDeviceSynchronize();
-    void* ptrs[] = {h->hand, h->lanes, h->lin, h->mix, h->aggF, h->aggS, h->bar, h->status, h->conv, h->iters_done, h->traj_iters, h->sensT, h->ptime,
+    void* ptrs[] = {h->hand, h->lanes, h->lin, h->mix, h->refw, h->aggF, h->aggS, h->bar, h->status, h->conv, h->iters_done, h->traj_iters, h->sensT, h->ptime,
                     h->hy, h->hoff, h->hm0, h->hP0, h->hx, h->hP, h->hsens};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -564,6 +678,7 @@ pes_status pes_launch_shape(pes_handle* h, pes_method method, pes_precision prec
 {
     if (!h || N < 1) return PES_ERR_INVALID_ARG;
     if (prec == PES_MIXED) return PES_ERR_UNSUPPORTED;
+    if (prec == PES_REFINED) prec = PES_FP32;   // its iterations run the FP32 kernel
     const int lin = lin_of(method);
     Shape s;
     pes_status r = (prec == PES_FP64) ? make_shape<double>(h, lin, prec, N, s) : make_shape<float>(h, lin, prec, N, s);
@@ -582,6 +697,11 @@ pes_status pes_ieks_graph_create(pes_handle* h, const pes_model* model, pes_meth
     if (!h || !out) return PES_ERR_INVALID_ARG;
     *out = nullptr;
     if (prec == PES_MIXED) return fail(h, PES_ERR_UNSUPPORTED, "PES_MIXED synchronises and cannot be captured");
+    if (prec == PES_REFINED) {
+        // allocate outside the capture
+        const pes_status ra = ensure_refine_workspace(h);
+        if (ra != PES_OK) return ra;
+    }
     cudaStream_t cs = nullptr;
     PES_CUDA(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
@@ -793,6 +913,9 @@ pes_status pes_ieks_run(pes_handle* h, const pes_model* model, pes_method method
     if (prec == PES_MIXED)
         return ieks_run_mixed(h, model, method, y, offsets, B, N, m0, P0, x_init, P_init, max_iters, tol, x_out, P_out,
                               iters_used, st);
+    if (prec == PES_REFINED)
+        return ieks_run_refined(h, model, method, y, offsets, B, N, m0, P0, x_init, P_init, max_iters, tol, x_out,
+                                P_out, iters_used, st);
     if (prec == PES_FP64)
         return ieks_run_t<double>(h, model, method, prec, y, offsets, B, N, m0, P0, x_init, P_init, max_iters, tol,
                                   x_out, P_out, iters_used, st);
@@ -838,8 +961,8 @@ pes_status pes_ieks_run_host(pes_handle* h, const pes_model* model, pes_method m
                              void* x_out, void* P_out, int32_t* iters_used, void* stream)
 {
     if (!h) return PES_ERR_INVALID_ARG;
-    if (prec == PES_MIXED) return fail(h, PES_ERR_UNSUPPORTED, "PES_MIXED is not supported yet");
-    if (prec != PES_FP32 && prec != PES_FP64) return fail(h, PES_ERR_INVALID_ARG, "unknown precision");
+    if (prec != PES_FP32 && prec != PES_FP64 && prec != PES_MIXED && prec != PES_REFINED)
+        return fail(h, PES_ERR_INVALID_ARG, "unknown precision");
     if (!model || !y || !offsets || !m0 || !P0 || !x_out || !P_out) return fail(h, PES_ERR_INVALID_ARG, "NULL array");
     if (B < 1 || N < B || N > h->max_states || B > h->max_batch)
         return fail(h, PES_ERR_INVALID_ARG, "sizes out of range (N %lld, B %d)", (long long)N, (int)B);

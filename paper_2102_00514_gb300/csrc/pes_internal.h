@@ -50,4 +50,15 @@ cudaError_t launch_sequential(const KParams<T>& p, cudaStream_t st);
 
 cudaError_t launch_validate_offsets(const int64_t* offsets, int B, int64_t N, int* status, cudaStream_t st);
 
+// Refinement of the final iteration (pes_refine.cu): the forward residual
+// elements (`lin` LIN_IEKS or LIN_CUBATURE), the RTS residual elements, and
+// the correction scan (cooperative: nb blocks of nt threads, nt 128 or 256).
+struct RefineParams;
+cudaError_t launch_refine_fwd(const RefineParams& p, int lin, cudaStream_t st);
+cudaError_t launch_refine_bwd(const RefineParams& p, cudaStream_t st);
+cudaError_t launch_refine_scan(const RefineParams& p, bool fwd, int nt, int nb, cudaStream_t st);
+// Largest cooperative grid of the correction scan at nt threads (negated CUDA
+// error code on failure).
+int refine_scan_capacity(int nt, int device);
+
 }  // namespace pes

@@ -64,6 +64,9 @@ struct KParams {
     // smoothed moments: MODE_SMOOTH output; MODE_RUN nominal (in place) and output
     T* x;
     T* P;
+    // MODE_RUN: the filtered moments of every state, [20][cs] in the layout of
+    // x and P (means then packed covariances), or NULL (not stored)
+    T* fstore;
     // workspace
     T* hand;           // MODE_RUN handoff of smoothing elements: [warp][s][c][32 lanes]
     T* lin;            // MODE_RUN cubature linearisation handed from the fold to the re-run: [warp][s][LINS][32]
@@ -710,6 +713,12 @@ PES_DEV bool rerun_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int l
             }
             if (!smooth) store_filtered(p, k, m, P);
             else if (!kStoreElements<LIN>) store_xP(p, s, lane, m, P);
+            if (p.fstore) {
+#pragma unroll
+                for (int i = 0; i < 5; ++i) p.fstore[i * p.cs + ix] = m[i];
+#pragma unroll
+                for (int i = 0; i < 15; ++i) p.fstore[(5 + i) * p.cs + ix] = P[i];
+            }
             if (!use_lin) {
                 sp = sc;
                 sc = sn;

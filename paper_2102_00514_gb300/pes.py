@@ -24,7 +24,7 @@ OK, INVALID_ARG, NOT_PD, NONFINITE, NOT_CONVERGED, CUDA, UNSUPPORTED, TIMEOUT = 
 STATUS_NAMES = {0: "PES_OK", 1: "PES_ERR_INVALID_ARG", 2: "PES_ERR_NOT_PD", 3: "PES_ERR_NONFINITE",
                 4: "PES_ERR_NOT_CONVERGED", 5: "PES_ERR_CUDA", 6: "PES_ERR_UNSUPPORTED", 7: "PES_ERR_TIMEOUT"}
 IEKS, CUBATURE, UNSCENTED, GAUSS_HERMITE = 0, 1, 2, 3
-FP64, FP32, MIXED = 0, 1, 2
+FP64, FP32, MIXED, REFINED = 0, 1, 2, 3
 MODEL_CT_BEARINGS, MODEL_LINEAR = 0, 1
 
 EXPORTED = ["pes_create", "pes_destroy", "pes_last_error", "pes_sync", "pes_linearize", "pes_filter_scan",

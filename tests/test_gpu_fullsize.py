@@ -1,0 +1,71 @@
+"""Parity at the benchmark's full size: one trajectory of T = 2^20 steps, the
+smoother kernel on its full grid (152 blocks x 256 lanes x 27 steps in FP32).
+
+* FP64: ten iterations against the oracle's ten, 1e-9 relative.
+* The final iteration of every reduced precision, against one oracle
+  iteration from the GPU's own FP32 nominal of nine iterations (with the float
+  inputs the GPU sees): PES_REFINED within 1e-5 (and its worst state within
+  1e-4), PES_MIXED within 1e-6. The plain FP32 final iteration is reported
+  and bounded by 5e-4: at this length it misses the 1e-4 tolerance (1.9e-4
+  IEKS, 2.5e-4 cubature covariances; the error is spread over the states,
+  mostly in the position variances of far-away targets), which is what the
+  refined precision is for.
+
+The errors are printed with the worst per-state error (R12).
+"""
+import numpy as np
+import pytest
+
+from paper_2102_00514_gb300 import pes, synth
+from tests.gpu_common import TOL_FP32, TOL_FP64, gpu_run, oracle_run, rel_err
+from tests.test_gpu_refined import TOL_REFINED, float_inputs, per_state_max
+
+pytestmark = pytest.mark.gpu
+
+T = 1 << 20
+
+
+@pytest.fixture(scope="module")
+def wl():
+    return synth.workload(f"sweep_T{T}")
+
+
+@pytest.fixture(scope="module")
+def sm(wl):
+    s = pes.Smoother(wl["y"].shape[1], 1)
+    yield s
+    s.close()
+
+
+@pytest.mark.parametrize("method", [pes.IEKS, pes.CUBATURE])
+def test_fullsize_fp64_ten_iterations_match_oracle(wl, sm, method):
+    nb, nt, L = sm.launch_shape(method, pes.FP64, wl["y"].shape[1])
+    ref = oracle_run(wl, method, iters=10)
+    x, P, used, _ = gpu_run(sm, wl, method, pes.FP64, iters=10)
+    ex, eP = rel_err(x, ref["x"], wl["offsets"]), rel_err(P, ref["P"], wl["offsets"])
+    print(f"T=2^20 method {method} FP64 ({nb}x{nt}x{L}): means {ex:.2e} covariances {eP:.2e} "
+          f"(worst state {per_state_max(x, ref['x']):.2e} / {per_state_max(P, ref['P']):.2e})")
+    assert used == 10 and ex < TOL_FP64 and eP < TOL_FP64
+
+
+@pytest.mark.parametrize("method", [pes.IEKS, pes.CUBATURE])
+def test_fullsize_final_iteration_reduced_precisions(wl, sm, method):
+    nb, nt, L = sm.launch_shape(method, pes.FP32, wl["y"].shape[1])
+    assert nb * nt >= 152 * 128   # the full grid
+    x9, P9, _, _ = gpu_run(sm, wl, method, pes.FP32, iters=9)
+    one = oracle_run(float_inputs(wl), method, iters=1, x_init=x9, P_init=P9)
+    off = wl["offsets"]
+    errs = {}
+    for prec, name in ((pes.REFINED, "refined"), (pes.MIXED, "mixed"), (pes.FP32, "fp32")):
+        x, P, used, _ = gpu_run(sm, wl, method, prec, iters=10)
+        assert used == 10
+        errs[name] = (rel_err(x, one["x"], off), rel_err(P, one["P"], off), per_state_max(x, one["x"]),
+                      per_state_max(P, one["P"]))
+        print(f"T=2^20 method {method} {name} final iteration ({nb}x{nt}x{L}): means {errs[name][0]:.2e} "
+              f"covariances {errs[name][1]:.2e} (worst state {errs[name][2]:.2e} / {errs[name][3]:.2e})")
+    ex, eP, sx, sP = errs["refined"]
+    assert ex < TOL_REFINED and eP < TOL_REFINED and sx < TOL_FP32 and sP < TOL_FP32
+    ex, eP, _, _ = errs["mixed"]
+    assert ex < 1e-6 and eP < 1e-6
+    ex, eP, _, _ = errs["fp32"]
+    assert ex < 5e-4 and eP < 5e-4

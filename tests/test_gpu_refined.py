@@ -1,0 +1,181 @@
+"""PES_REFINED: FP32 iterations, then a final iteration refined by one Newton
+step on its Kalman and RTS recursions (float-float residuals, FP32
+correction scans), checked against the oracle element by element.
+
+The reference for the final iteration is one oracle iteration (FP64) from the
+GPU's own FP32 nominal of the first M - 1 iterations, with the float inputs
+the GPU sees (measurements and prior rounded to float, widened): the FP32
+iterations before it are deterministic, so a plain FP32 run of M - 1
+iterations reproduces that nominal bit for bit. The bound is the FP32
+tolerance of 1e-4 on the per-trajectory relative Frobenius error (means and
+covariances), and 1e-5 is asserted as well: the refinement leaves the final
+FP32 narrowing (6e-8), the float linearisation (rounding F, c, Q', H, d, R'
+to float moves the smoother by about 6e-7 at T = 2^20) and the Newton step's
+second-order remainder (about 1e-7). The worst per-state error (R12: the
+state's ||.||_2 over its own norm) is held to 1e-4.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2102_00514_gb300 import pes, synth
+from tests.gpu_common import TOL_FP32, gpu_run, oracle_run, rel_err, workload_to_dev
+
+pytestmark = pytest.mark.gpu
+
+TOL_REFINED = 1e-5
+
+
+@pytest.fixture(scope="module")
+def sm():
+    s = pes.Smoother(1 << 17, 64)
+    yield s
+    s.close()
+
+
+def per_state_max(a, b):
+    """Worst per-state relative error ||a_k - b_k||_2 / ||b_k||_2 over all states."""
+    num = np.linalg.norm(a - b, axis=0)
+    den = np.maximum(np.linalg.norm(b, axis=0), 1e-300)
+    return float(np.max(num / den))
+
+
+def float_inputs(wl):
+    r32 = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)
+    return dict(wl, y=r32(wl["y"]), m0=r32(wl["m0"]), P0=r32(wl["P0"]))
+
+
+def final_iteration_errors(sm, wl, method, prec, iters=10, ut=None):
+    """(means, covariances, per-state means, per-state covariances) errors of the
+    final iteration of a run at `prec` against one oracle iteration from the
+    FP32 nominal of iters - 1 iterations."""
+    x, P, used, st = gpu_run(sm, wl, method, prec, iters=iters, ut=ut)
+    assert used == iters and st == pes.OK
+    x9, P9, _, _ = gpu_run(sm, wl, method, pes.FP32, iters=iters - 1, ut=ut)
+    one = oracle_run(float_inputs(wl), method, iters=1, x_init=x9, P_init=P9, ut=ut)
+    off = wl["offsets"]
+    return (rel_err(x, one["x"], off), rel_err(P, one["P"], off), per_state_max(x, one["x"]),
+            per_state_max(P, one["P"]))
+
+
+# sweep_T4096 (IEKS) and sweep_T65536 (cubature) are lengths at which the FP32
+# final iteration misses 1e-4 on its own
+@pytest.mark.parametrize("name,method", [("ieks_T500", pes.IEKS), ("ipls_T10000", pes.CUBATURE),
+                                         ("sweep_T4096", pes.IEKS), ("sweep_T65536", pes.CUBATURE),
+                                         ("batch8_T100_3000", pes.IEKS), ("batch8_T100_3000", pes.CUBATURE)])
+def test_refined_final_iteration_matches_oracle(sm, name, method):
+    wl = synth.workload(name)
+    ex, eP, sx, sP = final_iteration_errors(sm, wl, method, pes.REFINED)
+    print(f"{name} method {method} REFINED final iteration: means {ex:.2e} covariances {eP:.2e} "
+          f"(worst state {sx:.2e} / {sP:.2e})")
+    assert ex < TOL_FP32 and eP < TOL_FP32
+    assert ex < TOL_REFINED and eP < TOL_REFINED
+    assert sx < TOL_FP32 and sP < TOL_FP32
+
+
+def test_refined_unscented_matches_oracle(sm):
+    wl = synth.workload("ipls_T10000")
+    ut = (0.8, 2.0, 0.5)
+    ex, eP, sx, sP = final_iteration_errors(sm, wl, pes.UNSCENTED, pes.REFINED, ut=ut)
+    print(f"unscented REFINED final iteration: means {ex:.2e} covariances {eP:.2e}")
+    assert ex < TOL_REFINED and eP < TOL_REFINED and sx < TOL_FP32 and sP < TOL_FP32
+
+
+def test_refined_linear_model_one_iteration_is_exact(sm):
+    """On a linear-Gaussian model one iteration is the exact smoother (both
+    linearisations are the model itself): the refined single iteration equals
+    the oracle's Kalman filter + RTS to the refinement's accuracy."""
+    rng = np.random.default_rng(3)
+    F = np.eye(5) + 0.01 * rng.standard_normal((5, 5))
+    A = rng.standard_normal((5, 5))
+    Q = 1e-3 * A @ A.T
+    H = rng.standard_normal((2, 5))
+    R = 0.05 * np.eye(2)
+    c = 0.01 * rng.standard_normal(5)
+    d = 0.1 * rng.standard_normal(2)
+    # the model in float, on both sides: the comparison is then of the smoother alone
+    r32 = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)
+    F, Q, H, R, c, d = (r32(a) for a in (F, Q, H, R, c, d))
+    T = 3000
+    offsets = synth.offsets_from_lengths(np.array([T]))
+    x = np.zeros((T + 1, 5))
+    y = np.zeros((T + 1, 2))
+    x[0] = rng.standard_normal(5)
+    for k in range(1, T + 1):
+        x[k] = F @ x[k - 1] + c + np.linalg.cholesky(Q) @ rng.standard_normal(5)
+        y[k] = H @ x[k] + d + np.sqrt(0.05) * rng.standard_normal(2)
+    import oracle
+    om = oracle.Model.linear(F, c, Q, H, d, R)
+    m0 = np.zeros((1, 5))
+    P0 = oracle.sym_packed(np.eye(5))[None]
+    y32 = y.T.astype(np.float32).astype(np.float64)
+    ref = oracle.iterated_smoother(om, oracle.IEKS, offsets, y32, m0, P0, iters=1)
+    model = pes.Model.linear(F, c, oracle.sym_packed(Q), H, d, oracle.sym_packed(R))
+    dev = lambda a, dt=torch.float32: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    for method in (pes.IEKS, pes.CUBATURE):
+        xg, Pg, used, _ = sm.ieks_run(model, method, pes.REFINED, dev(y32), dev(offsets, torch.int64), dev(m0),
+                                      dev(P0), iters=1, want_iters=True)
+        assert used == 1
+        ex = rel_err(xg.double().cpu().numpy(), ref["x"], offsets)
+        eP = rel_err(Pg.double().cpu().numpy(), ref["P"], offsets)
+        print(f"linear model, method {method}: means {ex:.2e} covariances {eP:.2e}")
+        assert ex < TOL_REFINED and eP < TOL_REFINED
+
+
+def test_refined_tolerance_mode(sm):
+    """In tolerance mode the FP32 iterations stop at tol and the refined
+    iteration follows: one more iteration than the FP32 run alone."""
+    wl = synth.workload("ieks_T500")
+    d = workload_to_dev(wl, pes.FP32)
+    _, _, used32, _ = sm.ieks_run(d["model"], pes.IEKS, pes.FP32, d["y"], d["offsets"], d["m0"], d["P0"], iters=29,
+                                  tol=1e-5)
+    x, P, used, st = sm.ieks_run(d["model"], pes.IEKS, pes.REFINED, d["y"], d["offsets"], d["m0"], d["P0"],
+                                 iters=30, tol=1e-5)
+    assert st == pes.OK and used == used32 + 1
+    ref = oracle_run(wl, pes.IEKS, iters=used)
+    assert rel_err(x.double().cpu().numpy(), ref["x"], wl["offsets"]) < TOL_FP32
+    assert rel_err(P.double().cpu().numpy(), ref["P"], wl["offsets"]) < TOL_FP32
+
+
+def test_refined_graph_replay_equals_direct_call(sm):
+    wl = synth.workload("batch8_T1_3000")
+    for method in (pes.IEKS, pes.CUBATURE):
+        d = workload_to_dev(wl, pes.FP32)
+        x, P, _, _ = sm.ieks_run(d["model"], method, pes.REFINED, d["y"], d["offsets"], d["m0"], d["P0"], iters=3)
+        sm.sync()
+        g = sm.graph(d["model"], method, pes.REFINED, d["y"], d["offsets"], d["m0"], d["P0"], iters=3)
+        g.launch()
+        sm.sync()
+        assert torch.equal(g.x, x) and torch.equal(g.P, P)
+        g.close()
+
+
+def test_refined_host_entry_point_equals_device_entry_point(sm):
+    wl = synth.workload("ipls_T10000")
+    d = workload_to_dev(wl, pes.FP32)
+    xd, Pd, _, _ = sm.ieks_run(d["model"], pes.CUBATURE, pes.REFINED, d["y"], d["offsets"], d["m0"], d["P0"], iters=4)
+    sm.sync()
+    h = lambda a, dt=torch.float32: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).pin_memory()
+    xh, Ph, used, _ = sm.ieks_run_host(d["model"], pes.CUBATURE, pes.REFINED, h(wl["y"]),
+                                       h(wl["offsets"], torch.int64), h(wl["m0"]), h(wl["P0"]), iters=4,
+                                       sensors_host=h(wl["sensors"], torch.float64))
+    assert used == 4
+    assert torch.equal(xh, xd.cpu()) and torch.equal(Ph, Pd.cpu())
+
+
+def test_refined_unsupported_cases(sm):
+    wl = synth.workload("ieks_T500")
+    d = workload_to_dev(wl, pes.FP32)
+    with pytest.raises(pes.PesError) as ei:
+        sm.ieks_run(d["model"], pes.GAUSS_HERMITE, pes.REFINED, d["y"], d["offsets"], d["m0"], d["P0"], iters=2)
+    assert ei.value.status == pes.UNSUPPORTED
+    d = workload_to_dev(wl, pes.FP32, lm=1.0)
+    with pytest.raises(pes.PesError) as ei:
+        sm.ieks_run(d["model"], pes.IEKS, pes.REFINED, d["y"], d["offsets"], d["m0"], d["P0"], iters=2)
+    assert ei.value.status == pes.UNSUPPORTED
+    # the scan entry points keep FP32 / FP64 only
+    lin = {k: torch.zeros((n, d["y"].shape[1]), dtype=torch.float32, device="cuda")
+           for k, n in (("F", 25), ("c", 5), ("Qp", 15), ("H", 10), ("d", 2), ("Rp", 3))}
+    with pytest.raises(pes.PesError) as ei:
+        sm.filter_scan(pes.REFINED, lin, d["y"], d["m0"], d["P0"], d["offsets"])
+    assert ei.value.status == pes.UNSUPPORTED
