@@ -30,12 +30,15 @@ PES_DEV void store_elem(const RefineParams& p, int64_t ix, const float* A, const
     for (int c = 0; c < 15; ++c) e[(35 + c) * p.cs] = r[c];
 }
 
+// The elements are read-only while the correction scan runs: loads through
+// the non-coherent path, which the compiler may move ahead of the scan's
+// stores.
 PES_DEV void load_elem(const RefineParams& p, int64_t ix, RElem& el)
 {
     const float* e = p.elem + ix;
     float* d = reinterpret_cast<float*>(&el);
 #pragma unroll
-    for (int c = 0; c < RE; ++c) d[c] = e[c * p.cs];
+    for (int c = 0; c < RE; ++c) d[c] = __ldg(e + c * p.cs);
 }
 
 // (state, lane) of the thread's slot in the lane-major arrays; false past N.
@@ -55,13 +58,18 @@ PES_DEV int64_t next_slot(const RefineParams& p, int64_t ix, int s, int lane)
 
 }  // namespace
 
+constexpr int RT_THREADS = 128;   // threads per block of the residual kernels
+constexpr size_t RT_SMEM = sizeof(float) * SCR_N * RT_THREADS;
+
 // Forward residual elements. The thread of state k writes the element of
 // state k + 1 (the Kalman step k -> k+1 from the FP32 filtered moments of k)
 // and, for a trajectory's first state, its own (the prior: A = 0); it also
 // stores the transition out of k for the RTS residuals.
 template <int LIN>
-__global__ void __launch_bounds__(128) refine_fwd_kernel(const RefineParams p)
+__global__ void __launch_bounds__(RT_THREADS) refine_fwd_kernel(const RefineParams p)
 {
+    extern __shared__ float scr_raw[];
+    const Scratch<RT_THREADS> sc{scr_raw + threadIdx.x};
     const int64_t ix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int s, lane;
     int64_t k;
@@ -85,7 +93,7 @@ __global__ void __launch_bounds__(128) refine_fwd_kernel(const RefineParams p)
     }
     if (k + 1 >= next) return;
     const DevModel<float>& m = p.model;
-    // transition k -> k+1 about the nominal of k
+    // transition k -> k+1 about the nominal of k; its slope goes to the scratch
     Trans<float> tr;
     bool ok = true;
     {
@@ -93,17 +101,19 @@ __global__ void __launch_bounds__(128) refine_fwd_kernel(const RefineParams p)
         load20(p.nom, p.cs, ix, xn, Pn);
         if (LIN == LIN_IEKS) {
             lin_trans_taylor(m, xn, tr);
+#pragma unroll
+            for (int c = 0; c < 25; ++c) sc[SCR_F + c] = tr.F[c];
         } else {
             float Lc[25], rdc[5];
             ok &= cub_factor(Pn, Lc, rdc);
             lin_trans_cubature(m, xn, Lc, rdc, tr);
-            cub_trans_slope_ff(m, xn, Lc, tr.F);
+            cub_trans_slope_ff(m, xn, Lc, sc);
         }
     }
     {
         float* t = p.trans + ix;
-#pragma unroll
-        for (int c = 0; c < 25; ++c) t[c * p.cs] = tr.F[c];
+#pragma unroll 5
+        for (int c = 0; c < 25; ++c) t[c * p.cs] = sc[SCR_F + c];
 #pragma unroll
         for (int c = 0; c < 5; ++c) t[(25 + c) * p.cs] = tr.fx[c];
 #pragma unroll
@@ -127,7 +137,7 @@ __global__ void __launch_bounds__(128) refine_fwd_kernel(const RefineParams p)
     }
     ff mf[5], Pff[15];
     float A[25], w[5];
-    ok &= ff_kalman_step(tr, ob, xf, Pf, mf, Pff, A, w);
+    ok &= ff_kalman_step(tr, ob, xf, Pf, mf, Pff, A, w, sc);
     float x1[5], P1[15], sres[5], r[15];
     load20(p.filt, p.cs, ix1, x1, P1);
 #pragma unroll
@@ -140,45 +150,34 @@ __global__ void __launch_bounds__(128) refine_fwd_kernel(const RefineParams p)
 
 // RTS residual elements, one per state, from the refined filtered moments
 // (FP32 value + the filter's correction) and the FP32 smoothed moments.
-__global__ void __launch_bounds__(128) refine_bwd_kernel(const RefineParams p)
+__global__ void __launch_bounds__(RT_THREADS) refine_bwd_kernel(const RefineParams p)
 {
+    extern __shared__ float scr_raw[];
+    const Scratch<RT_THREADS> sc{scr_raw + threadIdx.x};
     const int64_t ix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int s, lane;
     int64_t k;
     if (!slot_state(p, ix, s, lane, k)) return;
     const int b = traj_of(p.offsets, p.B, k);
     const int64_t next = __ldg(p.offsets + b + 1);
-    ff mf[5], Pf[15];
-    {
-        float x[5], P[15], dx[5], dP[15];
-        load20(p.filt, p.cs, ix, x, P);
-        load20(p.dlt, p.cs, ix, dx, dP);
+    // the refined filtered moments as float-float pairs
+    auto filt_ff = [&](int c) { return two_sum(p.filt[c * p.cs + ix], p.dlt[c * p.cs + ix]); };
+    float* el = p.elem + ix;
 #pragma unroll
-        for (int c = 0; c < 5; ++c) mf[c] = two_sum(x[c], dx[c]);
-#pragma unroll
-        for (int c = 0; c < 15; ++c) Pf[c] = two_sum(P[c], dP[c]);
-    }
-    float xs[5], Ps[15];
-    load20(p.xs, p.cs, ix, xs, Ps);
-    float G[25], w[5], sres[5], r[15];
-#pragma unroll
-    for (int c = 0; c < 5; ++c) w[c] = 0.0f;
+    for (int c = 0; c < 5; ++c) el[(25 + c) * p.cs] = 0.0f;
     if (k + 1 >= next) {
         // last state: smoothed = filtered
+#pragma unroll 5
+        for (int c = 0; c < 25; ++c) el[c * p.cs] = 0.0f;
 #pragma unroll
-        for (int c = 0; c < 25; ++c) G[c] = 0.0f;
-#pragma unroll
-        for (int c = 0; c < 5; ++c) sres[c] = ff_to_f(ff_add_f(mf[c], -xs[c]));
-#pragma unroll
-        for (int c = 0; c < 15; ++c) r[c] = ff_to_f(ff_add_f(Pf[c], -Ps[c]));
-        store_elem(p, ix, G, w, sres, r);
+        for (int c = 0; c < 20; ++c) el[(30 + c) * p.cs] = ff_to_f(ff_add_f(filt_ff(c), -p.xs[c * p.cs + ix]));
         return;
     }
     Trans<float> tr;
     {
         const float* t = p.trans + ix;
-#pragma unroll
-        for (int c = 0; c < 25; ++c) tr.F[c] = t[c * p.cs];
+#pragma unroll 5
+        for (int c = 0; c < 25; ++c) sc[SCR_F + c] = t[c * p.cs];
 #pragma unroll
         for (int c = 0; c < 5; ++c) tr.fx[c] = t[(25 + c) * p.cs];
 #pragma unroll
@@ -187,15 +186,34 @@ __global__ void __launch_bounds__(128) refine_bwd_kernel(const RefineParams p)
         for (int c = 0; c < 5; ++c) tr.xn[c] = p.nom[c * p.cs + ix];
     }
     const int64_t ix1 = next_slot(p, ix, s, lane);
-    float xs1[5], Ps1[15];
-    load20(p.xs, p.cs, ix1, xs1, Ps1);
-    ff ms[5], Pss[15];
-    const bool ok = ff_rts_step(tr, mf, Pf, xs1, Ps1, ms, Pss, G);
+    ff ms[5], dP[15];
+    bool ok;
+    {
+        ff mf[5], Pf[15];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) sres[c] = ff_to_f(ff_add_f(ms[c], -xs[c]));
+        for (int c = 0; c < 5; ++c) mf[c] = filt_ff(c);
 #pragma unroll
-    for (int c = 0; c < 15; ++c) r[c] = ff_to_f(ff_add_f(Pss[c], -Ps[c]));
-    store_elem(p, ix, G, w, sres, r);
+        for (int c = 0; c < 15; ++c) Pf[c] = filt_ff(5 + c);
+        float xs1[5], Ps1[15];
+        load20(p.xs, p.cs, ix1, xs1, Ps1);
+        ok = ff_rts_gain(tr, mf, Pf, xs1, Ps1, ms, dP, sc);
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) el[(30 + c) * p.cs] = ff_to_f(ff_add_f(ms[c], -p.xs[c * p.cs + ix]));
+    // covariance residuals, row by row: Pf + G dP G^T - Ps
+#pragma unroll 1
+    for (int i = 0; i < 5; ++i) {
+        rts_cov_row(i, dP, sc, [&](int j, ff v) {
+            const int e = si_rt(i, j);
+            const ff Ps = ff_add(filt_ff(5 + e), v);
+            el[(35 + e) * p.cs] = ff_to_f(ff_add_f(Ps, -p.xs[(5 + e) * p.cs + ix]));
+        });
+    }
+    // G_ij = (G^T)_ji
+#pragma unroll 1
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) el[(i * 5 + j) * p.cs] = sc[SCR_M + 2 * (j * 5 + i)];
     if (!ok) atomicOr(p.status, ST_NOT_PD);
 }
 
@@ -271,20 +289,16 @@ __global__ void __launch_bounds__(NT, 1) refine_scan_kernel(const RefineParams p
     // ones already composed: forward from the chunk's first state, backward
     // from its last)
     {
-        RElem acc, ek;
+        RElem acc, ek, en;
         relem_identity(acc);
-        if (FWD) {
+        const int n = (int)(e - a);
+        if (n > 0) load_elem(p, (FWD ? 0 : n - 1) * (int64_t)p.NL + lane, en);
 #pragma unroll 1
-            for (int64_t k = a; k < e; ++k) {
-                load_elem(p, (k - a) * p.NL + lane, ek);
-                relem_compose<W>(ek, acc, acc);
-            }
-        } else {
-#pragma unroll 1
-            for (int64_t k = e - 1; k >= a; --k) {
-                load_elem(p, (k - a) * p.NL + lane, ek);
-                relem_compose<W>(ek, acc, acc);
-            }
+        for (int q = 0; q < n; ++q) {
+            ek = en;
+            const int sn = FWD ? q + 1 : n - 2 - q;   // the next state's step within the chunk
+            if (q + 1 < n) load_elem(p, sn * (int64_t)p.NL + lane, en);
+            relem_compose<W>(ek, acc, acc);
         }
         el[t] = acc;
     }
@@ -372,35 +386,49 @@ __global__ void __launch_bounds__(NT, 1) refine_scan_kernel(const RefineParams p
         }
     }
     RState d = gs[t];
-    // level 5: re-run
-    if (FWD) {
-#pragma unroll 1
-        for (int64_t k = a; k < e; ++k) {
-            const int64_t ix = (k - a) * p.NL + lane;
-            RElem ek;
-            load_elem(p, ix, ek);
-            relem_apply<W>(ek, d, d);
+    // level 5: re-run, the next state's element (and, backward, its FP32
+    // smoothed moments) loaded one step ahead
+    {
+        const int n = (int)(e - a);
+        RElem ek, en;
+        float xn[20], xc[20];
+        auto slot = [&](int q) { return (int64_t)(FWD ? q : n - 1 - q) * p.NL + lane; };
+        if (n > 0) {
+            load_elem(p, slot(0), en);
+            if (!FWD)
 #pragma unroll
-            for (int c = 0; c < 5; ++c) p.dlt[c * p.cs + ix] = d.m[c];
-#pragma unroll
-            for (int c = 0; c < 15; ++c) p.dlt[(5 + c) * p.cs + ix] = d.P[c];
+                for (int c = 0; c < 20; ++c) xn[c] = p.xs[c * p.cs + slot(0)];
         }
-    } else {
         bool finite = true;
 #pragma unroll 1
-        for (int64_t k = e - 1; k >= a; --k) {
-            const int64_t ix = (k - a) * p.NL + lane;
-            RElem ek;
-            load_elem(p, ix, ek);
-            relem_apply<W>(ek, d, d);
+        for (int q = 0; q < n; ++q) {
+            const int64_t ix = slot(q);
+            ek = en;
+            if (!FWD)
 #pragma unroll
-            for (int c = 0; c < 5; ++c) {
-                const float v = p.xs[c * p.cs + ix] + d.m[c];
-                finite = finite && isfinite(v);
-                p.xs[c * p.cs + ix] = v;
+                for (int c = 0; c < 20; ++c) xc[c] = xn[c];
+            if (q + 1 < n) {
+                load_elem(p, slot(q + 1), en);
+                if (!FWD)
+#pragma unroll
+                    for (int c = 0; c < 20; ++c) xn[c] = p.xs[c * p.cs + slot(q + 1)];
             }
+            relem_apply<W>(ek, d, d);
+            if (FWD) {
 #pragma unroll
-            for (int c = 0; c < 15; ++c) p.xs[(5 + c) * p.cs + ix] += d.P[c];
+                for (int c = 0; c < 5; ++c) p.dlt[c * p.cs + ix] = d.m[c];
+#pragma unroll
+                for (int c = 0; c < 15; ++c) p.dlt[(5 + c) * p.cs + ix] = d.P[c];
+            } else {
+#pragma unroll
+                for (int c = 0; c < 5; ++c) {
+                    const float v = xc[c] + d.m[c];
+                    finite = finite && isfinite(v);
+                    p.xs[c * p.cs + ix] = v;
+                }
+#pragma unroll
+                for (int c = 0; c < 15; ++c) p.xs[(5 + c) * p.cs + ix] = xc[5 + c] + d.P[c];
+            }
         }
         if (!finite) atomicOr(p.status, ST_NONFINITE);
     }
@@ -410,18 +438,20 @@ __global__ void __launch_bounds__(NT, 1) refine_scan_kernel(const RefineParams p
 
 cudaError_t launch_refine_fwd(const RefineParams& p, int lin, cudaStream_t st)
 {
-    const int threads = 128;
-    const unsigned blocks = (unsigned)((p.cs + threads - 1) / threads);
-    if (lin == LIN_IEKS) refine_fwd_kernel<LIN_IEKS><<<blocks, threads, 0, st>>>(p);
-    else refine_fwd_kernel<LIN_CUBATURE><<<blocks, threads, 0, st>>>(p);
+    const unsigned blocks = (unsigned)((p.cs + RT_THREADS - 1) / RT_THREADS);
+    auto kern = lin == LIN_IEKS ? refine_fwd_kernel<LIN_IEKS> : refine_fwd_kernel<LIN_CUBATURE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT_SMEM);
+    if (e != cudaSuccess) return e;
+    kern<<<blocks, RT_THREADS, RT_SMEM, st>>>(p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_refine_bwd(const RefineParams& p, cudaStream_t st)
 {
-    const int threads = 128;
-    const unsigned blocks = (unsigned)((p.cs + threads - 1) / threads);
-    refine_bwd_kernel<<<blocks, threads, 0, st>>>(p);
+    const unsigned blocks = (unsigned)((p.cs + RT_THREADS - 1) / RT_THREADS);
+    cudaError_t e = cudaFuncSetAttribute(refine_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT_SMEM);
+    if (e != cudaSuccess) return e;
+    refine_bwd_kernel<<<blocks, RT_THREADS, RT_SMEM, st>>>(p);
     return cudaGetLastError();
 }
 

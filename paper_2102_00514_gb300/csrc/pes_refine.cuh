@@ -92,6 +92,35 @@ PES_DEV int traj_of(const int64_t* off, int B, int64_t k)
     return lo;
 }
 
+// ---- per-thread scratch -----------------------------------------------------------
+//
+// The float-float steps below keep the matrices that a rolled loop indexes by
+// its counter in shared memory, one slice per thread: element e of the calling
+// thread at p[e * NT] (a warp's accesses to one element fall in consecutive
+// banks); a float-float value takes two consecutive elements. Rolling the outer
+// loop of each matrix product keeps the code a few thousand instructions long,
+// small enough for the instruction caches, where the fully unrolled form (about
+// 9,000 per step) left most warps waiting for instructions.
+constexpr int SCR_F = 0;     // F, 25 floats
+constexpr int SCR_M = 25;    // a 5x5 float-float matrix (F P, then the gain), 50 floats
+constexpr int SCR_S = 75;    // a packed symmetric float-float matrix (the prediction), 30 floats
+constexpr int SCR_N = 105;   // floats per thread
+
+template <int NT>
+struct Scratch {
+    float* p;
+    PES_DEV float& operator[](int e) const { return p[e * NT]; }
+    PES_DEV ff ld(int e) const { return ff{p[e * NT], p[(e + 1) * NT]}; }
+    PES_DEV void st(int e, ff v) const
+    {
+        p[e * NT] = v.hi;
+        p[(e + 1) * NT] = v.lo;
+    }
+};
+
+// packed index of (i, j), i <= j, for a runtime i
+PES_DEV int si_rt(int i, int j) { return i * 5 - (i * (i - 1)) / 2 + (j - i); }
+
 // ---- the cubature transition slope in float-float -------------------------------
 //
 // The sigma points are xbar +- S e_i with S = fl(scale L), the FP32 factor
@@ -101,24 +130,28 @@ PES_DEV int traj_of(const int64_t* off, int B, int64_t k)
 // formed here with every operation in float-float. The turn angles
 // (w +- S_4i) dt come by angle addition from the reference angle's sine and
 // cosine (float-float series after reduction) and the offsets' (series).
-PES_DEV void cub_trans_slope_ff(const DevModel<float>& m, const float* xbar, const float* L, float* F)
+// Writes F to the scratch (SCR_F); uses SCR_M .. SCR_M + 65 for S and D.
+template <int NT>
+PES_DEV void cub_trans_slope_ff(const DevModel<float>& m, const float* xbar, const float* L, Scratch<NT> sc)
 {
     if (m.kind == MODEL_LINEAR) {
 #pragma unroll
-        for (int i = 0; i < 25; ++i) F[i] = m.F[i];
+        for (int i = 0; i < 25; ++i) sc[SCR_F + i] = m.F[i];
         return;
     }
+    constexpr int SS = SCR_M;        // S, 25 floats
+    constexpr int SD = SCR_M + 25;   // D rows 0..3 by columns, float-float: 40 floats
     const float dt = m.dt;
-    float S[25];
 #pragma unroll
-    for (int i = 0; i < 25; ++i) S[i] = __fmul_rn(m.sp_scale, L[i]);
+    for (int i = 0; i < 25; ++i) sc[SS + i] = __fmul_rn(m.sp_scale, L[i]);
     ff s0, c0, o0;
     ff_sincos(two_prod(xbar[4], dt), &s0, &c0, &o0);
-    ff D[4][5];
-#pragma unroll
+#pragma unroll 1
     for (int i = 0; i < 5; ++i) {
+        const float Spx = sc[SS + i], Spy = sc[SS + 5 + i], Svx = sc[SS + 10 + i], Svy = sc[SS + 15 + i];
+        const float Sw = sc[SS + 20 + i];
         ff se, ce, oe;
-        ff_sincos(two_prod(S[20 + i], dt), &se, &ce, &oe);
+        ff_sincos(two_prod(Sw, dt), &se, &ce, &oe);
         const ff s0ce = ff_mul(s0, ce), c0se = ff_mul(c0, se), s0se = ff_mul(s0, se);
         const ff c0ce = ff_mul(c0, ce);
         const ff omc_base = ff_fma(c0, oe, o0);   // (1 - c0) + c0 (1 - ce)
@@ -130,7 +163,7 @@ PES_DEV void cub_trans_slope_ff(const DevModel<float>& m, const float* xbar, con
             const ff sn = sg == 0 ? ff_add(s0ce, c0se) : ff_sub(s0ce, c0se);
             const ff cs = sg == 0 ? ff_sub(c0ce, s0se) : ff_add(c0ce, s0se);
             const ff om = sg == 0 ? ff_add(omc_base, s0se) : ff_sub(omc_base, s0se);
-            const ff w = two_sum(xbar[4], sgn * S[20 + i]);
+            const ff w = two_sum(xbar[4], sgn * Sw);
             ff A1, A2;
             if (w.hi == 0.0f && w.lo == 0.0f) {
                 A1 = ff_make(dt);
@@ -140,8 +173,8 @@ PES_DEV void cub_trans_slope_ff(const DevModel<float>& m, const float* xbar, con
                 A1 = ff_mul(sn, iw);
                 A2 = ff_mul(om, iw);
             }
-            const ff vx = two_sum(xbar[2], sgn * S[10 + i]);
-            const ff vy = two_sum(xbar[3], sgn * S[15 + i]);
+            const ff vx = two_sum(xbar[2], sgn * Svx);
+            const ff vy = two_sum(xbar[3], sgn * Svy);
             // position increments and velocities of f at the point (the
             // positions themselves contribute 2 S_pi to D, added below)
             z[sg][0] = ff_sub(ff_mul(A1, vx), ff_mul(A2, vy));
@@ -149,96 +182,104 @@ PES_DEV void cub_trans_slope_ff(const DevModel<float>& m, const float* xbar, con
             z[sg][2] = ff_sub(ff_mul(cs, vx), ff_mul(sn, vy));
             z[sg][3] = ff_add(ff_mul(sn, vx), ff_mul(cs, vy));
         }
-        D[0][i] = ff_add_f(ff_sub(z[0][0], z[1][0]), 2.0f * S[i]);
-        D[1][i] = ff_add_f(ff_sub(z[0][1], z[1][1]), 2.0f * S[5 + i]);
-        D[2][i] = ff_sub(z[0][2], z[1][2]);
-        D[3][i] = ff_sub(z[0][3], z[1][3]);
+        sc.st(SD + 2 * (0 * 5 + i), ff_add_f(ff_sub(z[0][0], z[1][0]), 2.0f * Spx));
+        sc.st(SD + 2 * (1 * 5 + i), ff_add_f(ff_sub(z[0][1], z[1][1]), 2.0f * Spy));
+        sc.st(SD + 2 * (2 * 5 + i), ff_sub(z[0][2], z[1][2]));
+        sc.st(SD + 2 * (3 * 5 + i), ff_sub(z[0][3], z[1][3]));
     }
     // rows g of F solve g S = D_r / 2 (S lower triangular), from the last column
     ff rs[5];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) rs[c] = ff_rcp(ff_make(S[c * 5 + c]));
-#pragma unroll
+    for (int c = 0; c < 5; ++c) rs[c] = ff_rcp(ff_make(sc[SS + c * 5 + c]));
+#pragma unroll 1
     for (int r = 0; r < 4; ++r) {
         ff g[5];
 #pragma unroll
         for (int c = 4; c >= 0; --c) {
-            ff acc = ff{0.5f * D[r][c].hi, 0.5f * D[r][c].lo};
+            const ff dd = sc.ld(SD + 2 * (r * 5 + c));
+            ffacc acc = acc_of(ff{0.5f * dd.hi, 0.5f * dd.lo});
 #pragma unroll
-            for (int l = c + 1; l < 5; ++l) acc = ff_fma_f(g[l], -S[l * 5 + c], acc);
-            g[c] = ff_mul(acc, rs[c]);
+            for (int l = c + 1; l < 5; ++l) acc_add(acc, g[l], -sc[SS + l * 5 + c]);
+            g[c] = ff_mul(acc_done(acc), rs[c]);
         }
 #pragma unroll
-        for (int c = 0; c < 5; ++c) F[r * 5 + c] = g[c].hi;
+        for (int c = 0; c < 5; ++c) sc[SCR_F + r * 5 + c] = g[c].hi;
     }
-    F[20] = F[21] = F[22] = F[23] = 0.0f;
-    F[24] = 1.0f;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) sc[SCR_F + 20 + c] = c == 4 ? 1.0f : 0.0f;
 }
 
 // ---- residuals ---------------------------------------------------------------------
 
 // One Kalman step in float-float from the FP32 filtered moments (m, P) of
-// state k, through the transition tr (k -> k+1) and the observation ob of
-// state k+1: the step's exact-arithmetic image (mf, Pf), to about 1e-14
-// relative of the operands, and its derivatives Abar = (I - K H) F,
-// w = F^T H^T S^{-1} v in FP32. Returns false if S is not positive definite.
+// state k, through the transition (k -> k+1: F in the scratch at SCR_F, fx,
+// Q', xn of tr) and the observation ob of state k+1: the step's
+// exact-arithmetic image (mf, Pf), to about 1e-14 relative of the operands,
+// and its derivatives Abar = (I - K H) F, w = F^T H^T S^{-1} v in FP32.
+// Returns false if S is not positive definite.
+template <int NT>
 PES_DEV bool ff_kalman_step(const Trans<float>& tr, const Obs<float>& ob, const float* m, const float* P, ff* mf,
-                            ff* Pf, float* Abar, float* w)
+                            ff* Pf, float* Abar, float* w, Scratch<NT> sc)
 {
-    ff mp[5];
-    {
-        ff dx[5];
+    // F P by rows
+#pragma unroll 1
+    for (int i = 0; i < 5; ++i) {
+        float Fi[5];
 #pragma unroll
-        for (int i = 0; i < 5; ++i) dx[i] = ff_diff_f(m[i], tr.xn[i]);
+        for (int l = 0; l < 5; ++l) Fi[l] = sc[SCR_F + i * 5 + l];
 #pragma unroll
-        for (int i = 0; i < 5; ++i) {
-            ff acc = ff_make(tr.fx[i]);
+        for (int j = 0; j < 5; ++j) {
+            ffacc acc = acc_of(two_prod(Fi[0], P[si(0, j)]));
 #pragma unroll
-            for (int l = 0; l < 5; ++l) acc = ff_fma_f(dx[l], tr.F[i * 5 + l], acc);
-            mp[i] = acc;
+            for (int l = 1; l < 5; ++l) acc_add(acc, Fi[l], P[si(l, j)]);
+            sc.st(SCR_M + 2 * (i * 5 + j), acc_done(acc));
+        }
+    }
+    // (F P) F^T, upper triangle by rows
+#pragma unroll 1
+    for (int i = 0; i < 5; ++i) {
+        ff FPi[5];
+#pragma unroll
+        for (int l = 0; l < 5; ++l) FPi[l] = sc.ld(SCR_M + 2 * (i * 5 + l));
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            if (j < i) continue;
+            ffacc acc = acc_of(ff_mul_f(FPi[0], sc[SCR_F + j * 5]));
+#pragma unroll
+            for (int l = 1; l < 5; ++l) acc_add(acc, FPi[l], sc[SCR_F + j * 5 + l]);
+            sc.st(SCR_S + 2 * si_rt(i, j), acc_done(acc));
         }
     }
     ff Pp[15];
-    {
-        ff FP[25];
 #pragma unroll
-        for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 15; ++i) Pp[i] = ff_add_f(sc.ld(SCR_S + 2 * i), tr.Q[i]);
+    ff mp[5];
 #pragma unroll
-            for (int j = 0; j < 5; ++j) {
-                ff acc = two_prod(tr.F[i * 5], P[si(0, j)]);
+    for (int i = 0; i < 5; ++i) {
+        ffacc acc = acc_of_f(tr.fx[i]);
 #pragma unroll
-                for (int l = 1; l < 5; ++l) acc = ff_fma_ff(tr.F[i * 5 + l], P[si(l, j)], acc);
-                FP[i * 5 + j] = acc;
-            }
-#pragma unroll
-        for (int i = 0; i < 5; ++i)
-#pragma unroll
-            for (int j = i; j < 5; ++j) {
-                ff acc = ff_make(tr.Q[si(i, j)]);
-#pragma unroll
-                for (int l = 0; l < 5; ++l) acc = ff_fma_f(FP[i * 5 + l], tr.F[j * 5 + l], acc);
-                Pp[si(i, j)] = acc;
-            }
+        for (int l = 0; l < 5; ++l) acc_add(acc, ff_diff_f(m[l], tr.xn[l]), sc[SCR_F + i * 5 + l]);
+        mp[i] = acc_done(acc);
     }
     ff HP[10];
 #pragma unroll
     for (int r = 0; r < 2; ++r)
 #pragma unroll
         for (int j = 0; j < 5; ++j) {
-            ff acc = ff_mul_f(Pp[si(0, j)], ob.H[r * 5]);
+            ffacc acc = acc_of(ff_mul_f(Pp[si(0, j)], ob.H[r * 5]));
 #pragma unroll
-            for (int l = 1; l < 5; ++l) acc = ff_fma_f(Pp[si(l, j)], ob.H[r * 5 + l], acc);
-            HP[r * 5 + j] = acc;
+            for (int l = 1; l < 5; ++l) acc_add(acc, Pp[si(l, j)], ob.H[r * 5 + l]);
+            HP[r * 5 + j] = acc_done(acc);
         }
     ff S[3];
 #pragma unroll
     for (int r = 0; r < 2; ++r)
 #pragma unroll
         for (int q = r; q < 2; ++q) {
-            ff acc = ff_make(ob.R[si2(r, q)]);
+            ffacc acc = acc_of_f(ob.R[si2(r, q)]);
 #pragma unroll
-            for (int l = 0; l < 5; ++l) acc = ff_fma_f(HP[r * 5 + l], ob.H[q * 5 + l], acc);
-            S[si2(r, q)] = acc;
+            for (int l = 0; l < 5; ++l) acc_add(acc, HP[r * 5 + l], ob.H[q * 5 + l]);
+            S[si2(r, q)] = acc_done(acc);
         }
     const ff det = ff_sub(ff_mul(S[0], S[2]), ff_mul(S[1], S[1]));
     const bool ok = det.hi > 0.0f && S[0].hi > 0.0f;
@@ -253,154 +294,179 @@ PES_DEV bool ff_kalman_step(const Trans<float>& tr, const Obs<float>& ob, const 
     ff v[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-        ff acc = ff_make(ob.r[r]);
+        ffacc acc = acc_of_f(ob.r[r]);
 #pragma unroll
-        for (int l = 0; l < 5; ++l) acc = ff_fma_f(ff_add_f(mp[l], -ob.xn[l]), -ob.H[r * 5 + l], acc);
-        v[r] = acc;
+        for (int l = 0; l < 5; ++l) acc_add(acc, ff_add_f(mp[l], -ob.xn[l]), -ob.H[r * 5 + l]);
+        v[r] = acc_done(acc);
     }
 #pragma unroll
-    for (int i = 0; i < 5; ++i) mf[i] = ff_fma(KT[5 + i], v[1], ff_fma(KT[i], v[0], mp[i]));
-#pragma unroll
-    for (int i = 0; i < 5; ++i)
-#pragma unroll
-        for (int j = i; j < 5; ++j)
-            Pf[si(i, j)] = ff_fma(ff_neg(KT[5 + i]), HP[5 + j], ff_fma(ff_neg(KT[i]), HP[j], Pp[si(i, j)]));
-    // derivatives, FP32
-    float IKH[25];
-#pragma unroll
-    for (int i = 0; i < 5; ++i)
-#pragma unroll
-        for (int l = 0; l < 5; ++l)
-            IKH[i * 5 + l] = (i == l ? 1.0f : 0.0f) - KT[i].hi * ob.H[l] - KT[5 + i].hi * ob.H[5 + l];
-    mm(IKH, tr.F, Abar);
-    const float Siv0 = Si[0].hi * v[0].hi + Si[1].hi * v[1].hi;
-    const float Siv1 = Si[1].hi * v[0].hi + Si[2].hi * v[1].hi;
-    float hs[5];
-#pragma unroll
-    for (int l = 0; l < 5; ++l) hs[l] = ob.H[l] * Siv0 + ob.H[5 + l] * Siv1;
-    mtv(tr.F, hs, w);
-    return ok;
-}
-
-// One RTS step in float-float: from the refined filtered moments (mf, Pf) of
-// state k, the transition tr out of k, and the FP32 smoothed moments
-// (xs1, Ps1) of state k+1: the step's exact-arithmetic image (ms, Ps) and its
-// gain G = Pf F^T (F Pf F^T + Q')^{-1} in FP32. Returns false if the predicted
-// covariance is not positive definite.
-PES_DEV bool ff_rts_step(const Trans<float>& tr, const ff* mf, const ff* Pf, const float* xs1, const float* Ps1,
-                         ff* ms, ff* Ps, float* G)
-{
-    ff mp[5];
-    {
-        ff dx[5];
-#pragma unroll
-        for (int i = 0; i < 5; ++i) dx[i] = ff_add_f(mf[i], -tr.xn[i]);
-#pragma unroll
-        for (int i = 0; i < 5; ++i) {
-            ff acc = ff_make(tr.fx[i]);
-#pragma unroll
-            for (int l = 0; l < 5; ++l) acc = ff_fma_f(dx[l], tr.F[i * 5 + l], acc);
-            mp[i] = acc;
-        }
+    for (int i = 0; i < 5; ++i) {
+        ffacc acc = acc_of(mp[i]);
+        acc_add(acc, KT[i], v[0]);
+        acc_add(acc, KT[5 + i], v[1]);
+        mf[i] = acc_done(acc);
     }
-    // Gt = (F Pf F^T + Q')^{-1} F Pf, formed in place of F Pf
-    ff Gt[25];
-#pragma unroll
-    for (int i = 0; i < 5; ++i)
-#pragma unroll
-        for (int j = 0; j < 5; ++j) {
-            ff acc = ff_mul_f(Pf[si(0, j)], tr.F[i * 5]);
-#pragma unroll
-            for (int l = 1; l < 5; ++l) acc = ff_fma_f(Pf[si(l, j)], tr.F[i * 5 + l], acc);
-            Gt[i * 5 + j] = acc;
-        }
-    ff Pp[15];
 #pragma unroll
     for (int i = 0; i < 5; ++i)
 #pragma unroll
         for (int j = i; j < 5; ++j) {
-            ff acc = ff_make(tr.Q[si(i, j)]);
-#pragma unroll
-            for (int l = 0; l < 5; ++l) acc = ff_fma_f(Gt[i * 5 + l], tr.F[j * 5 + l], acc);
-            Pp[si(i, j)] = acc;
+            ffacc acc = acc_of(Pp[si(i, j)]);
+            acc_add(acc, ff_neg(KT[i]), HP[j]);
+            acc_add(acc, ff_neg(KT[5 + i]), HP[5 + j]);
+            Pf[si(i, j)] = acc_done(acc);
         }
-    // Cholesky Pp = C C^T (C lower, packed by rows into Pp's slots) with
-    // reciprocal diagonal rd
+    // derivatives, FP32
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            float t = 0.0f;
+#pragma unroll
+            for (int l = 0; l < 5; ++l) {
+                const float ikh = (i == l ? 1.0f : 0.0f) - KT[i].hi * ob.H[l] - KT[5 + i].hi * ob.H[5 + l];
+                t = fmaf(ikh, sc[SCR_F + l * 5 + j], t);
+            }
+            Abar[i * 5 + j] = t;
+        }
+    const float Siv0 = Si[0].hi * v[0].hi + Si[1].hi * v[1].hi;
+    const float Siv1 = Si[1].hi * v[0].hi + Si[2].hi * v[1].hi;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        float t = 0.0f;
+#pragma unroll
+        for (int l = 0; l < 5; ++l) t = fmaf(sc[SCR_F + l * 5 + i], ob.H[l] * Siv0 + ob.H[5 + l] * Siv1, t);
+        w[i] = t;
+    }
+    return ok;
+}
+
+// One RTS step in float-float: from the refined filtered moments (mf, Pf) of
+// state k, the transition out of k (F in the scratch at SCR_F, fx, Q', xn of
+// tr) and the FP32 smoothed moments (xs1, Ps1) of state k+1. Leaves the gain
+// transposed, G^T = (F Pf F^T + Q')^{-1} F Pf, in the scratch at SCR_M and
+// returns the smoothed mean ms and dP = Ps1 - (F Pf F^T + Q'); the covariance
+// rows Pf + G dP G^T are formed by rts_cov_row.
+// Returns false if the predicted covariance is not positive definite.
+template <int NT>
+PES_DEV bool ff_rts_gain(const Trans<float>& tr, const ff* mf, const ff* Pf, const float* xs1, const float* Ps1,
+                         ff* ms, ff* dP, Scratch<NT> sc)
+{
+    // F Pf by rows
+#pragma unroll 1
+    for (int i = 0; i < 5; ++i) {
+        float Fi[5];
+#pragma unroll
+        for (int l = 0; l < 5; ++l) Fi[l] = sc[SCR_F + i * 5 + l];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            ffacc acc = acc_of(ff_mul_f(Pf[si(0, j)], Fi[0]));
+#pragma unroll
+            for (int l = 1; l < 5; ++l) acc_add(acc, Pf[si(l, j)], Fi[l]);
+            sc.st(SCR_M + 2 * (i * 5 + j), acc_done(acc));
+        }
+    }
+    // (F Pf) F^T, upper triangle by rows
+#pragma unroll 1
+    for (int i = 0; i < 5; ++i) {
+        ff FPi[5];
+#pragma unroll
+        for (int l = 0; l < 5; ++l) FPi[l] = sc.ld(SCR_M + 2 * (i * 5 + l));
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            if (j < i) continue;
+            ffacc acc = acc_of(ff_mul_f(FPi[0], sc[SCR_F + j * 5]));
+#pragma unroll
+            for (int l = 1; l < 5; ++l) acc_add(acc, FPi[l], sc[SCR_F + j * 5 + l]);
+            sc.st(SCR_S + 2 * si_rt(i, j), acc_done(acc));
+        }
+    }
+    ff Pp[15];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) Pp[i] = ff_add_f(sc.ld(SCR_S + 2 * i), tr.Q[i]);
+    // Cholesky Pp = C C^T (C lower, in Pp's packed slots) with reciprocal diagonal rd
     ff C[15], rd[5];
     bool ok = true;
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
-        ff sjj = Pp[si(j, j)];
+        ffacc sj = acc_of(Pp[si(j, j)]);
 #pragma unroll
-        for (int l = 0; l < j; ++l) sjj = ff_fma(ff_neg(C[si(j, l)]), C[si(j, l)], sjj);
+        for (int l = 0; l < j; ++l) acc_add(sj, ff_neg(C[si(j, l)]), C[si(j, l)]);
+        const ff sjj = acc_done(sj);
         ok = ok && sjj.hi > 0.0f;
         const ff d = ff_sqrt(sjj.hi > 0.0f ? sjj : ff_make(1.0f));
         C[si(j, j)] = d;
         rd[j] = ff_rcp(d);
 #pragma unroll
         for (int i = j + 1; i < 5; ++i) {
-            ff t = Pp[si(i, j)];
+            ffacc t = acc_of(Pp[si(i, j)]);
 #pragma unroll
-            for (int l = 0; l < j; ++l) t = ff_fma(ff_neg(C[si(i, l)]), C[si(j, l)], t);
-            C[si(i, j)] = ff_mul(t, rd[j]);
+            for (int l = 0; l < j; ++l) acc_add(t, ff_neg(C[si(i, l)]), C[si(j, l)]);
+            C[si(i, j)] = ff_mul(acc_done(t), rd[j]);
         }
     }
-    // solve C C^T X = Gt column by column
-#pragma unroll
+    // G^T = Pp^{-1} (F Pf), column by column in place
+#pragma unroll 1
     for (int c = 0; c < 5; ++c) {
+        ff x[5];
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
-            ff t = Gt[i * 5 + c];
+            ffacc t = acc_of(sc.ld(SCR_M + 2 * (i * 5 + c)));
 #pragma unroll
-            for (int l = 0; l < i; ++l) t = ff_fma(ff_neg(C[si(i, l)]), Gt[l * 5 + c], t);
-            Gt[i * 5 + c] = ff_mul(t, rd[i]);
+            for (int l = 0; l < i; ++l) acc_add(t, ff_neg(C[si(i, l)]), x[l]);
+            x[i] = ff_mul(acc_done(t), rd[i]);
         }
 #pragma unroll
         for (int i = 4; i >= 0; --i) {
-            ff t = Gt[i * 5 + c];
+            ffacc t = acc_of(x[i]);
 #pragma unroll
-            for (int l = i + 1; l < 5; ++l) t = ff_fma(ff_neg(C[si(l, i)]), Gt[l * 5 + c], t);
-            Gt[i * 5 + c] = ff_mul(t, rd[i]);
+            for (int l = i + 1; l < 5; ++l) acc_add(t, ff_neg(C[si(l, i)]), x[l]);
+            x[i] = ff_mul(acc_done(t), rd[i]);
         }
+#pragma unroll
+        for (int i = 0; i < 5; ++i) sc.st(SCR_M + 2 * (i * 5 + c), x[i]);
     }
-    // G_ij = Gt_ji
+    // ms = mf + G (xs1 - mp), mp = fx + F (mf - xn)
     ff e[5];
 #pragma unroll
-    for (int j = 0; j < 5; ++j) e[j] = ff_add_f(ff_neg(mp[j]), xs1[j]);
+    for (int i = 0; i < 5; ++i) {
+        ffacc acc = acc_of_f(tr.fx[i]);
+#pragma unroll
+        for (int l = 0; l < 5; ++l) acc_add(acc, ff_add_f(mf[l], -tr.xn[l]), sc[SCR_F + i * 5 + l]);
+        e[i] = ff_add_f(ff_neg(acc_done(acc)), xs1[i]);
+    }
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-        ff acc = mf[i];
+        ffacc acc = acc_of(mf[i]);
 #pragma unroll
-        for (int j = 0; j < 5; ++j) acc = ff_fma(Gt[j * 5 + i], e[j], acc);
-        ms[i] = acc;
+        for (int j = 0; j < 5; ++j) acc_add(acc, sc.ld(SCR_M + 2 * (j * 5 + i)), e[j]);
+        ms[i] = acc_done(acc);
     }
-    // Ps = Pf + G (Ps1 - Pp) G^T, one row of G (Ps1 - Pp) at a time
-    ff dP[15];
 #pragma unroll
     for (int i = 0; i < 15; ++i) dP[i] = ff_add_f(ff_neg(Pp[i]), Ps1[i]);
+    return ok;
+}
+
+// Row i of G (Ps1 - Pp) G^T: G_il = Gt_li from the scratch; dP = Ps1 - Pp.
+// Writes the row's upper part (j >= i) through out(j, value).
+template <int NT, class Out>
+PES_DEV void rts_cov_row(int i, const ff* dP, Scratch<NT> sc, Out out)
+{
+    ff row[5];
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
-        ff row[5];
+    for (int j = 0; j < 5; ++j) {
+        ffacc acc = acc_of(ff_mul(sc.ld(SCR_M + 2 * (0 * 5 + i)), dP[si(0, j)]));
 #pragma unroll
-        for (int j = 0; j < 5; ++j) {
-            ff acc = ff_mul(Gt[i], dP[si(0, j)]);
-#pragma unroll
-            for (int l = 1; l < 5; ++l) acc = ff_fma(Gt[l * 5 + i], dP[si(l, j)], acc);
-            row[j] = acc;
-        }
-#pragma unroll
-        for (int j = i; j < 5; ++j) {
-            ff acc = Pf[si(i, j)];
-#pragma unroll
-            for (int l = 0; l < 5; ++l) acc = ff_fma(row[l], Gt[l * 5 + j], acc);
-            Ps[si(i, j)] = acc;
-        }
+        for (int l = 1; l < 5; ++l) acc_add(acc, sc.ld(SCR_M + 2 * (l * 5 + i)), dP[si(l, j)]);
+        row[j] = acc_done(acc);
     }
 #pragma unroll
-    for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) {
+        if (j < i) continue;
+        ffacc acc = acc_of(ff_mul(row[0], sc.ld(SCR_M + 2 * (0 * 5 + j))));
 #pragma unroll
-        for (int j = 0; j < 5; ++j) G[i * 5 + j] = Gt[j * 5 + i].hi;
-    return ok;
+        for (int l = 1; l < 5; ++l) acc_add(acc, row[l], sc.ld(SCR_M + 2 * (l * 5 + j)));
+        out(j, acc_done(acc));
+    }
 }
 
 // ---- correction elements and their composition --------------------------------------
