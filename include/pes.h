@@ -311,8 +311,11 @@ pes_status pes_traj_iterations(pes_handle* h, int32_t* iters, int32_t B, void* s
  * until the process exits.
  *
  * Arguments, layouts and results are those of pes_ieks_run (DEVICE pointers),
- * for PES_FP64 and PES_FP32; PES_MIXED, whose FP64 copies pes_ieks_run
- * allocates, returns PES_ERR_UNSUPPORTED. Limits: N <= PES_NOALLOC_MAX_STATES and B <= PES_NOALLOC_MAX_BATCH; larger
+ * for PES_FP64 and PES_FP32; PES_MIXED and PES_REFINED, whose FP64 copies or
+ * refinement workspace pes_ieks_run allocates, return PES_ERR_UNSUPPORTED.
+ * Per-trajectory iteration counts (pes_traj_iterations) are not kept, and only
+ * the status code reports a failure (there is no handle to hold its text).
+ * Grid-wide waits honour PES_BARRIER_TIMEOUT_MS as pes_create does. Limits: N <= PES_NOALLOC_MAX_STATES and B <= PES_NOALLOC_MAX_BATCH; larger
  * sizes return PES_ERR_INVALID_ARG before anything is launched.
  * The first call on a device sets the scratch up (it looks up the array's
  * device address and clears its counters), so make that first call before

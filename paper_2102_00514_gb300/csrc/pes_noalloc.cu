@@ -12,6 +12,7 @@
 // holds until the process exits.
 #include <cuda_runtime.h>
 
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -72,6 +73,11 @@ pes_status setup(int dev)
     pes_handle& h = g_handle[dev];
     h.device = dev;
     h.num_sms = sms;
+    // the same time limit on grid-wide waits as pes_create gives a handle
+    if (const char* env = getenv("PES_BARRIER_TIMEOUT_MS")) {
+        const long long ms = atoll(env);
+        if (ms > 0) h.timeout_ns = ms * 1000000LL;
+    }
     h.max_states = kMaxStates;
     h.max_batch = kMaxBatch;
     h.nb_max = kMaxBlocks;
@@ -107,7 +113,8 @@ extern "C" pes_status pes_ieks_run_noalloc(const pes_model* model, pes_method me
                                            int32_t* iters_used, void* stream)
 {
     if (N > kMaxStates || B > kMaxBatch || N < 1 || B < 1) return PES_ERR_INVALID_ARG;
-    if (prec == PES_MIXED) return PES_ERR_UNSUPPORTED;   // its FP64 copies would be allocated
+    // PES_MIXED's FP64 copies and PES_REFINED's workspace would be allocated
+    if (prec == PES_MIXED || prec == PES_REFINED) return PES_ERR_UNSUPPORTED;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PES_ERR_CUDA;
     const pes_status st = setup(dev);
@@ -117,6 +124,14 @@ extern "C" pes_status pes_ieks_run_noalloc(const pes_model* model, pes_method me
     // device status, so the call returns with its scratch no longer in use.
     const pes_status r = pes_ieks_run(&g_handle[dev], model, method, prec, y, offsets, B, N, m0, P0, x_init, P_init,
                                       max_iters, tol, x_out, P_out, &used, stream);
+    if (r != PES_OK && r != PES_ERR_NOT_CONVERGED) {
+        // a failure after some work was queued returns before that work is
+        // waited for: wait here, and clear the status word, so that the call
+        // still returns with the scratch idle and the next call starts clean
+        cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+        cudaMemset(g_handle[dev].status, 0, sizeof(int));
+        cudaGetLastError();
+    }
     if (iters_used) *iters_used = used;
     return r;
 }

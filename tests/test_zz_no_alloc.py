@@ -19,14 +19,15 @@ from tests.gpu_common import TOL_FP32, TOL_FP64, rel_err, workload_to_dev
 pytestmark = pytest.mark.gpu
 
 
-def run_noalloc(lib, d, method, prec, N, B, iters):
+def run_noalloc(lib, d, method, prec, N, B, iters, tol=0.0, out=None):
     dt = torch.float64 if prec == pes.FP64 else torch.float32
-    x = torch.empty((5, N), dtype=dt, device="cuda")
-    P = torch.empty((15, N), dtype=dt, device="cuda")
+    if out is None:
+        out = (torch.empty((5, N), dtype=dt, device="cuda"), torch.empty((15, N), dtype=dt, device="cuda"))
+    x, P = out
     used = ctypes.c_int32(0)
     ms = d["model"].as_struct()
     st = lib.pes_ieks_run_noalloc(ctypes.byref(ms), method, prec, d["y"].data_ptr(), d["offsets"].data_ptr(), B, N,
-                                  d["m0"].data_ptr(), d["P0"].data_ptr(), None, None, iters, 0.0, x.data_ptr(),
+                                  d["m0"].data_ptr(), d["P0"].data_ptr(), None, None, iters, tol, x.data_ptr(),
                                   P.data_ptr(), ctypes.byref(used), torch.cuda.current_stream().cuda_stream)
     return st, x, P, used.value
 
@@ -59,13 +60,63 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     assert st == pes.INVALID_ARG
 
 
-def test_noalloc_rejects_mixed_precision():
-    # PES_MIXED keeps FP64 copies that pes_ieks_run allocates
+def test_noalloc_rejects_mixed_and_refined_precision():
+    # PES_MIXED keeps FP64 copies, PES_REFINED a workspace, that pes_ieks_run allocates
     lib = pes.load_library()
     wl = synth.workload("ieks_T500")
     d = workload_to_dev(wl, pes.FP32)
-    st, _, _, _ = run_noalloc(lib, d, pes.IEKS, pes.MIXED, wl["y"].shape[1], 1, 2)
-    assert st == pes.UNSUPPORTED
+    for prec in (pes.MIXED, pes.REFINED):
+        st, _, _, _ = run_noalloc(lib, d, pes.IEKS, prec, wl["y"].shape[1], 1, 2)
+        assert st == pes.UNSUPPORTED
+
+
+@pytest.mark.parametrize("method", [pes.IEKS, pes.CUBATURE])
+def test_noalloc_at_its_limits_allocates_nothing(method):
+    """N = PES_NOALLOC_MAX_STATES states in B = PES_NOALLOC_MAX_BATCH
+    trajectories (the lane padding closest to the scratch's capacity, the
+    per-trajectory arrays full), equal to pes_ieks_run; free device memory as
+    cudaMemGetInfo reports it does not change between a first and a second call."""
+    lib = pes.load_library()
+    B, N = 64, 8192
+    wl = synth.ct_bearings(np.full(B, N // B - 1), seed=6, sensor_jitter=0.2, omega0_halfwidth=1.0)
+    assert wl["y"].shape[1] == N
+    d = workload_to_dev(wl, pes.FP32)
+    sm = pes.Smoother(N, B)
+    xr, Pr, _, _ = sm.ieks_run(d["model"], method, pes.FP32, d["y"], d["offsets"], d["m0"], d["P0"], iters=3)
+    sm.sync()
+    ref_x, ref_P = xr.double().cpu().numpy(), Pr.double().cpu().numpy()
+    sm.close()
+    out = (torch.empty((5, N), dtype=torch.float32, device="cuda"),
+           torch.empty((15, N), dtype=torch.float32, device="cuda"))
+    st, x, P, used = run_noalloc(lib, d, method, pes.FP32, N, B, 3, out=out)
+    assert st == pes.OK and used == 3
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    st, x, P, used = run_noalloc(lib, d, method, pes.FP32, N, B, 3, out=out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free_before
+    assert st == pes.OK and used == 3
+    assert rel_err(x.double().cpu().numpy(), ref_x, wl["offsets"]) < TOL_FP32
+    assert rel_err(P.double().cpu().numpy(), ref_P, wl["offsets"]) < TOL_FP32
+
+
+def test_noalloc_tolerance_mode_matches_handle_entry_point():
+    lib = pes.load_library()
+    wl = synth.workload("ieks_T500")
+    N = wl["y"].shape[1]
+    d = workload_to_dev(wl, pes.FP64)
+    sm = pes.Smoother(N, 1)
+    xr, Pr, used_r, _ = sm.ieks_run(d["model"], pes.IEKS, pes.FP64, d["y"], d["offsets"], d["m0"], d["P0"],
+                                    iters=40, tol=1e-6)
+    ref_x = xr.cpu().numpy()
+    sm.close()
+    for _ in range(2):
+        st, x, P, used = run_noalloc(lib, d, pes.IEKS, pes.FP64, N, 1, 40, tol=1e-6)
+        assert st == pes.OK and used == used_r
+        assert rel_err(x.cpu().numpy(), ref_x, wl["offsets"]) < TOL_FP64
+    # a tolerance the iteration cannot reach: not converged, outputs still set
+    st, x, _, used = run_noalloc(lib, d, pes.IEKS, pes.FP64, N, 1, 2, tol=1e-14)
+    assert st == pes.NOT_CONVERGED and used == 2 and np.isfinite(x.cpu().numpy()).all()
 
 
 def test_noalloc_unscented_and_damped_match_handle_entry_point():
