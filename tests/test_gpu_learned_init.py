@@ -156,10 +156,15 @@ def test_invalid_arguments_rejected(net):
 
 def test_trained_initialiser_saves_iterations():
     """Trained on the GPU (its own kernels) against converged FP64 smoother
-    means of 2,048 trajectories of T = 1,000, the network's start must bring
-    held-out trajectories of other lengths to the 1e-6 tolerance in fewer
-    iterations than the prior start, on the trajectories both starts bring
-    there, and to the same solution."""
+    means of 2,048 trajectories of T = 1,000, the network's start is compared
+    with the prior start on held-out trajectories of T = 1,000 .. 10,000 (its
+    validity domain, up to ten times the training length), paired over every
+    trajectory: a trajectory that does not reach the 1e-6 tolerance within 50
+    iterations counts at 50. Iterations saved, the number of trajectories
+    brought to tolerance, and the final position error against the truth per
+    trajectory and on average are held to the bounds below; where the
+    network's start ends at another fixed point of the iteration, that point
+    is worse about as often as it is better."""
     from paper_2102_00514_gb300 import learned_init as L
     wl = synth.workload("train2048_T1000")
     x, conv = L.converged_targets(wl)
@@ -175,9 +180,32 @@ def test_trained_initialiser_saves_iterations():
     print("evaluation:", s)
     n.close()
     assert log.losses[-1][1] < 0.5 * log.losses[0][1]
-    assert s["converged_learned"] >= s["converged_prior"] - 1
-    assert s["converged_both"] >= 0.5 * s["trajectories"]
-    assert s["iters_saved"] >= 1.0
-    # mostly the same fixed point; where the start picks another one it is no worse
-    assert s["same_solution_within_1e-4"] >= 0.75 * s["converged_both"]
-    assert s["median_position_rmse_learned"] <= 1.05 * s["median_position_rmse_prior"]
+    assert s["converged_learned"] >= s["converged_prior"]
+    assert s["iters_saved_capped"] >= 3.0
+    assert s["error_no_worse_fraction"] >= 0.92
+    assert s["mean_position_rmse_all_learned"] <= s["mean_position_rmse_all_prior"]
+
+
+def test_gated_start_falls_back_to_the_prior_beyond_its_domain():
+    """Past the validity length the library's start is the prior mean itself:
+    those trajectories take exactly the prior start's iterations to the same
+    result; the shorter ones take the network's start."""
+    from paper_2102_00514_gb300 import learned_init as L
+    ev = synth.ct_bearings([1500, 30000, 2500, 60000], seed=11, sensor_jitter=0.2)
+    n = pes.InitNet(ev["y"].shape[1] + 1, 8)
+    n.set_params(L.initial_params(1), np.zeros(5), np.ones(5))
+    r = L.evaluate(n, ev, t_valid=10000)
+    T = np.diff(ev["offsets"]) - 1
+    far = T > 10000
+    assert np.array_equal(r.iters_learned[far], r.iters_prior[far])
+    assert np.all(r.rel_diff[far] == 0.0)
+    x_net = n.forward(pes.FP64, to_dev(ev["y"]), to_dev(ev["offsets"], torch.int64))
+    xg = L.gated_start(x_net, ev, 10000).cpu().numpy()
+    off = ev["offsets"]
+    for b in range(4):
+        sl = slice(int(off[b]), int(off[b + 1]))
+        if far[b]:
+            assert np.all(xg[:, sl] == ev["m0"][b][:, None])
+        else:
+            assert np.array_equal(xg[:, sl], x_net.cpu().numpy()[:, sl])
+    n.close()
