@@ -121,6 +121,10 @@ def _load():
         lib.orc_kf_loglik.restype = i
         lib.orc_iterated_smoother.argtypes = [mp, i, i64, p, i64, p, p, p, p, p, i, d, p, p, p, p]
         lib.orc_iterated_smoother.restype = i
+        lib.orc_map_cost.argtypes = [mp, i64, p, i64, p, p, p, p, p]
+        lib.orc_map_cost.restype = i
+        lib.orc_iterated_smoother_lm.argtypes = [mp, i64, p, i64, p, p, p, p, i, d, d, d, p, p, p, p, p, p]
+        lib.orc_iterated_smoother_lm.restype = i
         lib.orc_filter_element.argtypes = [p] * 7 + [ctypes.POINTER(FElem)]
         lib.orc_filter_element.restype = i
         lib.orc_filter_prior_element.argtypes = [p, p, ctypes.POINTER(FElem)]
@@ -411,6 +415,48 @@ def iterated_smoother(model: Model, method: int, offsets, y, m0, P0, x_init=None
         raise np.linalg.LinAlgError(f"orc_iterated_smoother status {st}")
     return dict(x=np.ascontiguousarray(x.T), P=_sym_soa(P, 5), iters_used=used.value,
                 rel_history=hist[:used.value].copy(), status=st)
+
+
+def map_cost(model: Model, offsets, y, m0, P0, x) -> np.ndarray:
+    """The MAP objective of Eq. 4 per trajectory (positive definite Q), at the
+    trajectory x [5][N]."""
+    lib = _load()
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    N = int(offsets[-1])
+    B = len(offsets) - 1
+    m0a = _f64(m0).reshape(B, 5)
+    P0a = np.ascontiguousarray(sym_full(_f64(P0).reshape(B, 15), 5).reshape(B, 25))
+    out = np.zeros(B)
+    st = lib.orc_map_cost(ctypes.byref(model.s), N, _p(offsets), B, _p(_aos(y)), _p(m0a), _p(P0a), _p(_aos(x)),
+                          _p(out))
+    if st != OK:
+        raise np.linalg.LinAlgError(f"orc_map_cost status {st}")
+    return out
+
+
+def iterated_smoother_lm(model: Model, offsets, y, m0, P0, x_init=None, iters: int = 10, tol: float = 0.0,
+                         lambda0: float = 1.0, nu: float = 10.0) -> dict:
+    """The IEKS with Levenberg-Marquardt steps and adaptive per-trajectory
+    damping (Sec. 3). Returns SoA x [5][N], P [15][N], iters_used, and per
+    trajectory the final damping, the first converged iteration and the
+    number of accepted steps."""
+    lib = _load()
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    N = int(offsets[-1])
+    B = len(offsets) - 1
+    m0a = _f64(m0).reshape(B, 5)
+    P0a = np.ascontiguousarray(sym_full(_f64(P0).reshape(B, 15), 5).reshape(B, 25))
+    xi = _aos(x_init) if x_init is not None else None
+    x = np.zeros((N, 5)); P = np.zeros((N, 25))
+    used = ctypes.c_int(0)
+    lam = np.zeros(B); conv = np.zeros(B, dtype=np.int32); acc = np.zeros(B, dtype=np.int32)
+    st = lib.orc_iterated_smoother_lm(ctypes.byref(model.s), N, _p(offsets), B, _p(_aos(y)), _p(m0a), _p(P0a),
+                                      _p(xi) if xi is not None else None, int(iters), float(tol), float(lambda0),
+                                      float(nu), _p(x), _p(P), ctypes.byref(used), _p(lam), _p(conv), _p(acc))
+    if st not in (OK, NOT_CONVERGED):
+        raise np.linalg.LinAlgError(f"orc_iterated_smoother_lm status {st}")
+    return dict(x=np.ascontiguousarray(x.T), P=_sym_soa(P, 5), iters_used=used.value, lam=lam, conv_iter=conv,
+                accepted=acc, status=st)
 
 
 # ---- single elements (Eqs. 13-19) ------------------------------------------------

@@ -834,6 +834,152 @@ int orc_iterated_smoother(const orc_model* m, int method, int64_t N, const int64
 }
 
 /* ------------------------------------------------------------------------- */
+/* Levenberg-Marquardt with an adaptive damping (Sec. 3 names the LM variant)  */
+/* ------------------------------------------------------------------------- */
+
+/* The MAP objective of Eq. 4 that the IEKS minimises by Gauss-Newton steps
+ * (Sec. 3), per trajectory, for a positive definite Q:
+ *   J = 1/2 |x_0 - m0|^2_{P0^-1} + 1/2 sum_k |x_k - f(x_{k-1})|^2_{Q^-1}
+ *       + 1/2 sum_k |y_k - h(x_k)|^2_{R^-1},
+ * the bearing residuals taken on the branch nearest zero. Returns ORC_NOT_PD
+ * if Q, R or P0 is not positive definite. */
+int orc_map_cost(const orc_model* m, int64_t N, const int64_t* offsets, int64_t B, const double* y,
+                 const double* m0, const double* P0, const double* x, double* cost)
+{
+    (void)N;
+    double Q[25], R[4], Qi[25], Ri[4];
+    orc_process_noise(m, Q);
+    orc_measurement_noise(m, R);
+    double LQ[25];
+    if (!cholesky(NX, Q, LQ) || !inverse(NX, Q, Qi) || !inverse(NY, R, Ri) || R[0] <= 0.0) return ORC_NOT_PD;
+    for (int64_t b = 0; b < B; ++b) {
+        const int64_t k0 = offsets[b], k1 = offsets[b + 1];
+        double P0i[25], L0[25];
+        if (!cholesky(NX, P0 + 25 * b, L0) || !inverse(NX, P0 + 25 * b, P0i)) return ORC_NOT_PD;
+        double J = 0.0, e[NX], t[NX];
+        for (int i = 0; i < NX; ++i) e[i] = x[5 * k0 + i] - m0[5 * b + i];
+        mv(NX, NX, P0i, e, t);
+        for (int i = 0; i < NX; ++i) J += 0.5 * e[i] * t[i];
+        for (int64_t k = k0 + 1; k < k1; ++k) {
+            double fx[NX];
+            model_f(m, x + 5 * (k - 1), fx);
+            for (int i = 0; i < NX; ++i) e[i] = x[5 * k + i] - fx[i];
+            mv(NX, NX, Qi, e, t);
+            for (int i = 0; i < NX; ++i) J += 0.5 * e[i] * t[i];
+            double hx[NY], r[NY], u[NY];
+            model_h(m, b, x + 5 * k, hx);
+            for (int i = 0; i < NY; ++i) {
+                r[i] = y[2 * k + i] - hx[i];
+                if (angles(m)) r[i] = orc_wrap(r[i]);
+            }
+            mv(NY, NY, Ri, r, u);
+            for (int i = 0; i < NY; ++i) J += 0.5 * r[i] * u[i];
+        }
+        cost[b] = J;
+    }
+    return ORC_OK;
+}
+
+/* The IEKS with Levenberg-Marquardt steps and an adaptive damping, per
+ * trajectory b: the step of iteration i is the IEKS iteration about the
+ * current nominal with the pseudo-measurement damping lambda_b (the smoother
+ * of orc_kf_rts_damped); it is accepted if it lowers the MAP cost
+ * (orc_map_cost), and then lambda_b <- lambda_b / nu; otherwise the nominal
+ * stays and lambda_b <- lambda_b * nu. Every trajectory starts at lambda0.
+ * A trajectory has converged at the first iteration whose step (accepted or
+ * not: near the optimum the cost no longer separates a step from the nominal)
+ * has a relative size ||x_step - x_nom||_F / ||x_step||_F <= tol; with tol > 0
+ * the iteration stops
+ * once every trajectory has (ORC_NOT_CONVERGED if max_iters come first), with
+ * tol <= 0 it runs max_iters iterations. Outputs: the accepted nominal x_out
+ * [N][5], the damped smoother's covariances of each trajectory's last
+ * accepted step P_out [N][25] (the prior covariance P0 until one is accepted),
+ * iterations run, and per trajectory (each may be NULL) the final damping,
+ * the first converged iteration (0: none) and the number of accepted steps. */
+int orc_iterated_smoother_lm(const orc_model* m, int64_t N, const int64_t* offsets, int64_t B, const double* y,
+                             const double* m0, const double* P0, const double* x_init, int max_iters, double tol,
+                             double lambda0, double nu, double* x_out, double* P_out, int* iters_used,
+                             double* lambda_out, int* conv_iter, int* accepted)
+{
+    double* F = (double*)malloc(sizeof(double) * 25 * N);
+    double* c = (double*)malloc(sizeof(double) * 5 * N);
+    double* Qp = (double*)malloc(sizeof(double) * 25 * N);
+    double* H = (double*)malloc(sizeof(double) * 10 * N);
+    double* d = (double*)malloc(sizeof(double) * 2 * N);
+    double* Rp = (double*)malloc(sizeof(double) * 4 * N);
+    double* yu = (double*)malloc(sizeof(double) * 2 * N);
+    double* xf = (double*)malloc(sizeof(double) * 5 * N);
+    double* Pf = (double*)malloc(sizeof(double) * 25 * N);
+    double* xs = (double*)malloc(sizeof(double) * 5 * N);
+    double* Ps = (double*)malloc(sizeof(double) * 25 * N);
+    double* lam = (double*)malloc(sizeof(double) * B);
+    double* Jcur = (double*)malloc(sizeof(double) * B);
+    double* Jnew = (double*)malloc(sizeof(double) * B);
+    int* conv = (int*)calloc((size_t)B, sizeof(int));
+    int* acc = (int*)calloc((size_t)B, sizeof(int));
+    for (int64_t b = 0; b < B; ++b) {
+        lam[b] = lambda0;
+        for (int64_t k = offsets[b]; k < offsets[b + 1]; ++k) {
+            if (x_init) memcpy(x_out + 5 * k, x_init + 5 * k, sizeof(double) * 5);
+            else memcpy(x_out + 5 * k, m0 + 5 * b, sizeof(double) * 5);
+            memcpy(P_out + 25 * k, P0 + 25 * b, sizeof(double) * 25);
+        }
+    }
+    int status = orc_map_cost(m, N, offsets, B, y, m0, P0, x_out, Jcur);
+    int it = 0, all = 0;
+    for (it = 1; it <= max_iters && status == ORC_OK; ++it) {
+        status = orc_linearize(m, ORC_IEKS, N, offsets, B, x_out, NULL, y, F, c, Qp, H, d, Rp, yu);
+        if (status != ORC_OK) break;
+        /* each trajectory's damped step with its own lambda */
+        for (int64_t b = 0; b < B && status == ORC_OK; ++b) {
+            const int64_t k0 = offsets[b], n = offsets[b + 1] - k0;
+            const int64_t o1[2] = {0, n};
+            status = orc_kf_rts_damped(n, o1, 1, F + 25 * k0, c + 5 * k0, Qp + 25 * k0, H + 10 * k0, d + 2 * k0,
+                                       Rp + 4 * k0, yu + 2 * k0, m0 + 5 * b, P0 + 25 * b, x_out + 5 * k0, lam[b],
+                                       xf + 5 * k0, Pf + 25 * k0, xs + 5 * k0, Ps + 25 * k0);
+        }
+        if (status != ORC_OK) break;
+        status = orc_map_cost(m, N, offsets, B, y, m0, P0, xs, Jnew);
+        if (status != ORC_OK) break;
+        all = 1;
+        for (int64_t b = 0; b < B; ++b) {
+            const int64_t k0 = offsets[b], k1 = offsets[b + 1];
+            double num = 0.0, den = 0.0;
+            for (int64_t k = k0; k < k1; ++k)
+                for (int i = 0; i < 5; ++i) {
+                    const double dv = xs[5 * k + i] - x_out[5 * k + i];
+                    num += dv * dv;
+                    den += xs[5 * k + i] * xs[5 * k + i];
+                }
+            const double rel = den > 0.0 ? sqrt(num / den) : sqrt(num);
+            if (Jnew[b] < Jcur[b]) {
+                memcpy(x_out + 5 * k0, xs + 5 * k0, sizeof(double) * 5 * (k1 - k0));
+                memcpy(P_out + 25 * k0, Ps + 25 * k0, sizeof(double) * 25 * (k1 - k0));
+                Jcur[b] = Jnew[b];
+                lam[b] /= nu;
+                ++acc[b];
+            } else {
+                lam[b] *= nu;
+            }
+            if (!conv[b] && tol > 0.0 && rel <= tol) conv[b] = it;
+            all = all && conv[b];
+        }
+        if (tol > 0.0 && all) break;
+    }
+    if (it > max_iters) it = max_iters;
+    if (iters_used) *iters_used = it;
+    if (status == ORC_OK && tol > 0.0 && !all) status = ORC_NOT_CONVERGED;
+    for (int64_t b = 0; b < B; ++b) {
+        if (lambda_out) lambda_out[b] = lam[b];
+        if (conv_iter) conv_iter[b] = conv[b];
+        if (accepted) accepted[b] = acc[b];
+    }
+    free(F); free(c); free(Qp); free(H); free(d); free(Rp); free(yu);
+    free(xf); free(Pf); free(xs); free(Ps); free(lam); free(Jcur); free(Jnew); free(conv); free(acc);
+    return status;
+}
+
+/* ------------------------------------------------------------------------- */
 /* the paper's parallel-form elements and operators, written literally        */
 /* ------------------------------------------------------------------------- */
 

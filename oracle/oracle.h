@@ -94,6 +94,16 @@ int orc_iterated_smoother(const orc_model* m, int method, int64_t N, const int64
                           const double* x_init, const double* P_init, int max_iters, double tol,
                           double* x_out, double* P_out, int* iters_used, double* rel_history);
 
+/* MAP objective of Eq. 4 per trajectory (positive definite Q), and the IEKS
+ * with Levenberg-Marquardt steps whose damping adapts per trajectory (Sec. 3):
+ * see oracle.c. */
+int orc_map_cost(const orc_model* m, int64_t N, const int64_t* offsets, int64_t B, const double* y,
+                 const double* m0, const double* P0, const double* x, double* cost);
+int orc_iterated_smoother_lm(const orc_model* m, int64_t N, const int64_t* offsets, int64_t B, const double* y,
+                             const double* m0, const double* P0, const double* x_init, int max_iters, double tol,
+                             double lambda0, double nu, double* x_out, double* P_out, int* iters_used,
+                             double* lambda_out, int* conv_iter, int* accepted);
+
 int orc_filter_element(const double F[25], const double c[5], const double Qp[25],
                        const double H[10], const double d[2], const double Rp[4], const double y[2],
                        orc_felem* e);

@@ -144,3 +144,18 @@ def gauss_newton_step(x, f, fjac, h, hjac, Q, R, y, m0, P0, damping=0.0):
     g = Jm.T @ W @ r
     dx = -np.linalg.solve(A + damping * np.eye(nv), g)
     return x + dx.reshape(T + 1, n), 2.0 * g
+
+
+def map_objective(x, f, h, Q, R, y, m0, P0):
+    """The MAP objective of the model (without the factor 1/2):
+        |x_0 - m0|^2_{P0^-1} + sum_k |x_k - f(x_{k-1})|^2_{Q^-1} + sum_k |y_k - h(x_k)|^2_{R^-1}
+    for a trajectory x [T+1][5] (Q positive definite)."""
+    T = len(x) - 1
+    e0 = x[0] - m0
+    J = float(e0 @ np.linalg.solve(P0, e0))
+    for k in range(1, T + 1):
+        e = x[k] - f(x[k - 1])
+        J += float(e @ np.linalg.solve(Q, e))
+        r = y[k] - h(x[k])
+        J += float(r @ np.linalg.solve(R, r))
+    return J
