@@ -284,6 +284,39 @@ pes_status pes_ieks_run_sequential(pes_handle* h, const pes_model* model, pes_me
                                    void* stream);
 
 /*
+ * The IEKS with Levenberg-Marquardt steps whose damping adapts per trajectory
+ * (Sec. 3 names the Levenberg-Marquardt variant of the iteration). A step is
+ * one IEKS iteration about the current nominal with the damping of
+ * pes_model.lm_lambda taken per trajectory (the pseudo-measurement
+ * xbar_k = x_k + e, e ~ N(0, I / lambda_b), at every state): it is kept if it
+ * lowers the trajectory's MAP objective
+ *   J = 1/2 |x_0 - m0|^2_{P0^-1} + 1/2 sum_k |x_k - f(x_{k-1})|^2_{Q^-1}
+ *       + 1/2 sum_k |y_k - h(x_k)|^2_{R^-1}
+ * (bearing residuals on the branch nearest zero; evaluated in FP64), and then
+ * lambda_b <- lambda_b / nu; otherwise the trajectory's nominal and
+ * covariances stay and lambda_b <- lambda_b * nu. Every trajectory starts at
+ * lambda0 (> 0), nu > 1. The objective needs a positive definite Q and R
+ * (q_form 1, or a linear model with them): otherwise PES_ERR_UNSUPPORTED.
+ * Convergence: a trajectory has converged at the first iteration whose step,
+ * kept or not, has a relative size ||x_step - x_nom||_F / ||x_step||_F <= tol;
+ * with tol > 0 the iteration stops once all have (PES_ERR_NOT_CONVERGED if
+ * max_iters come first; the call then synchronises every iteration), with
+ * tol <= 0 it runs max_iters iterations. pes_model.lm_lambda must be 0.
+ * Arguments and layouts as pes_ieks_run (PES_FP64 or PES_FP32; x_init may be
+ * NULL for the prior start). Outputs: x_out [5][N] the kept nominal, P_out
+ * [15][N] the damped smoother's covariances of each trajectory's last kept
+ * step (its prior P0 if none was kept); HOST, each may be NULL:
+ * *iters_used, lambda_out [B] the final dampings, accepted_out [B] the steps
+ * kept, conv_iter_out [B] the converged iteration (0: none). Synchronises
+ * `stream` before returning.
+ */
+pes_status pes_ieks_run_lm(pes_handle* h, const pes_model* model, pes_precision prec, const void* y,
+                           const int64_t* offsets, int32_t B, int64_t N, const void* m0, const void* P0,
+                           const void* x_init, int32_t max_iters, double tol, double lambda0, double nu,
+                           void* x_out, void* P_out, int32_t* iters_used, double* lambda_out,
+                           int32_t* accepted_out, int32_t* conv_iter_out, void* stream);
+
+/*
  * Per-trajectory iteration counts of the last pes_ieks_run,
  * pes_ieks_run_host or pes_ieks_run_sequential call on this handle that ran in
  * tolerance mode (tol > 0) with PES_FP32 or PES_FP64: iters[b] (HOST int32 [B]) is the first iteration

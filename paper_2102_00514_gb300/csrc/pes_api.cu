@@ -11,6 +11,7 @@
 #include "pes.h"
 #include "pes_handle.h"
 #include "pes_internal.h"
+#include "pes_lm.cuh"
 #include "pes_refine.cuh"
 
 using namespace pes;
@@ -564,6 +565,179 @@ static pes_status ieks_run_refined(pes_handle* h, const pes_model* model, pes_me
     return PES_OK;
 }
 
+// Process and measurement noise of the model in FP64 (packed), as the
+// kernels receive them.
+static void model_noise(const pes_model& m, double Q[15], double R[3])
+{
+    for (int i = 0; i < 15; ++i) Q[i] = 0.0;
+    for (int i = 0; i < 3; ++i) R[i] = 0.0;
+    if (m.kind == PES_MODEL_LINEAR) {
+        for (int i = 0; i < 15; ++i) Q[i] = m.Q[i];
+        for (int i = 0; i < 3; ++i) R[i] = m.R[i];
+        return;
+    }
+    const double dt = m.dt;
+    if (m.q_form == 1) {
+        for (int ax = 0; ax < 2; ++ax) {
+            Q[si(ax, ax)] = m.q_c * dt * dt * dt / 3.0;
+            Q[si(ax, ax + 2)] = m.q_c * dt * dt / 2.0;
+            Q[si(ax + 2, ax + 2)] = m.q_c * dt;
+        }
+    } else {
+        Q[si(2, 2)] = m.q_c * dt;
+        Q[si(3, 3)] = m.q_c * dt;
+    }
+    Q[si(4, 4)] = m.q_w * dt;
+    R[0] = R[2] = m.r_std * m.r_std;
+}
+
+// Inverse of a packed symmetric n x n (n <= 5) matrix by its Cholesky factor;
+// false if it is not positive definite.
+static bool inv_spd_packed(const double* S, int n, double* Si)
+{
+    auto at = [&](int i, int j) { return n == 5 ? S[si(std::min(i, j), std::max(i, j))] : S[std::min(i, j) + std::max(i, j)]; };
+    double L[25] = {0}, X[25] = {0};
+    for (int j = 0; j < n; ++j) {
+        double d = at(j, j);
+        for (int l = 0; l < j; ++l) d -= L[j * 5 + l] * L[j * 5 + l];
+        if (!(d > 0.0)) return false;
+        L[j * 5 + j] = std::sqrt(d);
+        for (int i = j + 1; i < n; ++i) {
+            double t = at(i, j);
+            for (int l = 0; l < j; ++l) t -= L[i * 5 + l] * L[j * 5 + l];
+            L[i * 5 + j] = t / L[j * 5 + j];
+        }
+    }
+    for (int c = 0; c < n; ++c) {   // columns of S^{-1}: L L^T x = e_c
+        double z[5];
+        for (int i = 0; i < n; ++i) {
+            double t = (i == c) ? 1.0 : 0.0;
+            for (int l = 0; l < i; ++l) t -= L[i * 5 + l] * z[l];
+            z[i] = t / L[i * 5 + i];
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            double t = z[i];
+            for (int l = i + 1; l < n; ++l) t -= L[l * 5 + i] * X[l * 5 + c];
+            X[i * 5 + c] = t / L[i * 5 + i];
+        }
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = i; j < n; ++j) Si[n == 5 ? si(i, j) : i + j] = 0.5 * (X[i * 5 + j] + X[j * 5 + i]);
+    return true;
+}
+
+// The IEKS with Levenberg-Marquardt steps and adaptive per-trajectory damping
+// (host loop; kernels in pes_lm.cu). Every iteration: keep the nominal, run
+// one damped iteration of the smoother kernel with each trajectory's damping,
+// evaluate the MAP objective, keep or undo each trajectory's step.
+template <typename T>
+static pes_status ieks_run_lm_t(pes_handle* h, const pes_model* model, pes_precision prec, const void* y,
+                                const int64_t* offsets, int32_t B, int64_t N, const void* m0, const void* P0,
+                                const void* x_init, int32_t max_iters, double tol, double lambda0, double nu,
+                                void* x_out, void* P_out, int32_t* iters_used, double* lambda_out,
+                                int32_t* accepted_out, int32_t* conv_out, cudaStream_t st)
+{
+    LMParams lp{};
+    double Q[15], R[3];
+    model_noise(*model, Q, R);
+    if (!inv_spd_packed(Q, 5, lp.Qi) || !inv_spd_packed(R, 2, lp.Ri))
+        return fail(h, PES_ERR_UNSUPPORTED,
+                    "the MAP objective needs positive definite Q and R (q_form 1, or a linear model with them)");
+    Shape s;
+    pes_status r = make_shape<T>(h, LIN_IEKS, prec, N, s);
+    if (r != PES_OK) return r;
+    if ((r = ensure_refine_workspace(h)) != PES_OK) return r;
+    if (!h->lmw) {
+        const size_t per = 5 * sizeof(double) + 3 * sizeof(int);
+        PES_CUDA(h, cudaMalloc(&h->lmw, per * (size_t)h->max_batch + 16));
+    }
+    const int NL = s.nb * s.nt;
+    const int64_t cs = (int64_t)s.L * NL;
+    T* lx = static_cast<T*>(h->lanes);
+    T* lP = lx + 5 * cs;
+    T* ly = lP + 15 * cs;
+    T* xold = static_cast<T*>(h->refw);
+    T* Pold = xold + 5 * cs;
+    const size_t Bm = (size_t)h->max_batch;
+    double* dw = static_cast<double*>(h->lmw);
+    lp.cost = dw;
+    lp.cost_new = dw + Bm;
+    lp.num = dw + 2 * Bm;
+    lp.den = dw + 3 * Bm;
+    T* lam = reinterpret_cast<T*>(dw + 4 * Bm);
+    int* iw = reinterpret_cast<int*>(dw + 5 * Bm);
+    lp.reject = iw;
+    lp.accepted = iw + Bm;
+    lp.conv_iter = iw + 2 * Bm;
+    lp.unconv = iw + 3 * Bm;
+    lp.N = N; lp.offsets = offsets; lp.B = B; lp.L = s.L; lp.NL = NL; lp.cs = cs;
+    lp.kind = model->kind;
+    lp.dt = model->dt;
+    lp.sensors = model->sensors;
+    lp.sensors_per_traj = model->sensors_per_traj;
+    for (int i = 0; i < 25; ++i) lp.F[i] = model->F[i];
+    for (int i = 0; i < 5; ++i) lp.c[i] = model->c[i];
+    for (int i = 0; i < 10; ++i) lp.H[i] = model->H[i];
+    for (int i = 0; i < 2; ++i) lp.d[i] = model->d[i];
+    PES_CUDA(h, launch_lanes_transpose<T>((const T*)y, ly, 2, N, s.L, NL, true, st));
+    if (x_init) PES_CUDA(h, launch_lanes_transpose<T>((const T*)x_init, lx, 5, N, s.L, NL, true, st));
+    // covariances start at the prior's: a trajectory whose every step is
+    // rejected returns them
+    PES_CUDA(h, launch_init_nominal_lanes<T>(offsets, B, N, s.L, NL, (const T*)m0, (const T*)P0,
+                                             x_init ? nullptr : lx, lP, st));
+    PES_CUDA(h, cudaMemsetAsync(lp.accepted, 0, 2 * Bm * sizeof(int), st));
+    PES_CUDA(h, launch_lm_fill<T>(lam, B, lambda0, st));
+    PES_CUDA(h, cudaMemsetAsync(lp.cost, 0, B * sizeof(double), st));
+    PES_CUDA(h, launch_lm_cost<T>(lp, lp.cost, lx, nullptr, ly, (const T*)m0, (const T*)P0, st));
+    KParams<T> p{};
+    p.N = N; p.offsets = offsets; p.B = B; p.mode = MODE_RUN; p.iters = 1; p.tol = 0.0;
+    if ((r = device_model<T>(h, *model, B, st, p.model, PES_IEKS)) != PES_OK) return r;
+    p.model.lm = T(0);
+    p.model.lm_traj = lam;
+    p.y = ly; p.m0 = (const T*)m0; p.P0 = (const T*)P0;
+    p.x = lx; p.P = lP;
+    p.lanes_layout = 1;
+    int it = 0;
+    bool all = false;
+    for (it = 1; it <= max_iters; ++it) {
+        PES_CUDA(h, cudaMemcpyAsync(xold, lx, sizeof(T) * 20 * cs, cudaMemcpyDeviceToDevice, st));
+        if ((r = run_persistent_shaped<T>(h, p, LIN_IEKS, s, st)) != PES_OK) return r;
+        PES_CUDA(h, cudaMemsetAsync(lp.cost_new, 0, 3 * Bm * sizeof(double), st));
+        PES_CUDA(h, cudaMemsetAsync(lp.unconv, 0, sizeof(int), st));
+        PES_CUDA(h, launch_lm_cost<T>(lp, lp.cost_new, lx, xold, ly, (const T*)m0, (const T*)P0, st));
+        PES_CUDA(h, launch_lm_decide<T>(lp, lam, it, tol, nu, st));
+        PES_CUDA(h, launch_lm_restore<T>(lp, lx, lP, xold, Pold, st));
+        if (tol > 0.0) {
+            int un = 0;
+            PES_CUDA(h, cudaMemcpyAsync(&un, lp.unconv, sizeof(int), cudaMemcpyDeviceToHost, st));
+            PES_CUDA(h, cudaStreamSynchronize(st));
+            if (un == 0) {
+                all = true;
+                break;
+            }
+        }
+    }
+    if (it > max_iters) it = max_iters;
+    PES_CUDA(h, launch_lanes_transpose<T>(lx, (T*)x_out, 5, N, s.L, NL, false, st));
+    PES_CUDA(h, launch_lanes_transpose<T>(lP, (T*)P_out, 15, N, s.L, NL, false, st));
+    if (lambda_out) {
+        T* tmp = new (std::nothrow) T[B];
+        if (!tmp) return fail(h, PES_ERR_CUDA, "out of host memory");
+        cudaError_t e = cudaMemcpyAsync(tmp, lam, sizeof(T) * B, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        for (int b = 0; b < B && e == cudaSuccess; ++b) lambda_out[b] = (double)tmp[b];
+        delete[] tmp;
+        if (e != cudaSuccess) return cuda_fail(h, e, "reading the dampings");
+    }
+    if (accepted_out)
+        PES_CUDA(h, cudaMemcpyAsync(accepted_out, lp.accepted, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+    if (conv_out) PES_CUDA(h, cudaMemcpyAsync(conv_out, lp.conv_iter, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+    r = read_status(h, st);
+    if (iters_used) *iters_used = it;
+    if (r == PES_OK && tol > 0.0 && !all) r = fail(h, PES_ERR_NOT_CONVERGED, "the tolerance was not reached within max_iters");
+    return r;
+}
+
 struct pes_graph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -626,7 +800,7 @@ pes_status pes_destroy(pes_handle* h)
 {
     if (!h) return PES_ERR_INVALID_ARG;
     cudaDeviceSynchronize();
-    void* ptrs[] = {h->hand, h->lanes, h->lin, h->mix, h->refw, h->aggF, h->aggS, h->bar, h->status, h->conv, h->iters_done, h->traj_iters, h->sensT, h->ptime,
+    void* ptrs[] = {h->hand, h->lanes, h->lin, h->mix, h->refw, h->lmw, h->aggF, h->aggS, h->bar, h->status, h->conv, h->iters_done, h->traj_iters, h->sensT, h->ptime,
                     h->hy, h->hoff, h->hm0, h->hP0, h->hx, h->hP, h->hsens};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -921,6 +1095,29 @@ pes_status pes_ieks_run(pes_handle* h, const pes_model* model, pes_method method
                                   x_out, P_out, iters_used, st);
     return ieks_run_t<float>(h, model, method, prec, y, offsets, B, N, m0, P0, x_init, P_init, max_iters, tol, x_out,
                              P_out, iters_used, st);
+}
+
+pes_status pes_ieks_run_lm(pes_handle* h, const pes_model* model, pes_precision prec, const void* y,
+                           const int64_t* offsets, int32_t B, int64_t N, const void* m0, const void* P0,
+                           const void* x_init, int32_t max_iters, double tol, double lambda0, double nu,
+                           void* x_out, void* P_out, int32_t* iters_used, double* lambda_out,
+                           int32_t* accepted_out, int32_t* conv_iter_out, void* stream)
+{
+    pes_status r = check_common(h, prec, offsets, B, N);
+    if (r != PES_OK) return r;
+    if ((r = check_model(h, model)) != PES_OK) return r;
+    if (!y || !m0 || !P0 || !x_out || !P_out) return fail(h, PES_ERR_INVALID_ARG, "NULL array");
+    if (max_iters < 1) return fail(h, PES_ERR_INVALID_ARG, "max_iters must be >= 1");
+    if (!(lambda0 > 0.0) || !std::isfinite(lambda0) || !(nu > 1.0) || !std::isfinite(nu) || !(tol == tol))
+        return fail(h, PES_ERR_INVALID_ARG, "lambda0 > 0 and nu > 1 (finite), tol not NaN");
+    if (model->lm_lambda != 0.0) return fail(h, PES_ERR_INVALID_ARG, "the damping is adaptive here: lm_lambda must be 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    PES_CUDA(h, launch_validate_offsets(offsets, B, N, h->status, st));
+    if (prec == PES_FP64)
+        return ieks_run_lm_t<double>(h, model, prec, y, offsets, B, N, m0, P0, x_init, max_iters, tol, lambda0, nu,
+                                     x_out, P_out, iters_used, lambda_out, accepted_out, conv_iter_out, st);
+    return ieks_run_lm_t<float>(h, model, prec, y, offsets, B, N, m0, P0, x_init, max_iters, tol, lambda0, nu, x_out,
+                                P_out, iters_used, lambda_out, accepted_out, conv_iter_out, st);
 }
 
 pes_status pes_ieks_run_sequential(pes_handle* h, const pes_model* model, pes_method method, pes_precision prec,

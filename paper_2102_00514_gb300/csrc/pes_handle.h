@@ -41,6 +41,7 @@ struct pes_handle {
     void* lin = nullptr;     // cubature linearisation handed from the fold to the re-run
     void* mix = nullptr;     // FP64 copies for PES_MIXED (allocated by its first call)
     void* refw = nullptr;    // PES_REFINED workspace (allocated by its first call)
+    void* lmw = nullptr;     // per-trajectory state of pes_ieks_run_lm (allocated by its first call)
     long long* ptime = nullptr;   // phase timestamps (PES_PHASE_TIMES=1)
     int ptime_blocks = 0;
     long long timeout_ns = 2000000000LL;

@@ -461,10 +461,10 @@ PES_DEV bool fold_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int la
             if (store_lin) store_lin_obs(p, s, lane, ob);
             ok &= fold_update(acc, ob);
         }
-        if (LIN != LIN_ARRAYS && p.model.lm > T(0)) {
+        if (LIN != LIN_ARRAYS && lm_of(p.model, cur.b) > T(0)) {
             // Levenberg-Marquardt pseudo-measurement of this state's nominal
             FElem<T> dmp;
-            felem_damping(dmp, sc.x, p.model.lm);
+            felem_damping(dmp, sc.x, lm_of(p.model, cur.b));
             combine_filter(acc, dmp, acc);
         }
         if (!cur.is_tail(k) && (k + 1 < e || store_lin)) {
@@ -694,12 +694,12 @@ PES_DEV bool rerun_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int l
                     ok &= kf_update(ob, mp, Pp, m, P);
                 }
             }
-            if (LIN != LIN_ARRAYS && p.model.lm > T(0)) {
+            if (LIN != LIN_ARRAYS && lm_of(p.model, cur.b) > T(0)) {
                 // Levenberg-Marquardt pseudo-measurement of this state's nominal
                 T xb[5];
                 load_nominal(p, ix, xb);
                 FElem<T> dmp;
-                felem_damping(dmp, xb, p.model.lm);
+                felem_damping(dmp, xb, lm_of(p.model, cur.b));
                 Gauss<T> g, gd;
 #pragma unroll
                 for (int i = 0; i < 5; ++i) g.m[i] = m[i];

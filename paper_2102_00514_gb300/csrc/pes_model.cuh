@@ -41,7 +41,15 @@ struct DevModel {
     // sqrt(n), 1/n, 0)
     T sp_scale, sp_w, sp_w0c;
     T lm;   // Levenberg-Marquardt damping lambda (0: none)
+    const T* lm_traj;   // per-trajectory damping [B] (device), overriding lm; or NULL
 };
+
+// The Levenberg-Marquardt damping of trajectory b.
+template <typename T>
+PES_DEV T lm_of(const DevModel<T>& m, int b)
+{
+    return m.lm_traj ? __ldg(m.lm_traj + b) : m.lm;
+}
 
 // Transition k -> k+1 linearised about xn = xbar_k: x_{k+1} ~ fx + F (x_k - xn) + N(0, Q')
 template <typename T>

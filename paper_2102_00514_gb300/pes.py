@@ -29,7 +29,7 @@ MODEL_CT_BEARINGS, MODEL_LINEAR = 0, 1
 
 EXPORTED = ["pes_create", "pes_destroy", "pes_last_error", "pes_sync", "pes_linearize", "pes_filter_scan",
             "pes_smooth_scan", "pes_ieks_run", "pes_ieks_run_host", "pes_launch_shape", "pes_measure_fma_peak",
-            "pes_debug_phase_times", "pes_ieks_run_noalloc", "pes_traj_iterations", "pes_filter_loglik", "pes_ieks_run_sequential", "pes_autotune", "pes_ieks_graph_create", "pes_graph_launch", "pes_graph_destroy",
+            "pes_debug_phase_times", "pes_ieks_run_noalloc", "pes_traj_iterations", "pes_ieks_run_lm", "pes_filter_loglik", "pes_ieks_run_sequential", "pes_autotune", "pes_ieks_graph_create", "pes_graph_launch", "pes_graph_destroy",
             "pes_init_create", "pes_init_destroy", "pes_init_last_error", "pes_init_set_params",
             "pes_init_get_params", "pes_init_forward", "pes_init_loss_grad", "pes_init_train_step"]
 INIT_NPARAMS = 86661
@@ -91,6 +91,8 @@ def load_library():
     lib.pes_ieks_run_noalloc.argtypes = [mp, i32, i32, p, p, i32, i64, p, p, p, p, i32, d, p, p,
                                          ctypes.POINTER(i32), p]
     lib.pes_traj_iterations.argtypes = [p, ctypes.POINTER(i32), i32, p]
+    lib.pes_ieks_run_lm.argtypes = [p, mp, i32, p, p, i32, i64, p, p, p, i32, d, d, d, p, p, ctypes.POINTER(i32),
+                                    p, p, p, p]
     lib.pes_init_create.argtypes = [ctypes.POINTER(p), i64, i32]
     lib.pes_init_destroy.argtypes = [p]
     lib.pes_init_last_error.argtypes = [p]
@@ -363,6 +365,32 @@ class Smoother:
                                    ctypes.byref(used) if (want_iters or tol > 0) else None, _stream(stream))
         self._check(st, allow=(NOT_CONVERGED,) if allow_not_converged else ())
         return x_out, P_out, used.value, st
+
+    def ieks_run_lm(self, model: Model, prec: int, y, offsets, m0, P0, x_init=None, iters: int = 20,
+                    tol: float = 0.0, lambda0: float = 1.0, nu: float = 10.0, stream=None,
+                    allow_not_converged: bool = False):
+        """The IEKS with Levenberg-Marquardt steps and per-trajectory adaptive
+        damping (pes_ieks_run_lm). Returns x [5][N], P [15][N], iterations,
+        and per trajectory the final damping, the steps kept and the converged
+        iteration (0: none)."""
+        import numpy as np
+        dt = _dtype(prec)
+        N = y.shape[1]
+        B = offsets.shape[0] - 1
+        x_out = torch.empty((5, N), dtype=dt, device=y.device)
+        P_out = torch.empty((15, N), dtype=dt, device=y.device)
+        used = ctypes.c_int32(0)
+        lam = np.zeros(B, dtype=np.float64)
+        acc = np.zeros(B, dtype=np.int32)
+        conv = np.zeros(B, dtype=np.int32)
+        ms = model.as_struct()
+        st = self.lib.pes_ieks_run_lm(self.h, ctypes.byref(ms), prec, _ptr(y, dt), _ptr(offsets, torch.int64), B, N,
+                                      _ptr(m0, dt), _ptr(P0, dt), _ptr(x_init, dt), int(iters), float(tol),
+                                      float(lambda0), float(nu), _ptr(x_out, dt), _ptr(P_out, dt),
+                                      ctypes.byref(used), lam.ctypes.data, acc.ctypes.data, conv.ctypes.data,
+                                      _stream(stream))
+        self._check(st, allow=(NOT_CONVERGED,) if allow_not_converged else ())
+        return x_out, P_out, used.value, dict(lam=lam, accepted=acc, conv_iter=conv, status=st)
 
     def ieks_run_sequential(self, model: Model, method: int, prec: int, y, offsets, m0, P0, x_init=None,
                             P_init=None, iters: int = 10, tol: float = 0.0, x_out=None, P_out=None, stream=None,
