@@ -413,9 +413,10 @@ pes_status pes_launch_shape(pes_handle* h, pes_method method, pes_precision prec
  * PES_PHASE_TIMES=1 (else PES_ERR_UNSUPPORTED). mean_ns[i] / max_ns[i] (max_ns
  * may be NULL) receive the mean / maximum over blocks of the time between
  * phase boundaries i and i+1: 0 fold, 1 filter up-sweep, 2 barrier, 3 filter
- * top level, 4 filter down-sweep, 5 filter re-run, 6 smoother up-sweep,
- * 7 barrier, 8 smoother top level, 9 smoother down-sweep, 10 RTS re-run,
- * 11 (unused), 12 end-of-iteration barrier; -1 where not recorded.
+ * top level, 4 filter down-sweep, 5 filter re-run, 6 between the passes,
+ * 7 smoother up-sweep, 8 barrier, 9 smoother top level, 10 smoother
+ * down-sweep, 11 RTS re-run, 12 end-of-iteration barrier; -1 where not
+ * recorded.
  * Synchronises the device. */
 pes_status pes_debug_phase_times(pes_handle* h, double* mean_ns, double* max_ns, int32_t n);
 

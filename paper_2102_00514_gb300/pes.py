@@ -234,9 +234,9 @@ class Smoother:
     def sync(self, stream=None):
         return self._check(self.lib.pes_sync(self.h, _stream(stream)))
 
-    PHASES = ["fold", "filter up-sweep", "barrier", "filter top level", "filter down-sweep", "filter re-run",
-              "smoother up-sweep", "barrier", "smoother top level", "smoother down-sweep", "RTS re-run", "-",
-              "end barrier"]
+    PHASES = ["fold", "filter up-sweep", "filter barrier", "filter top level", "filter down-sweep", "filter re-run",
+              "between passes", "smoother up-sweep", "smoother barrier", "smoother top level", "smoother down-sweep",
+              "RTS re-run", "end barrier"]
 
     def phase_times(self):
         """Per-phase (mean, max) ns of the first iteration of the last launch
@@ -244,7 +244,7 @@ class Smoother:
         n = len(self.PHASES)
         mean, mx = (ctypes.c_double * n)(), (ctypes.c_double * n)()
         self._check(self.lib.pes_debug_phase_times(self.h, mean, mx, n))
-        return {name: (mean[i], mx[i]) for i, name in enumerate(self.PHASES) if name != "-"}
+        return {name: (mean[i], mx[i]) for i, name in enumerate(self.PHASES)}
 
     def traj_iterations(self, B: int, stream=None):
         """Per-trajectory iterations to tolerance of the last tolerance-mode run (0: not reached)."""
