@@ -68,8 +68,8 @@ def parse_args():
                     help="also time the sequential counterpart (one GPU thread per trajectory) on the workload")
     ap.add_argument("--cpu-sample", type=int, default=1 << 17, help="states in the oracle's timed sample")
     ap.add_argument("--profile", choices=["ieks", "cubature", "init"], default=None,
-                    help="profiling case: only `warmup` + 1 FP32 runs of one method, no JSON line")
-    ap.add_argument("--prec", choices=["fp32", "fp64"], default="fp32", help="precision of --profile")
+                    help="profiling case: only `warmup` + 1 runs of one method, no JSON line")
+    ap.add_argument("--prec", choices=["fp32", "fp64", "refined"], default="fp32", help="precision of --profile")
     ap.add_argument("--sweep", action="store_true",
                     help="the length sweep T = 2^10 .. 2^20: one JSON line per length, no benchmark line")
     ap.add_argument("--no-batched", action="store_true",
@@ -106,8 +106,8 @@ def run_profile_case(args):
         return
     wl = synth.workload(f"sweep_T{args.T}")
     N = wl["y"].shape[1]
-    prec = pes.FP32 if args.prec == "fp32" else pes.FP64
-    dt = torch.float32 if prec == pes.FP32 else torch.float64
+    prec = {"fp32": pes.FP32, "fp64": pes.FP64, "refined": pes.REFINED}[args.prec]
+    dt = torch.float64 if prec == pes.FP64 else torch.float32
     dev = lambda a, d=dt: torch.as_tensor(np.ascontiguousarray(a), dtype=d, device="cuda")
     sm = pes.Smoother(N, 1)
     m = pes.IEKS if args.profile == "ieks" else pes.CUBATURE
