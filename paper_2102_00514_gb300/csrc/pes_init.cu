@@ -24,8 +24,9 @@
 // applies bias and ReLU (or the ReLU mask of the backward pass), stages its
 // warp's 32 bf16 rows in shared memory and writes them with one TMA store. The
 // backward pass through a layer is the same GEMM with the weights transposed
-// and the taps reversed. Weight gradients (a reduction over rows) run on the
-// CUDA cores in FP32.
+// and the taps reversed. The weight gradients, a reduction over rows, are a
+// GEMM on the tensor cores too (wgrad_tc_kernel), split over the CTAs and
+// summed in a fixed order.
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
@@ -63,16 +64,34 @@ constexpr uint32_t kIdesc = tc::idesc_bf16_f32(TM, C);
 constexpr int kTaps[NLAYER] = {5, 5, 5, 5, 1, 1};
 constexpr int kWTile0[NLAYER] = {0, 5, 10, 15, 20, 21};   // first weight tile of each layer
 constexpr int kWTiles = 22;
-constexpr int kCoReal[NLAYER] = {64, 64, 64, 64, 64, 5};  // output channels that exist
 constexpr int kPOff[NLAYER + 1] = {0, 20544, 41088, 61632, 82176, 86336, 86661};   // packed offsets
 static_assert(kPOff[NLAYER] == PES_INIT_NPARAMS, "parameter packing");
 static_assert(kTaps[0] == 5 && kTaps[NLAYER - 1] == 1 && kWTile0[NLAYER - 1] + kTaps[NLAYER - 1] == kWTiles, "layer tables");
 constexpr int kOutCols = 8;            // the head's FP32 output row (5 used)
-constexpr int kWgradStride = C * C * 5 + C;
 constexpr int kOutWarpBytes = 32 * C * 2;                  // 32 bf16 rows of one epilogue warp
 constexpr int kOutStageOffset = 1024;                       // after the barriers and the bias (1024-aligned)
 
 enum { EPI_RELU = 0, EPI_F32 = 1, EPI_MASK = 2 };
+
+// Weight gradients on the tensor cores (wgrad_tc_kernel, and the backward
+// convolutions that fuse them): MN-major operands straight from the row-major
+// activation tiles, two taps stacked along M = 128, the odd last tap paired
+// with an all-ones block (its products are the bias gradient).
+constexpr int kWgStages = 4;
+constexpr int kWgThreads = 192;
+constexpr int kOnesBytes = TM * C * 2;                    // 128 rows of bf16 1.0
+constexpr int kDyBytes = TM * C * 2;
+constexpr int wg_groups(int taps) { return (taps + 1) / 2; }
+constexpr int wg_stage(int taps) { return stage_bytes(taps) + kDyBytes; }
+constexpr uint32_t wg_tmem_cols(int taps) { return wg_groups(taps) * C <= 64 ? 64u : 256u; }
+constexpr int kWgPart = 3 * C * TM;                       // floats per CTA partial ([group][o][m])
+constexpr uint32_t kIdescWg = tc::idesc_bf16_f32(TM, C, true, true);
+
+// The conv kernel's pipeline depth and tensor memory (a fused weight gradient
+// doubles the stage and adds its accumulators after the two conv ones).
+constexpr int conv_nstage(bool wg) { return wg ? 4 : NSTAGE; }
+constexpr int conv_stage(int taps, bool wg) { return stage_bytes(taps) * (wg ? 2 : 1); }
+constexpr uint32_t conv_tmem_cols(int taps, bool wg) { return !wg ? kTmemCols : (taps > 1 ? 512u : 256u); }
 
 // The same layer tables for device code.
 PES_DEV int taps_of(int l) { return l < 4 ? 5 : 1; }
@@ -89,6 +108,7 @@ struct ConvParams {
     bf16* out;                  // [R][64] (EPI_RELU, EPI_MASK)
     float* out_f32;             // [R][8] (EPI_F32)
     const bf16* relu_src;       // [R][64] (EPI_MASK): the layer input whose ReLU is differentiated
+    float* part;                // fused weight gradient: [gridDim.x][kWgPart] partials
     int* status;
 };
 
@@ -112,19 +132,31 @@ PES_DEV void drain_wait(uint64_t* bar, uint32_t parity)
         if (async_now_ns() - t0 > 1000000000LL) return;
 }
 
-template <int TAPS, int EPI>
+// WG (with EPI_MASK): the same launch also accumulates the layer's weight
+// gradient. The layer input's halo tile (tmX, the ReLU source) is loaded beside
+// each gradient tile; after a tile's conv MMAs the MMA thread adds, as in
+// wgrad_tc_kernel, the products of the input taps with the tile's own gradient
+// rows (rows TAPS / 2 .. TAPS / 2 + TM - 1 of the gradient's halo tile) into
+// accumulators after the two conv ones, and the epilogue warps write the
+// CTA's partial once all tiles are done.
+template <int TAPS, int EPI, bool WG = false>
 __global__ void __launch_bounds__(kConvThreads, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW,
-                   const __grid_constant__ CUtensorMap tmOut, const ConvParams p)
+                   const __grid_constant__ CUtensorMap tmOut, const __grid_constant__ CUtensorMap tmX,
+                   const ConvParams p)
 {
+    static_assert(!WG || EPI == EPI_MASK, "the weight gradient fuses into backward convolutions");
+    constexpr int NS = conv_nstage(WG);
+    constexpr int NG = wg_groups(TAPS);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     uint8_t* sW = smem;                                   // TAPS weight tiles
-    constexpr int kStage = stage_bytes(TAPS);
-    uint8_t* sA = smem + TAPS * kWTileBytes;              // NSTAGE activation (halo) tiles
-    uint64_t* full = reinterpret_cast<uint64_t*>(sA + NSTAGE * kStage);
-    uint64_t* empty = full + NSTAGE;
-    uint64_t* wbar = empty + NSTAGE;
+    uint8_t* sOnes = smem + TAPS * kWTileBytes;           // WG: the all-ones block
+    constexpr int kStage = conv_stage(TAPS, WG);
+    uint8_t* sA = sOnes + (WG ? kOnesBytes : 0);          // NS stages: halo tile (and, WG, the input's)
+    uint64_t* full = reinterpret_cast<uint64_t*>(sA + NS * kStage);
+    uint64_t* empty = full + NS;
+    uint64_t* wbar = empty + NS;
     uint64_t* tfull = wbar + 1;
     uint64_t* tempty = tfull + 2;
     uint64_t* done = tempty + 2;
@@ -133,11 +165,17 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     float* sbias = reinterpret_cast<float*>(tslot + 4);   // 16-byte aligned, 64 floats
     // bf16 outputs leave through TMA stores: per epilogue warp one 32-row
     // staging tile (4 KB, 128-byte swizzled like the tensor map)
-    uint8_t* sOut = sA + NSTAGE * kStage + kOutStageOffset;
+    uint8_t* sOut = sA + NS * kStage + kOutStageOffset;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if constexpr (WG) {
+        uint4* o = reinterpret_cast<uint4*>(sOnes);
+        for (int i = threadIdx.x; i < kOnesBytes / 16; i += kConvThreads)
+            o[i] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+        fence_proxy_async();   // generic writes, read by the tensor cores
+    }
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NSTAGE; ++s) {
+        for (int s = 0; s < NS; ++s) {
             mbar_init(full + s, 1);
             mbar_init(empty + s, 1);
         }
@@ -150,7 +188,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         *abort_flag = 0;
         mbar_init_fence();
     }
-    if (warp == 1) tc::tmem_alloc(tslot, kTmemCols);
+    if (warp == 1) tc::tmem_alloc(tslot, conv_tmem_cols(TAPS, WG));
     if (EPI != EPI_MASK && threadIdx.x >= 64 && threadIdx.x < 64 + C) sbias[threadIdx.x - 64] = p.bias[threadIdx.x - 64];
     tc::fence_before_sync();
     __syncthreads();
@@ -158,10 +196,10 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     const uint32_t tbase = *tslot;
 
     if (warp == 0) {
-        // ---- producer: weights once, then one halo tile per row tile
+        // ---- producer: weights once, then one halo tile (two, WG) per row tile
         if (lane == 0) {
-            int armed[NSTAGE];
-            for (int s = 0; s < NSTAGE; ++s) armed[s] = -1;
+            int armed[NS];
+            for (int s = 0; s < NS; ++s) armed[s] = -1;
             tc::mbar_expect_tx(wbar, TAPS * kWTileBytes);
             for (int j = 0; j < TAPS; ++j) tc::tma_load_2d(sW + j * kWTileBytes, &tmW, 0, (p.w_tile0 + j) * C, wbar);
             int st = 0;
@@ -170,10 +208,12 @@ __global__ void __launch_bounds__(kConvThreads, 1)
             for (int tile = blockIdx.x; ok && tile < p.ntiles; tile += gridDim.x) {
                 if (!tc::wait_or_abort(empty + st, ph ^ 1, p.status, abort_flag)) break;
                 // rows before 0 or past the end arrive as zeros and count in full
-                tc::mbar_expect_tx(full + st, halo_rows(TAPS) * C * 2);
+                tc::mbar_expect_tx(full + st, (WG ? 2 : 1) * halo_rows(TAPS) * C * 2);
                 tc::tma_load_2d(sA + st * kStage, &tmA, 0, tile * TM - TAPS / 2, full + st);
+                if constexpr (WG)
+                    tc::tma_load_2d(sA + st * kStage + stage_bytes(TAPS), &tmX, 0, tile * TM - TAPS / 2, full + st);
                 armed[st] = (int)ph;
-                if (++st == NSTAGE) {
+                if (++st == NS) {
                     st = 0;
                     ph ^= 1;
                 }
@@ -181,16 +221,18 @@ __global__ void __launch_bounds__(kConvThreads, 1)
             if (*abort_flag) {
                 // no copy of this block may still be landing when it exits
                 drain_wait(wbar, 0);
-                for (int s = 0; s < NSTAGE; ++s)
+                for (int s = 0; s < NS; ++s)
                     if (armed[s] >= 0) drain_wait(full + s, (uint32_t)armed[s]);
             }
         }
     } else if (warp == 1) {
-        // ---- MMA issuer: TAPS x 4 MMAs (K = 16 each) per tile into one of two accumulators
+        // ---- MMA issuer: TAPS x 4 MMAs (K = 16 each) per tile into one of two
+        // accumulators (WG: then 8 x NG weight-gradient MMAs)
         if (lane == 0) {
             bool ok = tc::wait_or_abort(wbar, 0, p.status, abort_flag);
             int st = 0, acc = 0;
             uint32_t ph = 0, tph = 0;
+            bool first = true;
             for (int tile = blockIdx.x; ok && tile < p.ntiles; tile += gridDim.x) {
                 if (!tc::wait_or_abort(tempty + acc, ((tph >> acc) & 1u) ^ 1u, p.status, abort_flag)) break;
                 tph ^= 1u << acc;
@@ -198,22 +240,41 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                 const uint32_t d = tbase + (uint32_t)(acc * C);
                 if (!tc::wait_or_abort(full + st, ph, p.status, abort_flag)) break;
                 tc::fence_after_sync();
+                const uint8_t* sa = sA + st * kStage;
 #pragma unroll
                 for (int j = 0; j < TAPS; ++j) {
                     // tap j: the TM rows starting at row j of the halo tile
-                    const uint64_t ad = tc::smem_desc_sw128(sA + st * kStage + j * C * 2);
+                    const uint64_t ad = tc::smem_desc_sw128(sa + j * C * 2);
                     const uint64_t bd = tc::smem_desc_sw128(sW + j * kWTileBytes);
 #pragma unroll
                     for (int k = 0; k < C / 16; ++k)   // +32 bytes along K per MMA
                         tc::mma_bf16(d, ad + 2 * k, bd + 2 * k, kIdesc, (j | k) != 0);
                 }
+                tc::mma_commit(tfull + acc);
+                acc ^= 1;
+                if constexpr (WG) {
+                    const uint8_t* xs = sa + stage_bytes(TAPS);
+                    const uint8_t* dy = sa + (TAPS / 2) * (C * 2);   // the tile's own gradient rows
+#pragma unroll
+                    for (int kk = 0; kk < TM / 16; ++kk) {
+                        const uint64_t bd = tc::smem_desc_sw128_mn(dy + kk * 2048, 128);
+#pragma unroll
+                        for (int g = 0; g < NG; ++g) {
+                            const uint64_t ad =
+                                g < NG - 1
+                                    ? tc::smem_desc_sw128_mn(xs + 2 * g * (C * 2) + kk * 2048, C * 2)
+                                    : tc::smem_desc_sw128_mn(sOnes + kk * 2048,
+                                                             (uint32_t)(xs + (TAPS - 1) * (C * 2) - sOnes));
+                            tc::mma_bf16(tbase + (uint32_t)(2 * C + g * C), ad, bd, kIdescWg, !(first && kk == 0));
+                        }
+                    }
+                    first = false;
+                }
                 tc::mma_commit(empty + st);
-                if (++st == NSTAGE) {
+                if (++st == NS) {
                     st = 0;
                     ph ^= 1;
                 }
-                tc::mma_commit(tfull + acc);
-                acc ^= 1;
             }
             tc::mma_commit(done);
             drain_wait(done, 0);
@@ -290,22 +351,40 @@ __global__ void __launch_bounds__(kConvThreads, 1)
             }
         }
         if (EPI != EPI_F32 && lane == 0) tc::bulk_wait_all();
+        if constexpr (WG) {
+            // the CTA's weight-gradient partial: warpgroup g writes groups g, g + 2
+            const bool ok = __all_sync(0xffffffffu, tc::wait_or_abort(done, 0, p.status, abort_flag));
+            if (ok) {
+                tc::fence_after_sync();
+                float* outp = p.part + (size_t)blockIdx.x * kWgPart;
+#pragma unroll 1
+                for (int gg = g; gg < NG; gg += 2) {
+                    float v[C];
+                    tc::tmem_ld64(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(2 * C + gg * C), v);
+#pragma unroll
+                    for (int o = 0; o < C; ++o) outp[(gg * C + o) * TM + rin] = v[o];
+                }
+            }
+        }
     }
 
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (warp == 1) tc::tmem_dealloc(tbase, kTmemCols);
+    if (warp == 1) tc::tmem_dealloc(tbase, conv_tmem_cols(TAPS, WG));
 }
 
-constexpr size_t conv_smem_bytes(int taps)
+constexpr size_t conv_smem_bytes(int taps, bool wg = false)
 {
-    return 1024 + (size_t)taps * kWTileBytes + (size_t)NSTAGE * stage_bytes(taps) + kOutStageOffset +
-           (size_t)2 * 4 * kOutWarpBytes;
+    return 1024 + (size_t)taps * kWTileBytes + (wg ? (size_t)kOnesBytes : 0) +
+           (size_t)conv_nstage(wg) * conv_stage(taps, wg) + kOutStageOffset + (size_t)2 * 4 * kOutWarpBytes;
 }
 static_assert(conv_smem_bytes(5) <= 227 * 1024 && conv_smem_bytes(1) <= 227 * 1024, "shared memory per CTA");
+static_assert(conv_smem_bytes(5, true) <= 227 * 1024 && conv_smem_bytes(1, true) <= 227 * 1024, "shared memory per CTA");
 // tap j of a halo tile ends at row j + TM, inside its stage
 static_assert(halo_rows(5) * C * 2 <= stage_bytes(5) && stage_bytes(1) == TM * C * 2, "halo stages");
+// barriers, TMEM slot, abort flag and bias fit before the output staging
+static_assert((2 * NSTAGE + 6) * 8 + 16 + C * 4 <= kOutStageOffset, "control block");
 
 // ---- rows, features, loss, gradients, optimiser ----------------------------------
 
@@ -378,169 +457,291 @@ __global__ void features_kernel(const T* y, const int64_t* off, int B, int64_t N
     }
 }
 
-struct ZeroList {
-    bf16* buf[10];
-    int n;
-};
-
-// Zero the gap rows of every listed buffer.
-__global__ void gap_rows_kernel(const int64_t* off, int B, int64_t N, int64_t R, ZeroList zl)
-{
-    const int64_t total = (int64_t)G * (B + 1);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int b = (int)(i / G);
-        const int64_t o = off[b];
-        if (o < 0 || o > N) continue;   // malformed offsets: leave the row alone
-        const int64_t row = o + (int64_t)G * b + (i % G);
-        if (row >= R) continue;
-        for (int j = 0; j < zl.n; ++j) {
-            uint4* dst = reinterpret_cast<uint4*>(zl.buf[j] + (size_t)row * C);
-#pragma unroll
-            for (int c = 0; c < C / 8; ++c) dst[c] = make_uint4(0, 0, 0, 0);
-        }
-    }
-}
-
 struct Norm {
-    double mu[5], sigma[5];
+    double mu[5], sigma[5], inv_sigma[5];
 };
 
-// Loss terms (o - t)^2 and the output gradient dO = 2 (o - t) / (5 N) in bf16.
+// Loss terms (o - t)^2 and the output gradient dO = 2 (o - t) / (5 N) in bf16,
+// with t the normalised target (x - mu) / sigma, for entries 0 .. N - 1 (the
+// states); entries N .. N + G (B + 1) - 1 zero the gap rows of dO. Each block
+// leaves its sum in part[block]; the last block to finish adds the partials in
+// block order (so the loss does not depend on scheduling), writes
+// loss_scale x the total to *loss and re-arms the ticket.
 template <typename T>
-__global__ void loss_kernel(const float* o, const T* xt, const int64_t* off, int B, int64_t N, Norm nm, float scale,
-                            bf16* dO, double* part)
+__global__ void __launch_bounds__(256) loss_kernel(const float* o, const T* xt, const int64_t* off, int B, int64_t N,
+                                                   Norm nm, float scale, double loss_scale, bf16* dO, double* part,
+                                                   unsigned* ticket, double* loss)
 {
     double s = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += stride) {
-        const int b = traj_of_state(off, B, k);
-        const int64_t row = k + (int64_t)G * (b + 1);
-        float e[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const int64_t total = N + (int64_t)G * (B + 1);
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += stride) {
+        if (k < N) {
+            const int b = traj_of_state(off, B, k);
+            const int64_t row = k + (int64_t)G * (b + 1);
+            float e[5];
 #pragma unroll
-        for (int c = 0; c < 5; ++c) {
-            const float t = (float)(((double)xt[(size_t)c * N + k] - nm.mu[c]) / nm.sigma[c]);
-            e[c] = o[(size_t)row * kOutCols + c] - t;
-            s += (double)e[c] * (double)e[c];
-        }
-        uint4* dst = reinterpret_cast<uint4*>(dO + (size_t)row * C);
-        dst[0] = make_uint4(pack_bf16x2(scale * e[0], scale * e[1]), pack_bf16x2(scale * e[2], scale * e[3]),
-                            pack_bf16x2(scale * e[4], 0.f), 0u);
-#pragma unroll
-        for (int i = 1; i < C / 8; ++i) dst[i] = make_uint4(0, 0, 0, 0);
-    }
-    __shared__ double red[256];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
-}
-
-__global__ void sum_kernel(const double* part, int n, double scale, double* out)
-{
-    __shared__ double red[256];
-    double s = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *out = red[0] * scale;
-}
-
-// Weight and bias gradients of one layer, partial per block:
-//   dW[o][i][j] = sum_r dY[r][o] X[r + j - TAPS/2][i],  db[o] = sum_r dY[r][o].
-// Thread (cb, ib) owns output channels 4cb..4cb+3 x input channels 4ib..4ib+3
-// x all taps, accumulated in FP32 over chunks of 32 rows staged in shared memory.
-template <int TAPS>
-__global__ void __launch_bounds__(256) wgrad_kernel(const bf16* dY, const bf16* X, int64_t R, float* part)
-{
-    constexpr int CH = 32;
-    constexpr int H = TAPS / 2;
-    __shared__ float4 sdy[CH][C / 4];
-    __shared__ float4 sx[CH + TAPS - 1][C / 4];
-    const int t = threadIdx.x, cb = t >> 4, ib = t & 15;
-    float acc[4][TAPS][4];
-    float bacc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int j = 0; j < TAPS; ++j)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[a][j][c] = 0.f;
-    const int64_t nchunks = (R + CH - 1) / CH;
-    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-        const int64_t r0 = ch * CH;
-        __syncthreads();
-        {   // dY rows r0 .. r0 + CH - 1: one 16-byte load per thread
-            const int rr = t >> 3, part8 = t & 7;
-            uint4 u = make_uint4(0, 0, 0, 0);
-            if (r0 + rr < R) u = __ldg(reinterpret_cast<const uint4*>(dY + (size_t)(r0 + rr) * C) + part8);
-            const float2 a = unpack_bf16x2(u.x), b = unpack_bf16x2(u.y), c = unpack_bf16x2(u.z),
-                         d = unpack_bf16x2(u.w);
-            sdy[rr][2 * part8] = make_float4(a.x, a.y, b.x, b.y);
-            sdy[rr][2 * part8 + 1] = make_float4(c.x, c.y, d.x, d.y);
-        }
-        for (int i = t; i < (CH + TAPS - 1) * 8; i += 256) {
-            const int rr = i >> 3, part8 = i & 7;
-            const int64_t r = r0 + rr - H;
-            uint4 u = make_uint4(0, 0, 0, 0);
-            if (r >= 0 && r < R) u = __ldg(reinterpret_cast<const uint4*>(X + (size_t)r * C) + part8);
-            const float2 a = unpack_bf16x2(u.x), b = unpack_bf16x2(u.y), c = unpack_bf16x2(u.z),
-                         d = unpack_bf16x2(u.w);
-            sx[rr][2 * part8] = make_float4(a.x, a.y, b.x, b.y);
-            sx[rr][2 * part8 + 1] = make_float4(c.x, c.y, d.x, d.y);
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int r = 0; r < CH; ++r) {
-            const float4 d4 = sdy[r][cb];
-            const float dv[4] = {d4.x, d4.y, d4.z, d4.w};
-#pragma unroll
-            for (int j = 0; j < TAPS; ++j) {
-                const float4 x4 = sx[r + j][ib];
-                const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) acc[a][j][c] = fmaf(dv[a], xv[c], acc[a][j][c]);
+            for (int c = 0; c < 5; ++c) {
+                const float t = (float)(((double)xt[(size_t)c * N + k] - nm.mu[c]) * nm.inv_sigma[c]);
+                e[c] = o[(size_t)row * kOutCols + c] - t;
+                s += (double)(e[c] * e[c]);
             }
+            uint4* dst = reinterpret_cast<uint4*>(dO + (size_t)row * C);
+            dst[0] = make_uint4(pack_bf16x2(scale * e[0], scale * e[1]), pack_bf16x2(scale * e[2], scale * e[3]),
+                                pack_bf16x2(scale * e[4], 0.f), 0u);
 #pragma unroll
-            for (int a = 0; a < 4; ++a) bacc[a] += dv[a];
+            for (int i = 1; i < C / 8; ++i) dst[i] = make_uint4(0, 0, 0, 0);
+        } else {
+            const int64_t g = k - N;
+            const int b = (int)(g / G);
+            const int64_t ob = off[b];
+            if (ob < 0 || ob > N) continue;   // malformed offsets: leave the row alone
+            const int64_t row = ob + (int64_t)G * b + g % G;
+            uint4* dst = reinterpret_cast<uint4*>(dO + (size_t)row * C);
+#pragma unroll
+            for (int i = 0; i < C / 8; ++i) dst[i] = make_uint4(0, 0, 0, 0);
         }
     }
-    float* out = part + (size_t)blockIdx.x * kWgradStride;
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-            for (int j = 0; j < TAPS; ++j) out[((4 * cb + a) * C + 4 * ib + c) * TAPS + j] = acc[a][j][c];
-    if (ib == 0)
-#pragma unroll
-        for (int a = 0; a < 4; ++a) out[C * C * TAPS + 4 * cb + a] = bacc[a];
-}
-
-// Sum the per-block partials into the packed gradient of one layer (fixed
-// order, so the result does not depend on scheduling).
-__global__ void wgrad_reduce_kernel(const float* part, int nblk, int nw_real, int nb_real, int bias_src,
-                                    float* grad)
-{
-    const int n = nw_real + nb_real;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int src = i < nw_real ? i : bias_src + (i - nw_real);
-        float s = 0.f;
-        for (int b = 0; b < nblk; ++b) s += part[(size_t)b * kWgradStride + src];
-        grad[i] = s;
+    __shared__ double red[256];
+    __shared__ bool last;
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = red[0];
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double t = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(part + i);
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *loss = red[0] * loss_scale;
+        *ticket = 0u;
     }
 }
 
+// Weight and bias gradients of one layer on the tensor cores:
+//   dW_j[o][i] = sum_r dY[r][o] X[r + j - TAPS/2][i],  db[o] = sum_r dY[r][o],
+// a GEMM whose reduction dimension is the rows. The activation arrays are
+// row-major [rows][64], so a TMA tile of them is an MN-major operand with the
+// rows as K, and no transpose is needed: per 128-row tile, B = the dY tile
+// (N = 64 output channels) and A = two taps of the X halo tile stacked along
+// M = 128 (tap pair (2g, 2g + 1): the second 64-row block of A starts one row,
+// 128 bytes, after the first). The odd last tap is paired with a constant
+// all-ones tile, whose products with dY are the bias gradient. Each CTA owns a
+// fixed set of row tiles (split-K), accumulates them in tensor memory, and
+// writes its partial [group][o][m] to `part`; wgrad_reduce_kernel sums the
+// partials in a fixed order, so the gradient does not depend on scheduling.
+// Warp 0 issues the TMA loads, warp 1 the MMAs, warps 2-5 write the partial.
+struct WgradParams {
+    int ntiles;     // ceil(R / TM)
+    float* part;    // [gridDim.x][kWgPart]
+    int* status;
+};
+
+template <int TAPS>
+__global__ void __launch_bounds__(kWgThreads, 1)
+    wgrad_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmDY,
+                    const WgradParams p)
+{
+    constexpr int NG = wg_groups(TAPS);
+    constexpr int kStage = wg_stage(TAPS);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    uint8_t* sOnes = smem;
+    uint8_t* sStage = smem + kOnesBytes;                  // per stage: X halo tile, then dY tile
+    uint64_t* full = reinterpret_cast<uint64_t*>(sStage + kWgStages * kStage);
+    uint64_t* empty = full + kWgStages;
+    uint64_t* done = empty + kWgStages;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    {   // the ones tile (no swizzle matters: every element is 1)
+        uint4* o = reinterpret_cast<uint4*>(sOnes);
+        for (int i = threadIdx.x; i < kOnesBytes / 16; i += kWgThreads) o[i] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+        fence_proxy_async();   // generic writes, read by the tensor cores
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kWgStages; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, 1);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        mbar_init_fence();
+    }
+    if (warp == 1) tc::tmem_alloc(tslot, wg_tmem_cols(TAPS));
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *tslot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int armed[kWgStages];
+            for (int s = 0; s < kWgStages; ++s) armed[s] = -1;
+            int st = 0;
+            uint32_t ph = 0;
+            for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
+                if (!tc::wait_or_abort(empty + st, ph ^ 1, p.status, abort_flag)) break;
+                uint8_t* xs = sStage + st * kStage;
+                tc::mbar_expect_tx(full + st, halo_rows(TAPS) * C * 2 + kDyBytes);
+                tc::tma_load_2d(xs, &tmX, 0, tile * TM - TAPS / 2, full + st);
+                tc::tma_load_2d(xs + stage_bytes(TAPS), &tmDY, 0, tile * TM, full + st);
+                armed[st] = (int)ph;
+                if (++st == kWgStages) {
+                    st = 0;
+                    ph ^= 1;
+                }
+            }
+            if (*abort_flag)
+                for (int s = 0; s < kWgStages; ++s)
+                    if (armed[s] >= 0) drain_wait(full + s, (uint32_t)armed[s]);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int st = 0;
+            uint32_t ph = 0;
+            bool first = true;
+            for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
+                if (!tc::wait_or_abort(full + st, ph, p.status, abort_flag)) break;
+                tc::fence_after_sync();
+                const uint8_t* xs = sStage + st * kStage;
+                const uint8_t* ds = xs + stage_bytes(TAPS);
+#pragma unroll
+                for (int kk = 0; kk < TM / 16; ++kk) {   // 16 rows (two 8-row K groups) per MMA
+                    const uint64_t bd = tc::smem_desc_sw128_mn(ds + kk * 2048, 128);
+#pragma unroll
+                    for (int g = 0; g < NG; ++g) {
+                        // group g < NG - 1: taps 2g, 2g + 1; the last: ones, tap TAPS - 1
+                        const uint64_t ad =
+                            g < NG - 1
+                                ? tc::smem_desc_sw128_mn(xs + 2 * g * (C * 2) + kk * 2048, C * 2)
+                                : tc::smem_desc_sw128_mn(sOnes + kk * 2048,
+                                                         (uint32_t)(xs + (TAPS - 1) * (C * 2) - sOnes));
+                        tc::mma_bf16(tbase + (uint32_t)(g * C), ad, bd, kIdescWg, !(first && kk == 0));
+                    }
+                }
+                first = false;
+                tc::mma_commit(empty + st);
+                if (++st == kWgStages) {
+                    st = 0;
+                    ph ^= 1;
+                }
+            }
+            tc::mma_commit(done);
+            drain_wait(done, 0);
+        }
+    } else {
+        // the CTA's partial: TMEM lane m (quadrant warp % 4) holds row m of A
+        const int q = warp & 3;
+        const int m = q * 32 + lane;
+        const bool ok = __all_sync(0xffffffffu, tc::wait_or_abort(done, 0, p.status, abort_flag));
+        if (ok) {
+            tc::fence_after_sync();
+            float* out = p.part + (size_t)blockIdx.x * kWgPart;
+#pragma unroll 1
+            for (int g = 0; g < NG; ++g) {
+                float v[C];
+                tc::tmem_ld64(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * C), v);
+#pragma unroll
+                for (int o = 0; o < C; ++o) out[(g * C + o) * TM + m] = v[o];
+            }
+        }
+    }
+
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 1) tc::tmem_dealloc(tbase, wg_tmem_cols(TAPS));
+}
+
+constexpr size_t wgrad_smem_bytes(int taps)
+{
+    return 1024 + (size_t)kOnesBytes + (size_t)kWgStages * wg_stage(taps) + 256;
+}
+static_assert(wgrad_smem_bytes(5) <= 227 * 1024 && wgrad_smem_bytes(1) <= 227 * 1024, "shared memory per CTA");
+// the last MMA of a tile reads rows up to TAPS - 1 + TM - 1 of the halo tile
+static_assert(stage_bytes(5) % 1024 == 0 && kDyBytes % 1024 == 0 && kOnesBytes % 1024 == 0, "swizzle atoms");
+
+// Sum the CTAs' partials into the packed gradients of all six layers, one
+// launch after the backward pass (layer l's partials at part + l x
+// layer_stride). Block b of layer l covers partial entries 128 b .. 128 b + 127;
+// warp w sums the CTAs w, w + 8, ... in order and the eight sums are added in
+// warp order, so the result does not depend on scheduling. Entry (g, o, m):
+// m < 64 is tap 2g, input channel m; m >= 64 tap 2g + 1, channel m - 64; in the
+// last group m < 64 is the ones block (row 0 kept: the bias gradient) and
+// m >= 64 tap TAPS - 1.
+constexpr int kRedBlocks5 = wg_groups(5) * C * TM / 128;
+constexpr int kRedBlocks1 = wg_groups(1) * C * TM / 128;
+constexpr int kRedBlocks = 4 * kRedBlocks5 + 2 * kRedBlocks1;
+
+__global__ void __launch_bounds__(256) wgrad_reduce_kernel(const float* part, size_t layer_stride, int nblk,
+                                                           float* grad)
+{
+    int blk = blockIdx.x, l;
+    if (blk < 4 * kRedBlocks5) {
+        l = blk / kRedBlocks5;
+        blk -= l * kRedBlocks5;
+    } else {
+        blk -= 4 * kRedBlocks5;
+        l = 4 + blk / kRedBlocks1;
+        blk -= (l - 4) * kRedBlocks1;
+    }
+    const int taps = taps_of(l), ng = (taps + 1) / 2, co_real = coreal_of(l);
+    const float* pl = part + (size_t)l * layer_stride;
+    float* gl = grad + poff_of(l);
+    __shared__ float4 red[8][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s4 = blk * 128 + lane * 4;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+    for (int b = w; b < nblk; b += 8) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(pl + (size_t)b * kWgPart + s4));
+        acc.x += v.x;
+        acc.y += v.y;
+        acc.z += v.z;
+        acc.w += v.w;
+    }
+    red[w][lane] = acc;
+    __syncthreads();
+    if (threadIdx.x < 128) {
+        float s = 0.f;
+#pragma unroll
+        for (int v = 0; v < 8; ++v) s += reinterpret_cast<const float*>(red[v])[threadIdx.x];
+        const int e = blk * 128 + threadIdx.x;
+        const int g = e / (C * TM), o = (e / TM) % C, m = e % TM, half = m / C, ci = m % C;
+        if (g < ng && o < co_real) {
+            if (g == ng - 1 && half == 0) {
+                if (ci == 0) gl[co_real * C * taps + o] = s;
+            } else {
+                const int j = g == ng - 1 ? taps - 1 : 2 * g + half;
+                gl[(o * C + ci) * taps + j] = s;
+            }
+        }
+    }
+}
+
+// One Adam step on every parameter, and the new value published where the
+// GEMMs read it: a weight W_l[o][i][j] into forward tile (l, j) at [o][i] and
+// backward tile (l, TAPS - 1 - j) at [i][o] (bf16), a bias into the FP32 bias
+// row. Entries of output channels that do not exist stay the zeros that
+// publish_kernel wrote.
 __global__ void adam_kernel(float* p, float* m, float* v, const float* g, int n, float lr, float b1, float b2,
-                            float eps, float c1, float c2)
+                            float eps, float c1, float c2, bf16* Wf, bf16* Wb, float* bias)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float gi = g[i];
@@ -548,7 +749,19 @@ __global__ void adam_kernel(float* p, float* m, float* v, const float* g, int n,
         const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
         m[i] = mi;
         v[i] = vi;
-        p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+        const float pi = p[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+        p[i] = pi;
+        int l = 0;
+        while (l + 1 < NLAYER && poff_of(l + 1) <= i) ++l;
+        const int taps = taps_of(l), nw = coreal_of(l) * C * taps, loc = i - poff_of(l);
+        if (loc < nw) {
+            const int o = loc / (C * taps), ci = (loc / taps) % C, j = loc % taps;
+            const bf16 w = __float2bfloat16_rn(pi);
+            Wf[(size_t)(wtile0_of(l) + j) * C * C + o * C + ci] = w;
+            Wb[(size_t)(wtile0_of(l) + taps - 1 - j) * C * C + ci * C + o] = w;
+        } else {
+            bias[l * C + (loc - nw)] = pi;
+        }
     }
 }
 
@@ -612,6 +825,7 @@ struct pes_init_net {
     int32_t max_batch = 0;
     float *params = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr, *bias = nullptr, *wpart = nullptr;
     double *lpart = nullptr, *loss_dev = nullptr;
+    unsigned* ticket = nullptr;
     bf16 *Wf = nullptr, *Wb = nullptr;
     bf16* act[NLAYER] = {};      // X0, H1..H4, Z
     bf16 *dO = nullptr, *dA = nullptr, *dB = nullptr;
@@ -673,15 +887,20 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t rows, uint32_t box_rows
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int TAPS, int EPI>
+// One layer's GEMM; WG (backward only) also accumulates the layer's weight
+// gradient from relu_src (the layer input) into its partials.
+template <int TAPS, int EPI, bool WG = false>
 cudaError_t launch_conv(pes_init_net* n, const bf16* in, int64_t R, bool backward, int layer, bf16* out,
                         float* out_f32, const bf16* relu_src, cudaStream_t st)
 {
-    CUtensorMap mA, mOut;
+    CUtensorMap mA, mOut, mX;
     if (!make_map(&mA, in, (uint64_t)R, halo_rows(TAPS))) return cudaErrorInvalidValue;
     // bf16 outputs: boxes of the 32 rows of one epilogue warp (the head's FP32
     // output is stored directly; its map is a placeholder)
     if (!make_map(&mOut, out ? (const void*)out : (const void*)in, (uint64_t)R, 32)) return cudaErrorInvalidValue;
+    // the weight gradient's input tiles (otherwise a placeholder)
+    if (!make_map(&mX, WG ? (const void*)relu_src : (const void*)in, (uint64_t)R, halo_rows(TAPS)))
+        return cudaErrorInvalidValue;
     ConvParams p;
     p.R = (int)R;
     p.ntiles = (int)((R + TM - 1) / TM);
@@ -691,13 +910,14 @@ cudaError_t launch_conv(pes_init_net* n, const bf16* in, int64_t R, bool backwar
     p.out = out;
     p.out_f32 = out_f32;
     p.relu_src = relu_src;
+    p.part = WG ? n->wpart + (size_t)layer * kWgPart * n->num_sms : nullptr;
     p.status = n->status;
-    const size_t smem = conv_smem_bytes(TAPS);
-    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<TAPS, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = conv_smem_bytes(TAPS, WG);
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<TAPS, EPI, WG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = (int)std::min<int64_t>(p.ntiles, n->num_sms);
-    conv_tc_kernel<TAPS, EPI><<<grid, kConvThreads, smem, st>>>(mA, backward ? n->mapWb : n->mapWf, mOut, p);
+    conv_tc_kernel<TAPS, EPI, WG><<<grid, kConvThreads, smem, st>>>(mA, backward ? n->mapWb : n->mapWf, mOut, mX, p);
     return cudaGetLastError();
 }
 
@@ -711,25 +931,18 @@ pes_status check_sizes(pes_init_net* n, pes_precision prec, const void* y, const
     return PES_OK;
 }
 
-// Rows, features and gap rows of a call; returns R.
+// Rows and features of a call; returns R.
 template <typename T>
-pes_status prepare_rows(pes_init_net* n, const T* y, const int64_t* off, int32_t B, int64_t N, bool training,
-                        cudaStream_t st, int64_t* R_out)
+pes_status prepare_rows(pes_init_net* n, const T* y, const int64_t* off, int32_t B, int64_t N, cudaStream_t st,
+                        int64_t* R_out)
 {
     const int64_t R = N + (int64_t)G * (B + 1);
     const int blocks = (int)std::min<int64_t>((R + 255) / 256, (int64_t)n->num_sms * 16);
     features_kernel<T><<<blocks, 256, 0, st>>>(y, off, B, N, R, n->mask, n->act[0]);
     NET_CUDA(n, cudaGetLastError());
-    // Every convolution writes zeros on the gap rows of its output; the loss
-    // gradient does not, and the weight gradients sum over all rows.
-    if (training) {
-        ZeroList zl;
-        zl.n = 0;
-        zl.buf[zl.n++] = n->dO;
-        const int gblocks = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)G * (B + 1) + 255) / 256, 1024));
-        gap_rows_kernel<<<gblocks, 256, 0, st>>>(off, B, N, R, zl);
-        NET_CUDA(n, cudaGetLastError());
-    }
+    // Every convolution writes zeros on the gap rows of its output, and so
+    // does the loss kernel on those of the loss gradient: the weight gradients
+    // sum over all rows.
     *R_out = R;
     return PES_OK;
 }
@@ -747,35 +960,43 @@ template <int TAPS>
 pes_status layer_grad(pes_init_net* n, const bf16* dY, const bf16* X, int64_t R, int layer, float* grad,
                       cudaStream_t st)
 {
-    const int nblk = 2 * n->num_sms;
-    wgrad_kernel<TAPS><<<nblk, 256, 0, st>>>(dY, X, R, n->wpart);
-    NET_CUDA(n, cudaGetLastError());
-    const int nw = kCoReal[layer] * C * TAPS, nb = kCoReal[layer];
-    wgrad_reduce_kernel<<<(nw + nb + 255) / 256, 256, 0, st>>>(n->wpart, nblk, nw, nb, C * C * TAPS,
-                                                                grad + kPOff[layer]);
+    CUtensorMap mX, mDY;
+    if (!make_map(&mX, X, (uint64_t)R, halo_rows(TAPS)) || !make_map(&mDY, dY, (uint64_t)R, TM))
+        return net_fail(n, PES_ERR_CUDA, "tensor map of a weight-gradient operand");
+    WgradParams p;
+    p.ntiles = (int)((R + TM - 1) / TM);
+    p.part = n->wpart + (size_t)layer * kWgPart * n->num_sms;
+    p.status = n->status;
+    const int nblk = std::min(p.ntiles, n->num_sms);
+    const size_t smem = wgrad_smem_bytes(TAPS);
+    NET_CUDA(n, cudaFuncSetAttribute(wgrad_tc_kernel<TAPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    wgrad_tc_kernel<TAPS><<<nblk, kWgThreads, smem, st>>>(mX, mDY, p);
     NET_CUDA(n, cudaGetLastError());
     return PES_OK;
 }
 
-// Backward pass from dO: every layer's packed gradient into `grad`.
+// Backward pass from dO: every layer's packed gradient into `grad`. Each
+// backward convolution also accumulates its layer's weight gradient (both read
+// the same gradient tiles, and the layer input that gives the ReLU mask is the
+// gradient's other operand); the first layer has no backward convolution, so
+// its weight gradient runs alone. One launch then sums all partials.
 pes_status backward_layers(pes_init_net* n, int64_t R, float* grad, cudaStream_t st)
 {
     pes_status s;
-    if ((s = layer_grad<1>(n, n->dO, n->act[5], R, 5, grad, st)) != PES_OK) return s;
-    NET_CUDA(n, (launch_conv<1, EPI_MASK>(n, n->dO, R, true, 5, n->dA, nullptr, n->act[5], st)));
-    if ((s = layer_grad<1>(n, n->dA, n->act[4], R, 4, grad, st)) != PES_OK) return s;
-    NET_CUDA(n, (launch_conv<1, EPI_MASK>(n, n->dA, R, true, 4, n->dB, nullptr, n->act[4], st)));
+    NET_CUDA(n, (launch_conv<1, EPI_MASK, true>(n, n->dO, R, true, 5, n->dA, nullptr, n->act[5], st)));
+    NET_CUDA(n, (launch_conv<1, EPI_MASK, true>(n, n->dA, R, true, 4, n->dB, nullptr, n->act[4], st)));
     bf16* cur = n->dB;
     bf16* nxt = n->dA;
-    for (int l = 3; l >= 0; --l) {   // cur: gradient at the pre-activation of conv layer l
-        if ((s = layer_grad<5>(n, cur, n->act[l], R, l, grad, st)) != PES_OK) return s;
-        if (l > 0) {
-            NET_CUDA(n, (launch_conv<5, EPI_MASK>(n, cur, R, true, l, nxt, nullptr, n->act[l], st)));
-            bf16* t = cur;
-            cur = nxt;
-            nxt = t;
-        }
+    for (int l = 3; l > 0; --l) {   // cur: gradient at the pre-activation of conv layer l
+        NET_CUDA(n, (launch_conv<5, EPI_MASK, true>(n, cur, R, true, l, nxt, nullptr, n->act[l], st)));
+        bf16* t = cur;
+        cur = nxt;
+        nxt = t;
     }
+    if ((s = layer_grad<5>(n, cur, n->act[0], R, 0, grad, st)) != PES_OK) return s;
+    const int nblk = (int)std::min<int64_t>((R + TM - 1) / TM, n->num_sms);
+    wgrad_reduce_kernel<<<kRedBlocks, 256, 0, st>>>(n->wpart, (size_t)kWgPart * n->num_sms, nblk, grad);
+    NET_CUDA(n, cudaGetLastError());
     return PES_OK;
 }
 
@@ -796,13 +1017,12 @@ pes_status loss_grad_t(pes_init_net* n, const T* y, const int64_t* off, int32_t 
                        float* grad, double* loss, cudaStream_t st)
 {
     int64_t R = 0;
-    pes_status s = prepare_rows<T>(n, y, off, B, N, true, st, &R);
+    pes_status s = prepare_rows<T>(n, y, off, B, N, st, &R);
     if (s != PES_OK) return s;
     if ((s = forward_layers(n, R, st)) != PES_OK) return s;
     const float scale = (float)(2.0 / (5.0 * (double)N));
-    loss_kernel<T><<<kLossBlocks, 256, 0, st>>>(n->out, xt, off, B, N, n->norm, scale, n->dO, n->lpart);
-    NET_CUDA(n, cudaGetLastError());
-    sum_kernel<<<1, 256, 0, st>>>(n->lpart, kLossBlocks, 1.0 / (5.0 * (double)N), n->loss_dev);
+    loss_kernel<T><<<kLossBlocks, 256, 0, st>>>(n->out, xt, off, B, N, n->norm, scale, 1.0 / (5.0 * (double)N),
+                                                 n->dO, n->lpart, n->ticket, n->loss_dev);
     NET_CUDA(n, cudaGetLastError());
     if ((s = backward_layers(n, R, grad, st)) != PES_OK) return s;
     if (loss) {
@@ -848,9 +1068,10 @@ pes_status pes_init_create(pes_init_net** out, int64_t max_states, int32_t max_b
               cudaMalloc(&n->v, sizeof(float) * PES_INIT_NPARAMS) == cudaSuccess &&
               cudaMalloc(&n->grad, sizeof(float) * PES_INIT_NPARAMS) == cudaSuccess &&
               cudaMalloc(&n->bias, sizeof(float) * NLAYER * C) == cudaSuccess &&
-              cudaMalloc(&n->wpart, sizeof(float) * (size_t)kWgradStride * 2 * n->num_sms) == cudaSuccess &&
+              cudaMalloc(&n->wpart, sizeof(float) * (size_t)kWgPart * NLAYER * n->num_sms) == cudaSuccess &&
               cudaMalloc(&n->lpart, sizeof(double) * kLossBlocks) == cudaSuccess &&
               cudaMalloc(&n->loss_dev, sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&n->ticket, sizeof(unsigned)) == cudaSuccess &&
               cudaMalloc(&n->Wf, sizeof(bf16) * kWTiles * C * C) == cudaSuccess &&
               cudaMalloc(&n->Wb, sizeof(bf16) * kWTiles * C * C) == cudaSuccess &&
               cudaMalloc(&n->out, sizeof(float) * kOutCols * rows) == cudaSuccess &&
@@ -864,11 +1085,13 @@ pes_status pes_init_create(pes_init_net** out, int64_t max_states, int32_t max_b
          cudaMemset(n->m, 0, sizeof(float) * PES_INIT_NPARAMS) == cudaSuccess &&
          cudaMemset(n->v, 0, sizeof(float) * PES_INIT_NPARAMS) == cudaSuccess &&
          cudaMemset(n->status, 0, sizeof(int)) == cudaSuccess &&
+         cudaMemset(n->ticket, 0, sizeof(unsigned)) == cudaSuccess &&
          cudaMemset(n->dO, 0, sizeof(bf16) * C * rows) == cudaSuccess;
     if (!ok) return bail(PES_ERR_CUDA);
     for (int c = 0; c < 5; ++c) {
         n->norm.mu[c] = 0.0;
         n->norm.sigma[c] = 1.0;
+        n->norm.inv_sigma[c] = 1.0;
     }
     if (!make_map(&n->mapWf, n->Wf, (uint64_t)kWTiles * C, C) || !make_map(&n->mapWb, n->Wb, (uint64_t)kWTiles * C, C))
         return bail(PES_ERR_CUDA);
@@ -880,7 +1103,7 @@ pes_status pes_init_create(pes_init_net** out, int64_t max_states, int32_t max_b
 pes_status pes_init_destroy(pes_init_net* n)
 {
     if (!n) return PES_ERR_INVALID_ARG;
-    void* ptrs[] = {n->params, n->m, n->v, n->grad, n->bias, n->wpart, n->lpart, n->loss_dev, n->Wf, n->Wb,
+    void* ptrs[] = {n->params, n->m, n->v, n->grad, n->bias, n->wpart, n->lpart, n->loss_dev, n->ticket, n->Wf, n->Wb,
                     n->out, n->mask, n->status, n->dO, n->dA, n->dB};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -901,6 +1124,7 @@ pes_status pes_init_set_params(pes_init_net* n, const float* params, const doubl
     for (int c = 0; c < 5; ++c) {
         n->norm.mu[c] = mu[c];
         n->norm.sigma[c] = sigma[c];
+        n->norm.inv_sigma[c] = 1.0 / sigma[c];
     }
     NET_CUDA(n, cudaMemcpy(n->params, params, sizeof(float) * PES_INIT_NPARAMS, cudaMemcpyHostToDevice));
     NET_CUDA(n, cudaMemset(n->m, 0, sizeof(float) * PES_INIT_NPARAMS));
@@ -928,8 +1152,8 @@ pes_status pes_init_forward(pes_init_net* n, pes_precision prec, const void* y, 
     if (!x_init) return net_fail(n, PES_ERR_INVALID_ARG, "NULL x_init");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int64_t R = 0;
-    s = prec == PES_FP64 ? prepare_rows<double>(n, (const double*)y, offsets, B, N, false, st, &R)
-                         : prepare_rows<float>(n, (const float*)y, offsets, B, N, false, st, &R);
+    s = prec == PES_FP64 ? prepare_rows<double>(n, (const double*)y, offsets, B, N, st, &R)
+                         : prepare_rows<float>(n, (const float*)y, offsets, B, N, st, &R);
     if (s != PES_OK) return s;
     if ((s = forward_layers(n, R, st)) != PES_OK) return s;
     const int blocks = (int)std::min<int64_t>((N + 255) / 256, (int64_t)n->num_sms * 16);
@@ -965,9 +1189,10 @@ pes_status pes_init_train_step(pes_init_net* n, pes_precision prec, const void* 
     const float c1 = (float)(1.0 / (1.0 - std::pow(b1, n->adam_t)));
     const float c2 = (float)(1.0 / (1.0 - std::pow(b2, n->adam_t)));
     adam_kernel<<<(PES_INIT_NPARAMS + 255) / 256, 256, 0, st>>>(n->params, n->m, n->v, n->grad, PES_INIT_NPARAMS,
-                                                                lr, (float)b1, (float)b2, 1e-8f, c1, c2);
+                                                                lr, (float)b1, (float)b2, 1e-8f, c1, c2, n->Wf,
+                                                                n->Wb, n->bias);
     NET_CUDA(n, cudaGetLastError());
-    return publish(n, st);
+    return PES_OK;
 }
 
 }  // extern "C"

@@ -113,13 +113,34 @@ PES_DEV uint64_t smem_desc_sw128(const void* tile)
            | (2ull << 61);                  // 128-byte swizzle
 }
 
-// Instruction descriptor of kind::f16: bf16 A and B (both K-major), f32
-// accumulator, shape M x N.
-constexpr uint32_t idesc_bf16_f32(int M, int N)
+// Shared-memory matrix descriptor of an MN-major, 128-byte-swizzled bf16
+// operand: 64 consecutive M (or N) elements fill one 128-byte row, and
+// consecutive K indices are consecutive rows, 8 rows to a 1024-byte atom
+// (stride byte offset 1024 between 8-row K groups). This is what a TMA load of
+// a row-major [rows][64] bf16 array with a 128-byte swizzle writes when the
+// array's rows are the reduction (K) dimension. A 128-wide M spans two such
+// 64-element blocks, `lbo` bytes apart (leading byte offset). As for the
+// K-major form, the start may sit at any 128-byte row of a 1024-aligned
+// swizzled region; the next K = 16 slice starts 2048 bytes further on.
+PES_DEV uint64_t smem_desc_sw128_mn(const void* tile, uint32_t lbo)
+{
+    const uint64_t addr = smem_u32(tile);
+    return ((addr >> 4) & 0x3FFFull)              // start address
+           | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16)   // leading byte offset: next 64 M (N) elements
+           | ((1024ull >> 4) << 32)               // stride byte offset: next 8 K rows
+           | (1ull << 46)                         // descriptor version
+           | (2ull << 61);                        // 128-byte swizzle
+}
+
+// Instruction descriptor of kind::f16: bf16 A and B (both K-major unless
+// a_mn / b_mn select the MN-major form), f32 accumulator, shape M x N.
+constexpr uint32_t idesc_bf16_f32(int M, int N, bool a_mn = false, bool b_mn = false)
 {
     return (1u << 4)                        // D: f32
            | (1u << 7)                      // A: bf16
            | (1u << 10)                     // B: bf16
+           | ((uint32_t)a_mn << 15)         // A major-ness (1: MN-major)
+           | ((uint32_t)b_mn << 16)         // B major-ness
            | ((uint32_t)(N >> 3) << 17)     // N / 8
            | ((uint32_t)(M >> 4) << 24);    // M / 16
 }
