@@ -132,6 +132,13 @@ PES_DEV void drain_wait(uint64_t* bar, uint32_t parity)
         if (async_now_ns() - t0 > 1000000000LL) return;
 }
 
+// Programmatic dependent launch: every kernel here is launched so that it may
+// start while its predecessor in the stream is still finishing. A kernel
+// waits for the predecessor (and so, transitively, for everything before it)
+// before its first global-memory access, then lets its own successor launch.
+PES_DEV void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+PES_DEV void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // WG (with EPI_MASK): the same launch also accumulates the layer's weight
 // gradient. The layer input's halo tile (tmX, the ReLU source) is loaded beside
 // each gradient tile; after a tile's conv MMAs the MMA thread adds, as in
@@ -189,6 +196,8 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         mbar_init_fence();
     }
     if (warp == 1) tc::tmem_alloc(tslot, conv_tmem_cols(TAPS, WG));
+    pdl_wait();
+    pdl_trigger();
     if (EPI != EPI_MASK && threadIdx.x >= 64 && threadIdx.x < 64 + C) sbias[threadIdx.x - 64] = p.bias[threadIdx.x - 64];
     tc::fence_before_sync();
     __syncthreads();
@@ -421,6 +430,8 @@ PES_DEV int traj_of_row(const int64_t* off, int B, int64_t r)
 template <typename T>
 __global__ void features_kernel(const T* y, const int64_t* off, int B, int64_t N, int64_t R, uint8_t* mask, bf16* X0)
 {
+    pdl_wait();
+    pdl_trigger();
     const int lane = threadIdx.x & 31;
     const int64_t nw = (R + 31) / 32;
     const int64_t wstride = (int64_t)gridDim.x * (blockDim.x / 32);
@@ -459,59 +470,76 @@ __global__ void features_kernel(const T* y, const int64_t* off, int B, int64_t N
 
 struct Norm {
     double mu[5], sigma[5], inv_sigma[5];
+    float mu_f[5], inv_sigma_f[5];
 };
 
-// Loss terms (o - t)^2 and the output gradient dO = 2 (o - t) / (5 N) in bf16,
-// with t the normalised target (x - mu) / sigma, for entries 0 .. N - 1 (the
-// states); entries N .. N + G (B + 1) - 1 zero the gap rows of dO. Each block
-// leaves its sum in part[block]; the last block to finish adds the partials in
-// block order (so the loss does not depend on scheduling), writes
-// loss_scale x the total to *loss and re-arms the ticket.
+// The normalised target (x - mu) / sigma: in FP32 for FP32 targets (FP64 is
+// a slow pipe on this GPU; the result is rounded to bf16 in the gradient), in
+// FP64 for FP64 ones.
+PES_DEV float norm_target(float x, const Norm& nm, int c) { return (x - nm.mu_f[c]) * nm.inv_sigma_f[c]; }
+PES_DEV float norm_target(double x, const Norm& nm, int c) { return (float)((x - nm.mu[c]) * nm.inv_sigma[c]); }
+
+// Loss terms (o - t)^2 and the output gradient dO = 2 (o - t) / (5 N) in bf16
+// over all R rows (gap rows get zeros). A warp owns 32 consecutive rows, one
+// lane each, and stores them as eight 512-byte runs (four rows each, the first
+// 16 bytes of a row taken from its lane by shuffles), so every store is
+// coalesced. Squares and block sums are FP32 (a thread holds about one row);
+// each block leaves its sum in part[block] and the last block to finish adds
+// the partials in block order in FP64 (so the loss does not depend on
+// scheduling), writes loss_scale x the total to *loss and re-arms the ticket.
 template <typename T>
 __global__ void __launch_bounds__(256) loss_kernel(const float* o, const T* xt, const int64_t* off, int B, int64_t N,
-                                                   Norm nm, float scale, double loss_scale, bf16* dO, double* part,
-                                                   unsigned* ticket, double* loss)
+                                                   int64_t R, Norm nm, float scale, double loss_scale, bf16* dO,
+                                                   double* part, unsigned* ticket, double* loss)
 {
-    double s = 0.0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t total = N + (int64_t)G * (B + 1);
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += stride) {
-        if (k < N) {
-            const int b = traj_of_state(off, B, k);
-            const int64_t row = k + (int64_t)G * (b + 1);
-            float e[5];
-#pragma unroll
-            for (int c = 0; c < 5; ++c) {
-                const float t = (float)(((double)xt[(size_t)c * N + k] - nm.mu[c]) * nm.inv_sigma[c]);
-                e[c] = o[(size_t)row * kOutCols + c] - t;
-                s += (double)(e[c] * e[c]);
+    pdl_wait();
+    pdl_trigger();
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (R + 31) / 32;
+    const int64_t wstride = (int64_t)gridDim.x * (blockDim.x / 32);
+    float s = 0.f;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; w < nw; w += wstride) {
+        const int64_t r = w * 32 + lane;
+        uint4 u = make_uint4(0, 0, 0, 0);
+        if (r < R) {
+            const int b = traj_of_row(off, B, r);
+            const int64_t k = r - (int64_t)G * (b + 1);
+            if (b < B && r - (off[b] + (int64_t)G * b) >= G && k >= 0 && k < N) {
+                const float4 o0 = *reinterpret_cast<const float4*>(o + (size_t)r * kOutCols);
+                const float o4 = o[(size_t)r * kOutCols + 4];
+                const float e0 = o0.x - norm_target(xt[k], nm, 0);
+                const float e1 = o0.y - norm_target(xt[(size_t)N + k], nm, 1);
+                const float e2 = o0.z - norm_target(xt[(size_t)2 * N + k], nm, 2);
+                const float e3 = o0.w - norm_target(xt[(size_t)3 * N + k], nm, 3);
+                const float e4 = o4 - norm_target(xt[(size_t)4 * N + k], nm, 4);
+                s = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, fmaf(e3, e3, e4 * e4))));
+                u = make_uint4(pack_bf16x2(scale * e0, scale * e1), pack_bf16x2(scale * e2, scale * e3),
+                               pack_bf16x2(scale * e4, 0.f), 0u);
             }
-            uint4* dst = reinterpret_cast<uint4*>(dO + (size_t)row * C);
-            dst[0] = make_uint4(pack_bf16x2(scale * e[0], scale * e[1]), pack_bf16x2(scale * e[2], scale * e[3]),
-                                pack_bf16x2(scale * e[4], 0.f), 0u);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(dO) + (size_t)w * 32 * (C / 8);
 #pragma unroll
-            for (int i = 1; i < C / 8; ++i) dst[i] = make_uint4(0, 0, 0, 0);
-        } else {
-            const int64_t g = k - N;
-            const int b = (int)(g / G);
-            const int64_t ob = off[b];
-            if (ob < 0 || ob > N) continue;   // malformed offsets: leave the row alone
-            const int64_t row = ob + (int64_t)G * b + g % G;
-            uint4* dst = reinterpret_cast<uint4*>(dO + (size_t)row * C);
-#pragma unroll
-            for (int i = 0; i < C / 8; ++i) dst[i] = make_uint4(0, 0, 0, 0);
+        for (int i = 0; i < C / 8; ++i) {
+            const int src = 4 * i + (lane >> 3);   // row w * 32 + src, chunk lane & 7
+            uint4 v;
+            v.x = __shfl_sync(0xffffffffu, u.x, src);
+            v.y = __shfl_sync(0xffffffffu, u.y, src);
+            v.z = __shfl_sync(0xffffffffu, u.z, src);
+            v.w = __shfl_sync(0xffffffffu, u.w, src);
+            if (w * 32 + src < R) dst[32 * i + lane] = (lane & 7) == 0 ? v : make_uint4(0, 0, 0, 0);
         }
     }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+    __shared__ float wsum[8];
     __shared__ double red[256];
     __shared__ bool last;
-    red[threadIdx.x] = s;
+    if (lane == 0) wsum[threadIdx.x >> 5] = s;
     __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-    }
     if (threadIdx.x == 0) {
-        part[blockIdx.x] = red[0];
+        double t = 0.0;
+        for (int v = 0; v < (int)(blockDim.x >> 5); ++v) t += (double)wsum[v];
+        part[blockIdx.x] = t;
         __threadfence();
         last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
@@ -522,8 +550,8 @@ __global__ void __launch_bounds__(256) loss_kernel(const float* o, const T* xt, 
     for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(part + i);
     red[threadIdx.x] = t;
     __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    for (int v = blockDim.x / 2; v > 0; v >>= 1) {
+        if ((int)threadIdx.x < v) red[threadIdx.x] += red[threadIdx.x + v];
         __syncthreads();
     }
     if (threadIdx.x == 0) {
@@ -584,6 +612,8 @@ __global__ void __launch_bounds__(kWgThreads, 1)
         mbar_init_fence();
     }
     if (warp == 1) tc::tmem_alloc(tslot, wg_tmem_cols(TAPS));
+    pdl_wait();
+    pdl_trigger();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -692,6 +722,8 @@ constexpr int kRedBlocks = 4 * kRedBlocks5 + 2 * kRedBlocks1;
 __global__ void __launch_bounds__(256) wgrad_reduce_kernel(const float* part, size_t layer_stride, int nblk,
                                                            float* grad)
 {
+    pdl_wait();
+    pdl_trigger();
     int blk = blockIdx.x, l;
     if (blk < 4 * kRedBlocks5) {
         l = blk / kRedBlocks5;
@@ -743,6 +775,8 @@ __global__ void __launch_bounds__(256) wgrad_reduce_kernel(const float* part, si
 __global__ void adam_kernel(float* p, float* m, float* v, const float* g, int n, float lr, float b1, float b2,
                             float eps, float c1, float c2, bf16* Wf, bf16* Wb, float* bias)
 {
+    pdl_wait();
+    pdl_trigger();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float gi = g[i];
         const float mi = b1 * m[i] + (1.f - b1) * gi;
@@ -770,6 +804,8 @@ __global__ void adam_kernel(float* p, float* m, float* v, const float* g, int n,
 // the FP32 biases padded to 64 channels.
 __global__ void publish_kernel(const float* p, bf16* Wf, bf16* Wb, float* bias)
 {
+    pdl_wait();
+    pdl_trigger();
     const int total = kWTiles * C * C;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total + NLAYER * C;
          idx += gridDim.x * blockDim.x) {
@@ -798,6 +834,8 @@ __global__ void publish_kernel(const float* p, bf16* Wf, bf16* Wb, float* bias)
 template <typename T>
 __global__ void denorm_kernel(const float* o, const int64_t* off, int B, int64_t N, Norm nm, T* x)
 {
+    pdl_wait();
+    pdl_trigger();
     float mu[5], sg[5];
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
@@ -887,6 +925,24 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t rows, uint32_t box_rows
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Launch with programmatic stream serialization (the kernels call pdl_wait
+// before touching global memory).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // One layer's GEMM; WG (backward only) also accumulates the layer's weight
 // gradient from relu_src (the layer input) into its partials.
 template <int TAPS, int EPI, bool WG = false>
@@ -917,8 +973,8 @@ cudaError_t launch_conv(pes_init_net* n, const bf16* in, int64_t R, bool backwar
                                          (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = (int)std::min<int64_t>(p.ntiles, n->num_sms);
-    conv_tc_kernel<TAPS, EPI, WG><<<grid, kConvThreads, smem, st>>>(mA, backward ? n->mapWb : n->mapWf, mOut, mX, p);
-    return cudaGetLastError();
+    return launch_pdl(conv_tc_kernel<TAPS, EPI, WG>, grid, kConvThreads, smem, st, mA, backward ? n->mapWb : n->mapWf,
+                      mOut, mX, p);
 }
 
 pes_status check_sizes(pes_init_net* n, pes_precision prec, const void* y, const int64_t* off, int32_t B, int64_t N)
@@ -938,8 +994,7 @@ pes_status prepare_rows(pes_init_net* n, const T* y, const int64_t* off, int32_t
 {
     const int64_t R = N + (int64_t)G * (B + 1);
     const int blocks = (int)std::min<int64_t>((R + 255) / 256, (int64_t)n->num_sms * 16);
-    features_kernel<T><<<blocks, 256, 0, st>>>(y, off, B, N, R, n->mask, n->act[0]);
-    NET_CUDA(n, cudaGetLastError());
+    NET_CUDA(n, launch_pdl(features_kernel<T>, blocks, 256, 0, st, y, off, B, N, R, n->mask, n->act[0]));
     // Every convolution writes zeros on the gap rows of its output, and so
     // does the loss kernel on those of the loss gradient: the weight gradients
     // sum over all rows.
@@ -970,8 +1025,7 @@ pes_status layer_grad(pes_init_net* n, const bf16* dY, const bf16* X, int64_t R,
     const int nblk = std::min(p.ntiles, n->num_sms);
     const size_t smem = wgrad_smem_bytes(TAPS);
     NET_CUDA(n, cudaFuncSetAttribute(wgrad_tc_kernel<TAPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    wgrad_tc_kernel<TAPS><<<nblk, kWgThreads, smem, st>>>(mX, mDY, p);
-    NET_CUDA(n, cudaGetLastError());
+    NET_CUDA(n, launch_pdl(wgrad_tc_kernel<TAPS>, nblk, kWgThreads, smem, st, mX, mDY, p));
     return PES_OK;
 }
 
@@ -995,8 +1049,8 @@ pes_status backward_layers(pes_init_net* n, int64_t R, float* grad, cudaStream_t
     }
     if ((s = layer_grad<5>(n, cur, n->act[0], R, 0, grad, st)) != PES_OK) return s;
     const int nblk = (int)std::min<int64_t>((R + TM - 1) / TM, n->num_sms);
-    wgrad_reduce_kernel<<<kRedBlocks, 256, 0, st>>>(n->wpart, (size_t)kWgPart * n->num_sms, nblk, grad);
-    NET_CUDA(n, cudaGetLastError());
+    NET_CUDA(n, launch_pdl(wgrad_reduce_kernel, kRedBlocks, 256, 0, st, (const float*)n->wpart,
+                           (size_t)kWgPart * n->num_sms, nblk, grad));
     return PES_OK;
 }
 
@@ -1021,9 +1075,9 @@ pes_status loss_grad_t(pes_init_net* n, const T* y, const int64_t* off, int32_t 
     if (s != PES_OK) return s;
     if ((s = forward_layers(n, R, st)) != PES_OK) return s;
     const float scale = (float)(2.0 / (5.0 * (double)N));
-    loss_kernel<T><<<kLossBlocks, 256, 0, st>>>(n->out, xt, off, B, N, n->norm, scale, 1.0 / (5.0 * (double)N),
-                                                 n->dO, n->lpart, n->ticket, n->loss_dev);
-    NET_CUDA(n, cudaGetLastError());
+    const int lblocks = (int)std::min<int64_t>((R + 255) / 256, kLossBlocks);
+    NET_CUDA(n, launch_pdl(loss_kernel<T>, lblocks, 256, 0, st, (const float*)n->out, xt, off, B, N, R, n->norm, scale,
+                           1.0 / (5.0 * (double)N), n->dO, n->lpart, n->ticket, n->loss_dev));
     if ((s = backward_layers(n, R, grad, st)) != PES_OK) return s;
     if (loss) {
         NET_CUDA(n, cudaMemcpyAsync(loss, n->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1034,8 +1088,8 @@ pes_status loss_grad_t(pes_init_net* n, const T* y, const int64_t* off, int32_t 
 
 pes_status publish(pes_init_net* n, cudaStream_t st)
 {
-    publish_kernel<<<(kWTiles * C * C + NLAYER * C + 255) / 256, 256, 0, st>>>(n->params, n->Wf, n->Wb, n->bias);
-    NET_CUDA(n, cudaGetLastError());
+    NET_CUDA(n, launch_pdl(publish_kernel, (kWTiles * C * C + NLAYER * C + 255) / 256, 256, 0, st,
+                           (const float*)n->params, n->Wf, n->Wb, n->bias));
     return PES_OK;
 }
 
@@ -1092,6 +1146,8 @@ pes_status pes_init_create(pes_init_net** out, int64_t max_states, int32_t max_b
         n->norm.mu[c] = 0.0;
         n->norm.sigma[c] = 1.0;
         n->norm.inv_sigma[c] = 1.0;
+        n->norm.mu_f[c] = 0.f;
+        n->norm.inv_sigma_f[c] = 1.f;
     }
     if (!make_map(&n->mapWf, n->Wf, (uint64_t)kWTiles * C, C) || !make_map(&n->mapWb, n->Wb, (uint64_t)kWTiles * C, C))
         return bail(PES_ERR_CUDA);
@@ -1125,6 +1181,8 @@ pes_status pes_init_set_params(pes_init_net* n, const float* params, const doubl
         n->norm.mu[c] = mu[c];
         n->norm.sigma[c] = sigma[c];
         n->norm.inv_sigma[c] = 1.0 / sigma[c];
+        n->norm.mu_f[c] = (float)mu[c];
+        n->norm.inv_sigma_f[c] = (float)(1.0 / sigma[c]);
     }
     NET_CUDA(n, cudaMemcpy(n->params, params, sizeof(float) * PES_INIT_NPARAMS, cudaMemcpyHostToDevice));
     NET_CUDA(n, cudaMemset(n->m, 0, sizeof(float) * PES_INIT_NPARAMS));
@@ -1158,10 +1216,11 @@ pes_status pes_init_forward(pes_init_net* n, pes_precision prec, const void* y, 
     if ((s = forward_layers(n, R, st)) != PES_OK) return s;
     const int blocks = (int)std::min<int64_t>((N + 255) / 256, (int64_t)n->num_sms * 16);
     if (prec == PES_FP64)
-        denorm_kernel<double><<<blocks, 256, 0, st>>>(n->out, offsets, B, N, n->norm, (double*)x_init);
+        NET_CUDA(n, launch_pdl(denorm_kernel<double>, blocks, 256, 0, st, (const float*)n->out, offsets, B, N, n->norm,
+                               (double*)x_init));
     else
-        denorm_kernel<float><<<blocks, 256, 0, st>>>(n->out, offsets, B, N, n->norm, (float*)x_init);
-    NET_CUDA(n, cudaGetLastError());
+        NET_CUDA(n, launch_pdl(denorm_kernel<float>, blocks, 256, 0, st, (const float*)n->out, offsets, B, N, n->norm,
+                               (float*)x_init));
     return PES_OK;
 }
 
@@ -1188,10 +1247,9 @@ pes_status pes_init_train_step(pes_init_net* n, pes_precision prec, const void* 
     const double b1 = 0.9, b2 = 0.999;
     const float c1 = (float)(1.0 / (1.0 - std::pow(b1, n->adam_t)));
     const float c2 = (float)(1.0 / (1.0 - std::pow(b2, n->adam_t)));
-    adam_kernel<<<(PES_INIT_NPARAMS + 255) / 256, 256, 0, st>>>(n->params, n->m, n->v, n->grad, PES_INIT_NPARAMS,
-                                                                lr, (float)b1, (float)b2, 1e-8f, c1, c2, n->Wf,
-                                                                n->Wb, n->bias);
-    NET_CUDA(n, cudaGetLastError());
+    NET_CUDA(n, launch_pdl(adam_kernel, (PES_INIT_NPARAMS + 255) / 256, 256, 0, st, n->params, n->m, n->v,
+                           (const float*)n->grad, (int)PES_INIT_NPARAMS, lr, (float)b1, (float)b2, 1e-8f, c1, c2, n->Wf,
+                           n->Wb, n->bias));
     return PES_OK;
 }
 
