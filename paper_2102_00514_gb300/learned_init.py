@@ -144,6 +144,11 @@ class EvalResult:
     err_learned: np.ndarray
     rel_diff: np.ndarray           # ||x_learned - x_prior|| / ||x_prior|| per trajectory
     seconds: float
+    # with the fallback: trajectories re-run from the prior start, and the
+    # iterations the learned policy spent per trajectory (a run that does not
+    # reach the tolerance counted at the cap, both runs where there are two)
+    fallback: np.ndarray | None = None
+    spent_learned: np.ndarray | None = None
 
 
 def gated_start(x_net: torch.Tensor, wl: dict, t_valid: int) -> torch.Tensor:
@@ -163,11 +168,43 @@ def gated_start(x_net: torch.Tensor, wl: dict, t_valid: int) -> torch.Tensor:
     return x
 
 
+def _subset(wl: dict, idx: np.ndarray) -> dict:
+    """The trajectories idx of a workload, packed into one of their own."""
+    off = wl["offsets"]
+    lens = np.diff(off)[idx]
+    cols = np.concatenate([np.arange(off[b], off[b + 1]) for b in idx])
+    sub = dict(wl, y=wl["y"][:, cols], offsets=np.concatenate([[0], np.cumsum(lens)]).astype(np.int64),
+               m0=wl["m0"][idx], P0=wl["P0"][idx])
+    if len(wl["sensors"]) > 1:
+        sub["sensors"] = wl["sensors"][idx]
+    return sub
+
+
+def rerun_from_prior(wl: dict, idx: np.ndarray, method: int, tol: float, max_iters: int):
+    """The fallback: trajectories idx iterated from the prior start in a batch
+    of their own. Returns (x [5][states of idx] float64 host, iterations to
+    tol per trajectory, 0 = not reached)."""
+    sub = _subset(wl, idx)
+    B = len(idx)
+    sm = pes.Smoother(int(sub["offsets"][-1]), B)
+    xs, _, _, _ = sm.ieks_run(pes.Model.from_workload(sub), method, pes.FP64, _dev(sub["y"], torch.float64),
+                              _dev(sub["offsets"], torch.int64), _dev(sub["m0"], torch.float64),
+                              _dev(sub["P0"], torch.float64), iters=max_iters, tol=tol, allow_not_converged=True)
+    it = sm.traj_iterations(B)
+    x = xs.cpu().numpy()
+    sm.close()
+    return x, it
+
+
 def evaluate(net: pes.InitNet, wl: dict, method: int = pes.IEKS, tol: float = TOL_EVAL,
-             max_iters: int = MAX_ITERS, t_valid: int | None = None) -> EvalResult:
+             max_iters: int = MAX_ITERS, t_valid: int | None = None, fallback: bool = False) -> EvalResult:
     """Iterations to `tol` and converged results from the prior start and from
     the network's start (gated by trajectory length when `t_valid` is given),
-    every trajectory of `wl` in one FP64 batch each."""
+    every trajectory of `wl` in one FP64 batch each. With `fallback`, the
+    trajectories the network's start does not bring to `tol` within
+    `max_iters` are iterated again from the prior start in a batch of their
+    own, and that run's result replaces theirs; its iterations are added to
+    what the learned policy spent."""
     off = wl["offsets"]
     B = len(off) - 1
     N = int(off[-1])
@@ -186,10 +223,25 @@ def evaluate(net: pes.InitNet, wl: dict, method: int = pes.IEKS, tol: float = TO
     xb, _, _, _ = sm.ieks_run(model, method, pes.FP64, y, o, m0, P0, x_init=x0, iters=max_iters, tol=tol,
                               allow_not_converged=True)
     ib = sm.traj_iterations(B)
-    torch.cuda.synchronize()
-    secs = time.perf_counter() - t0
     xa, xb = xa.cpu().numpy(), xb.cpu().numpy()
     sm.close()
+    fb = spent = None
+    if fallback:
+        spent = np.where(ib > 0, ib, max_iters).astype(np.int64)
+        fb = ib == 0
+        idx = np.flatnonzero(fb)
+        if len(idx):
+            xf, itf = rerun_from_prior(wl, idx, method, tol, max_iters)
+            a = 0
+            for j, b in enumerate(idx):
+                n = int(off[b + 1] - off[b])
+                xb[:, off[b]:off[b + 1]] = xf[:, a:a + n]
+                a += n
+                spent[b] += itf[j] if itf[j] > 0 else max_iters
+            ib = ib.copy()
+            ib[idx] = itf
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
     xt = wl["x_true"]
     ea, eb, rd = np.zeros(B), np.zeros(B), np.zeros(B)
     for b in range(B):
@@ -197,18 +249,19 @@ def evaluate(net: pes.InitNet, wl: dict, method: int = pes.IEKS, tol: float = TO
         ea[b] = np.sqrt(np.mean((xa[0:2, sl] - xt[0:2, sl]) ** 2) * 2)
         eb[b] = np.sqrt(np.mean((xb[0:2, sl] - xt[0:2, sl]) ** 2) * 2)
         rd[b] = np.linalg.norm(xb[:, sl] - xa[:, sl]) / max(np.linalg.norm(xa[:, sl]), 1e-300)
-    return EvalResult(ia, ib, ea, eb, rd, secs)
+    return EvalResult(ia, ib, ea, eb, rd, secs, fb, spent)
 
 
 def summary(r: EvalResult, max_iters: int = MAX_ITERS) -> dict:
     """Paired comparison of the two starts over every trajectory: iterations to
-    tolerance with a trajectory that does not get there counted at the cap,
+    tolerance with a trajectory that does not get there counted at the cap
+    (for the learned policy with the fallback, the iterations of both its runs),
     final position error against the truth (the learned start is "no worse"
     where its error is within 0.1 % of the prior start's), and the same figures
     on the trajectories both starts bring to tolerance."""
     both = (r.iters_prior > 0) & (r.iters_learned > 0)
     ip = np.where(r.iters_prior > 0, r.iters_prior, max_iters)
-    il = np.where(r.iters_learned > 0, r.iters_learned, max_iters)
+    il = r.spent_learned if r.spent_learned is not None else np.where(r.iters_learned > 0, r.iters_learned, max_iters)
     no_worse = r.err_learned <= 1.001 * r.err_prior
     out = {"trajectories": int(len(r.iters_prior)),
            "converged_prior": int((r.iters_prior > 0).sum()),
@@ -221,11 +274,13 @@ def summary(r: EvalResult, max_iters: int = MAX_ITERS) -> dict:
            "mean_position_rmse_all_prior": float(r.err_prior.mean()),
            "mean_position_rmse_all_learned": float(r.err_learned.mean()),
            "same_solution_all_within_1e-4": int((r.rel_diff < 1e-4).sum())}
+    if r.fallback is not None:
+        out["fallback_runs"] = int(r.fallback.sum())
     if both.any():
         out.update({
             "mean_iters_prior": float(r.iters_prior[both].mean()),
-            "mean_iters_learned": float(r.iters_learned[both].mean()),
-            "iters_saved": float((r.iters_prior[both] - r.iters_learned[both]).mean()),
+            "mean_iters_learned": float(il[both].mean()),
+            "iters_saved": float((r.iters_prior[both] - il[both]).mean()),
             "same_solution_within_1e-4": int((r.rel_diff[both] < 1e-4).sum()),
             "median_position_rmse_prior": float(np.median(r.err_prior[both])),
             "median_position_rmse_learned": float(np.median(r.err_learned[both])),
@@ -282,6 +337,9 @@ def run(n_train: int = 100_000, T_train: int = 1000, n_heldout: int = 1024, held
         # domain, the prior start (the fallback) beyond it
         rg = evaluate(net, ev, method=m, t_valid=t_valid)
         out[name]["gated"] = summary(rg)
+        # and with the fallback: trajectories the start does not bring to
+        # tolerance are iterated again from the prior start
+        out[name]["gated_fallback"] = summary(evaluate(net, ev, method=m, t_valid=t_valid, fallback=True))
         T = np.diff(ev["offsets"]) - 1
         inside = T <= t_valid
         if inside.any():

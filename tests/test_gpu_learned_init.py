@@ -160,11 +160,14 @@ def test_trained_initialiser_saves_iterations():
     with the prior start on held-out trajectories of T = 1,000 .. 10,000 (its
     validity domain, up to ten times the training length), paired over every
     trajectory: a trajectory that does not reach the 1e-6 tolerance within 50
-    iterations counts at 50. Iterations saved, the number of trajectories
-    brought to tolerance, and the final position error against the truth per
-    trajectory and on average are held to the bounds below; where the
-    network's start ends at another fixed point of the iteration, that point
-    is worse about as often as it is better."""
+    iterations counts at 50. The start as the library uses it falls back to the
+    prior start for the trajectories it does not bring to tolerance (their
+    iterations are those of both runs). That policy is held to converging at
+    least as many trajectories, saving at least three iterations, a final
+    position error against the truth no worse on 95 % of the trajectories and
+    no worse on average. The network's start alone saves more iterations but
+    ends, on about one trajectory in twenty, at another fixed point of the
+    iteration, worse about as often as better."""
     from paper_2102_00514_gb300 import learned_init as L
     wl = synth.workload("train2048_T1000")
     x, conv = L.converged_targets(wl)
@@ -175,14 +178,17 @@ def test_trained_initialiser_saves_iterations():
     n.set_params(L.initial_params(0), mu, sigma)
     log = L.train(n, wl, x, conv, batch_traj=64, steps=3000, lr=2e-3, lr_final=1e-4)
     print(f"training: {log.steps} steps in {log.seconds:.2f} s, loss {log.losses[0][1]:.4f} -> {log.losses[-1][1]:.4f}")
-    r = L.evaluate(n, ev)
+    raw = L.summary(L.evaluate(n, ev))
+    print("network start:", raw)
+    r = L.evaluate(n, ev, fallback=True)
     s = L.summary(r)
-    print("evaluation:", s)
+    print("with the fallback:", s)
     n.close()
     assert log.losses[-1][1] < 0.5 * log.losses[0][1]
+    assert raw["iters_saved_capped"] >= 3.0
     assert s["converged_learned"] >= s["converged_prior"]
     assert s["iters_saved_capped"] >= 3.0
-    assert s["error_no_worse_fraction"] >= 0.92
+    assert s["error_no_worse_fraction"] >= 0.95
     assert s["mean_position_rmse_all_learned"] <= s["mean_position_rmse_all_prior"]
 
 
