@@ -67,7 +67,7 @@ def parse_args():
     ap.add_argument("--sequential", action="store_true",
                     help="also time the sequential counterpart (one GPU thread per trajectory) on the workload")
     ap.add_argument("--cpu-sample", type=int, default=1 << 17, help="states in the oracle's timed sample")
-    ap.add_argument("--profile", choices=["ieks", "cubature", "init"], default=None,
+    ap.add_argument("--profile", choices=["ieks", "cubature", "init", "train"], default=None,
                     help="profiling case: only `warmup` + 1 runs of one method, no JSON line")
     ap.add_argument("--prec", choices=["fp32", "fp64", "refined"], default="fp32", help="precision of --profile")
     ap.add_argument("--sweep", action="store_true",
@@ -82,7 +82,10 @@ def parse_args():
 def run_profile_case(args):
     """A short, single-method case for ncu captures: `warmup` launches, then one.
     --profile init: forward passes of the learned initialiser on 64 held-out
-    trajectories (log T uniform in 1,000 .. 100,000), six GEMM launches each."""
+    trajectories (log T uniform in 1,000 .. 100,000), six GEMM launches each.
+    --profile train: `warmup` + `iters` training steps of the learned
+    initialiser on one minibatch of 128 trajectories of T = 1,000 (the
+    training configuration), the true states as targets."""
     import numpy as np
     import torch
 
@@ -102,6 +105,28 @@ def run_profile_case(args):
             net.forward(pes.FP32, y, o)
             torch.cuda.synchronize()
             print(f"forward {i}: {N} states, {1e3 * (time.perf_counter() - t0):.3f} ms", flush=True)
+        net.close()
+        return
+    if args.profile == "train":
+        from paper_2102_00514_gb300 import learned_init as LI
+        wl = synth.workload("train128_T1000")
+        N = wl["y"].shape[1]
+        xt = wl["x_true"]
+        net = pes.InitNet(N, 128)
+        net.set_params(LI.initial_params(0), xt.mean(axis=1), xt.std(axis=1) + 1e-3)
+        y = torch.as_tensor(wl["y"], dtype=torch.float32, device="cuda")
+        o = torch.as_tensor(wl["offsets"], dtype=torch.int64, device="cuda")
+        x = torch.as_tensor(xt, dtype=torch.float32, device="cuda")
+        n = args.warmup + args.iters
+        for i in range(n):
+            net.train_step(pes.FP32, y, o, x, 1e-3, want_loss=(i == n - 1))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(n):
+            net.train_step(pes.FP32, y, o, x, 1e-3, want_loss=False)
+        torch.cuda.synchronize()
+        dt_s = (time.perf_counter() - t0) / n
+        print(f"train step: {N} states, {1e6 * dt_s:.1f} us, {N / dt_s:.3e} states/s", flush=True)
         net.close()
         return
     wl = synth.workload(f"sweep_T{args.T}")

@@ -201,10 +201,11 @@ def evaluate(net: pes.InitNet, wl: dict, method: int = pes.IEKS, tol: float = TO
     """Iterations to `tol` and converged results from the prior start and from
     the network's start (gated by trajectory length when `t_valid` is given),
     every trajectory of `wl` in one FP64 batch each. With `fallback`, the
-    trajectories the network's start does not bring to `tol` within
-    `max_iters` are iterated again from the prior start in a batch of their
-    own, and that run's result replaces theirs; its iterations are added to
-    what the learned policy spent."""
+    trajectories that the network's start (not the prior one it is gated to
+    beyond `t_valid`) does not bring to `tol` within `max_iters` are iterated
+    again from the prior start in a batch of their own, and that run's result
+    replaces theirs; its iterations are added to what the learned policy
+    spent."""
     off = wl["offsets"]
     B = len(off) - 1
     N = int(off[-1])
@@ -228,7 +229,11 @@ def evaluate(net: pes.InitNet, wl: dict, method: int = pes.IEKS, tol: float = TO
     fb = spent = None
     if fallback:
         spent = np.where(ib > 0, ib, max_iters).astype(np.int64)
+        # only where the network's start was used (beyond t_valid the start
+        # already is the prior mean)
         fb = ib == 0
+        if t_valid is not None:
+            fb &= (np.diff(off) - 1) <= t_valid
         idx = np.flatnonzero(fb)
         if len(idx):
             xf, itf = rerun_from_prior(wl, idx, method, tol, max_iters)
