@@ -403,6 +403,50 @@ PES_DEV void load_lin_trans(const KParams<T>& p, int s, int lane, Trans<T>& tr)
     for (int i = 0; i < 15; ++i) tr.Q[i] = h[(50 + i) * 32];
 }
 
+// Per-thread asynchronous prefetch of the next state's inputs (nominal mean
+// and covariance, measurement: 22 scalars) into shared memory, for the
+// sigma-point folds, whose register pressure rules out a register prefetch.
+// Each thread copies its own scalars with cp.async (L1-allocating, like the
+// plain loads it replaces; every read of the nominal follows a grid barrier's
+// acquire) into one of two stages and reads only its own stage back after
+// cp.async.wait_group, so no block synchronisation is involved. Element c of
+// stage s sits at base[(s * NS + c) * stride] (thread-contiguous columns).
+template <typename T>
+struct StatePrefetch {
+    static constexpr int NS = 22;
+    T* base;
+    int stride;
+    PES_DEV void copy(T* dst, const T* src) const
+    {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src), "n"(sizeof(T))
+                     : "memory");
+    }
+    PES_DEV void issue(const KParams<T>& p, int64_t ix, int s) const
+    {
+        T* d = base + (size_t)s * NS * stride;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) copy(d + i * stride, p.x + i * p.cs + ix);
+#pragma unroll
+        for (int i = 0; i < 15; ++i) copy(d + (5 + i) * stride, p.P + i * p.cs + ix);
+        copy(d + 20 * stride, p.y + ix);
+        copy(d + 21 * stride, p.y + p.cs + ix);
+    }
+    PES_DEV static void commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+    // all but the most recent group complete
+    PES_DEV static void wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+    template <int LIN>
+    PES_DEV void take(int s, StateIn<T, LIN>& st) const
+    {
+        const T* d = base + (size_t)s * NS * stride;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) st.x[i] = d[i * stride];
+#pragma unroll
+        for (int i = 0; i < 15; ++i) st.P[i] = d[(5 + i) * stride];
+        st.y[0] = d[20 * stride];
+        st.y[1] = d[21 * stride];
+    }
+};
+
 // Filtering, level 1: fold the lane's chunk [a, e) into one element. Step k
 // folds the update with its own observation and then the prediction through
 // its outgoing transition (k -> k+1), both linearised about the nominal of k,
@@ -413,7 +457,8 @@ PES_DEV void load_lin_trans(const KParams<T>& p, int s, int lane, Trans<T>& tr)
 // With a stored linearisation (MODE_RUN, cubature) both are kept for the
 // re-run, the transition at the slot of its source state.
 template <typename T, int LIN>
-PES_DEV bool fold_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int lane, FElem<T>& acc)
+PES_DEV bool fold_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int lane, FElem<T>& acc,
+                               const StatePrefetch<T>* pf = nullptr)
 {
     bool ok = true;
     T zero[5] = {T(0), T(0), T(0), T(0), T(0)};
@@ -435,17 +480,29 @@ PES_DEV bool fold_filter_chunk(const KParams<T>& p, int64_t a, int64_t e, int la
         felem_identity(acc, tr.xn);
         fold_predict(acc, tr);
     }
-    // the next state's inputs are loaded a step ahead, except for cubature,
-    // whose register pressure makes the prefetch cost more in spills than it
-    // hides (measured: fold 202 -> 194 us per iteration at T = 2^20 without it)
+    // the next state's inputs are loaded a step ahead: into registers for
+    // the Taylor linearisation; for the sigma-point ones, whose register
+    // pressure makes a register prefetch cost more in spills than it hides
+    // (measured: fold 202 -> 194 us per iteration at T = 2^20 without it),
+    // into shared memory by cp.async when the caller provides the stages
     constexpr bool prefetch = !kSigma<LIN>;
+    const bool async_pf = kSigma<LIN> && pf != nullptr;
     if (prefetch) load_state(p, ix, sc);
+    if (async_pf) {
+        pf->issue(p, ix, 0);
+        StatePrefetch<T>::commit();
+    }
 #pragma unroll 1
     for (int64_t k = a; k < e; ++k, ix += dix) {
         cur.forward(k);
         const int s = (int)(k - a);
         if (prefetch) {
             if (k + 1 < e) load_state(p, ix + dix, sn);
+        } else if (async_pf) {
+            if (k + 1 < e) pf->issue(p, ix + dix, (s + 1) & 1);
+            StatePrefetch<T>::commit();
+            StatePrefetch<T>::wait_prev();
+            pf->take(s & 1, sc);
         } else {
             load_state(p, ix, sc);
         }
@@ -1073,6 +1130,7 @@ constexpr size_t smem_bytes_for(size_t scalar)
     // buffer, down-sweep Gaussians, one block Gaussian; the per-warp stream
     // stages (2 x LINS x 32 scalars per warp) reuse this memory
     static_assert(size_t(NT) * FE * 2 + size_t(NT) * GE + GE >= size_t(NT) * 2 * LINS, "stream stages must fit");
+    static_assert(FE >= 2 * StatePrefetch<double>::NS, "the fold's prefetch stages fit the top-level buffer");
     return scalar * (size_t(NT) * FE * 2 + size_t(NT) * GE + GE);
 }
 
@@ -1121,7 +1179,13 @@ __global__ void __launch_bounds__(NT, 1) pes_persistent_kernel(const KParams<T> 
         PES_PHASE(p, it, 0);
         if (do_filter) {
             FElem<T> acc;
-            ok &= fold_filter_chunk<T, LIN>(p, a, e, lane, acc);
+            // the sigma-point folds prefetch each next state into the
+            // top-level tree's memory, idle until after the block up-sweep
+            StatePrefetch<T> pf;
+            pf.base = reinterpret_cast<T*>(topF) + t;
+            pf.stride = NT;
+            ok &= fold_filter_chunk<T, LIN>(p, a, e, lane, acc, &pf);
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
             elemF[t] = acc;
             Gauss<T> G;
             filter_block_scan<T, NT>(p, elemF, topF, gs, gblock, gen, G, it);
