@@ -218,6 +218,38 @@ def test_host_entry_point_equals_device_entry_point(sm):
     assert torch.equal(xh, xd.cpu()) and torch.equal(Ph, Pd.cpu())
 
 
+@pytest.mark.parametrize("method,prec", [(pes.IEKS, pes.FP32), (pes.CUBATURE, pes.FP64), (pes.CUBATURE, pes.REFINED)])
+def test_host_entry_point_pinned_and_pageable_buffers(sm, method, prec):
+    """Pinned or pageable host buffers, mixed, and outputs that are views
+    inside larger pinned allocations (written exactly where they lie): the
+    results equal the device entry point's bit for bit."""
+    wl = synth.workload("ieks_T500")
+    dt = torch.float64 if prec == pes.FP64 else torch.float32
+    d = workload_to_dev(wl, pes.FP64 if prec == pes.FP64 else pes.FP32)
+    xd, Pd, _, _ = sm.ieks_run(d["model"], method, prec, d["y"], d["offsets"], d["m0"], d["P0"], iters=3)
+    sm.sync()
+    xd, Pd = xd.cpu(), Pd.cpu()
+    N = wl["y"].shape[1]
+    host = lambda a, t=dt, pin=True: (torch.as_tensor(np.ascontiguousarray(a), dtype=t).pin_memory() if pin
+                                      else torch.as_tensor(np.ascontiguousarray(a), dtype=t).clone())
+    sens = host(wl["sensors"], torch.float64)
+    off, m0, P0 = host(wl["offsets"], torch.int64), host(wl["m0"]), host(wl["P0"])
+    big_x = torch.zeros(5 * N + 37, dtype=dt).pin_memory()
+    big_P = torch.zeros(15 * N + 11, dtype=dt).pin_memory()
+    cases = {
+        "pinned": (host(wl["y"]), None, None),
+        "pageable": (host(wl["y"], pin=False), torch.empty((5, N), dtype=dt), torch.empty((15, N), dtype=dt)),
+        "mixed": (host(wl["y"], pin=False), None, torch.empty((15, N), dtype=dt)),
+        "views": (host(wl["y"]), big_x[37:].view(5, N), big_P[11:].view(15, N)),
+    }
+    for name, (y, xo, Po) in cases.items():
+        xh, Ph, used, _ = sm.ieks_run_host(d["model"], method, prec, y, off, m0, P0, iters=3, x_out=xo, P_out=Po,
+                                           sensors_host=sens)
+        assert used == 3
+        assert torch.equal(xh, xd) and torch.equal(Ph, Pd), name
+    assert torch.all(big_x[:37] == 0) and torch.all(big_P[:11] == 0)
+
+
 def test_invalid_arguments_rejected_before_launch(sm):
     wl = synth.workload("ieks_T500")
     d = workload_to_dev(wl, pes.FP64)
