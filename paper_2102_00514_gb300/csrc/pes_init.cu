@@ -1011,9 +1011,10 @@ pes_status forward_layers(pes_init_net* n, int64_t R, cudaStream_t st)
     return PES_OK;
 }
 
+// A layer's weight-gradient partials on their own (the layer without a
+// backward convolution to fuse them into), into the layer's slot of n->wpart.
 template <int TAPS>
-pes_status layer_grad(pes_init_net* n, const bf16* dY, const bf16* X, int64_t R, int layer, float* grad,
-                      cudaStream_t st)
+pes_status layer_grad(pes_init_net* n, const bf16* dY, const bf16* X, int64_t R, int layer, cudaStream_t st)
 {
     CUtensorMap mX, mDY;
     if (!make_map(&mX, X, (uint64_t)R, halo_rows(TAPS)) || !make_map(&mDY, dY, (uint64_t)R, TM))
@@ -1047,7 +1048,7 @@ pes_status backward_layers(pes_init_net* n, int64_t R, float* grad, cudaStream_t
         cur = nxt;
         nxt = t;
     }
-    if ((s = layer_grad<5>(n, cur, n->act[0], R, 0, grad, st)) != PES_OK) return s;
+    if ((s = layer_grad<5>(n, cur, n->act[0], R, 0, st)) != PES_OK) return s;
     const int nblk = (int)std::min<int64_t>((R + TM - 1) / TM, n->num_sms);
     NET_CUDA(n, launch_pdl(wgrad_reduce_kernel, kRedBlocks, 256, 0, st, (const float*)n->wpart,
                            (size_t)kWgPart * n->num_sms, nblk, grad));
