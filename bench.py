@@ -969,9 +969,11 @@ def main():
         from paper_2102_00514_gb300 import learned_init as LI
         li = LI.run(n_train=8192, T_train=1000, n_heldout=256, steps=3000, batch_traj=128)
         # the start as the library uses it (network within ten times its
-        # training length, prior start beyond), paired over every held-out
-        # trajectory with non-converged runs counted at the cap
-        result["iters_saved"] = li["ieks"]["gated"]["iters_saved_capped"]
+        # training length, prior start beyond, and the prior start again where
+        # the network's does not converge), paired over every held-out
+        # trajectory with non-converged runs counted at the cap: the policy
+        # whose final error is no worse (the metric's "at equal final error")
+        result["iters_saved"] = li["ieks"]["gated_fallback"]["iters_saved_capped"]
         result["learned_init"] = li
 
     if rank == 0:
