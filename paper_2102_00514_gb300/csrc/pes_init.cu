@@ -135,7 +135,11 @@ PES_DEV void drain_wait(uint64_t* bar, uint32_t parity)
 // Programmatic dependent launch: every kernel here is launched so that it may
 // start while its predecessor in the stream is still finishing. A kernel
 // waits for the predecessor (and so, transitively, for everything before it)
-// before its first global-memory access, then lets its own successor launch.
+// before it touches data that the predecessor may write or read, then lets
+// its own successor launch. Since every kernel triggers only after its own
+// wait, whatever was written two or more launches earlier is final when a
+// kernel starts: the layers read their weights before the wait (every entry
+// point runs the features kernel between a parameter update and a layer).
 PES_DEV void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 PES_DEV void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
@@ -196,21 +200,29 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         mbar_init_fence();
     }
     if (warp == 1) tc::tmem_alloc(tslot, conv_tmem_cols(TAPS, WG));
+    // The weights and biases are written only by the Adam step or the
+    // publication of new parameters, at least two launches before any layer;
+    // the predecessor has passed its own wait before this launch could start,
+    // so they are final here and load before this launch's wait, overlapping
+    // the predecessor's tail. Activations load after it.
+    if (EPI != EPI_MASK && threadIdx.x >= 64 && threadIdx.x < 64 + C) sbias[threadIdx.x - 64] = p.bias[threadIdx.x - 64];
+    if (threadIdx.x == 0) {
+        tc::mbar_expect_tx(wbar, TAPS * kWTileBytes);
+        for (int j = 0; j < TAPS; ++j) tc::tma_load_2d(sW + j * kWTileBytes, &tmW, 0, (p.w_tile0 + j) * C, wbar);
+    }
     pdl_wait();
     pdl_trigger();
-    if (EPI != EPI_MASK && threadIdx.x >= 64 && threadIdx.x < 64 + C) sbias[threadIdx.x - 64] = p.bias[threadIdx.x - 64];
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tbase = *tslot;
 
     if (warp == 0) {
-        // ---- producer: weights once, then one halo tile (two, WG) per row tile
+        // ---- producer (the weights are already on their way): one halo tile
+        // (two, WG) per row tile
         if (lane == 0) {
             int armed[NS];
             for (int s = 0; s < NS; ++s) armed[s] = -1;
-            tc::mbar_expect_tx(wbar, TAPS * kWTileBytes);
-            for (int j = 0; j < TAPS; ++j) tc::tma_load_2d(sW + j * kWTileBytes, &tmW, 0, (p.w_tile0 + j) * C, wbar);
             int st = 0;
             uint32_t ph = 0;
             bool ok = true;
