@@ -24,7 +24,8 @@
 // applies bias and ReLU (or the ReLU mask of the backward pass), stages its
 // warp's 32 bf16 rows in shared memory and writes them with one TMA store. The
 // backward pass through a layer is the same GEMM with the weights transposed
-// and the taps reversed. The weight gradients, a reduction over rows, are a
+// and the taps reversed. The last convolution and the two head layers run as
+// one launch (tail_tc_kernel), their intermediate tiles kept in shared memory. The weight gradients, a reduction over rows, are a
 // GEMM on the tensor cores too (wgrad_tc_kernel), split over the CTAs and
 // summed in a fixed order.
 #include <cuda_runtime.h>
@@ -406,6 +407,273 @@ static_assert(conv_smem_bytes(5, true) <= 227 * 1024 && conv_smem_bytes(1, true)
 static_assert(halo_rows(5) * C * 2 <= stage_bytes(5) && stage_bytes(1) == TM * C * 2, "halo stages");
 // barriers, TMEM slot, abort flag and bias fit before the output staging
 static_assert((2 * NSTAGE + 6) * 8 + 16 + C * 4 <= kOutStageOffset, "control block");
+
+// ---- the last convolution and the head, fused -------------------------------------
+//
+// Layer 3 (5 taps, ReLU), layer 4 (64 -> 64, ReLU) and layer 5 (64 -> 5, FP32
+// output) in one launch. Per row tile the convolution's output stays in shared
+// memory as the A operand of layer 4's GEMM, and layer 4's as that of layer
+// 5's (N = 16, five outputs used); both are also stored, for the backward
+// pass. The MMA warp runs the three GEMMs of the CTA's tiles one tile apart
+// (for its j-th tile the convolution, then layer 4 of tile j - 1, then layer 5
+// of tile j - 2); epilogue warpgroup g takes tiles j = g (mod 2) through the
+// three epilogues in order, so the accumulators and output tiles are double
+// buffered by warpgroup.
+constexpr int kTailStages = 4;
+constexpr int kTailW = 7 * kWTileBytes;                 // layer 3's five taps, then W4, W5
+constexpr int kTailAct = TM * C * 2;                    // one 128-row bf16 tile
+constexpr int kHeadN = 16;                              // layer 5's MMA width
+constexpr uint32_t kIdescHead = tc::idesc_bf16_f32(TM, kHeadN);
+constexpr int kTailLayer = 3;                           // first fused layer
+
+struct TailParams {
+    int R, ntiles;
+    const float* bias;          // [3][64]: layers 3, 4, 5
+    const uint8_t* rowmask;
+    float* out_f32;             // [R][8]
+    int* status;
+};
+
+__global__ void __launch_bounds__(kConvThreads, 1)
+    tail_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW,
+                   const __grid_constant__ CUtensorMap tmS4, const __grid_constant__ CUtensorMap tmS5,
+                   const TailParams p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    uint8_t* sW = smem;
+    uint8_t* sA = sW + kTailW;
+    uint8_t* sS4 = sA + kTailStages * stage_bytes(5);
+    uint8_t* sS5 = sS4 + 2 * kTailAct;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sS5 + 2 * kTailAct);
+    uint64_t* empty = full + kTailStages;
+    uint64_t* wbar = empty + kTailStages;
+    uint64_t* a0f = wbar + 1;     // [2] each
+    uint64_t* a0e = a0f + 2;
+    uint64_t* s4f = a0e + 2;
+    uint64_t* a1f = s4f + 2;
+    uint64_t* a1e = a1f + 2;
+    uint64_t* s5f = a1e + 2;
+    uint64_t* a2f = s5f + 2;
+    uint64_t* a2e = a2f + 2;
+    uint64_t* done = a2e + 2;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+    float* sbias = reinterpret_cast<float*>(tslot + 4);   // 3 x 64
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nlocal = (int)blockIdx.x < p.ntiles ? (p.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kTailStages; ++i) {
+            mbar_init(full + i, 1);
+            mbar_init(empty + i, 1);
+        }
+        mbar_init(wbar, 1);
+        for (int g = 0; g < 2; ++g) {
+            mbar_init(a0f + g, 1);
+            mbar_init(a1f + g, 1);
+            mbar_init(a2f + g, 1);
+            mbar_init(a0e + g, kEpiThreads);
+            mbar_init(a1e + g, kEpiThreads);
+            mbar_init(a2e + g, kEpiThreads);
+            mbar_init(s4f + g, kEpiThreads);
+            mbar_init(s5f + g, kEpiThreads);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        mbar_init_fence();
+        // parameters: final before this launch (see pdl_wait)
+        tc::mbar_expect_tx(wbar, kTailW);
+        for (int j = 0; j < 7; ++j)
+            tc::tma_load_2d(sW + j * kWTileBytes, &tmW, 0, (wtile0_of(kTailLayer) + j) * C, wbar);
+    }
+    if (warp == 1) tc::tmem_alloc(tslot, 512);
+    if (threadIdx.x >= 64 && threadIdx.x < 64 + 3 * C) sbias[threadIdx.x - 64] = p.bias[threadIdx.x - 64];
+    pdl_wait();
+    pdl_trigger();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *tslot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int armed[kTailStages];
+            for (int i = 0; i < kTailStages; ++i) armed[i] = -1;
+            int st = 0;
+            uint32_t ph = 0;
+            for (int j = 0; j < nlocal; ++j) {
+                const int tile = blockIdx.x + j * gridDim.x;
+                if (!tc::wait_or_abort(empty + st, ph ^ 1, p.status, abort_flag)) break;
+                tc::mbar_expect_tx(full + st, halo_rows(5) * C * 2);
+                tc::tma_load_2d(sA + st * stage_bytes(5), &tmA, 0, tile * TM - 2, full + st);
+                armed[st] = (int)ph;
+                if (++st == kTailStages) {
+                    st = 0;
+                    ph ^= 1;
+                }
+            }
+            if (*abort_flag) {
+                drain_wait(wbar, 0);
+                for (int i = 0; i < kTailStages; ++i)
+                    if (armed[i] >= 0) drain_wait(full + i, (uint32_t)armed[i]);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            bool ok = tc::wait_or_abort(wbar, 0, p.status, abort_flag);
+            int st = 0;
+            uint32_t ph = 0, e0 = 0, e1 = 0, e2 = 0, f4 = 0, f5 = 0;   // parity bits per buffer
+            for (int j = 0; ok && j < nlocal + 2; ++j) {
+                if (j < nlocal) {   // layer 3 of tile j
+                    const int g = j & 1;
+                    if (!(ok = tc::wait_or_abort(a0e + g, ((e0 >> g) & 1u) ^ 1u, p.status, abort_flag))) break;
+                    e0 ^= 1u << g;
+                    if (!(ok = tc::wait_or_abort(full + st, ph, p.status, abort_flag))) break;
+                    tc::fence_after_sync();
+                    const uint8_t* sa = sA + st * stage_bytes(5);
+#pragma unroll
+                    for (int t = 0; t < 5; ++t) {
+                        const uint64_t ad = tc::smem_desc_sw128(sa + t * C * 2);
+                        const uint64_t bd = tc::smem_desc_sw128(sW + t * kWTileBytes);
+#pragma unroll
+                        for (int k = 0; k < C / 16; ++k)
+                            tc::mma_bf16(tbase + (uint32_t)(g * C), ad + 2 * k, bd + 2 * k, kIdesc, (t | k) != 0);
+                    }
+                    tc::mma_commit(empty + st);
+                    if (++st == kTailStages) {
+                        st = 0;
+                        ph ^= 1;
+                    }
+                    tc::mma_commit(a0f + g);
+                }
+                if (j >= 1 && j - 1 < nlocal) {   // layer 4 of tile j - 1
+                    const int g = (j - 1) & 1;
+                    if (!(ok = tc::wait_or_abort(s4f + g, (f4 >> g) & 1u, p.status, abort_flag))) break;
+                    f4 ^= 1u << g;
+                    if (!(ok = tc::wait_or_abort(a1e + g, ((e1 >> g) & 1u) ^ 1u, p.status, abort_flag))) break;
+                    e1 ^= 1u << g;
+                    tc::fence_after_sync();
+                    const uint64_t ad = tc::smem_desc_sw128(sS4 + g * kTailAct);
+                    const uint64_t bd = tc::smem_desc_sw128(sW + 5 * kWTileBytes);
+#pragma unroll
+                    for (int k = 0; k < C / 16; ++k)
+                        tc::mma_bf16(tbase + (uint32_t)(2 * C + g * C), ad + 2 * k, bd + 2 * k, kIdesc, k != 0);
+                    tc::mma_commit(a1f + g);
+                }
+                if (j >= 2) {   // layer 5 of tile j - 2
+                    const int g = (j - 2) & 1;
+                    if (!(ok = tc::wait_or_abort(s5f + g, (f5 >> g) & 1u, p.status, abort_flag))) break;
+                    f5 ^= 1u << g;
+                    if (!(ok = tc::wait_or_abort(a2e + g, ((e2 >> g) & 1u) ^ 1u, p.status, abort_flag))) break;
+                    e2 ^= 1u << g;
+                    tc::fence_after_sync();
+                    const uint64_t ad = tc::smem_desc_sw128(sS5 + g * kTailAct);
+                    const uint64_t bd = tc::smem_desc_sw128(sW + 6 * kWTileBytes);
+#pragma unroll
+                    for (int k = 0; k < C / 16; ++k)
+                        tc::mma_bf16(tbase + (uint32_t)(4 * C + g * kHeadN), ad + 2 * k, bd + 2 * k, kIdescHead, k != 0);
+                    tc::mma_commit(a2f + g);
+                }
+            }
+            tc::mma_commit(done);
+            drain_wait(done, 0);
+        }
+    } else {
+        const int g = (warp - 2) >> 2;
+        const int q = warp & 3;
+        const int rin = q * 32 + lane;
+        uint8_t* s4 = sS4 + g * kTailAct + q * kOutWarpBytes;
+        uint8_t* s5 = sS5 + g * kTailAct + q * kOutWarpBytes;
+        const uint32_t trow = (uint32_t)(q * 32) << 16;
+        uint32_t w0 = 0, w1 = 0, w2 = 0;
+        // bias + ReLU of one 64-column row, packed into this warp's swizzled
+        // 32-row slice of an output tile (gap and padding rows as zeros)
+        auto emit = [&](uint8_t* slice, const float* v, const float* b, bool live) {
+#pragma unroll
+            for (int i = 0; i < C / 8; ++i) {
+                uint4 u = make_uint4(0, 0, 0, 0);
+                if (live)
+                    u = make_uint4(pack_bf16x2(fmaxf(v[8 * i] + b[8 * i], 0.f), fmaxf(v[8 * i + 1] + b[8 * i + 1], 0.f)),
+                                   pack_bf16x2(fmaxf(v[8 * i + 2] + b[8 * i + 2], 0.f), fmaxf(v[8 * i + 3] + b[8 * i + 3], 0.f)),
+                                   pack_bf16x2(fmaxf(v[8 * i + 4] + b[8 * i + 4], 0.f), fmaxf(v[8 * i + 5] + b[8 * i + 5], 0.f)),
+                                   pack_bf16x2(fmaxf(v[8 * i + 6] + b[8 * i + 6], 0.f), fmaxf(v[8 * i + 7] + b[8 * i + 7], 0.f)));
+                *reinterpret_cast<uint4*>(slice + lane * 128 + ((i ^ (lane & 7)) << 4)) = u;
+            }
+        };
+        for (int j = g; j < nlocal; j += 2) {
+            const int tile = blockIdx.x + j * gridDim.x;
+            const int r = tile * TM + rin;
+            const bool live = r < p.R && p.rowmask[r];
+            float v[C];
+            // layer 3: the tile's output into s4 (and to global)
+            bool ok = tc::wait_or_abort(a0f + g, w0, p.status, abort_flag);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            w0 ^= 1u;
+            tc::fence_after_sync();
+            tc::tmem_ld64(tbase + trow + (uint32_t)(g * C), v);
+            tc::fence_before_sync();
+            tc::mbar_arrive(a0e + g);
+            if (lane == 0) tc::bulk_wait_read<0>();   // the slices' previous stores have read them
+            __syncwarp();
+            emit(s4, v, sbias, live);
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) {
+                tc::tma_store_2d(&tmS4, 0, tile * TM + q * 32, s4);
+                tc::bulk_commit();
+            }
+            tc::mbar_arrive(s4f + g);
+            // layer 4: into s5 (and to global)
+            ok = tc::wait_or_abort(a1f + g, w1, p.status, abort_flag);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            w1 ^= 1u;
+            tc::fence_after_sync();
+            tc::tmem_ld64(tbase + trow + (uint32_t)(2 * C + g * C), v);
+            tc::fence_before_sync();
+            tc::mbar_arrive(a1e + g);
+            emit(s5, v, sbias + C, live);
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) {
+                tc::tma_store_2d(&tmS5, 0, tile * TM + q * 32, s5);
+                tc::bulk_commit();
+            }
+            tc::mbar_arrive(s5f + g);
+            // layer 5: the FP32 output of the state rows
+            ok = tc::wait_or_abort(a2f + g, w2, p.status, abort_flag);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            w2 ^= 1u;
+            tc::fence_after_sync();
+            float o[16];
+            tc::tmem_ld16(tbase + trow + (uint32_t)(4 * C + g * kHeadN), o);
+            tc::fence_before_sync();
+            tc::mbar_arrive(a2e + g);
+            if (live) {
+                const float* b = sbias + 2 * C;
+                float4* dst = reinterpret_cast<float4*>(p.out_f32 + (size_t)r * kOutCols);
+                dst[0] = make_float4(o[0] + b[0], o[1] + b[1], o[2] + b[2], o[3] + b[3]);
+                dst[1] = make_float4(o[4] + b[4], o[5] + b[5], o[6] + b[6], o[7] + b[7]);
+            }
+        }
+        if (lane == 0) tc::bulk_wait_all();
+    }
+
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 1) tc::tmem_dealloc(tbase, 512);
+}
+
+constexpr size_t tail_smem_bytes()
+{
+    return 1024 + (size_t)kTailW + (size_t)kTailStages * stage_bytes(5) + 4 * (size_t)kTailAct + 1024;
+}
+static_assert(tail_smem_bytes() <= 227 * 1024, "shared memory per CTA");
+// barriers (4 + 4 + 1 + 16 + 1) x 8 B, TMEM slot, abort flag and 3 x 64 biases fit the last KB
+static_assert((2 * kTailStages + 18) * 8 + 16 + 3 * C * 4 <= 1024, "tail control block");
+static_assert(kConvThreads - 64 >= 3 * C, "the tail's bias loaders");
+static_assert(kWTile0[kTailLayer] + 5 == kWTile0[4] && kWTile0[4] + 1 == kWTile0[5], "the tail's weight tiles are consecutive");
 
 // ---- rows, features, loss, gradients, optimiser ----------------------------------
 
@@ -1014,12 +1282,32 @@ pes_status prepare_rows(pes_init_net* n, const T* y, const int64_t* off, int32_t
     return PES_OK;
 }
 
+// Layers 3-5 in one launch (tail_tc_kernel): act[3] -> act[4], act[5], out.
+cudaError_t launch_tail(pes_init_net* n, int64_t R, cudaStream_t st)
+{
+    CUtensorMap mA, mS4, mS5;
+    if (!make_map(&mA, n->act[3], (uint64_t)R, halo_rows(5)) || !make_map(&mS4, n->act[4], (uint64_t)R, 32) ||
+        !make_map(&mS5, n->act[5], (uint64_t)R, 32))
+        return cudaErrorInvalidValue;
+    TailParams p;
+    p.R = (int)R;
+    p.ntiles = (int)((R + TM - 1) / TM);
+    p.bias = n->bias + kTailLayer * C;
+    p.rowmask = n->mask;
+    p.out_f32 = n->out;
+    p.status = n->status;
+    const size_t smem = tail_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(tail_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)std::min<int64_t>(p.ntiles, n->num_sms);
+    return launch_pdl(tail_tc_kernel, grid, kConvThreads, smem, st, mA, n->mapWf, mS4, mS5, p);
+}
+
 pes_status forward_layers(pes_init_net* n, int64_t R, cudaStream_t st)
 {
-    for (int l = 0; l < 4; ++l)
+    for (int l = 0; l < kTailLayer; ++l)
         NET_CUDA(n, (launch_conv<5, EPI_RELU>(n, n->act[l], R, false, l, n->act[l + 1], nullptr, nullptr, st)));
-    NET_CUDA(n, (launch_conv<1, EPI_RELU>(n, n->act[4], R, false, 4, n->act[5], nullptr, nullptr, st)));
-    NET_CUDA(n, (launch_conv<1, EPI_F32>(n, n->act[5], R, false, 5, nullptr, n->out, nullptr, st)));
+    NET_CUDA(n, launch_tail(n, R, st));
     return PES_OK;
 }
 
