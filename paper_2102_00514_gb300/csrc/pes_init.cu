@@ -428,6 +428,7 @@ constexpr int kTailLayer = 3;                           // first fused layer
 
 struct TailParams {
     int R, ntiles;
+    int store_acts;             // store layers 3 and 4's outputs (the backward pass reads them)
     const float* bias;          // [3][64]: layers 3, 4, 5
     const uint8_t* rowmask;
     float* out_f32;             // [R][8]
@@ -619,7 +620,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
             emit(s4, v, sbias, live);
             fence_proxy_async();
             __syncwarp();
-            if (lane == 0) {
+            if (lane == 0 && p.store_acts) {
                 tc::tma_store_2d(&tmS4, 0, tile * TM + q * 32, s4);
                 tc::bulk_commit();
             }
@@ -635,7 +636,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
             emit(s5, v, sbias + C, live);
             fence_proxy_async();
             __syncwarp();
-            if (lane == 0) {
+            if (lane == 0 && p.store_acts) {
                 tc::tma_store_2d(&tmS5, 0, tile * TM + q * 32, s5);
                 tc::bulk_commit();
             }
@@ -1282,8 +1283,9 @@ pes_status prepare_rows(pes_init_net* n, const T* y, const int64_t* off, int32_t
     return PES_OK;
 }
 
-// Layers 3-5 in one launch (tail_tc_kernel): act[3] -> act[4], act[5], out.
-cudaError_t launch_tail(pes_init_net* n, int64_t R, cudaStream_t st)
+// Layers 3-5 in one launch (tail_tc_kernel): act[3] -> out, and act[4], act[5]
+// when a backward pass follows.
+cudaError_t launch_tail(pes_init_net* n, int64_t R, bool store_acts, cudaStream_t st)
 {
     CUtensorMap mA, mS4, mS5;
     if (!make_map(&mA, n->act[3], (uint64_t)R, halo_rows(5)) || !make_map(&mS4, n->act[4], (uint64_t)R, 32) ||
@@ -1292,6 +1294,7 @@ cudaError_t launch_tail(pes_init_net* n, int64_t R, cudaStream_t st)
     TailParams p;
     p.R = (int)R;
     p.ntiles = (int)((R + TM - 1) / TM);
+    p.store_acts = store_acts ? 1 : 0;
     p.bias = n->bias + kTailLayer * C;
     p.rowmask = n->mask;
     p.out_f32 = n->out;
@@ -1303,11 +1306,13 @@ cudaError_t launch_tail(pes_init_net* n, int64_t R, cudaStream_t st)
     return launch_pdl(tail_tc_kernel, grid, kConvThreads, smem, st, mA, n->mapWf, mS4, mS5, p);
 }
 
-pes_status forward_layers(pes_init_net* n, int64_t R, cudaStream_t st)
+// The forward pass; `training` keeps every layer's activations for the
+// backward pass (inference does not store the last two).
+pes_status forward_layers(pes_init_net* n, int64_t R, bool training, cudaStream_t st)
 {
     for (int l = 0; l < kTailLayer; ++l)
         NET_CUDA(n, (launch_conv<5, EPI_RELU>(n, n->act[l], R, false, l, n->act[l + 1], nullptr, nullptr, st)));
-    NET_CUDA(n, launch_tail(n, R, st));
+    NET_CUDA(n, launch_tail(n, R, training, st));
     return PES_OK;
 }
 
@@ -1374,7 +1379,7 @@ pes_status loss_grad_t(pes_init_net* n, const T* y, const int64_t* off, int32_t 
     int64_t R = 0;
     pes_status s = prepare_rows<T>(n, y, off, B, N, st, &R);
     if (s != PES_OK) return s;
-    if ((s = forward_layers(n, R, st)) != PES_OK) return s;
+    if ((s = forward_layers(n, R, true, st)) != PES_OK) return s;
     const float scale = (float)(2.0 / (5.0 * (double)N));
     const int lblocks = (int)std::min<int64_t>((R + 255) / 256, kLossBlocks);
     NET_CUDA(n, launch_pdl(loss_kernel<T>, lblocks, 256, 0, st, (const float*)n->out, xt, off, B, N, R, n->norm, scale,
@@ -1514,7 +1519,7 @@ pes_status pes_init_forward(pes_init_net* n, pes_precision prec, const void* y, 
     s = prec == PES_FP64 ? prepare_rows<double>(n, (const double*)y, offsets, B, N, st, &R)
                          : prepare_rows<float>(n, (const float*)y, offsets, B, N, st, &R);
     if (s != PES_OK) return s;
-    if ((s = forward_layers(n, R, st)) != PES_OK) return s;
+    if ((s = forward_layers(n, R, false, st)) != PES_OK) return s;
     const int blocks = (int)std::min<int64_t>((N + 255) / 256, (int64_t)n->num_sms * 16);
     if (prec == PES_FP64)
         NET_CUDA(n, launch_pdl(denorm_kernel<double>, blocks, 256, 0, st, (const float*)n->out, offsets, B, N, n->norm,
