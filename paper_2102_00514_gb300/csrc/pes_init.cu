@@ -110,6 +110,7 @@ struct ConvParams {
     float* out_f32;             // [R][8] (EPI_F32)
     const bf16* relu_src;       // [R][64] (EPI_MASK): the layer input whose ReLU is differentiated
     float* part;                // fused weight gradient: [gridDim.x][kWgPart] partials
+    int co_real;                // output channels that exist (the partial rows written)
     int* status;
 };
 
@@ -383,8 +384,11 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                 for (int gg = g; gg < NG; gg += 2) {
                     float v[C];
                     tc::tmem_ld64(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(2 * C + gg * C), v);
+                    // rows of the all-ones block are all the bias gradient: row 0 is kept
+                    if (gg < NG - 1 || rin >= C || rin == 0)
 #pragma unroll
-                    for (int o = 0; o < C; ++o) outp[(gg * C + o) * TM + rin] = v[o];
+                        for (int o = 0; o < C; ++o)
+                            if (o < p.co_real) outp[(gg * C + o) * TM + rin] = v[o];
                 }
             }
         }
@@ -857,6 +861,7 @@ __global__ void __launch_bounds__(256) loss_kernel(const float* o, const T* xt, 
 struct WgradParams {
     int ntiles;     // ceil(R / TM)
     float* part;    // [gridDim.x][kWgPart]
+    int co_real;    // output channels that exist (the partial rows written)
     int* status;
 };
 
@@ -968,8 +973,11 @@ __global__ void __launch_bounds__(kWgThreads, 1)
             for (int g = 0; g < NG; ++g) {
                 float v[C];
                 tc::tmem_ld64(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * C), v);
+                // rows of the all-ones block are all the bias gradient: row 0 is kept
+                if (g < NG - 1 || m >= C || m == 0)
 #pragma unroll
-                for (int o = 0; o < C; ++o) out[(g * C + o) * TM + m] = v[o];
+                    for (int o = 0; o < C; ++o)
+                        if (o < p.co_real) out[(g * C + o) * TM + m] = v[o];
             }
         }
     }
@@ -988,9 +996,43 @@ static_assert(wgrad_smem_bytes(5) <= 227 * 1024 && wgrad_smem_bytes(1) <= 227 * 
 // the last MMA of a tile reads rows up to TAPS - 1 + TM - 1 of the halo tile
 static_assert(stage_bytes(5) % 1024 == 0 && kDyBytes % 1024 == 0 && kOnesBytes % 1024 == 0, "swizzle atoms");
 
+// One Adam step of packed parameter i with gradient g, and the new value
+// published where the GEMMs read it: a weight W_l[o][i][j] into forward tile
+// (l, j) at [o][i] and backward tile (l, TAPS - 1 - j) at [i][o] (bf16), a bias
+// into the FP32 bias row. Entries of output channels that do not exist stay
+// the zeros that publish_kernel wrote.
+struct AdamStep {
+    float *p, *m, *v;
+    bf16 *Wf, *Wb;
+    float* bias;
+    float lr, b1, b2, eps, c1, c2;
+};
+
+PES_DEV void adam_apply(const AdamStep& a, int i, float g)
+{
+    const float mi = a.b1 * a.m[i] + (1.f - a.b1) * g;
+    const float vi = a.b2 * a.v[i] + (1.f - a.b2) * g * g;
+    a.m[i] = mi;
+    a.v[i] = vi;
+    const float pi = a.p[i] - a.lr * (mi * a.c1) / (sqrtf(vi * a.c2) + a.eps);
+    a.p[i] = pi;
+    int l = 0;
+    while (l + 1 < NLAYER && poff_of(l + 1) <= i) ++l;
+    const int taps = taps_of(l), nw = coreal_of(l) * C * taps, loc = i - poff_of(l);
+    if (loc < nw) {
+        const int o = loc / (C * taps), ci = (loc / taps) % C, j = loc % taps;
+        const bf16 w = __float2bfloat16_rn(pi);
+        a.Wf[(size_t)(wtile0_of(l) + j) * C * C + o * C + ci] = w;
+        a.Wb[(size_t)(wtile0_of(l) + taps - 1 - j) * C * C + ci * C + o] = w;
+    } else {
+        a.bias[l * C + (loc - nw)] = pi;
+    }
+}
+
 // Sum the CTAs' partials into the packed gradients of all six layers, one
 // launch after the backward pass (layer l's partials at part + l x
-// layer_stride). Block b of layer l covers partial entries 128 b .. 128 b + 127;
+// layer_stride), and with apply_adam take the Adam step on each parameter as
+// its gradient is complete. Block b of layer l covers partial entries 128 b .. 128 b + 127;
 // warp w sums the CTAs w, w + 8, ... in order and the eight sums are added in
 // warp order, so the result does not depend on scheduling. Entry (g, o, m):
 // m < 64 is tap 2g, input channel m; m >= 64 tap 2g + 1, channel m - 64; in the
@@ -1001,7 +1043,7 @@ constexpr int kRedBlocks1 = wg_groups(1) * C * TM / 128;
 constexpr int kRedBlocks = 4 * kRedBlocks5 + 2 * kRedBlocks1;
 
 __global__ void __launch_bounds__(256) wgrad_reduce_kernel(const float* part, size_t layer_stride, int nblk,
-                                                           float* grad)
+                                                           float* grad, const AdamStep adam, int apply_adam)
 {
     pdl_wait();
     pdl_trigger();
@@ -1015,14 +1057,18 @@ __global__ void __launch_bounds__(256) wgrad_reduce_kernel(const float* part, si
         blk -= (l - 4) * kRedBlocks1;
     }
     const int taps = taps_of(l), ng = (taps + 1) / 2, co_real = coreal_of(l);
+    // block blk holds the partial row (group blk / 64, output channel blk % 64)
+    if ((blk % C) >= co_real) return;   // absent channel: never written, not read
     const float* pl = part + (size_t)l * layer_stride;
     float* gl = grad + poff_of(l);
     __shared__ float4 red[8][32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s4 = blk * 128 + lane * 4;
+    // in the last group only entry 0 of the all-ones half is written (and used)
+    const bool read = !(blk / C == ng - 1 && lane > 0 && lane < C / 4);
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 4
-    for (int b = w; b < nblk; b += 8) {
+    for (int b = w; read && b < nblk; b += 8) {
         const float4 v = __ldg(reinterpret_cast<const float4*>(pl + (size_t)b * kWgPart + s4));
         acc.x += v.x;
         acc.y += v.y;
@@ -1037,45 +1083,18 @@ __global__ void __launch_bounds__(256) wgrad_reduce_kernel(const float* part, si
         for (int v = 0; v < 8; ++v) s += reinterpret_cast<const float*>(red[v])[threadIdx.x];
         const int e = blk * 128 + threadIdx.x;
         const int g = e / (C * TM), o = (e / TM) % C, m = e % TM, half = m / C, ci = m % C;
+        int dst = -1;
         if (g < ng && o < co_real) {
             if (g == ng - 1 && half == 0) {
-                if (ci == 0) gl[co_real * C * taps + o] = s;
+                if (ci == 0) dst = co_real * C * taps + o;
             } else {
                 const int j = g == ng - 1 ? taps - 1 : 2 * g + half;
-                gl[(o * C + ci) * taps + j] = s;
+                dst = (o * C + ci) * taps + j;
             }
         }
-    }
-}
-
-// One Adam step on every parameter, and the new value published where the
-// GEMMs read it: a weight W_l[o][i][j] into forward tile (l, j) at [o][i] and
-// backward tile (l, TAPS - 1 - j) at [i][o] (bf16), a bias into the FP32 bias
-// row. Entries of output channels that do not exist stay the zeros that
-// publish_kernel wrote.
-__global__ void adam_kernel(float* p, float* m, float* v, const float* g, int n, float lr, float b1, float b2,
-                            float eps, float c1, float c2, bf16* Wf, bf16* Wb, float* bias)
-{
-    pdl_wait();
-    pdl_trigger();
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const float gi = g[i];
-        const float mi = b1 * m[i] + (1.f - b1) * gi;
-        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-        m[i] = mi;
-        v[i] = vi;
-        const float pi = p[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
-        p[i] = pi;
-        int l = 0;
-        while (l + 1 < NLAYER && poff_of(l + 1) <= i) ++l;
-        const int taps = taps_of(l), nw = coreal_of(l) * C * taps, loc = i - poff_of(l);
-        if (loc < nw) {
-            const int o = loc / (C * taps), ci = (loc / taps) % C, j = loc % taps;
-            const bf16 w = __float2bfloat16_rn(pi);
-            Wf[(size_t)(wtile0_of(l) + j) * C * C + o * C + ci] = w;
-            Wb[(size_t)(wtile0_of(l) + taps - 1 - j) * C * C + ci * C + o] = w;
-        } else {
-            bias[l * C + (loc - nw)] = pi;
+        if (dst >= 0) {
+            gl[dst] = s;
+            if (apply_adam) adam_apply(adam, poff_of(l) + dst, s);   // each parameter once
         }
     }
 }
@@ -1248,6 +1267,7 @@ cudaError_t launch_conv(pes_init_net* n, const bf16* in, int64_t R, bool backwar
     p.out_f32 = out_f32;
     p.relu_src = relu_src;
     p.part = WG ? n->wpart + (size_t)layer * kWgPart * n->num_sms : nullptr;
+    p.co_real = layer == NLAYER - 1 ? 5 : C;
     p.status = n->status;
     const size_t smem = conv_smem_bytes(TAPS, WG);
     cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<TAPS, EPI, WG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1327,6 +1347,7 @@ pes_status layer_grad(pes_init_net* n, const bf16* dY, const bf16* X, int64_t R,
     WgradParams p;
     p.ntiles = (int)((R + TM - 1) / TM);
     p.part = n->wpart + (size_t)layer * kWgPart * n->num_sms;
+    p.co_real = layer == NLAYER - 1 ? 5 : C;
     p.status = n->status;
     const int nblk = std::min(p.ntiles, n->num_sms);
     const size_t smem = wgrad_smem_bytes(TAPS);
@@ -1340,7 +1361,7 @@ pes_status layer_grad(pes_init_net* n, const bf16* dY, const bf16* X, int64_t R,
 // the same gradient tiles, and the layer input that gives the ReLU mask is the
 // gradient's other operand); the first layer has no backward convolution, so
 // its weight gradient runs alone. One launch then sums all partials.
-pes_status backward_layers(pes_init_net* n, int64_t R, float* grad, cudaStream_t st)
+pes_status backward_layers(pes_init_net* n, int64_t R, float* grad, const AdamStep* adam, cudaStream_t st)
 {
     pes_status s;
     NET_CUDA(n, (launch_conv<1, EPI_MASK, true>(n, n->dO, R, true, 5, n->dA, nullptr, n->act[5], st)));
@@ -1355,8 +1376,9 @@ pes_status backward_layers(pes_init_net* n, int64_t R, float* grad, cudaStream_t
     }
     if ((s = layer_grad<5>(n, cur, n->act[0], R, 0, st)) != PES_OK) return s;
     const int nblk = (int)std::min<int64_t>((R + TM - 1) / TM, n->num_sms);
+    const AdamStep none{};
     NET_CUDA(n, launch_pdl(wgrad_reduce_kernel, kRedBlocks, 256, 0, st, (const float*)n->wpart,
-                           (size_t)kWgPart * n->num_sms, nblk, grad));
+                           (size_t)kWgPart * n->num_sms, nblk, grad, adam ? *adam : none, adam ? 1 : 0));
     return PES_OK;
 }
 
@@ -1374,7 +1396,7 @@ pes_status read_status(pes_init_net* n, cudaStream_t st)
 
 template <typename T>
 pes_status loss_grad_t(pes_init_net* n, const T* y, const int64_t* off, int32_t B, int64_t N, const T* xt,
-                       float* grad, double* loss, cudaStream_t st)
+                       float* grad, double* loss, const AdamStep* adam, cudaStream_t st)
 {
     int64_t R = 0;
     pes_status s = prepare_rows<T>(n, y, off, B, N, st, &R);
@@ -1384,7 +1406,7 @@ pes_status loss_grad_t(pes_init_net* n, const T* y, const int64_t* off, int32_t 
     const int lblocks = (int)std::min<int64_t>((R + 255) / 256, kLossBlocks);
     NET_CUDA(n, launch_pdl(loss_kernel<T>, lblocks, 256, 0, st, (const float*)n->out, xt, off, B, N, R, n->norm, scale,
                            1.0 / (5.0 * (double)N), n->dO, n->lpart, n->ticket, n->loss_dev));
-    if ((s = backward_layers(n, R, grad, st)) != PES_OK) return s;
+    if ((s = backward_layers(n, R, grad, adam, st)) != PES_OK) return s;
     if (loss) {
         NET_CUDA(n, cudaMemcpyAsync(loss, n->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
         return read_status(n, st);
@@ -1538,24 +1560,40 @@ pes_status pes_init_loss_grad(pes_init_net* n, pes_precision prec, const void* y
     if (!x_target || !grad) return net_fail(n, PES_ERR_INVALID_ARG, "NULL x_target or grad");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     return prec == PES_FP64
-               ? loss_grad_t<double>(n, (const double*)y, offsets, B, N, (const double*)x_target, grad, loss, st)
-               : loss_grad_t<float>(n, (const float*)y, offsets, B, N, (const float*)x_target, grad, loss, st);
+               ? loss_grad_t<double>(n, (const double*)y, offsets, B, N, (const double*)x_target, grad, loss, nullptr, st)
+               : loss_grad_t<float>(n, (const float*)y, offsets, B, N, (const float*)x_target, grad, loss, nullptr, st);
 }
 
 pes_status pes_init_train_step(pes_init_net* n, pes_precision prec, const void* y, const int64_t* offsets,
                                int32_t B, int64_t N, const void* x_target, float lr, double* loss, void* stream)
 {
-    if (n && !(lr > 0.f)) return net_fail(n, PES_ERR_INVALID_ARG, "lr must be positive");
-    pes_status s = pes_init_loss_grad(n, prec, y, offsets, B, N, x_target, n ? n->grad : nullptr, loss, stream);
+    pes_status s = check_sizes(n, prec, y, offsets, B, N);
     if (s != PES_OK) return s;
+    if (!(lr > 0.f)) return net_fail(n, PES_ERR_INVALID_ARG, "lr must be positive");
+    if (!x_target) return net_fail(n, PES_ERR_INVALID_ARG, "NULL x_target");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    n->adam_t += 1;
+    // the Adam step runs in the gradient reduction, each parameter as soon as
+    // its gradient is summed
     const double b1 = 0.9, b2 = 0.999;
-    const float c1 = (float)(1.0 / (1.0 - std::pow(b1, n->adam_t)));
-    const float c2 = (float)(1.0 / (1.0 - std::pow(b2, n->adam_t)));
-    NET_CUDA(n, launch_pdl(adam_kernel, (PES_INIT_NPARAMS + 255) / 256, 256, 0, st, n->params, n->m, n->v,
-                           (const float*)n->grad, (int)PES_INIT_NPARAMS, lr, (float)b1, (float)b2, 1e-8f, c1, c2, n->Wf,
-                           n->Wb, n->bias));
+    const int t = n->adam_t + 1;
+    AdamStep a;
+    a.p = n->params;
+    a.m = n->m;
+    a.v = n->v;
+    a.Wf = n->Wf;
+    a.Wb = n->Wb;
+    a.bias = n->bias;
+    a.lr = lr;
+    a.b1 = (float)b1;
+    a.b2 = (float)b2;
+    a.eps = 1e-8f;
+    a.c1 = (float)(1.0 / (1.0 - std::pow(b1, t)));
+    a.c2 = (float)(1.0 / (1.0 - std::pow(b2, t)));
+    s = prec == PES_FP64
+            ? loss_grad_t<double>(n, (const double*)y, offsets, B, N, (const double*)x_target, n->grad, loss, &a, st)
+            : loss_grad_t<float>(n, (const float*)y, offsets, B, N, (const float*)x_target, n->grad, loss, &a, st);
+    if (s != PES_OK) return s;
+    n->adam_t = t;
     return PES_OK;
 }
 
