@@ -197,7 +197,8 @@ def rerun_from_prior(wl: dict, idx: np.ndarray, method: int, tol: float, max_ite
 
 
 def evaluate(net: pes.InitNet, wl: dict, method: int = pes.IEKS, tol: float = TOL_EVAL,
-             max_iters: int = MAX_ITERS, t_valid: int | None = None, fallback: bool = False) -> EvalResult:
+             max_iters: int = MAX_ITERS, t_valid: int | None = None, fallback: bool = False,
+             judge: bool = False) -> EvalResult:
     """Iterations to `tol` and converged results from the prior start and from
     the network's start (gated by trajectory length when `t_valid` is given),
     every trajectory of `wl` in one FP64 batch each. With `fallback`, the
@@ -205,7 +206,12 @@ def evaluate(net: pes.InitNet, wl: dict, method: int = pes.IEKS, tol: float = TO
     beyond `t_valid`) does not bring to `tol` within `max_iters` are iterated
     again from the prior start in a batch of their own, and that run's result
     replaces theirs; its iterations are added to what the learned policy
-    spent."""
+    spent. With `judge`, both starts' converged solutions are kept side by side
+    and, per trajectory, the one whose filter log-likelihood under its own
+    final linearisation (pes_filter_loglik) is higher is the result; the
+    policy then spends both runs' iterations (the prior start's run is the
+    judge), and `fallback` marks the trajectories where the prior start's
+    solution was kept."""
     off = wl["offsets"]
     B = len(off) - 1
     N = int(off[-1])
@@ -215,18 +221,32 @@ def evaluate(net: pes.InitNet, wl: dict, method: int = pes.IEKS, tol: float = TO
     o = _dev(off, torch.int64)
     m0, P0 = _dev(wl["m0"], torch.float64), _dev(wl["P0"], torch.float64)
     t0 = time.perf_counter()
-    xa, _, _, _ = sm.ieks_run(model, method, pes.FP64, y, o, m0, P0, iters=max_iters, tol=tol,
-                              allow_not_converged=True)
+    xa, Pa, _, _ = sm.ieks_run(model, method, pes.FP64, y, o, m0, P0, iters=max_iters, tol=tol,
+                               allow_not_converged=True)
     ia = sm.traj_iterations(B)
     x0 = net.forward(pes.FP64, y, o)
     if t_valid is not None:
         x0 = gated_start(x0, wl, t_valid)
-    xb, _, _, _ = sm.ieks_run(model, method, pes.FP64, y, o, m0, P0, x_init=x0, iters=max_iters, tol=tol,
-                              allow_not_converged=True)
+    xb, Pb, _, _ = sm.ieks_run(model, method, pes.FP64, y, o, m0, P0, x_init=x0, iters=max_iters, tol=tol,
+                               allow_not_converged=True)
     ib = sm.traj_iterations(B)
+    lla = llb = None
+    if judge:
+        def loglik(x, P):
+            lin = sm.linearize(model, method, pes.FP64, x, P, y, o)
+            _, _, ll = sm.filter_loglik(pes.FP64, lin, lin["y_used"], m0, P0, o)
+            return ll.cpu().numpy()
+        lla, llb = loglik(xa, Pa), loglik(xb, Pb)
     xa, xb = xa.cpu().numpy(), xb.cpu().numpy()
     sm.close()
     fb = spent = None
+    if judge:
+        spent = (np.where(ib > 0, ib, max_iters) + np.where(ia > 0, ia, max_iters)).astype(np.int64)
+        fb = llb < lla
+        for b in np.flatnonzero(fb):
+            xb[:, off[b]:off[b + 1]] = xa[:, off[b]:off[b + 1]]
+        ib = np.where(fb, ia, ib)
+        fallback = False
     if fallback:
         spent = np.where(ib > 0, ib, max_iters).astype(np.int64)
         # only where the network's start was used (beyond t_valid the start
@@ -345,6 +365,8 @@ def run(n_train: int = 100_000, T_train: int = 1000, n_heldout: int = 1024, held
         # and with the fallback: trajectories the start does not bring to
         # tolerance are iterated again from the prior start
         out[name]["gated_fallback"] = summary(evaluate(net, ev, method=m, t_valid=t_valid, fallback=True))
+        # and judged by the converged solutions' log-likelihoods (both runs paid)
+        out[name]["gated_judged"] = summary(evaluate(net, ev, method=m, t_valid=t_valid, judge=True))
         T = np.diff(ev["offsets"]) - 1
         inside = T <= t_valid
         if inside.any():
