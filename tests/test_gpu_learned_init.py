@@ -167,7 +167,9 @@ def test_trained_initialiser_saves_iterations():
     position error against the truth no worse on 95 % of the trajectories and
     no worse on average. The network's start alone saves more iterations but
     ends, on about one trajectory in twenty, at another fixed point of the
-    iteration, worse about as often as better."""
+    iteration, worse about as often as better; keeping, per trajectory, the
+    solution of the two starts with the higher filter log-likelihood is no
+    worse on 98 % and on average (at the cost of both runs)."""
     from paper_2102_00514_gb300 import learned_init as L
     wl = synth.workload("train2048_T1000")
     x, conv = L.converged_targets(wl)
@@ -183,6 +185,8 @@ def test_trained_initialiser_saves_iterations():
     r = L.evaluate(n, ev, fallback=True)
     s = L.summary(r)
     print("with the fallback:", s)
+    sj = L.summary(L.evaluate(n, ev, judge=True))
+    print("judged by log-likelihood:", sj)
     n.close()
     assert log.losses[-1][1] < 0.5 * log.losses[0][1]
     assert raw["iters_saved_capped"] >= 3.0
@@ -190,6 +194,10 @@ def test_trained_initialiser_saves_iterations():
     assert s["iters_saved_capped"] >= 3.0
     assert s["error_no_worse_fraction"] >= 0.95
     assert s["mean_position_rmse_all_learned"] <= s["mean_position_rmse_all_prior"]
+    # keeping the higher-likelihood solution of the two starts (both runs paid)
+    assert sj["error_no_worse_fraction"] >= 0.98
+    assert sj["mean_position_rmse_all_learned"] <= sj["mean_position_rmse_all_prior"]
+    assert sj["converged_learned"] >= sj["converged_prior"]
 
 
 def test_gated_start_falls_back_to_the_prior_beyond_its_domain():
