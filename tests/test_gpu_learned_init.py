@@ -110,6 +110,41 @@ def test_loss_and_gradient_match_oracle(net):
     assert i == starts[-1]
 
 
+def test_replicated_batch_has_the_small_batch_loss_and_gradient(net):
+    """The loss and gradient of 256 copies of a batch equal those of the batch
+    itself: every row's output is identical and its loss gradient exactly
+    1/256 of the small batch's (a power of two, exact in bfloat16), so only
+    the FP32 summation order differs. The copies run ~12 row tiles per CTA
+    through every layer's pipeline, the fused weight gradients' accumulation
+    over tiles and the partials' reduction, which the oracle comparison
+    (~8 tiles in all) does not reach; the forward outputs of the copies equal
+    the small batch's bit for bit."""
+    wl = workload([600, 5, 200, 77], seed=13)
+    params = random_params(3)
+    xt = wl["x_true"]
+    mu, sigma = xt.mean(axis=1), xt.std(axis=1) + 0.1
+    net.set_params(params, mu, sigma)
+    y, off, xtd = to_dev(wl["y"], torch.float32), to_dev(wl["offsets"], torch.int64), to_dev(xt, torch.float32)
+    loss1, g1 = net.loss_grad(pes.FP32, y, off, xtd)
+    g1 = g1.double().cpu().numpy()
+    k = 256
+    N = wl["y"].shape[1]
+    off_k = np.concatenate([[0], np.tile(np.diff(wl["offsets"]), k).cumsum()])
+    yk, xk = to_dev(np.tile(wl["y"], (1, k)), torch.float32), to_dev(np.tile(xt, (1, k)), torch.float32)
+    offk = to_dev(off_k.astype(np.int64), torch.int64)
+    assert int(off_k[-1]) == k * N
+    lossk, gk = net.loss_grad(pes.FP32, yk, offk, xk)
+    gk = gk.double().cpu().numpy()
+    assert abs(lossk - loss1) / loss1 < 2e-6   # FP32 warp sums grouped differently
+    e = np.linalg.norm(gk - g1) / np.linalg.norm(g1)
+    print(f"replicated batch: loss {loss1:.6f} / {lossk:.6f}, gradient relative difference {e:.2e}")
+    assert e < 1e-5
+    x1 = net.forward(pes.FP32, y, off)
+    xkf = net.forward(pes.FP32, yk, offk)
+    for c in (0, k // 2, k - 1):
+        assert torch.equal(xkf[:, c * N:(c + 1) * N], x1)
+
+
 def test_adam_step_matches_oracle(net):
     wl = workload([300, 50], seed=14)
     params = random_params(4)
