@@ -1058,7 +1058,7 @@ def main():
                 return all(r[k] <= tol for r in got for k in keys) if got else None
 
             finals = [v["final_iteration"] for v in par.values() if "final_iteration" in v]
-            # one verdict per check: the final iteration from a given nominal is what
+            # one outcome per check: the final iteration from a given nominal is what
             # the kernel's precision decides; all iterations also carry the
             # iteration's own amplification wherever the oracle has not converged
             result["parity"] = {"vs": f"CPU FP64 oracle, {scope}; final_iteration: one oracle iteration from "
