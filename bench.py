@@ -380,6 +380,24 @@ def set_headline(result, key, value, ms):
     result["gpu_launches"] = launches.get(key, 7) * 2 * result["steps"]
 
 
+def choose_headline(result):
+    """`value` is the rate of this run's fastest precision whose final
+    iteration meets the tolerance (parity.within_tol); with none, the FP32
+    rate stays and `at_oracle_tol` is None."""
+    wt = result["parity"]["within_tol"]
+    cands = []
+    for key in ("fp32", "refined", "mixed"):
+        if wt.get(key + "_final_iteration") and key in result:
+            cands.append((key, result[key]["value"], result[key]["ms_per_step"]))
+    if cands:
+        key, v, ms = max(cands, key=lambda c: c[1])
+        result["at_oracle_tol"] = {"precision": key, "value": v, "unit": UNIT}
+        set_headline(result, key, v, ms)
+    else:
+        result["at_oracle_tol"] = None
+        result["config"]["precision"] = "fp32 (no precision met the tolerance in this run)"
+
+
 def executed_for(method: str):
     """Executed instructions per state and iteration of the FP32 smoother kernel
     from the committed ncu capture (profiles/traffic.json), if it was taken on
@@ -1071,23 +1089,7 @@ def main():
                                                "refined_final_iteration": within(finals, "refined", 1e-4),
                                                "fp32_all_iterations": within(par.values(), "fp32", 1e-4),
                                                "mixed_all_iterations": within(par.values(), "mixed", 1e-4)}}
-            # `value` is the rate of this run's fastest precision whose final
-            # iteration meets the tolerance
-            wt = result["parity"]["within_tol"]
-            cands = []
-            if wt["fp32_final_iteration"]:
-                cands.append(("fp32", result["fp32"]["value"], result["fp32"]["ms_per_step"]))
-            if wt["refined_final_iteration"]:
-                cands.append(("refined", result["refined"]["value"], result["refined"]["ms_per_step"]))
-            if wt["mixed_final_iteration"] and "mixed" in result:
-                cands.append(("mixed", result["mixed"]["value"], result["mixed"]["ms_per_step"]))
-            if cands:
-                key, v, ms = max(cands, key=lambda c: c[1])
-                result["at_oracle_tol"] = {"precision": key, "value": v, "unit": UNIT}
-                set_headline(result, key, v, ms)
-            else:
-                result["at_oracle_tol"] = None
-                result["config"]["precision"] = "fp32 (no precision met the tolerance in this run)"
+            choose_headline(result)
         if B == 1 and world == 1:
             if not args.no_length_sweep:
                 result["length_sweep"] = length_sweep_key(args, flush)
