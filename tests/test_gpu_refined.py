@@ -73,11 +73,13 @@ def test_refined_final_iteration_matches_oracle(sm, name, method):
     assert sx < TOL_FP32 and sP < TOL_FP32
 
 
-def test_refined_unscented_matches_oracle(sm):
-    wl = synth.workload("ipls_T10000")
+@pytest.mark.parametrize("name", ["ipls_T10000", "sweep_T65536"])
+def test_refined_unscented_matches_oracle(sm, name):
+    wl = synth.workload(name)
     ut = (0.8, 2.0, 0.5)
     ex, eP, sx, sP = final_iteration_errors(sm, wl, pes.UNSCENTED, pes.REFINED, ut=ut)
-    print(f"unscented REFINED final iteration: means {ex:.2e} covariances {eP:.2e}")
+    print(f"{name} unscented REFINED final iteration: means {ex:.2e} covariances {eP:.2e} "
+          f"(worst state {sx:.2e} / {sP:.2e})")
     assert ex < TOL_REFINED and eP < TOL_REFINED and sx < TOL_FP32 and sP < TOL_FP32
 
 
