@@ -70,6 +70,25 @@ def gpu_run(sm: pes.Smoother, wl: dict, method: int, prec: int, iters: int = 10,
     return x.double().cpu().numpy(), P.double().cpu().numpy(), used, st
 
 
+def prior_only(wl: dict, bs) -> dict:
+    """`wl` with trajectories `bs` cut to their prior state: T_b = 0, one state
+    and no measurement (the prior element is the whole trajectory)."""
+    off = wl["offsets"]
+    keep = np.ones(int(off[-1]), dtype=bool)
+    T = np.diff(off) - 1
+    for b in bs:
+        keep[int(off[b]) + 1:int(off[b + 1])] = False
+        T[b] = 0
+    return dict(wl, offsets=synth.offsets_from_lengths(T), y=np.ascontiguousarray(wl["y"][:, keep]),
+                x_true=np.ascontiguousarray(wl["x_true"][:, keep]))
+
+
+def ragged_with_prior_only() -> dict:
+    """Seven trajectories of 0, 1, 2, 37, 0, 513 and 3,000 measurements."""
+    wl = synth.ct_bearings([1, 1, 2, 37, 1, 513, 3000], seed=41, sensor_jitter=0.2, omega0_halfwidth=1.0)
+    return prior_only(wl, (0, 4))
+
+
 def random_linear_workload(T_list, seed: int, singular_q: bool = False):
     """Random per-step affine parameters (SoA, packed) plus data, for the scan
     entry points; returns (lin, y, m0, P0, offsets)."""

@@ -6,8 +6,8 @@ import torch
 
 import oracle
 from paper_2102_00514_gb300 import pes, synth
-from tests.gpu_common import (ORACLE_METHOD, TOL_FP32, TOL_FP64, gpu_run, oracle_run, rel_err, to_dev,
-                               workload_to_dev)
+from tests.gpu_common import (ORACLE_METHOD, TOL_FP32, TOL_FP64, gpu_run, oracle_run, ragged_with_prior_only,
+                               rel_err, to_dev, workload_to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -125,6 +125,54 @@ def test_batched_segmented_fp64(sm, method):
     x, P, used, _ = gpu_run(sm, wl, method, pes.FP64, iters=5)
     assert rel_err(x, ref["x"], wl["offsets"]) < TOL_FP64
     assert rel_err(P, ref["P"], wl["offsets"]) < TOL_FP64
+
+
+@pytest.mark.parametrize("method", [pes.IEKS, pes.CUBATURE])
+def test_prior_only_trajectories_in_a_ragged_batch(sm, method):
+    """Trajectories without a measurement (T_b = 0) beside one-, two-step and
+    longer ones: FP64 (persistent and sequential), FP32 and PES_MIXED agree with
+    the oracle, and a prior-only trajectory's smoothed moments are its prior,
+    exactly (its only element is the prior element)."""
+    wl = ragged_with_prior_only()
+    off = wl["offsets"]
+    ref = oracle_run(wl, method, iters=10)
+    heads = [int(off[b]) for b in range(len(off) - 1) if off[b + 1] - off[b] == 1]
+    assert len(heads) == 2
+    for prec, tol in ((pes.FP64, TOL_FP64), (pes.FP32, TOL_FP32), (pes.MIXED, TOL_FP32)):
+        x, P, used, st = gpu_run(sm, wl, method, prec, iters=10)
+        assert used == 10 and st == pes.OK
+        assert rel_err(x, ref["x"], off) < tol, prec
+        assert rel_err(P, ref["P"], off) < tol, prec
+        narrow = (lambda a: a) if prec == pes.FP64 else (lambda a: np.float32(a).astype(np.float64))
+        for h, b in zip(heads, (0, 4)):
+            np.testing.assert_array_equal(x[:, h], narrow(wl["m0"][b]))
+            np.testing.assert_array_equal(P[:, h], narrow(wl["P0"][b]))
+    d = workload_to_dev(wl, pes.FP64)
+    xs, Ps, _, _ = sm.ieks_run_sequential(d["model"], method, pes.FP64, d["y"], d["offsets"], d["m0"], d["P0"],
+                                          iters=10)
+    assert rel_err(xs.cpu().numpy(), ref["x"], off) < TOL_FP64
+    assert rel_err(Ps.cpu().numpy(), ref["P"], off) < TOL_FP64
+
+
+@pytest.mark.parametrize("method", [pes.IEKS, pes.CUBATURE])
+def test_handle_at_exact_capacity_equals_a_larger_handle(sm, method):
+    """N = max_states and B = max_batch: every precision runs within the
+    handle's workspace (the lane padding and the refinement's workspace at
+    their largest) and reproduces, bit for bit, a handle with room to spare
+    (the launch shape depends on N alone)."""
+    wl = synth.workload("batch8_T1_3000")
+    N, B = wl["y"].shape[1], len(wl["offsets"]) - 1
+    tight = pes.Smoother(N, B)
+    try:
+        for prec in (pes.FP64, pes.FP32, pes.MIXED, pes.REFINED):
+            d = workload_to_dev(wl, prec)
+            args = (d["model"], method, prec, d["y"], d["offsets"], d["m0"], d["P0"])
+            xa, Pa, _, _ = sm.ieks_run(*args, iters=4)
+            xb, Pb, _, _ = tight.ieks_run(*args, iters=4)
+            torch.cuda.synchronize()
+            assert torch.equal(xa, xb) and torch.equal(Pa, Pb), prec
+    finally:
+        tight.close()
 
 
 def test_batched_equals_separate_runs(sm):

@@ -19,7 +19,7 @@ import pytest
 import torch
 
 from paper_2102_00514_gb300 import pes, synth
-from tests.gpu_common import TOL_FP32, gpu_run, oracle_run, rel_err, workload_to_dev
+from tests.gpu_common import TOL_FP32, gpu_run, oracle_run, ragged_with_prior_only, rel_err, workload_to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -81,6 +81,24 @@ def test_refined_unscented_matches_oracle(sm, name):
     print(f"{name} unscented REFINED final iteration: means {ex:.2e} covariances {eP:.2e} "
           f"(worst state {sx:.2e} / {sP:.2e})")
     assert ex < TOL_REFINED and eP < TOL_REFINED and sx < TOL_FP32 and sP < TOL_FP32
+
+
+@pytest.mark.parametrize("method", [pes.IEKS, pes.CUBATURE])
+def test_refined_ragged_batch_with_prior_only_trajectories(sm, method):
+    """Trajectories of 0, 1, 2, 37, 0, 513 and 3,000 measurements: the refined
+    final iteration is within the bounds, and a prior-only trajectory keeps its
+    prior exactly (its residuals vanish)."""
+    wl = ragged_with_prior_only()
+    ex, eP, sx, sP = final_iteration_errors(sm, wl, method, pes.REFINED)
+    print(f"ragged method {method} REFINED final iteration: means {ex:.2e} covariances {eP:.2e}")
+    assert ex < TOL_REFINED and eP < TOL_REFINED and sx < TOL_FP32 and sP < TOL_FP32
+    x, P, _, _ = gpu_run(sm, wl, method, pes.REFINED, iters=10)
+    off = wl["offsets"]
+    f32 = lambda a: np.float32(a).astype(np.float64)
+    for b in (0, 4):
+        assert off[b + 1] - off[b] == 1
+        np.testing.assert_array_equal(x[:, off[b]], f32(wl["m0"][b]))
+        np.testing.assert_array_equal(P[:, off[b]], f32(wl["P0"][b]))
 
 
 def test_refined_linear_model_one_iteration_is_exact(sm):
