@@ -15,7 +15,7 @@ import torch
 
 from oracle import learned_init as li
 from paper_2102_00514_gb300 import pes, synth
-from tests.gpu_common import gpu_run, rel_err, to_dev
+from tests.gpu_common import rel_err, to_dev
 
 pytestmark = pytest.mark.gpu
 

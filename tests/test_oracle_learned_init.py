@@ -3,7 +3,6 @@ what does not depend on it: a library convolution, finite differences of its
 own forward pass, the closed form of Adam's first step, and PyTorch's
 bfloat16 conversion."""
 import numpy as np
-import pytest
 import torch
 
 from oracle import learned_init as li
