@@ -22,6 +22,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
+# A replacement build of oracle.c to load instead: the mutation test points it
+# at copies with one planted mistake each, to check that the pins reject them.
+# Unset in every other use.
+_LIB_OVERRIDE = os.environ.get("PES_ORACLE_LIBRARY")
 _lib = None
 
 IEKS = 0
@@ -92,8 +96,11 @@ class SElem(ctypes.Structure):
 def _load():
     global _lib
     if _lib is None:
-        build()
-        lib = ctypes.CDLL(_LIB_PATH)
+        if _LIB_OVERRIDE:
+            lib = ctypes.CDLL(_LIB_OVERRIDE)
+        else:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
         p = ctypes.c_void_p
         i64 = ctypes.c_int64
         d = ctypes.c_double

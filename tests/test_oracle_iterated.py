@@ -125,6 +125,88 @@ def test_unscented_mean_exact_for_quadratics(alpha, beta, kappa):
     np.testing.assert_allclose(zbar, exact, atol=1e-9)
 
 
+def _residual_covariance_1d(f, x0, axis, sig, nodes=60):
+    """The Gaussian SLR residual covariance Var(f) - Cov(f, u) Cov(f, u)^T / sig^2
+    of f(x0 + u e_axis), u ~ N(0, sig^2), by Gauss-Hermite quadrature."""
+    t, w = np.polynomial.hermite_e.hermegauss(nodes)
+    w = w / w.sum()
+    Z = np.array([f(x0 + sig * ti * np.eye(5)[axis]) for ti in t])
+    zbar = w @ Z
+    D = Z - zbar
+    C = (w * sig * t) @ D
+    return (D.T * w) @ D - np.outer(C, C) / sig ** 2
+
+
+@pytest.mark.parametrize("alpha,beta,kappa,exact", [(1.0, 0.0, -2.0, True), (0.5, 2.0, -4.0, True),
+                                                    (1.0, 2.0, 1.0, False)])
+def test_unscented_residual_covariance_of_a_quadratic(alpha, beta, kappa, exact):
+    """For a function of one Gaussian coordinate u ~ N(0, s^2) that is quadratic,
+    a u^2 + b u, the rule's residual covariance is a^2 s^4 (alpha^2 (n + kappa - 1)
+    + beta) (n = 5) against the true 2 a^2 s^4: exact when alpha^2 (n + kappa - 1)
+    + beta = 2, as for kappa = 3 - n with beta = 0, or kappa = 1 - n with the
+    Gaussian-optimal beta = 2 at any alpha. The coordinated turn with only the
+    turn rate uncertain, N(0.8, 0.3^2) over dt = 0.01, is quadratic up to a
+    relative remainder of order (0.3 dt)^2; the truth is integrated by
+    60-node Gauss-Hermite. The centre point's covariance weight (beta) and
+    the spread lambda enter only here."""
+    m = ct_model().unscented(alpha, beta, kappa)
+    xbar = np.array([0.4, -0.2, 1.1, 0.3, 0.8])
+    P = np.diag([1e-30] * 4 + [0.3 ** 2])
+    _, _, Lam = oracle.slr(m, 0, 0, xbar, P, method=oracle.UNSCENTED)
+    true = _residual_covariance_1d(lambda v: oracle.ct_f(v, synth.DT), xbar, 4, 0.3)
+    err = np.abs(Lam - true).max() / np.abs(true).max()
+    if exact:
+        assert err < 1e-3
+    else:
+        assert err > 1.0   # 3.5 times the truth: the check discriminates
+
+
+def _residual_covariance_2d(f, x0, axes, sigs, nodes=24):
+    """The Gaussian SLR residual covariance of f over two independent Gaussian
+    coordinates (tensor-product Gauss-Hermite quadrature)."""
+    t, w = np.polynomial.hermite_e.hermegauss(nodes)
+    w = w / w.sum()
+    U, Zs, W = [], [], []
+    for ti, wi in zip(t, w):
+        for tj, wj in zip(t, w):
+            u = np.array([sigs[0] * ti, sigs[1] * tj])
+            x = x0.copy()
+            x[axes[0]] += u[0]
+            x[axes[1]] += u[1]
+            U.append(u); Zs.append(f(x)); W.append(wi * wj)
+    U, Z, W = np.array(U), np.array(Zs), np.array(W)
+    D = Z - W @ Z
+    C = (U.T * W) @ D                       # Cov(u, z), 2 x nz
+    return (D.T * W) @ D - C.T @ np.diag(1.0 / np.square(sigs)) @ C
+
+
+def test_linearised_noise_adds_the_slr_residual_covariance():
+    """Q' = Q + Lambda and R' = R + Omega (Eq. 10), with Lambda and Omega the
+    residual covariances of the statistical linear regression: through the
+    Gauss-Hermite rule, which integrates the quadratic part of f and h exactly,
+    the linearisation's Q' - Q and R' - R must match the true residual
+    covariances (tensor-product quadrature) of the coordinated turn with the
+    turn rate and one velocity uncertain (the bilinear turn term) and of the
+    bearings with the position uncertain."""
+    m = ct_model()
+    x0 = np.array([0.1, 0.2, 1.1, 0.3, 0.8])
+    x1 = np.array([0.12, 0.19, 1.0, 0.4, 0.7])
+    P0 = np.diag([1e-30, 1e-30, 1e-30, 0.5 ** 2, 2.0 ** 2])
+    P1 = np.diag([0.05 ** 2, 0.04 ** 2, 1e-30, 1e-30, 1e-30])
+    xbar = np.stack([x0, x1], axis=1)
+    Pbar = np.stack([oracle.sym_packed(P0), oracle.sym_packed(P1)], axis=1)
+    offsets = np.array([0, 2], dtype=np.int64)
+    y = np.zeros((2, 2))
+    lin = oracle.linearize(m, oracle.GAUSS_HERMITE, offsets, xbar, Pbar, y)
+    Lam = oracle.sym_full(lin["Qp"][:, 0], 5) - m.Q()
+    Om = oracle.sym_full(lin["Rp"][:, 1], 2) - m.R()
+    Lt = _residual_covariance_2d(lambda v: oracle.ct_f(v, synth.DT), x0, (3, 4), (0.5, 2.0))
+    Ot = _residual_covariance_2d(lambda v: oracle.bearings_h(v, np.array(synth.SENSORS)), x1, (0, 1), (0.05, 0.04))
+    assert np.abs(Lt).max() > 1e-9 and np.abs(Ot).max() > 1e-9
+    np.testing.assert_allclose(Lam, Lt, atol=1e-3 * np.abs(Lt).max())
+    np.testing.assert_allclose(Om, Ot, atol=2e-2 * np.abs(Ot).max())
+
+
 def test_gauss_hermite_exact_for_linear_model():
     rng = np.random.default_rng(6)
     F = rng.standard_normal((5, 5)); c = rng.standard_normal(5)

@@ -32,6 +32,20 @@ def test_map_cost_is_half_the_dense_objective():
         assert got == pytest.approx(0.5 * map_objective(x, f, h, Q, R, y, m0, P0), rel=1e-12)
 
 
+def test_map_cost_is_periodic_in_each_bearing():
+    """A bearing and the same bearing plus or minus 2 pi are one measurement: the
+    objective's angle residuals are taken on the branch nearest zero."""
+    wl = synth.ct_bearings([12], seed=23, q_form=1)
+    model = oracle.Model.from_workload(wl)
+    x = wl["x_true"] + 0.02
+    base = oracle.map_cost(model, wl["offsets"], wl["y"], wl["m0"], wl["P0"], x)[0]
+    for k, r, turn in ((3, 0, 1), (7, 1, -1), (12, 0, 2)):
+        y = wl["y"].copy()
+        y[r, k] += 2 * np.pi * turn
+        got = oracle.map_cost(model, wl["offsets"], y, wl["m0"], wl["P0"], x)[0]
+        assert got == pytest.approx(base, rel=1e-9)
+
+
 def test_map_cost_needs_positive_definite_q():
     wl = synth.ct_bearings([5], seed=22, q_form=0)   # diag(0, 0, ...): singular
     model = oracle.Model.from_workload(wl)
