@@ -80,11 +80,13 @@ def test_gradient_equals_central_finite_differences():
     params, trajs, mu, sigma = _tiny_problem(4)
     loss, g = li.loss_and_grad(params, trajs, mu, sigma, rounding=False)
     rng = np.random.default_rng(5)
-    # offsets of each tensor in the flat vector, and a few entries of each
-    starts = np.cumsum([0] + [int(np.prod(w)) + int(np.prod(b)) for w, b in li.SHAPES])
+    # offsets of each weight and bias tensor in the flat vector, and a few
+    # entries of each (every one of the output layer's five biases)
+    sizes = [int(np.prod(t)) for w, b in li.SHAPES for t in (w, b)]
+    starts = np.cumsum([0] + sizes)
     idx = []
     for s0, s1 in zip(starts[:-1], starts[1:]):
-        idx += list(rng.integers(s0, s1, 6))
+        idx += list(range(s0, s1)) if s1 - s0 <= 6 else list(rng.integers(s0, s1, 6))
     eps = 1e-6
     for i in idx:
         p1 = params.copy(); p1[i] += eps
@@ -107,16 +109,39 @@ def test_loss_is_mean_square_error():
 
 def test_adam_first_step_closed_form():
     # from zero moments the bias-corrected first step is lr * g / (|g| + eps)
+    # (Kingma and Ba: the step divides by sqrt(v_hat) + eps); gradients of the
+    # order of eps show where eps enters
     rng = np.random.default_rng(7)
     p = rng.standard_normal(100).astype(np.float32)
     g = rng.standard_normal(100)
+    g[:4] = [1e-8, -3e-8, 1e-7, -1e-6]
     opt = li.Adam(lr=1e-2)
     p1 = opt.step(p, g)
     expect = p.astype(np.float64) - 1e-2 * g / (np.abs(g) + 1e-8)
     assert np.allclose(p1, expect.astype(np.float32), rtol=0, atol=1e-6)
-    # a constant gradient keeps the step at lr (m_hat = g, v_hat = g^2 exactly)
+    # a constant gradient keeps the step (m_hat = g, v_hat = g^2 exactly): lr
+    # where |g| >> eps
     p2 = opt.step(p1, g)
-    assert np.allclose(p2.astype(np.float64), p1.astype(np.float64) - 1e-2 * np.sign(g), atol=1e-6)
+    assert np.allclose(p2.astype(np.float64), p1.astype(np.float64) - 1e-2 * g / (np.abs(g) + 1e-8), atol=1e-6)
+
+
+def test_a_network_that_outputs_the_normalised_target_gives_the_target():
+    """Training compares the output with t = (x - mu) / sigma and inference maps
+    the output back: a network whose output is t has zero loss, and its
+    initial nominal is x. Zero weights with output bias t0 output t0 at every
+    state (a constant target)."""
+    rng = np.random.default_rng(9)
+    mu, sigma = rng.standard_normal(5), 0.5 + rng.random(5)
+    x_star = rng.standard_normal(5)
+    layers = [(np.zeros(w), np.zeros(b)) for w, b in li.SHAPES]
+    layers[-1] = (layers[-1][0], (x_star - mu) / sigma)
+    params = li.pack(layers)
+    T = 7
+    y = rng.uniform(-3, 3, (2, T + 1))
+    target = np.tile(x_star[:, None], (1, T + 1))
+    loss, _ = li.loss_and_grad(params, [(y, target)], mu, sigma, rounding=False)
+    assert loss < 1e-28
+    np.testing.assert_allclose(li.initial_nominal(params, y, T, mu, sigma, rounding=False), target, atol=1e-14)
 
 
 def test_training_reduces_loss_on_a_fixed_batch():

@@ -1,13 +1,15 @@
 """The oracle's pins must reject a wrong oracle.
 
-Each mutant below plants one plausible mistake in a copy of oracle/oracle.c: a
+Each mutant below plants one plausible mistake in a copy of the oracle: a
 dropped term, a wrong sign, a wrong index, a transposed or swapped operand, a
-wrong weight or coefficient. The copy is compiled beside the test and the pin
-suites of the C oracle (tests/test_oracle_{model,smoother,iterated,lm}.py)
-run against it in a child process (oracle/__init__.py loads the library that
-PES_ORACLE_LIBRARY names); at least one pin has to fail. An unmodified copy,
-built the same way, has to pass them all, which also shows that the child
-processes load the copies.
+wrong weight or coefficient. For oracle/oracle.c the copy is compiled beside
+the test and the pin suites of the C oracle (tests/test_oracle_{model,
+smoother,iterated,lm}.py) run against it in a child process (oracle/
+__init__.py loads the library that PES_ORACLE_LIBRARY names); for
+oracle/learned_init.py the child process imports the mutated copy in its
+place and runs tests/test_oracle_learned_init.py. At least one pin has to
+fail. Unmodified copies, run the same way, have to pass them all, which also
+shows that the child processes use the copies.
 """
 import os
 import shutil
@@ -20,6 +22,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE_DIR = os.path.join(ROOT, "oracle")
 PIN_SUITES = [os.path.join(ROOT, "tests", f"test_oracle_{n}.py") for n in ("model", "smoother", "iterated", "lm")]
+LI_PINS = os.path.join(ROOT, "tests", "test_oracle_learned_init.py")
 
 # (name, anchor, old, new): `old` is replaced by `new` at its first occurrence
 # after the first occurrence of `anchor` (the function it sits in).
@@ -129,6 +132,49 @@ MUTANTS = [
     ("loglik_normalising_constant", "int orc_kf_loglik(", "- 0.5 * NY * log_2pi;", "- 0.5 * log_2pi;"),
 ]
 
+# the same for oracle/learned_init.py
+LI_MUTANTS = [
+    ("bf16_ties_away", "def bf16(", "(u + 0x7FFF + ((u >> 16) & 1))", "(u + 0x8000)"),
+    ("features_sin_for_cos", "def features(", "phi[1:, 1] = np.cos(yy[0, 1:])", "phi[1:, 1] = np.sin(yy[0, 1:])"),
+    ("features_head_marker", "def features(", "phi[0, 5] = 1.0", "phi[0, 4] = 1.0"),
+    ("shift_direction", "def shift(", "s[:n - d] = h[d:]", "s[d:] = h[:n - d]"),
+    ("conv_flipped_taps", "def conv(", "shift(h, j - TAPS // 2)", "shift(h, TAPS // 2 - j)"),
+    ("conv_weight_transposed", "def conv(", "@ W[:, :, j].T", "@ W[:, :, j]"),
+    ("head_without_relu", "def forward(", "z = _r(np.maximum(h[-1] @ W5.T + b5, 0.0), rounding)",
+     "z = _r(h[-1] @ W5.T + b5, rounding)"),
+    ("nominal_drops_scale", "def initial_nominal(", "np.asarray(sigma)[None, :] * o", "o"),
+    ("loss_gradient_scale", "def loss_and_grad(", "_r(2.0 * e / (NOUT * n_total), rounding)",
+     "_r(2.0 * e / n_total, rounding)"),
+    ("head_gradient_drops_mask", "def loss_and_grad(", "dz = _r((dO @ W6) * (z > 0), rounding)",
+     "dz = _r(dO @ W6, rounding)"),
+    ("output_bias_gradient", "def loss_and_grad(", "grads[NCONV + 1][1][...] += dO.sum(axis=0)",
+     "grads[NCONV + 1][1][...] += dO.sum(axis=1).sum()"),
+    ("conv_bias_gradient_dropped", "def loss_and_grad(", "gb += dh.sum(axis=0)", "gb += 0.0"),
+    ("conv_weight_gradient_taps", "def loss_and_grad(", "gW[:, :, j] += dh.T @ shift(h[l], j - TAPS // 2)",
+     "gW[:, :, j] += dh.T @ shift(h[l], TAPS // 2 - j)"),
+    ("backward_conv_direction", "def loss_and_grad(", "back += shift(dh, TAPS // 2 - j) @ W[:, :, j]",
+     "back += shift(dh, j - TAPS // 2) @ W[:, :, j]"),
+    ("backward_relu_mask_of_next_layer", "def loss_and_grad(", "dh = _r(back * (h[l] > 0), rounding)",
+     "dh = _r(back * (h[l + 1] > 0), rounding)"),
+    ("adam_no_bias_correction", "def step(", "mhat = self.m / (1 - self.b1 ** self.t)", "mhat = self.m"),
+    ("adam_second_moment_not_squared", "def step(", "(1 - self.b2) * g * g", "(1 - self.b2) * np.abs(g)"),
+    ("adam_eps_inside_root", "def step(", "(np.sqrt(vhat) + self.eps)", "np.sqrt(vhat + self.eps)"),
+]
+
+# Runs the learned-initialiser pins with the module at argv[1] standing in for
+# oracle.learned_init.
+LI_RUNNER = """
+import importlib.util, sys
+spec = importlib.util.spec_from_file_location("oracle.learned_init", sys.argv[1])
+mod = importlib.util.module_from_spec(spec)
+sys.modules["oracle.learned_init"] = mod
+spec.loader.exec_module(mod)
+import oracle
+oracle.learned_init = mod
+import pytest
+sys.exit(pytest.main(["-x", "-q", "-p", "no:cacheprovider", sys.argv[2]]))
+"""
+
 
 def mutate(src: str, anchor: str, old: str, new: str) -> str:
     a = src.index(anchor)
@@ -147,44 +193,67 @@ def build(src: str, where: str) -> str:
     return lib
 
 
+def _tail(r) -> str:
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    return lines[-1] if lines else r.stderr[-200:]
+
+
 def run_pins(lib: str) -> tuple[int, str]:
     env = dict(os.environ, PES_ORACLE_LIBRARY=lib)
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
                         *PIN_SUITES], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
-    return r.returncode, lines[-1] if lines else r.stderr[-200:]
+    return r.returncode, _tail(r)
+
+
+def run_li_pins(module: str) -> tuple[int, str]:
+    r = subprocess.run([sys.executable, "-c", LI_RUNNER, module, LI_PINS], cwd=ROOT, capture_output=True, text=True,
+                       timeout=600)
+    return r.returncode, _tail(r)
 
 
 @pytest.fixture(scope="module")
 def outcomes(tmp_path_factory):
     src = open(os.path.join(ORACLE_DIR, "oracle.c")).read()
+    li_src = open(os.path.join(ORACLE_DIR, "learned_init.py")).read()
     base = tmp_path_factory.mktemp("mutants")
 
     def one(item):
-        name, anchor, old, new = item
-        text = src if name == "control" else mutate(src, anchor, old, new)
-        return name, run_pins(build(text, str(base / name)))
+        kind, (name, anchor, old, new) = item
+        where = str(base / kind / name)
+        if kind == "c":
+            text = src if name == "control" else mutate(src, anchor, old, new)
+            return (kind, name), run_pins(build(text, where))
+        text = li_src if name == "control" else mutate(li_src, anchor, old, new)
+        os.makedirs(where, exist_ok=True)
+        path = os.path.join(where, "learned_init.py")
+        with open(path, "w") as f:
+            f.write(text)
+        return (kind, name), run_li_pins(path)
 
+    control = ("control", "", "", "")
+    items = [("c", control)] + [("c", m) for m in MUTANTS] + [("li", control)] + [("li", m) for m in LI_MUTANTS]
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
-        return dict(ex.map(one, [("control", "", "", "")] + MUTANTS))
+        return dict(ex.map(one, items))
 
 
-def test_mutations_apply_to_distinct_sites():
-    src = open(os.path.join(ORACLE_DIR, "oracle.c")).read()
-    names = [m[0] for m in MUTANTS]
+@pytest.mark.parametrize("path,mutants", [("oracle.c", MUTANTS), ("learned_init.py", LI_MUTANTS)])
+def test_mutations_apply_to_distinct_sites(path, mutants):
+    src = open(os.path.join(ORACLE_DIR, path)).read()
+    names = [m[0] for m in mutants]
     assert len(set(names)) == len(names)
-    for name, anchor, old, new in MUTANTS:
+    for name, anchor, old, new in mutants:
         assert src.count(anchor) == 1, name
         assert old in src[src.index(anchor):], name
         assert mutate(src, anchor, old, new) != src, name
 
 
-def test_unmodified_copy_passes_the_pins(outcomes):
-    rc, tail = outcomes["control"]
+@pytest.mark.parametrize("kind", ["c", "li"])
+def test_unmodified_copy_passes_the_pins(outcomes, kind):
+    rc, tail = outcomes[(kind, "control")]
     assert rc == 0, tail
 
 
-@pytest.mark.parametrize("name", [m[0] for m in MUTANTS])
-def test_pins_reject_the_mutant(outcomes, name):
-    rc, tail = outcomes[name]
+@pytest.mark.parametrize("kind,name", [("c", m[0]) for m in MUTANTS] + [("li", m[0]) for m in LI_MUTANTS])
+def test_pins_reject_the_mutant(outcomes, kind, name):
+    rc, tail = outcomes[(kind, name)]
     assert rc == 1, f"{name} survived the pins ({tail})"
