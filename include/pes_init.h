@@ -67,6 +67,20 @@ pes_status pes_init_set_params(pes_init_net* net, const float* params, const dou
  * Synchronous. */
 pes_status pes_init_get_params(pes_init_net* net, float* params);
 
+/* The training state, for checkpointing a run and resuming it: the FP32 master
+ * parameters (HOST float [PES_INIT_NPARAMS]), the output normalisation mu,
+ * sigma (HOST double [5]), Adam's first and second moments (HOST float
+ * [PES_INIT_NPARAMS] each) and its step count. pes_init_get_state copies them
+ * out (any pointer may be NULL to skip that part); pes_init_set_state copies
+ * them in (all required; sigma > 0, moments finite, v >= 0, adam_t >= 0) and
+ * republishes the layers' bfloat16 weights, so that the next
+ * pes_init_train_step continues the saved run exactly. Both synchronise the
+ * device. */
+pes_status pes_init_get_state(pes_init_net* net, float* params, double* mu, double* sigma, float* adam_m,
+                              float* adam_v, int64_t* adam_t);
+pes_status pes_init_set_state(pes_init_net* net, const float* params, const double* mu, const double* sigma,
+                              const float* adam_m, const float* adam_v, int64_t adam_t);
+
 /* Inference: x_init [5][N] (component-major, float or double per `prec`) for
  * the B trajectories in y / offsets. */
 pes_status pes_init_forward(pes_init_net* net, pes_precision prec, const void* y, const int64_t* offsets, int32_t B,

@@ -1530,6 +1530,40 @@ pes_status pes_init_get_params(pes_init_net* n, float* params)
     return PES_OK;
 }
 
+pes_status pes_init_get_state(pes_init_net* n, float* params, double* mu, double* sigma, float* adam_m,
+                              float* adam_v, int64_t* adam_t)
+{
+    if (!n) return net_fail(n, PES_ERR_INVALID_ARG, "NULL net");
+    NET_CUDA(n, cudaDeviceSynchronize());
+    const size_t bytes = sizeof(float) * PES_INIT_NPARAMS;
+    if (params) NET_CUDA(n, cudaMemcpy(params, n->params, bytes, cudaMemcpyDeviceToHost));
+    if (adam_m) NET_CUDA(n, cudaMemcpy(adam_m, n->m, bytes, cudaMemcpyDeviceToHost));
+    if (adam_v) NET_CUDA(n, cudaMemcpy(adam_v, n->v, bytes, cudaMemcpyDeviceToHost));
+    for (int c = 0; c < 5; ++c) {
+        if (mu) mu[c] = n->norm.mu[c];
+        if (sigma) sigma[c] = n->norm.sigma[c];
+    }
+    if (adam_t) *adam_t = n->adam_t;
+    return PES_OK;
+}
+
+pes_status pes_init_set_state(pes_init_net* n, const float* params, const double* mu, const double* sigma,
+                              const float* adam_m, const float* adam_v, int64_t adam_t)
+{
+    if (!n || !params || !mu || !sigma || !adam_m || !adam_v) return net_fail(n, PES_ERR_INVALID_ARG, "NULL argument");
+    if (adam_t < 0 || adam_t > INT32_MAX) return net_fail(n, PES_ERR_INVALID_ARG, "adam_t out of range");
+    for (int i = 0; i < PES_INIT_NPARAMS; ++i)
+        if (!std::isfinite(adam_m[i]) || !std::isfinite(adam_v[i]) || !(adam_v[i] >= 0.f))
+            return net_fail(n, PES_ERR_INVALID_ARG, "Adam moments must be finite, the second ones non-negative");
+    pes_status s = pes_init_set_params(n, params, mu, sigma);
+    if (s != PES_OK) return s;
+    const size_t bytes = sizeof(float) * PES_INIT_NPARAMS;
+    NET_CUDA(n, cudaMemcpy(n->m, adam_m, bytes, cudaMemcpyHostToDevice));
+    NET_CUDA(n, cudaMemcpy(n->v, adam_v, bytes, cudaMemcpyHostToDevice));
+    n->adam_t = (int)adam_t;
+    return PES_OK;
+}
+
 pes_status pes_init_forward(pes_init_net* n, pes_precision prec, const void* y, const int64_t* offsets, int32_t B,
                             int64_t N, void* x_init, void* stream)
 {

@@ -13,6 +13,8 @@ arranges device buffers (PyTorch) and bookkeeping on the host.
 """
 from __future__ import annotations
 
+import json
+import os
 import time
 from dataclasses import dataclass, field
 
@@ -92,13 +94,45 @@ class TrainLog:
     losses: list = field(default_factory=list)
 
 
+def save_checkpoint(path: str, net, step: int, rng: np.random.Generator, order: np.ndarray) -> None:
+    """The training run after `step` steps: the network's training state
+    (parameters, normalisation, Adam's moments and step count), the minibatch
+    sampler's generator state and its current permutation. Written to a
+    temporary file first and renamed over `path`, so that an interrupted save
+    leaves the previous checkpoint intact."""
+    st = net.get_state()
+    rng_state = np.frombuffer(json.dumps(rng.bit_generator.state).encode(), dtype=np.uint8)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "wb") as f:
+        np.savez(f, step=np.int64(step), order=np.asarray(order, dtype=np.int64), rng_state=rng_state,
+                 params=st["params"], mu=st["mu"], sigma=st["sigma"], adam_m=st["m"], adam_v=st["v"],
+                 adam_t=np.int64(st["t"]))
+    os.replace(tmp, path)
+
+
+def load_checkpoint(path: str, net):
+    """Restore the network's training state from a checkpoint; returns (step,
+    the sampler's generator state, its permutation)."""
+    with np.load(path) as z:
+        net.set_state(dict(params=z["params"], mu=z["mu"], sigma=z["sigma"], m=z["adam_m"], v=z["adam_v"],
+                           t=int(z["adam_t"])))
+        return int(z["step"]), json.loads(bytes(z["rng_state"]).decode()), z["order"].copy()
+
+
 def train(net: pes.InitNet, wl: dict, targets: np.ndarray, keep: np.ndarray, *, batch_traj: int = 128,
           steps: int = 2000, lr: float = 2e-3, lr_final: float = 2e-4, seed: int = 0,
-          log_every: int = 100) -> TrainLog:
+          log_every: int = 100, checkpoint: str | None = None, checkpoint_every: int = 0,
+          resume: bool = False, stop_at: int | None = None) -> TrainLog:
     """Adam on minibatches of `batch_traj` whole trajectories of one length,
-    the learning rate decayed geometrically from lr to lr_final. Only the
-    trajectories with keep[b] (converged targets) are used. The network's
-    parameters and normalisation must be set before."""
+    the learning rate decayed geometrically from lr to lr_final over `steps`
+    steps. Only the trajectories with keep[b] (converged targets) are used. The
+    network's parameters and normalisation must be set before (or restored:
+    with `resume`, from the checkpoint at `checkpoint`, and the run continues
+    at the step it was saved after). With `checkpoint` and `checkpoint_every`,
+    the run is saved there every `checkpoint_every` steps and when it stops;
+    `stop_at` ends this call after that many steps of the schedule (a job
+    split over several calls resumes where the previous one stopped and gives
+    the same parameters, bit for bit, as one uninterrupted call)."""
     off = wl["offsets"]
     lens = np.diff(off)
     if not np.all(lens == lens[0]):
@@ -117,11 +151,20 @@ def train(net: pes.InitNet, wl: dict, targets: np.ndarray, keep: np.ndarray, *, 
     X = xt.reshape(5, nmb, batch_traj * n1).permute(1, 0, 2).contiguous().cuda()
     moff = _dev(np.arange(batch_traj + 1, dtype=np.int64) * n1, torch.int64)
     rng = np.random.default_rng(seed)
-    log = TrainLog()
     order = rng.permutation(nmb)
+    s0 = 0
+    if resume:
+        if not checkpoint:
+            raise ValueError("resume needs the checkpoint's path")
+        s0, rng_state, order = load_checkpoint(checkpoint, net)
+        if len(order) != nmb:
+            raise ValueError("the checkpoint was taken with another training set or minibatch size")
+        rng.bit_generator.state = rng_state
+    end = steps if stop_at is None else min(steps, stop_at)
+    log = TrainLog()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for s in range(steps):
+    for s in range(s0, end):
         if s and s % nmb == 0:
             order = rng.permutation(nmb)
         m = int(order[s % nmb])
@@ -130,9 +173,11 @@ def train(net: pes.InitNet, wl: dict, targets: np.ndarray, keep: np.ndarray, *, 
         loss = net.train_step(pes.FP32, Y[m], moff, X[m], a, want_loss=want)
         if want:
             log.losses.append((s, loss))
+        if checkpoint and checkpoint_every and ((s + 1) % checkpoint_every == 0 or s + 1 == end):
+            save_checkpoint(checkpoint, net, s + 1, rng, order)
     torch.cuda.synchronize()
     log.seconds = time.perf_counter() - t0
-    log.steps = steps
+    log.steps = end - s0
     return log
 
 

@@ -31,7 +31,8 @@ EXPORTED = ["pes_create", "pes_destroy", "pes_last_error", "pes_sync", "pes_line
             "pes_smooth_scan", "pes_ieks_run", "pes_ieks_run_host", "pes_launch_shape", "pes_measure_fma_peak",
             "pes_debug_phase_times", "pes_ieks_run_noalloc", "pes_traj_iterations", "pes_ieks_run_lm", "pes_filter_loglik", "pes_ieks_run_sequential", "pes_autotune", "pes_ieks_graph_create", "pes_graph_launch", "pes_graph_destroy",
             "pes_init_create", "pes_init_destroy", "pes_init_last_error", "pes_init_set_params",
-            "pes_init_get_params", "pes_init_forward", "pes_init_loss_grad", "pes_init_train_step"]
+            "pes_init_get_params", "pes_init_get_state", "pes_init_set_state", "pes_init_forward",
+            "pes_init_loss_grad", "pes_init_train_step"]
 INIT_NPARAMS = 86661
 
 
@@ -99,6 +100,8 @@ def load_library():
     lib.pes_init_last_error.restype = ctypes.c_char_p
     lib.pes_init_set_params.argtypes = [p, p, p, p]
     lib.pes_init_get_params.argtypes = [p, p]
+    lib.pes_init_get_state.argtypes = [p, p, p, p, p, p, ctypes.POINTER(i64)]
+    lib.pes_init_set_state.argtypes = [p, p, p, p, p, p, i64]
     lib.pes_init_forward.argtypes = [p, i32, p, p, i32, i64, p, p]
     lib.pes_init_loss_grad.argtypes = [p, i32, p, p, i32, i64, p, p, ctypes.POINTER(d), p]
     lib.pes_init_train_step.argtypes = [p, i32, p, p, i32, i64, p, ctypes.c_float, ctypes.POINTER(d), p]
@@ -506,6 +509,31 @@ class InitNet:
         p = np.empty(INIT_NPARAMS, dtype=np.float32)
         self._check(self.lib.pes_init_get_params(self.h, p.ctypes.data))
         return p
+
+    def get_state(self) -> dict:
+        """The training state (pes_init_get_state): params, mu, sigma, Adam's
+        moments m and v, and its step count t."""
+        import numpy as np
+        st = dict(params=np.empty(INIT_NPARAMS, dtype=np.float32), mu=np.empty(5), sigma=np.empty(5),
+                  m=np.empty(INIT_NPARAMS, dtype=np.float32), v=np.empty(INIT_NPARAMS, dtype=np.float32))
+        t = ctypes.c_int64()
+        self._check(self.lib.pes_init_get_state(self.h, st["params"].ctypes.data, st["mu"].ctypes.data,
+                                                st["sigma"].ctypes.data, st["m"].ctypes.data, st["v"].ctypes.data,
+                                                ctypes.byref(t)))
+        st["t"] = int(t.value)
+        return st
+
+    def set_state(self, state: dict):
+        """Restore a state from get_state (pes_init_set_state)."""
+        import numpy as np
+        f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+        f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+        p, m, v = f32(state["params"]), f32(state["m"]), f32(state["v"])
+        mu, sg = f64(state["mu"]), f64(state["sigma"])
+        if p.shape != (INIT_NPARAMS,) or m.shape != p.shape or v.shape != p.shape or mu.shape != (5,) or sg.shape != (5,):
+            raise ValueError("malformed training state")
+        self._check(self.lib.pes_init_set_state(self.h, p.ctypes.data, mu.ctypes.data, sg.ctypes.data, m.ctypes.data,
+                                                v.ctypes.data, int(state["t"])))
 
     def forward(self, prec: int, y, offsets, x_out=None, stream=None):
         dt = _dtype(prec)

@@ -189,6 +189,51 @@ def test_invalid_arguments_rejected(net):
     assert ei.value.status == pes.INVALID_ARG
 
 
+def test_training_resumes_bit_exactly_from_a_checkpoint(tmp_path):
+    """Ten training steps in one call against the same ten split over two
+    networks: seven steps saved every three (and at the stop), then a fresh
+    network resumed from the checkpoint. The minibatch order (three
+    minibatches, a new permutation every three steps), the learning-rate
+    schedule and Adam's state continue where they stopped, so parameters and
+    moments are bit-identical (the gradients' reduction order is fixed)."""
+    from paper_2102_00514_gb300 import learned_init as L
+    wl = synth.ct_bearings(np.full(192, 200), seed=17, omega0_halfwidth=1.0)
+    x, keep = wl["x_true"], np.ones(192, dtype=bool)
+    mu, sigma = L.normalisation(x)
+    p0 = L.initial_params(4)
+    kw = dict(batch_traj=64, steps=10, lr=2e-3, lr_final=1e-3, seed=5)
+    a = pes.InitNet(64 * 201, 64)
+    a.set_params(p0, mu, sigma)
+    log_a = L.train(a, wl, x, keep, log_every=1, **kw)
+    ckpt = str(tmp_path / "ckpt.npz")
+    b = pes.InitNet(64 * 201, 64)
+    b.set_params(p0, mu, sigma)
+    log_b = L.train(b, wl, x, keep, log_every=1, checkpoint=ckpt, checkpoint_every=3, stop_at=7, **kw)
+    b.close()
+    c = pes.InitNet(64 * 201, 64)
+    log_c = L.train(c, wl, x, keep, log_every=1, checkpoint=ckpt, resume=True, **kw)
+    sa, sc = a.get_state(), c.get_state()
+    a.close()
+    c.close()
+    assert log_b.steps == 7 and log_c.steps == 3 and sa["t"] == sc["t"] == 10
+    for k in ("params", "m", "v", "mu", "sigma"):
+        assert np.array_equal(sa[k], sc[k]), k
+    assert [l for _, l in log_a.losses] == [l for _, l in log_b.losses + log_c.losses]
+
+
+def test_training_state_is_validated(net):
+    st = net.get_state()
+    for bad in (dict(st, t=-1), dict(st, v=-np.abs(st["v"]) - 1.0), dict(st, m=np.full_like(st["m"], np.nan)),
+                dict(st, sigma=np.zeros(5))):
+        with pytest.raises(pes.PesError) as ei:
+            net.set_state(bad)
+        assert ei.value.status == pes.INVALID_ARG
+    net.set_state(st)
+    back = net.get_state()
+    for k in ("params", "m", "v", "mu", "sigma"):
+        assert np.array_equal(back[k], st[k]), k
+
+
 def test_trained_initialiser_saves_iterations():
     """Trained on the GPU (its own kernels) against converged FP64 smoother
     means of 2,048 trajectories of T = 1,000, the network's start is compared

@@ -1,7 +1,7 @@
-"""Host logic of the learned initialiser's start policy (paper_2102_00514_gb300/
-learned_init.py), on the CPU: the packing of a subset of trajectories for the
-fallback run, the length gate, and the paired summary's iteration accounting
-when the fallback ran."""
+"""Host logic of the learned initialiser (paper_2102_00514_gb300/learned_init.py),
+on the CPU: the packing of a subset of trajectories for the fallback run, the
+length gate, the paired summary's iteration accounting when the fallback ran,
+and the training checkpoint's file (with a stand-in for the network's state)."""
 import numpy as np
 import torch
 
@@ -71,3 +71,42 @@ def test_summary_counts_both_runs_of_a_fallback():
     # on the trajectories both converge, the fallback's own iterations count in full
     both = np.array([True, True, False, True])
     assert s["iters_saved"] == (ip[both] - spent[both]).mean()
+
+
+class _StateHolder:
+    """Stands in for pes.InitNet's get_state / set_state."""
+
+    def __init__(self, state=None):
+        self.state = state
+
+    def get_state(self):
+        return self.state
+
+    def set_state(self, state):
+        self.state = state
+
+
+def test_checkpoint_round_trip_restores_state_and_sampler(tmp_path):
+    rng = np.random.default_rng(5)
+    n = L.pes.INIT_NPARAMS
+    st = dict(params=rng.standard_normal(n).astype(np.float32), mu=rng.standard_normal(5),
+              sigma=0.5 + rng.random(5), m=rng.standard_normal(n).astype(np.float32),
+              v=rng.random(n).astype(np.float32), t=17)
+    g = np.random.default_rng(3)
+    order = g.permutation(11)
+    g.permutation(11)                        # the sampler has moved on
+    path = str(tmp_path / "ckpt.npz")
+    L.save_checkpoint(path, _StateHolder(st), 42, g, order)
+    expect = g.permutation(11)               # what the uninterrupted sampler draws next
+    net = _StateHolder()
+    step, rng_state, order2 = L.load_checkpoint(path, net)
+    assert step == 42 and np.array_equal(order2, order)
+    for k in ("params", "mu", "sigma", "m", "v"):
+        assert net.state[k].dtype == st[k].dtype and np.array_equal(net.state[k], st[k]), k
+    assert net.state["t"] == 17
+    g2 = np.random.default_rng(0)
+    g2.bit_generator.state = rng_state
+    assert np.array_equal(g2.permutation(11), expect)
+    # a second save replaces the file whole
+    L.save_checkpoint(path, _StateHolder(dict(st, t=18)), 43, g, order)
+    assert L.load_checkpoint(path, net)[0] == 43 and net.state["t"] == 18
