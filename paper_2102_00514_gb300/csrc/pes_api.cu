@@ -10,6 +10,7 @@
 
 #include "pes.h"
 #include "pes_handle.h"
+#include "pes_trace.h"
 #include "pes_internal.h"
 #include "pes_lm.cuh"
 #include "pes_refine.cuh"
@@ -431,12 +432,14 @@ static pes_status ieks_run_mixed(pes_handle* h, const pes_model* model, pes_meth
     const void* xi32 = x_init;
     const void* Pi32 = P_init;
     if (max_iters > 1) {
+        pes::TraceRange trace_("FP32 iterations");
         pes_status r = ieks_run_t<float>(h, model, method, PES_FP32, y, offsets, B, N, m0, P0, x_init, P_init,
                                          max_iters - 1, tol, x_out, P_out, &it32, st);
         if (r != PES_OK && r != PES_ERR_NOT_CONVERGED) return r;
         xi32 = x_out;
         Pi32 = P_out;
     }
+    pes::TraceRange trace_("final FP64 iteration");
     PES_CUDA(h, (launch_convert_ff<float, double>((const float*)y, y64, 2 * N, st)));
     PES_CUDA(h, (launch_convert_ff<float, double>((const float*)m0, m064, 5 * (int64_t)B, st)));
     PES_CUDA(h, (launch_convert_ff<float, double>((const float*)P0, P064, 15 * (int64_t)B, st)));
@@ -519,6 +522,7 @@ static pes_status ieks_run_refined(pes_handle* h, const pes_model* model, pes_me
     int32_t it32 = 0;
     pes_status r32 = PES_OK;
     if (max_iters > 1) {
+        pes::TraceRange trace_("FP32 iterations");
         p.iters = max_iters - 1;
         p.tol = tol;
         p.write_P_every_iter = tol > 0.0 ? 1 : 0;
@@ -536,25 +540,31 @@ static pes_status ieks_run_refined(pes_handle* h, const pes_model* model, pes_me
     p.tol = 0.0;
     p.write_P_every_iter = 1;
     p.fstore = filt;
-    if ((r = run_persistent_shaped<float>(h, p, lin, s, st)) != PES_OK) return r;
-    RefineParams rp{};
-    rp.N = N; rp.offsets = offsets; rp.B = B; rp.L = s.L; rp.NL = NL; rp.cs = cs;
-    rp.model = p.model;
-    rp.y = ly; rp.m0 = (const float*)m0; rp.P0 = (const float*)P0;
-    rp.nom = nom; rp.filt = filt; rp.xs = lx;
-    rp.elem = elem; rp.trans = trans; rp.dlt = dlt;
-    rp.agg = static_cast<float*>(h->aggF);
-    rp.bar = h->bar;
-    rp.status = h->status;
-    rp.timeout_ns = h->timeout_ns;
-    PES_CUDA(h, launch_refine_fwd(rp, lin, st));
-    PES_CUDA(h, cudaMemsetAsync(h->bar, 0, sizeof(unsigned), st));
-    cudaError_t e = launch_refine_scan(rp, true, s.nt, s.nb, st);
-    if (e != cudaSuccess) return cuda_fail(h, e, "cooperative launch of the refinement scan");
-    PES_CUDA(h, launch_refine_bwd(rp, st));
-    PES_CUDA(h, cudaMemsetAsync(h->bar, 0, sizeof(unsigned), st));
-    e = launch_refine_scan(rp, false, s.nt, s.nb, st);
-    if (e != cudaSuccess) return cuda_fail(h, e, "cooperative launch of the refinement scan");
+    {
+        pes::TraceRange trace_("final FP32 iteration");
+        if ((r = run_persistent_shaped<float>(h, p, lin, s, st)) != PES_OK) return r;
+    }
+    {
+        pes::TraceRange trace_refine_("refinement");
+        RefineParams rp{};
+        rp.N = N; rp.offsets = offsets; rp.B = B; rp.L = s.L; rp.NL = NL; rp.cs = cs;
+        rp.model = p.model;
+        rp.y = ly; rp.m0 = (const float*)m0; rp.P0 = (const float*)P0;
+        rp.nom = nom; rp.filt = filt; rp.xs = lx;
+        rp.elem = elem; rp.trans = trans; rp.dlt = dlt;
+        rp.agg = static_cast<float*>(h->aggF);
+        rp.bar = h->bar;
+        rp.status = h->status;
+        rp.timeout_ns = h->timeout_ns;
+        PES_CUDA(h, launch_refine_fwd(rp, lin, st));
+        PES_CUDA(h, cudaMemsetAsync(h->bar, 0, sizeof(unsigned), st));
+        cudaError_t e = launch_refine_scan(rp, true, s.nt, s.nb, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cooperative launch of the refinement scan");
+        PES_CUDA(h, launch_refine_bwd(rp, st));
+        PES_CUDA(h, cudaMemsetAsync(h->bar, 0, sizeof(unsigned), st));
+        e = launch_refine_scan(rp, false, s.nt, s.nb, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cooperative launch of the refinement scan");
+    }
     PES_CUDA(h, launch_lanes_transpose<float>(lx, (float*)x_out, 5, N, s.L, NL, false, st));
     PES_CUDA(h, launch_lanes_transpose<float>(lP, (float*)P_out, 15, N, s.L, NL, false, st));
     if (tol > 0.0 || iters_used) {
@@ -868,6 +878,7 @@ pes_status pes_ieks_graph_create(pes_handle* h, const pes_model* model, pes_meth
                                  const void* P0, const void* x_init, const void* P_init, int32_t iters, void* x_out,
                                  void* P_out, pes_graph** out)
 {
+    pes::TraceRange trace_("pes_ieks_graph_create");
     if (!h || !out) return PES_ERR_INVALID_ARG;
     *out = nullptr;
     if (prec == PES_MIXED) return fail(h, PES_ERR_UNSUPPORTED, "PES_MIXED synchronises and cannot be captured");
@@ -932,6 +943,7 @@ pes_status pes_autotune(pes_handle* h, const pes_model* model, pes_method method
                         int32_t iters, void* x_scratch, void* P_scratch, int32_t* threads, int32_t* min_steps,
                         float* ms_per_run, void* stream)
 {
+    pes::TraceRange trace_("pes_autotune");
     if (!h) return PES_ERR_INVALID_ARG;
     if (prec != PES_FP32 && prec != PES_FP64) return fail(h, PES_ERR_INVALID_ARG, "autotune FP32 or FP64");
     if (iters < 1 || !x_scratch || !P_scratch) return fail(h, PES_ERR_INVALID_ARG, "iters >= 1 and scratch needed");
@@ -996,6 +1008,7 @@ pes_status pes_linearize(pes_handle* h, const pes_model* model, pes_method metho
                          int64_t N, void* F, void* c, void* Qp, void* H, void* d, void* Rp, void* y_used,
                          void* stream)
 {
+    pes::TraceRange trace_("pes_linearize");
     pes_status r = check_common(h, prec, offsets, B, N);
     if (r != PES_OK) return r;
     if ((r = check_model(h, model)) != PES_OK) return r;
@@ -1029,6 +1042,7 @@ pes_status pes_filter_scan(pes_handle* h, pes_precision prec, const void* F, con
                            const void* P0, const int64_t* offsets, int32_t B, int64_t N, void* xf, void* Pf,
                            void* stream)
 {
+    pes::TraceRange trace_("pes_filter_scan");
     pes_status r = check_common(h, prec, offsets, B, N);
     if (r != PES_OK) return r;
     if (!F || !c || !Qp || !H || !d || !Rp || !y || !m0 || !P0 || !xf || !Pf)
@@ -1045,6 +1059,7 @@ pes_status pes_filter_loglik(pes_handle* h, pes_precision prec, const void* F, c
                              const void* P0, const int64_t* offsets, int32_t B, int64_t N, void* xf, void* Pf,
                              double* loglik, void* stream)
 {
+    pes::TraceRange trace_("pes_filter_loglik");
     pes_status r = check_common(h, prec, offsets, B, N);
     if (r != PES_OK) return r;
     if (!F || !c || !Qp || !H || !d || !Rp || !y || !m0 || !P0 || !xf || !Pf || !loglik)
@@ -1060,6 +1075,7 @@ pes_status pes_smooth_scan(pes_handle* h, pes_precision prec, const void* F, con
                            const void* xf, const void* Pf, const int64_t* offsets, int32_t B, int64_t N, void* xs,
                            void* Ps, void* stream)
 {
+    pes::TraceRange trace_("pes_smooth_scan");
     pes_status r = check_common(h, prec, offsets, B, N);
     if (r != PES_OK) return r;
     if (!F || !c || !Qp || !xf || !Pf || !xs || !Ps) return fail(h, PES_ERR_INVALID_ARG, "NULL array");
@@ -1075,6 +1091,7 @@ pes_status pes_ieks_run(pes_handle* h, const pes_model* model, pes_method method
                         const void* x_init, const void* P_init, int32_t max_iters, double tol, void* x_out,
                         void* P_out, int32_t* iters_used, void* stream)
 {
+    pes::TraceRange trace_("pes_ieks_run");
     pes_status r = check_common(h, prec, offsets, B, N, true);
     if (r != PES_OK) return r;
     if ((r = check_model(h, model)) != PES_OK) return r;
@@ -1103,6 +1120,7 @@ pes_status pes_ieks_run_lm(pes_handle* h, const pes_model* model, pes_precision 
                            void* x_out, void* P_out, int32_t* iters_used, double* lambda_out,
                            int32_t* accepted_out, int32_t* conv_iter_out, void* stream)
 {
+    pes::TraceRange trace_("pes_ieks_run_lm");
     pes_status r = check_common(h, prec, offsets, B, N);
     if (r != PES_OK) return r;
     if ((r = check_model(h, model)) != PES_OK) return r;
@@ -1125,6 +1143,7 @@ pes_status pes_ieks_run_sequential(pes_handle* h, const pes_model* model, pes_me
                                    const void* P0, const void* x_init, const void* P_init, int32_t max_iters,
                                    double tol, void* x_out, void* P_out, int32_t* iters_used, void* stream)
 {
+    pes::TraceRange trace_("pes_ieks_run_sequential");
     pes_status r = check_common(h, prec, offsets, B, N);
     if (r != PES_OK) return r;
     if ((r = check_model(h, model)) != PES_OK) return r;
@@ -1157,6 +1176,7 @@ pes_status pes_ieks_run_host(pes_handle* h, const pes_model* model, pes_method m
                              const void* P0, const void* x_init, const void* P_init, int32_t max_iters, double tol,
                              void* x_out, void* P_out, int32_t* iters_used, void* stream)
 {
+    pes::TraceRange trace_("pes_ieks_run_host");
     if (!h) return PES_ERR_INVALID_ARG;
     if (prec != PES_FP32 && prec != PES_FP64 && prec != PES_MIXED && prec != PES_REFINED)
         return fail(h, PES_ERR_INVALID_ARG, "unknown precision");
@@ -1195,19 +1215,23 @@ pes_status pes_ieks_run_host(pes_handle* h, const pes_model* model, pes_method m
         PES_CUDA(h, cudaMemcpyAsync(h->hsens, model->sensors, sizeof(double) * 4 * ns, cudaMemcpyHostToDevice, st));
         dm.sensors = h->hsens;
     }
-    PES_CUDA(h, cudaMemcpyAsync(h->hy, y, ts * 2 * N, cudaMemcpyHostToDevice, st));
-    PES_CUDA(h, cudaMemcpyAsync(h->hoff, offsets, sizeof(int64_t) * (B + 1), cudaMemcpyHostToDevice, st));
-    PES_CUDA(h, cudaMemcpyAsync(h->hm0, m0, ts * 5 * B, cudaMemcpyHostToDevice, st));
-    PES_CUDA(h, cudaMemcpyAsync(h->hP0, P0, ts * 15 * B, cudaMemcpyHostToDevice, st));
-    if (x_init) PES_CUDA(h, cudaMemcpyAsync(h->hx, x_init, ts * 5 * N, cudaMemcpyHostToDevice, st));
-    if (P_init && method != PES_IEKS)
-        PES_CUDA(h, cudaMemcpyAsync(h->hP, P_init, ts * 15 * N, cudaMemcpyHostToDevice, st));
+    {
+        pes::TraceRange trace_in_("copies in");
+        PES_CUDA(h, cudaMemcpyAsync(h->hy, y, ts * 2 * N, cudaMemcpyHostToDevice, st));
+        PES_CUDA(h, cudaMemcpyAsync(h->hoff, offsets, sizeof(int64_t) * (B + 1), cudaMemcpyHostToDevice, st));
+        PES_CUDA(h, cudaMemcpyAsync(h->hm0, m0, ts * 5 * B, cudaMemcpyHostToDevice, st));
+        PES_CUDA(h, cudaMemcpyAsync(h->hP0, P0, ts * 15 * B, cudaMemcpyHostToDevice, st));
+        if (x_init) PES_CUDA(h, cudaMemcpyAsync(h->hx, x_init, ts * 5 * N, cudaMemcpyHostToDevice, st));
+        if (P_init && method != PES_IEKS)
+            PES_CUDA(h, cudaMemcpyAsync(h->hP, P_init, ts * 15 * N, cudaMemcpyHostToDevice, st));
+    }
     int32_t it = 0;
     pes_status r = pes_ieks_run(h, &dm, method, prec, h->hy, h->hoff, B, N, h->hm0, h->hP0, x_init ? h->hx : nullptr,
                                 (P_init && method != PES_IEKS) ? h->hP : nullptr, max_iters, tol, h->hx, h->hP,
                                 &it, stream);
     if (iters_used) *iters_used = it;
     if (r != PES_OK && r != PES_ERR_NOT_CONVERGED) return r;
+    pes::TraceRange trace_out_("copies out");
     PES_CUDA(h, cudaMemcpyAsync(x_out, h->hx, ts * 5 * N, cudaMemcpyDeviceToHost, st));
     PES_CUDA(h, cudaMemcpyAsync(P_out, h->hP, ts * 15 * N, cudaMemcpyDeviceToHost, st));
     PES_CUDA(h, cudaStreamSynchronize(st));

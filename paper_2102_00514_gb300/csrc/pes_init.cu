@@ -39,6 +39,7 @@
 
 #include "pes.h"
 #include "pes_init.h"
+#include "pes_trace.h"
 #include "pes_tc.cuh"
 
 namespace {
@@ -1567,6 +1568,7 @@ pes_status pes_init_set_state(pes_init_net* n, const float* params, const double
 pes_status pes_init_forward(pes_init_net* n, pes_precision prec, const void* y, const int64_t* offsets, int32_t B,
                             int64_t N, void* x_init, void* stream)
 {
+    pes::TraceRange trace_("pes_init_forward");
     pes_status s = check_sizes(n, prec, y, offsets, B, N);
     if (s != PES_OK) return s;
     if (!x_init) return net_fail(n, PES_ERR_INVALID_ARG, "NULL x_init");
@@ -1589,6 +1591,7 @@ pes_status pes_init_forward(pes_init_net* n, pes_precision prec, const void* y, 
 pes_status pes_init_loss_grad(pes_init_net* n, pes_precision prec, const void* y, const int64_t* offsets, int32_t B,
                               int64_t N, const void* x_target, float* grad, double* loss, void* stream)
 {
+    pes::TraceRange trace_("pes_init_loss_grad");
     pes_status s = check_sizes(n, prec, y, offsets, B, N);
     if (s != PES_OK) return s;
     if (!x_target || !grad) return net_fail(n, PES_ERR_INVALID_ARG, "NULL x_target or grad");
@@ -1601,6 +1604,7 @@ pes_status pes_init_loss_grad(pes_init_net* n, pes_precision prec, const void* y
 pes_status pes_init_train_step(pes_init_net* n, pes_precision prec, const void* y, const int64_t* offsets,
                                int32_t B, int64_t N, const void* x_target, float lr, double* loss, void* stream)
 {
+    pes::TraceRange trace_("pes_init_train_step");
     pes_status s = check_sizes(n, prec, y, offsets, B, N);
     if (s != PES_OK) return s;
     if (!(lr > 0.f)) return net_fail(n, PES_ERR_INVALID_ARG, "lr must be positive");

@@ -19,6 +19,7 @@
 #include "pes.h"
 #include "pes_handle.h"
 #include "pes_internal.h"
+#include "pes_trace.h"
 
 namespace {
 
@@ -112,6 +113,7 @@ extern "C" pes_status pes_ieks_run_noalloc(const pes_model* model, pes_method me
                                            int32_t max_iters, double tol, void* x_out, void* P_out,
                                            int32_t* iters_used, void* stream)
 {
+    pes::TraceRange trace_("pes_ieks_run_noalloc");
     if (N > kMaxStates || B > kMaxBatch || N < 1 || B < 1) return PES_ERR_INVALID_ARG;
     // PES_MIXED's FP64 copies and PES_REFINED's workspace would be allocated
     if (prec == PES_MIXED || prec == PES_REFINED) return PES_ERR_UNSUPPORTED;
