@@ -537,6 +537,40 @@ def _time_runs(sm, pes, m, prec, dev_in, iters, reps=3, warm=1, flush=None):
     return statistics.median(ms)
 
 
+def batched_cpu_baseline(wl, iters, budget_states=1 << 20, cores=None):
+    """The oracle as it stands on the batched workload, one trajectory per
+    thread on all host cores (the C oracle releases the interpreter lock): a
+    seeded sample of whole trajectories up to about `budget_states` states, both
+    methods, `iters` iterations each. Returns the cpu_baseline record (smoothed
+    steps/s per iteration, both methods, like the GPU figure)."""
+    import numpy as np
+
+    import oracle
+    off = wl["offsets"]
+    B = len(off) - 1
+    order = np.random.default_rng(B).permutation(B)
+    lens = np.diff(off)[order]
+    n = max(1, int(np.searchsorted(np.cumsum(lens), budget_states, side="right")))
+    picked = sorted(int(b) for b in order[:n])
+    units = [one_trajectory(wl, b)[0] for b in picked]
+    steps = int(sum(int(u["offsets"][-1]) - 1 for u in units))
+    cores = cores or os.cpu_count() or 1
+
+    def run(item):
+        u, om = item
+        oracle.iterated_smoother(oracle.Model.from_workload(u), om, u["offsets"], u["y"], u["m0"], u["P0"],
+                                 iters=iters)
+
+    work = [(u, om) for om in (oracle.IEKS, oracle.CUBATURE) for u in units]
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(cores) as ex:
+        list(ex.map(run, work))
+    t = time.perf_counter() - t0
+    return {"value": 2 * steps * iters / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} of {B} trajectories ({steps} steps), one trajectory per thread, IEKS + cubature, "
+                      f"{iters} iterations, sequential FP64 oracle", "seconds": t}
+
+
 def batched_key(args, fp32_peak, flush):
     """The batched workload: 4,096 trajectories, T_b uniform in 100..20,000
     (about 41.9 million states), truth turn rate U(-1, 1), sensors jittered by
@@ -579,6 +613,8 @@ def batched_key(args, fp32_peak, flush):
         out[key] = {"value": 2 * steps * iters / (tot[key] * 1e-3), "ms_per_step": tot[key]}
     out["parity_scope"] = f"{len(units)} sampled trajectories (first, last, shortest, longest, 4 seeded), each alone"
     sm.close()
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = batched_cpu_baseline(wl, iters)
     return out
 
 

@@ -1,7 +1,9 @@
-"""The benchmark line's headline choice (bench.choose_headline), on the CPU:
-`value` is the rate of the fastest precision whose final iteration met the
-tolerance in the run, with its step time, its host-buffer run and its launch
-count; with none, the FP32 rate stays and no at-tolerance rate is claimed."""
+"""Host logic of the benchmark line, on the CPU. The headline choice
+(bench.choose_headline): `value` is the rate of the fastest precision whose
+final iteration met the tolerance in the run, with its step time, its
+host-buffer run and its launch count; with none, the FP32 rate stays and no
+at-tolerance rate is claimed. The batched workload's CPU baseline
+(bench.batched_cpu_baseline): whole trajectories, one per thread."""
 import copy
 
 import bench
@@ -50,3 +52,15 @@ def test_mixed_only_and_none():
     bench.choose_headline(r)
     assert r["at_oracle_tol"] is None and r["value"] == before["value"]
     assert r["config"]["precision"].startswith("fp32 (no precision met")
+
+
+def test_batched_cpu_baseline_times_whole_trajectories_on_all_cores():
+    from paper_2102_00514_gb300 import synth
+    wl = synth.ct_bearings([30, 50, 20, 40, 10], seed=3, omega0_halfwidth=1.0)
+    rec = bench.batched_cpu_baseline(wl, iters=2, budget_states=100, cores=3)
+    assert rec["kind"] == "oracle" and rec["cores"] == 3 and rec["unit"] == bench.UNIT
+    n = int(rec["sample"].split(" of ")[0])
+    assert 1 <= n <= 5 and rec["value"] > 0
+    # whole trajectories, at most the budget of states unless one alone exceeds it
+    steps = int(rec["sample"].split("(")[1].split(" steps")[0])
+    assert steps <= 100 or n == 1
