@@ -403,6 +403,16 @@ pes_status pes_autotune(pes_handle* h, const pes_model* model, pes_method method
                         const void* P0, int32_t iters, void* x_scratch, void* P_scratch, int32_t* threads,
                         int32_t* min_steps, float* ms_per_run, void* stream);
 
+/* Set the launch shape that pes_autotune would keep for (method, precision)
+ * without timing anything: a choice recorded by an earlier pes_autotune (for
+ * example one cached on disk for this GPU). threads: a compiled block size
+ * (128 or 256 for PES_FP32, 128 for PES_FP64), or 0 with min_steps 0 for the
+ * defaults; min_steps: at least 1, the minimum steps per lane. prec PES_FP32
+ * also sets the shape of PES_MIXED's and PES_REFINED's FP32 iterations.
+ * PES_ERR_INVALID_ARG for anything else; the previous choice then stays. */
+pes_status pes_set_launch_shape(pes_handle* h, pes_method method, pes_precision prec, int32_t threads,
+                                int32_t min_steps);
+
 /* Launch shape the next call of the given kind would use (for tests and the
  * benchmark): blocks, threads per block, steps per thread. */
 pes_status pes_launch_shape(pes_handle* h, pes_method method, pes_precision prec, int64_t N,

@@ -857,6 +857,23 @@ pes_status pes_debug_phase_times(pes_handle* h, double* mean_ns, double* max_ns,
     return PES_OK;
 }
 
+pes_status pes_set_launch_shape(pes_handle* h, pes_method method, pes_precision prec, int32_t threads,
+                                int32_t min_steps)
+{
+    if (!h) return PES_ERR_INVALID_ARG;
+    if (prec != PES_FP32 && prec != PES_FP64) return fail(h, PES_ERR_INVALID_ARG, "launch shapes are per FP32 or FP64");
+    if (method < PES_IEKS || method > PES_GAUSS_HERMITE) return fail(h, PES_ERR_INVALID_ARG, "unknown method");
+    const bool defaults = (threads == 0 && min_steps == 0);
+    const bool compiled = prec == PES_FP64 ? nt_supported(0.0, threads) : nt_supported(0.0f, threads);
+    if (!defaults && (!compiled || min_steps < 1 || min_steps > (1 << 20)))
+        return fail(h, PES_ERR_INVALID_ARG, "no compiled launch of %d threads with at least %d steps per lane",
+                    (int)threads, (int)min_steps);
+    pes_tune& slot = h->tune[lin_of(method)][prec == PES_FP64 ? 1 : 0];
+    slot.nt = threads;
+    slot.min_steps = min_steps;
+    return PES_OK;
+}
+
 pes_status pes_launch_shape(pes_handle* h, pes_method method, pes_precision prec, int64_t N, int32_t* blocks,
                             int32_t* threads, int32_t* steps_per_thread)
 {

@@ -29,7 +29,7 @@ MODEL_CT_BEARINGS, MODEL_LINEAR = 0, 1
 
 EXPORTED = ["pes_create", "pes_destroy", "pes_last_error", "pes_sync", "pes_linearize", "pes_filter_scan",
             "pes_smooth_scan", "pes_ieks_run", "pes_ieks_run_host", "pes_launch_shape", "pes_measure_fma_peak",
-            "pes_debug_phase_times", "pes_ieks_run_noalloc", "pes_traj_iterations", "pes_ieks_run_lm", "pes_filter_loglik", "pes_ieks_run_sequential", "pes_autotune", "pes_ieks_graph_create", "pes_graph_launch", "pes_graph_destroy",
+            "pes_debug_phase_times", "pes_ieks_run_noalloc", "pes_traj_iterations", "pes_ieks_run_lm", "pes_filter_loglik", "pes_ieks_run_sequential", "pes_autotune", "pes_set_launch_shape", "pes_ieks_graph_create", "pes_graph_launch", "pes_graph_destroy",
             "pes_init_create", "pes_init_destroy", "pes_init_last_error", "pes_init_set_params",
             "pes_init_get_params", "pes_init_get_state", "pes_init_set_state", "pes_init_forward",
             "pes_init_loss_grad", "pes_init_train_step"]
@@ -83,6 +83,7 @@ def load_library():
     lib.pes_ieks_graph_create.argtypes = [p, mp, i32, i32, p, p, i32, i64, p, p, p, p, i32, p, p, ctypes.POINTER(p)]
     lib.pes_graph_launch.argtypes = [p, p]
     lib.pes_graph_destroy.argtypes = [p]
+    lib.pes_set_launch_shape.argtypes = [p, i32, i32, i32, i32]
     lib.pes_autotune.argtypes = [p, mp, i32, i32, p, p, i32, i64, p, p, i32, p, p, ctypes.POINTER(i32),
                                  ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float), p]
     lib.pes_launch_shape.argtypes = [p, i32, i32, i64, ctypes.POINTER(i32), ctypes.POINTER(i32),
@@ -257,12 +258,27 @@ class Smoother:
                                                  _stream(stream)))
         return out
 
-    def autotune(self, model: Model, method: int, prec: int, y, offsets, m0, P0, iters: int = 2, stream=None):
+    def set_launch_shape(self, method: int, prec: int, threads: int, min_steps: int):
+        """Keep this launch shape for (method, precision) (pes_set_launch_shape)."""
+        self._check(self.lib.pes_set_launch_shape(self.h, method, prec, int(threads), int(min_steps)))
+
+    def autotune(self, model: Model, method: int, prec: int, y, offsets, m0, P0, iters: int = 2, stream=None,
+                 cache: str | None = None):
         """Time the candidate launch shapes on this workload and keep the fastest
-        for (method, precision); returns (threads, min_steps, ms_per_run)."""
+        for (method, precision); returns (threads, min_steps, ms_per_run). With
+        `cache` (a JSON file), a choice recorded there for this GPU, method,
+        precision and size class (tune_cache_key) is applied without timing,
+        and a new one is recorded."""
         dt = _dtype(prec)
         N = y.shape[1]
         B = offsets.shape[0] - 1
+        key = None
+        if cache is not None:
+            key = tune_cache_key(torch.cuda.get_device_name(y.device), method, prec, N, B)
+            hit = read_tune_cache(cache).get(key)
+            if hit is not None:
+                self.set_launch_shape(method, prec, hit["threads"], hit["min_steps"])
+                return hit["threads"], hit["min_steps"], hit["ms_per_run"]
         xs = torch.empty((5, N), dtype=dt, device=y.device)
         Ps = torch.empty((15, N), dtype=dt, device=y.device)
         nt, ms_, t = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
@@ -271,6 +287,8 @@ class Smoother:
                                    _ptr(xs), _ptr(Ps), ctypes.byref(nt), ctypes.byref(ms_), ctypes.byref(t),
                                    _stream(stream))
         self._check(st)
+        if key is not None:
+            update_tune_cache(cache, key, {"threads": nt.value, "min_steps": ms_.value, "ms_per_run": t.value})
         return nt.value, ms_.value, t.value
 
     def graph(self, model: Model, method: int, prec: int, y, offsets, m0, P0, x_init=None, P_init=None,
@@ -438,6 +456,41 @@ class Smoother:
                                         h(P_out), ctypes.byref(used), _stream(stream))
         self._check(st, allow=(NOT_CONVERGED,) if allow_not_converged else ())
         return x_out, P_out, used.value, st
+
+
+_METHOD_NAMES = {IEKS: "ieks", CUBATURE: "cubature", UNSCENTED: "unscented", GAUSS_HERMITE: "gauss_hermite"}
+
+
+def tune_cache_key(device_name: str, method: int, prec: int, N: int, B: int) -> str:
+    """Key of a launch-shape choice: the GPU's name, the method, the
+    precision (FP32 or FP64), and the size class: N and B each rounded up to a
+    power of two (the shape a tuning finds depends on the lanes per state,
+    which those fix to a factor of two)."""
+    up = lambda n: 1 << max(0, int(n - 1).bit_length())
+    return f"{device_name}|{_METHOD_NAMES[method]}|{'fp64' if prec == FP64 else 'fp32'}|N<={up(N)}|B<={up(B)}"
+
+
+def read_tune_cache(path: str) -> dict:
+    """The cache's entries; an absent file is an empty cache."""
+    import json
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except FileNotFoundError:
+        return {}
+
+
+def update_tune_cache(path: str, key: str, entry: dict) -> None:
+    """Add or replace one entry: the file is rewritten whole through a
+    temporary file and a rename, so a reader never sees half of it."""
+    import json
+    import os
+    data = read_tune_cache(path)
+    data[key] = entry
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
 
 
 class Graph:

@@ -357,6 +357,38 @@ def test_autotune_keeps_a_valid_shape_and_results():
     s.close()
 
 
+def test_tuning_cache_reapplies_a_recorded_shape(tmp_path):
+    """A tuning recorded in a cache file is applied by a fresh handle without
+    timing: the same launch shape and bit-identical results."""
+    cache = str(tmp_path / "tune.json")
+    wl = synth.workload("batch16_T100_3000")
+    d = workload_to_dev(wl, pes.FP32)
+    N = wl["y"].shape[1]
+    args = (d["model"], pes.CUBATURE, pes.FP32, d["y"], d["offsets"], d["m0"], d["P0"])
+    a = pes.Smoother(1 << 16, 64)
+    tuned = a.autotune(*args, iters=2, cache=cache)
+    assert len(pes.read_tune_cache(cache)) == 1
+    b = pes.Smoother(1 << 16, 64)
+    assert b.autotune(*args, iters=2, cache=cache) == tuned
+    assert a.launch_shape(pes.CUBATURE, pes.FP32, N) == b.launch_shape(pes.CUBATURE, pes.FP32, N)
+    xa, Pa, _, _ = a.ieks_run(*args, iters=3)
+    xb, Pb, _, _ = b.ieks_run(*args, iters=3)
+    torch.cuda.synchronize()
+    assert torch.equal(xa, xb) and torch.equal(Pa, Pb)
+    # shapes that are not compiled are refused and the choice stays
+    for nt, steps in ((64, 8), (256, 0), (0, 4)):
+        with pytest.raises(pes.PesError) as ei:
+            b.set_launch_shape(pes.CUBATURE, pes.FP32, nt, steps)
+        assert ei.value.status == pes.INVALID_ARG
+    with pytest.raises(pes.PesError):
+        b.set_launch_shape(pes.CUBATURE, pes.FP64, 256, 8)
+    assert b.launch_shape(pes.CUBATURE, pes.FP32, N) == a.launch_shape(pes.CUBATURE, pes.FP32, N)
+    b.set_launch_shape(pes.CUBATURE, pes.FP32, 0, 0)   # back to the defaults
+    assert b.launch_shape(pes.CUBATURE, pes.FP32, N)[1] == 256
+    a.close()
+    b.close()
+
+
 def test_graph_replay_equals_direct_call(sm):
     wl = synth.workload("batch8_T1_3000")
     for method in (pes.IEKS, pes.CUBATURE):
