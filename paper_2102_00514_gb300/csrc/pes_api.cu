@@ -267,7 +267,9 @@ template <typename T>
 pes_status run_persistent_shaped(pes_handle* h, KParams<T>& p, int lin, const Shape& s, cudaStream_t st)
 {
     fill_workspace(h, p, s);
-    PES_CUDA(h, cudaMemsetAsync(h->bar, 0, sizeof(unsigned), st));
+    // the grid barriers count arrivals up from 0; the timeout test starts the
+    // count one short (all ones: -1), so that no barrier completes
+    PES_CUDA(h, cudaMemsetAsync(h->bar, h->bar_short ? 0xFF : 0, sizeof(unsigned), st));
     if (p.mode == MODE_RUN && p.tol > 0.0) {
         PES_CUDA(h, cudaMemsetAsync(h->conv, 0, sizeof(double) * 4 * p.B, st));
         if (h->traj_iters) {
@@ -777,6 +779,7 @@ pes_status pes_create(pes_handle** out, int64_t max_states, int32_t max_batch)
         const long long ms = atoll(env);
         if (ms > 0) h->timeout_ns = ms * 1000000LL;
     }
+    if (const char* env = getenv("PES_TEST_BARRIER_SHORT")) h->bar_short = atoi(env) != 0;
     h->max_states = max_states;
     h->max_batch = max_batch;
     h->nb_max = h->num_sms * kMaxBlocksPerSM;

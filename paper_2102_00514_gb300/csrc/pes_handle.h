@@ -45,5 +45,10 @@ struct pes_handle {
     long long* ptime = nullptr;   // phase timestamps (PES_PHASE_TIMES=1)
     int ptime_blocks = 0;
     long long timeout_ns = 2000000000LL;
+    // The test of the smoother kernel's barrier timeout (PES_TEST_BARRIER_SHORT
+    // at pes_create): its launches start the barrier count one arrival short,
+    // so no grid barrier completes; the first gives up after timeout_ns, the
+    // kernel ends and the call returns PES_ERR_TIMEOUT. false otherwise.
+    bool bar_short = false;
     char err[512] = {0};
 };

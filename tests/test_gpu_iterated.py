@@ -333,6 +333,36 @@ def test_not_positive_definite_prior_reported(sm):
     assert ei.value.status in (pes.NOT_PD, pes.NONFINITE)
 
 
+def test_a_grid_barrier_that_cannot_complete_times_out_and_the_context_survives(monkeypatch):
+    """The failure path of the smoother kernel's grid barriers, with no GPU
+    fault: a handle created with PES_TEST_BARRIER_SHORT starts every launch's
+    barrier count one arrival short, so no barrier can complete. With a 50 ms
+    limit (PES_BARRIER_TIMEOUT_MS) the first barrier gives up, the others see
+    the status and do not wait, the kernel ends, and the call returns
+    PES_ERR_TIMEOUT well within a second. A handle created afterwards runs
+    normally on the same context."""
+    import time
+    wl = synth.workload("ieks_T500")
+    N = wl["y"].shape[1]
+    monkeypatch.setenv("PES_TEST_BARRIER_SHORT", "1")
+    monkeypatch.setenv("PES_BARRIER_TIMEOUT_MS", "50")
+    bad = pes.Smoother(N, 1)
+    monkeypatch.delenv("PES_TEST_BARRIER_SHORT")
+    monkeypatch.delenv("PES_BARRIER_TIMEOUT_MS")
+    t0 = time.perf_counter()
+    with pytest.raises(pes.PesError) as ei:
+        gpu_run(bad, wl, pes.IEKS, pes.FP32, iters=3)
+    assert ei.value.status == pes.TIMEOUT
+    assert time.perf_counter() - t0 < 1.0
+    bad.close()
+    good = pes.Smoother(N, 1)
+    ref = oracle_run(wl, pes.IEKS, iters=3)
+    x, P, used, st = gpu_run(good, wl, pes.IEKS, pes.FP64, iters=3)
+    assert used == 3 and st == pes.OK
+    assert rel_err(x, ref["x"], wl["offsets"]) < TOL_FP64 and rel_err(P, ref["P"], wl["offsets"]) < TOL_FP64
+    good.close()
+
+
 def test_autotune_keeps_a_valid_shape_and_results():
     s = pes.Smoother(1 << 16, 64)
     wl = synth.workload("batch16_T100_3000")
