@@ -11,7 +11,8 @@ smoother kernel on its full grid (152 blocks x 256 lanes x 27 steps in FP32).
   mostly in the position variances of far-away targets), which is what the
   refined precision is for.
 
-The errors are printed with the worst per-state error (R12).
+The unscented rule is held to the same bounds (FP64 and the refined final
+iteration). The errors are printed with the worst per-state error (R12).
 """
 import numpy as np
 import pytest
@@ -69,3 +70,27 @@ def test_fullsize_final_iteration_reduced_precisions(wl, sm, method):
     assert ex < 1e-6 and eP < 1e-6
     ex, eP, _, _ = errs["fp32"]
     assert ex < 5e-4 and eP < 5e-4
+
+
+UT = (0.8, 2.0, 0.5)
+
+
+def test_fullsize_unscented_fp64_and_refined(wl, sm):
+    """The unscented rule (alpha 0.8, beta 2, kappa 0.5) through the same
+    kernels at full size: ten FP64 iterations against the oracle's at 1e-9, and
+    the refined final iteration against one oracle iteration from the FP32
+    nominal at 1e-5 (worst state 1e-4)."""
+    off = wl["offsets"]
+    ref = oracle_run(wl, pes.UNSCENTED, iters=10, ut=UT)
+    x, P, used, _ = gpu_run(sm, wl, pes.UNSCENTED, pes.FP64, iters=10, ut=UT)
+    ex, eP = rel_err(x, ref["x"], off), rel_err(P, ref["P"], off)
+    print(f"T=2^20 unscented FP64: means {ex:.2e} covariances {eP:.2e}")
+    assert used == 10 and ex < TOL_FP64 and eP < TOL_FP64
+    x9, P9, _, _ = gpu_run(sm, wl, pes.UNSCENTED, pes.FP32, iters=9, ut=UT)
+    one = oracle_run(float_inputs(wl), pes.UNSCENTED, iters=1, x_init=x9, P_init=P9, ut=UT)
+    x, P, used, _ = gpu_run(sm, wl, pes.UNSCENTED, pes.REFINED, iters=10, ut=UT)
+    ex, eP = rel_err(x, one["x"], off), rel_err(P, one["P"], off)
+    sx, sP = per_state_max(x, one["x"]), per_state_max(P, one["P"])
+    print(f"T=2^20 unscented refined final iteration: means {ex:.2e} covariances {eP:.2e} "
+          f"(worst state {sx:.2e} / {sP:.2e})")
+    assert used == 10 and ex < TOL_REFINED and eP < TOL_REFINED and sx < TOL_FP32 and sP < TOL_FP32
