@@ -152,6 +152,9 @@ typedef struct {
     double lm_lambda;
 } pes_model;
 
+/* A handle owns its workspace and nothing else that is shared: handles are
+ * independent, so several host threads may each drive their own handle (on
+ * their own streams) at the same time. One handle serves one call at a time. */
 typedef struct pes_handle pes_handle;
 
 /* Create a handle on the current CUDA device with workspace for up to
