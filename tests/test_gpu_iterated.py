@@ -363,6 +363,43 @@ def test_a_grid_barrier_that_cannot_complete_times_out_and_the_context_survives(
     good.close()
 
 
+def test_handles_on_concurrent_host_threads_give_the_sequential_results():
+    """Handles are independent: two host threads, each with its own handle and
+    stream, running the host-buffer entry point at the same time (IEKS on one,
+    cubature on the other, several calls each) get bit for bit what the same
+    calls give one after the other."""
+    import concurrent.futures as cf
+    wl = synth.workload("batch8_T100_3000")
+    N, B = wl["y"].shape[1], len(wl["offsets"]) - 1
+    pin = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).pin_memory()
+    hy, hoff = pin(wl["y"], torch.float32), pin(wl["offsets"], torch.int64)
+    hm0, hP0, hs = pin(wl["m0"], torch.float32), pin(wl["P0"], torch.float32), pin(wl["sensors"], torch.float64)
+    model = workload_to_dev(wl, pes.FP32)["model"]
+    methods = (pes.IEKS, pes.CUBATURE)
+    handles = {m: pes.Smoother(N, B) for m in methods}
+    streams = {m: torch.cuda.Stream() for m in methods}
+    device = torch.cuda.current_device()
+
+    def run(m, prec, reps):
+        torch.cuda.set_device(device)
+        out = []
+        for _ in range(reps):
+            x, P, _, _ = handles[m].ieks_run_host(model, m, prec, hy, hoff, hm0, hP0, iters=4, sensors_host=hs,
+                                                  stream=streams[m])
+            out.append((x.clone(), P.clone()))
+        return out
+
+    for prec in (pes.FP32, pes.REFINED):
+        seq = {m: run(m, prec, 1)[0] for m in methods}
+        with cf.ThreadPoolExecutor(2) as ex:
+            conc = dict(zip(methods, ex.map(lambda m: run(m, prec, 3), methods)))
+        for m in methods:
+            for x, P in conc[m]:
+                assert torch.equal(x, seq[m][0]) and torch.equal(P, seq[m][1]), (prec, m)
+    for h_ in handles.values():
+        h_.close()
+
+
 def test_autotune_keeps_a_valid_shape_and_results():
     s = pes.Smoother(1 << 16, 64)
     wl = synth.workload("batch16_T100_3000")
