@@ -356,12 +356,17 @@ class NvmlPoller:
                 "reasons": reasons, "samples": len(self.samples), "source": "NVML, every 1 ms during the timed region"}
 
 
-def per_state_max(a, b):
-    """Worst per-state relative error ||a_k - b_k||_2 / ||b_k||_2 ([ncomp][N])."""
+def per_state_errors(a, b):
+    """Per-state relative errors ||a_k - b_k||_2 / ||b_k||_2 ([ncomp][N])."""
     import numpy as np
     num = np.linalg.norm(a - b, axis=0)
     den = np.maximum(np.linalg.norm(b, axis=0), 1e-300)
-    return float(np.max(num / den))
+    return num / den
+
+
+def per_state_max(a, b):
+    """Worst per-state relative error ([ncomp][N])."""
+    return float(per_state_errors(a, b).max())
 
 
 def set_headline(result, key, value, ms):
@@ -1131,6 +1136,13 @@ def main():
                         per_state_max(xref[name][1][:, u[1]], last[(name, i)]["P"]) for i, u in enumerate(units))
                     fi["fp32_covs_worst_state"] = max(
                         per_state_max(x32[name][1][:, u[1]], last[(name, i)]["P"]) for i, u in enumerate(units))
+                    # and the median state (R12 reports both)
+                    med = lambda arr, c: float(np.median(np.concatenate(
+                        [per_state_errors(arr[:, u[1]], last[(name, i)][c]) for i, u in enumerate(units)])))
+                    fi["refined_means_median_state"] = med(xref[name][0], "x")
+                    fi["refined_covs_median_state"] = med(xref[name][1], "P")
+                    fi["fp32_means_median_state"] = med(x32[name][0], "x")
+                    fi["fp32_covs_median_state"] = med(x32[name][1], "P")
                     par[name]["final_iteration"] = fi
             scope = ("full workload" if len(units) == 1 else
                      f"{len(units)} sampled trajectories, each smoothed alone by the oracle (worst reported)")

@@ -64,3 +64,12 @@ def test_batched_cpu_baseline_times_whole_trajectories_on_all_cores():
     # whole trajectories, at most the budget of states unless one alone exceeds it
     steps = int(rec["sample"].split("(")[1].split(" steps")[0])
     assert steps <= 100 or n == 1
+
+
+def test_per_state_errors_are_relative_to_each_state():
+    import numpy as np
+    b = np.array([[1.0, 0.0, 3.0], [0.0, 2.0, 4.0]])
+    a = b + np.array([[0.1, 0.0, 0.0], [0.0, 0.0, 0.5]])
+    e = bench.per_state_errors(a, b)
+    assert np.allclose(e, [0.1, 0.0, 0.1])
+    assert bench.per_state_max(a, b) == e.max()
